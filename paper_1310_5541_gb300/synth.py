@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs shared by the CUDA path, the CPU oracle, the tests and the bench.
+
+This module holds no filter arithmetic.  It only draws the random numbers the
+filter consumes (process noise, resampling uniforms) and simulates the
+microscope that produces the observed images, so that both implementations
+can be fed identical inputs.
+
+Workload shape follows the paper's simulated fluorescence-microscopy
+sequences (Section 5.3): a single Gaussian-PSF spot (Eq. object) on a constant
+background, Poisson photon noise, moving under a nearly-constant-velocity
+model (Section 5.1).  The SNR of a Poisson image is taken as
+SNR = I0 / sqrt(I0 + bg), so I0 is recovered from a target SNR by solving that
+quadratic.
+
+State layout is structure-of-arrays: ``state[d, i]`` with
+``d in (x, y, vx, vy, I0)``; images are row-major ``Z[y, x]`` with pixel
+(x, y) centred on integer coordinates.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+D2 = 5  # (x, y, vx, vy, I0)
+
+
+@dataclasses.dataclass(frozen=True)
+class Model:
+    """Parameters of the tracking model (dynamics, appearance and likelihood)."""
+
+    sigma_psf: float = 1.5        # PSF standard deviation in pixels
+    I0: float = 100.0             # peak intensity of the spot
+    bg: float = 10.0              # background intensity
+    patch: int = 9                # odd side of the likelihood patch S_x
+    q: tuple = (0.5, 0.5, 0.1, 0.1, 1.0)  # process-noise std per state component
+    lik: str = "poisson"          # "poisson" or "sse"
+    sigma_xi: float = 20.0        # SSE likelihood peakiness (paper Eq. likelihood)
+
+
+def i0_from_snr(snr: float, bg: float) -> float:
+    """Peak intensity for a Poisson SNR defined as I0 / sqrt(I0 + bg)."""
+    s2 = snr * snr
+    return 0.5 * (s2 + math.sqrt(s2 * s2 + 4.0 * s2 * bg))
+
+
+def render(W: int, H: int, x0: float, y0: float, I0: float, bg: float, sigma: float) -> np.ndarray:
+    """Noise-free image of one spot, point-sampled at integer pixel centres (FP64)."""
+    xs = np.arange(W, dtype=np.float64)
+    ys = np.arange(H, dtype=np.float64)
+    gx = np.exp(-((xs - x0) ** 2) / (2.0 * sigma * sigma))
+    gy = np.exp(-((ys - y0) ** 2) / (2.0 * sigma * sigma))
+    return I0 * np.outer(gy, gx) + bg
+
+
+@dataclasses.dataclass
+class Sequence:
+    gt: np.ndarray        # [K+1, 5] ground-truth states, frame 0 = initial state
+    images: np.ndarray    # [K, H, W] float32 Poisson images for frames 1..K
+
+
+def make_sequence(W: int, H: int, n_frames: int, model: Model, seed: int,
+                  start=None, vmax=None) -> Sequence:
+    """Ground-truth track and its noisy image sequence.
+
+    The track starts at ``start`` (default: image centre) with a speed drawn
+    uniformly in [vmax/2, vmax] px/frame in a uniformly random direction and
+    then follows the nearly-constant-velocity model with the model's process
+    noise on velocity and intensity (positions advance by the velocity only,
+    so the spot moves smoothly).  ``vmax`` defaults to the largest speed that
+    keeps a straight track inside the image margin for the whole sequence.
+    """
+    rng = np.random.default_rng([seed, 0x5EED])
+    margin = model.patch
+    if start is None:
+        start = ((W - 1) / 2.0, (H - 1) / 2.0)
+    if vmax is None:
+        vmax = max(0.05, (min(W, H) / 2.0 - margin) / max(n_frames, 1))
+    for _attempt in range(1000):
+        speed = rng.uniform(vmax / 2.0, vmax)
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        s = np.array([start[0], start[1], speed * math.cos(ang), speed * math.sin(ang), model.I0])
+        gt = [s.copy()]
+        ok = True
+        for _k in range(n_frames):
+            s = s.copy()
+            s[0] += s[2]
+            s[1] += s[3]
+            s[2] += rng.normal() * model.q[2]
+            s[3] += rng.normal() * model.q[3]
+            s[4] = max(1.0, s[4] + rng.normal() * model.q[4])
+            if not (margin <= s[0] <= W - 1 - margin and margin <= s[1] <= H - 1 - margin):
+                ok = False
+                break
+            gt.append(s)
+        if ok:
+            break
+    gt = np.array(gt)
+    images = np.empty((n_frames, H, W), dtype=np.float32)
+    for k in range(n_frames):
+        lam = render(W, H, gt[k + 1, 0], gt[k + 1, 1], gt[k + 1, 4], model.bg, model.sigma_psf)
+        images[k] = rng.poisson(lam).astype(np.float32)
+    return Sequence(gt=gt, images=images)
+
+
+def initial_state(gt0, N: int, dtype=np.float64) -> np.ndarray:
+    """All N particles at the ground-truth initial state (paper Section 5.3)."""
+    st = np.empty((D2, N), dtype=dtype)
+    for d in range(D2):
+        st[d, :] = gt0[d]
+    return st
+
+
+def make_noise(N: int, q, seed: int, frame: int, dtype=np.float64) -> np.ndarray:
+    """Process noise epsilon[d, i] ~ N(0, q_d^2), drawn in FP64 and rounded to the state dtype."""
+    rng = np.random.default_rng([seed, 1, frame])
+    out = np.empty((len(q), N), dtype=dtype)
+    for d, qd in enumerate(q):
+        out[d] = (rng.standard_normal(N) * qd).astype(dtype)
+    return out
+
+
+def make_u0(seed: int, frame: int) -> float:
+    """Systematic-resampling offset u0 ~ U[0, 1)."""
+    return float(np.random.default_rng([seed, 2, frame]).random())
+
+
+def random_weights_case(N: int, seed: int):
+    """Random positive log-weights for resampling tests (no filter arithmetic)."""
+    rng = np.random.default_rng([seed, 3])
+    return rng.normal(size=N) * 3.0
