@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of one pcSIR filter step on GB300 (one JSON line on stdout).
+
+Workload: single-target tracking in 512 x 512 Poisson images (Gaussian PSF
+sigma 1.5 px, I0 100, background 10, nearly-constant-velocity motion with
+process std 0.5 px), 21 x 21 likelihood patch, N = 2^24 FP32 particles,
+cells of h = 0.5 px (pcSIR-2x2).  A step is one full pass of the hot path:
+propagate, cells, dummies (centre of mass), dummy likelihood, weight copy,
+normalisation, systematic resampling.  Inputs are synthetic and seeded; the
+state and noise arrays (335 MB each) are larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent filter (replicas; no data-path
+collective); the value is all ranks' particle-steps over the slowest rank's
+time.  ``--impl reference`` times the CPU oracle instead, on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s & steps/s: SIR vs pcSIR vs surrogate-pcSIR at matched RMSE, %roofline"
+UNIT = "particles/s"
+W_IMG = H_IMG = 512
+PATCH = 21
+SIGMA, I0, BG = 1.5, 100.0, 10.0
+Q = (0.5, 0.5, 0.1, 0.1, 1.0)
+N_DEFAULT = 1 << 24
+H_DEFAULT = 0.5
+NOISE_POOL = 3
+SEED = 1310554100 + 200
+# algorithmic bytes per particle of the propagate + cell + centre-of-mass kernel (FP32 state):
+# read state 20 + noise 20, write propagated state 20 + cell slot 4
+PROP_BIN_BYTES = 64
+# scan + resample kernel: read cell slot 4, gather one propagated state 20 and write it 20 per output
+RESAMPLE_BYTES = 44
+KERNELS_PER_STEP = 4
+
+
+def workload_name(N, h):
+    return "single-target pcSIR, 512x512 Poisson images, 21x21 patch, N=%d FP32, h=%g px" % (N, h)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pcsir_kernels.cu", "pcsir_device.cuh", "pcsir_internal.h"):
+        with open(os.path.join(ROOT, "paper_1310_5541_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(N):
+    """dram bytes per launch of the propagate/bin kernel from the committed ncu summary,
+    scaled to N particles; None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_prop_bin_512x512_h0.5.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
+    m_bpp = re.search(r"dram bytes per particle:\s*([0-9.]+)", txt)
+    if not (m_hash and m_bpp) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bpp.group(1)) * N
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", uuid, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(n_sample, budget_s, seed, h, steps=None, warmup=0):
+    """Time the oracle's pcSIR step on a bounded sample of the workload (host cores)."""
+    import numpy as np
+
+    from oracle import pcsir_oracle as O
+    from paper_1310_5541_gb300 import synth
+
+    model = synth.Model(sigma_psf=SIGMA, I0=I0, bg=BG, patch=PATCH, q=Q)
+    nfr = (steps or 64) + warmup + 1
+    seq = synth.make_sequence(W_IMG, H_IMG, min(nfr, 64), model, seed)
+    st = synth.initial_state(seq.gt[0], n_sample, np.float32)
+    times = []
+    k = 0
+    t_start = time.perf_counter()
+    while True:
+        nz = synth.make_noise(n_sample, Q, seed, k, np.float32)
+        u0 = synth.make_u0(seed, k)
+        img = seq.images[k % seq.images.shape[0]]
+        t0 = time.perf_counter()
+        st = O.pcsir_step(st, img, nz, u0, h, model)["new_state"]
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+        k += 1
+        if steps is not None:
+            if len(times) >= steps:
+                break
+        elif time.perf_counter() - t_start > budget_s and len(times) >= 2:
+            break
+    return n_sample * len(times) / sum(times), len(times), sum(times)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    n_s = 1 << 18
+    rate, steps, tot = cpu_oracle_rate(n_s, 0, SEED, args.h, steps=args.steps, warmup=args.warmup)
+    sample = "oracle pcSIR steps on N=2^18 particles of the same workload (h=%g), %d timed steps" % (args.h, steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args.n, args.h), "sample_particles": n_s},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--h", type=float, default=H_DEFAULT)
+    ap.add_argument("--sir-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if pg:
+        pg.barrier()
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    N, h, K, Wm = args.n, args.h, args.steps, args.warmup
+    seed = SEED + 1000 * rank
+    model = synth.Model(sigma_psf=SIGMA, I0=I0, bg=BG, patch=PATCH, q=Q)
+    n_frames = Wm + K + max(args.sir_steps, 2) + 4
+    seq = synth.make_sequence(W_IMG, H_IMG, n_frames, model, seed)
+    dev = torch.device("cuda", local)
+    images = torch.from_numpy(seq.images).to(dev)
+    noise_host = [torch.from_numpy(synth.make_noise(N, Q, seed, j, np.float32)).pin_memory()
+                  for j in range(NOISE_POOL)]
+    noise = [t.to(dev) for t in noise_host]
+    u0s = [synth.make_u0(seed, k) for k in range(n_frames)]
+    state0 = torch.from_numpy(synth.initial_state(seq.gt[0], N, np.float32)).to(dev)
+    state = state0.clone()
+    ctx = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG, keep=0)
+    stream = torch.cuda.current_stream()
+    res_host = torch.zeros((n_frames, 12), dtype=torch.float64).pin_memory()  # 96-byte pcsir_result each
+
+    def step(k, st):
+        r = pcsir.lib.pcsir_step(ctx.handle, pcsir._ptr(st), N, pcsir._ptr(images[k]), W_IMG, H_IMG, float(h),
+                                 pcsir._ptr(noise[k % NOISE_POOL]), float(u0s[k]), pcsir._stream_ptr(stream),
+                                 pcsir.ctypes.c_void_p(res_host[k].data_ptr()))
+        if r != 0:
+            ctx._raise(r)
+
+    for k in range(Wm):
+        step(k, state)
+    torch.cuda.synchronize()
+    ctx.timing_enable(K)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid)
+    time.sleep(0.4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(Wm, Wm + K):
+        step(k, state)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    stages = np.array(ctx.timing_read(K))
+    if pg:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        pg.barrier()
+    res = np.frombuffer(res_host.numpy().tobytes(), dtype=np.dtype([
+        ("est", "f8", 5), ("ess", "f8"), ("maxll", "f8"), ("sumw", "f8"), ("n", "i8"), ("nb", "i8"),
+        ("err", "i4"), ("kind", "i4")]))
+    timed = res[Wm:Wm + K]
+    derr = int(np.bitwise_or.reduce(timed["err"]))
+    est = timed["est"][:, :2]
+    gt = seq.gt[1 + Wm:1 + Wm + K, :2]
+    rmse = float(np.sqrt(np.mean(np.sum((est - gt) ** 2, axis=1))))
+    value = N * K * world / (elapsed_ms / 1e3)
+
+    # roofline of the dominant kernel (propagate + cells + centre-of-mass sums)
+    hbm, peak_kind = peaks()
+    st_mean = stages.mean(axis=0)
+    share = st_mean / st_mean.sum()
+    dom = int(np.argmax(st_mean))
+    bytes_pb = PROP_BIN_BYTES * N
+    achieved = bytes_pb / (st_mean[0] * 1e-3) / 1e9
+    traffic = profiled_traffic(N)
+    roofline = {"kernel": "k_prop_bin", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes": bytes_pb}
+    resample_gbs = RESAMPLE_BYTES * N / (st_mean[3] * 1e-3) / 1e9
+
+    # end to end through the C ABI: host inputs copied in, result read back, every step
+    img_host = [torch.from_numpy(seq.images[k]).pin_memory() for k in range(n_frames)]
+    img_dev = torch.empty((H_IMG, W_IMG), dtype=torch.float32, device=dev)
+    nz_dev = torch.empty((5, N), dtype=torch.float32, device=dev)
+    res1 = pcsir.pcsir_result()
+    state.copy_(state0)
+    torch.cuda.synchronize()
+    K_e2e = max(3, K // 2)
+    t0 = time.perf_counter()
+    for k in range(K_e2e):
+        img_dev.copy_(img_host[k], non_blocking=True)
+        nz_dev.copy_(noise_host[k % NOISE_POOL], non_blocking=True)
+        r = pcsir.lib.pcsir_step(ctx.handle, pcsir._ptr(state), N, pcsir._ptr(img_dev), W_IMG, H_IMG, float(h),
+                                 pcsir._ptr(nz_dev), float(u0s[k]), pcsir._stream_ptr(stream), None)
+        if r != 0:
+            ctx._raise(r)
+        torch.cuda.current_stream().synchronize()
+        pcsir.lib.pcsir_last_result(ctx.handle, pcsir.ctypes.byref(res1))
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * K_e2e * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": 96}
+
+    # plain SIR on the same workload (the comparison path; likelihood for every particle)
+    sir = None
+    if args.sir_steps > 0:
+        state.copy_(state0)
+        for k in range(2):
+            pcsir.sir_step(ctx, state, images[k], noise[k % NOISE_POOL], u0s[k], stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(2, 2 + args.sir_steps):
+            pcsir.sir_step(ctx, state, images[k], noise[k % NOISE_POOL], u0s[k], stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.sir_steps
+        sir = {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.sir_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = 1 << 18
+        rate, steps, tot = cpu_oracle_rate(n_s, 12.0, SEED + 17, h)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "N=2^18 particles of the same workload, %d oracle pcSIR steps (%.1f s)" % (steps, tot)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": elapsed_ms / K, "steps_per_s": 1e3 * K / elapsed_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(N, h), "N": N, "h": h, "image": "512x512", "patch": PATCH,
+                       "state": "f32 SoA", "noise_pool": NOISE_POOL,
+                       "l2": "inputs larger than L2 (state and noise 335 MB each)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "stages_ms": {"prop_bin": st_mean[0], "dummies_lik": st_mean[1], "weights": st_mean[2],
+                          "scan_resample": st_mean[3], "share": [float(s) for s in share],
+                          "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
+                          "scan_resample_gbs": resample_gbs},
+            "e2e": e2e, "sir": sir, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),
+            "device_error": derr,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * pcsir.h - C ABI of the GB300 (sm_103a) piecewise-constant SIR particle filter.
+ *
+ * One call advances one particle filter by one time step k on the GPU, either
+ * by plain sequential importance resampling (Algorithm 1 of Demirel et al.,
+ * "Piecewise Constant Sequential Importance Sampling for Fast Particle
+ * Filtering") or by its piecewise-constant variant pcSIR (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *  - All pointers named "device" point to memory of the current CUDA device;
+ *    the library never frees caller memory.
+ *  - State arrays are structure-of-arrays, component-major: element (d, i)
+ *    of an N-particle state lives at state[d * N + i] with components
+ *    d = 0..4 = (x, y, vx, vy, I0) (Section 5.1), in the context's state
+ *    dtype (float or double).  Positions are in pixels; pixel (x, y) of an
+ *    image is centred on integer coordinates (Eq. likelihood).
+ *  - Images are float32, row-major: Z[y * W + x].
+ *  - Work is enqueued on the given cudaStream_t (passed as void*, NULL = the
+ *    legacy default stream) and is asynchronous: results are valid after the
+ *    stream is synchronised.  No entry point allocates device memory except
+ *    pcsir_create; every step call is capturable in a CUDA graph.
+ *  - Every call returns a pcsir_status.  Argument errors are detected on the
+ *    host before anything is enqueued.  Errors the GPU detects while running
+ *    (non-finite or out-of-range states, a timed-out wait) are reported as
+ *    bit flags in pcsir_result.device_error of that step.  Once a call has
+ *    failed with PCSIR_ECUDA the context is unusable (sticky) and every later
+ *    call returns PCSIR_ESTATE; pcsir_last_error() describes the failure.
+ *  - A context is not thread-safe; steps on one context must be ordered on
+ *    one stream (they share the context's workspace).
+ */
+#ifndef PCSIR_H_
+#define PCSIR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcsir_ctx pcsir_ctx;
+
+typedef enum pcsir_status {
+  PCSIR_OK = 0,
+  PCSIR_EINVAL = -1,    /* invalid argument (checked on the host) */
+  PCSIR_ENOMEM = -2,    /* device allocation failed in pcsir_create */
+  PCSIR_ECUDA = -3,     /* a CUDA call failed; the context becomes sticky-failed */
+  PCSIR_ETIMEDOUT = -4, /* reserved for bounded device waits reported on the host */
+  PCSIR_ESTATE = -5,    /* context already failed, or outputs requested before any step */
+  PCSIR_ENOTSUP = -6,   /* combination of options not supported */
+  PCSIR_ERANGE = -7     /* size beyond the limits fixed at pcsir_create */
+} pcsir_status;
+
+/* state dtype */
+enum { PCSIR_F32 = 0, PCSIR_F64 = 1 };
+
+/* likelihood of one image given a position (Eq. likelihood over the patch S_x) */
+enum {
+  /* Poisson log-likelihood ratio against a perfect fit, per pixel
+     z*log(lambda/z) - (lambda - z) (0 when lambda = z, -lambda when z = 0) */
+  PCSIR_LIK_POISSON = 0,
+  /* the paper's Gaussian sum of squares, per pixel -(z - lambda)^2 / (2 sigma_xi^2) */
+  PCSIR_LIK_SSE = 1
+};
+
+/* flags of pcsir_config.keep: optional per-particle outputs kept for inspection */
+enum {
+  PCSIR_KEEP_ANCESTORS = 1,    /* int32 ancestor index s(i) of every output particle */
+  PCSIR_KEEP_WEIGHTS = 2,      /* float64 normalised weight w_k^i of every propagated particle */
+  PCSIR_KEEP_PARTICLE_BIN = 4  /* uint32 bin index (into the bin arrays) of every particle */
+};
+
+/* bit flags of pcsir_result.device_error */
+enum {
+  PCSIR_DERR_RANGE = 1,     /* non-finite state, |position| >= 2^30, cell index or spread beyond limits */
+  PCSIR_DERR_TIMEOUT = 2,   /* a bounded inter-block wait gave up (results of the step are invalid) */
+  PCSIR_DERR_NONFINITE = 4, /* a log-likelihood was not finite (its weight was set to 0) */
+  PCSIR_DERR_ZEROSUM = 8    /* every weight was zero: no resampling possible (state left propagated) */
+};
+
+/*
+ * Model and limits, fixed for the life of a context.
+ * psf_sigma, bg: Gaussian point-spread function of Eq. (object),
+ *   lambda(px, py) = max(I0, 0) * exp(-((px - x)^2 + (py - y)^2) / (2 psf_sigma^2)) + bg,
+ *   point-sampled at pixel centres.
+ * patch: odd side P of the square patch S_x of Eq. (likelihood), centred on the
+ *   pixel nearest the evaluated position, (floor(x + 0.5), floor(y + 0.5));
+ *   pixels outside the image contribute nothing.
+ * max_particles: largest N any step of this context will use (1 .. 2^26).
+ */
+typedef struct pcsir_config {
+  int32_t state_dtype;   /* PCSIR_F32 or PCSIR_F64 */
+  int32_t lik_kind;      /* PCSIR_LIK_POISSON or PCSIR_LIK_SSE */
+  int32_t patch;         /* odd, 1 .. 63 */
+  int32_t keep;          /* PCSIR_KEEP_* flags */
+  double psf_sigma;      /* > 0, pixels */
+  double bg;             /* background intensity; > 0 for PCSIR_LIK_POISSON */
+  double sigma_xi;       /* > 0; used by PCSIR_LIK_SSE only */
+  int64_t max_particles; /* 1 .. 2^26 */
+} pcsir_config;
+
+/* Scalars of one step, in host memory (see result_host below). */
+typedef struct pcsir_result {
+  double estimate[5];   /* posterior mean of (x, y, vx, vy, I0) before resampling */
+  double ess;           /* effective sample size 1 / sum_i w_i^2 (Algorithm 1) */
+  double max_loglik;    /* max over particles of the log-likelihood */
+  double sum_wtilde;    /* sum_i exp(ll_i - max_loglik); w_i = exp(ll_i - max_loglik) / sum_wtilde */
+  int64_t n_particles;  /* N of the step */
+  int64_t n_bins;       /* pcSIR: occupied bins B; SIR: 0 */
+  int32_t device_error; /* PCSIR_DERR_* flags, 0 if none */
+  int32_t kind;         /* 0 = SIR step, 1 = pcSIR step */
+} pcsir_result;
+
+/* Device pointers to intermediates of the most recent step of a context,
+   valid until the next step on that context (read them after synchronising).
+   Bin arrays hold the B occupied bins in an unspecified order that is the
+   same across all bin arrays; NULL where the step kind or keep flags do not
+   produce the array. */
+typedef struct pcsir_outputs {
+  int64_t n_particles;
+  int64_t n_bins;
+  int64_t bin_stride;            /* element (d, b) of bin_xy / dummy is at [d * bin_stride + b] */
+  const void* prop_state;        /* [5][N] propagated states x~_k (state dtype) */
+  const int32_t* bin_xy;         /* [2][bin_stride] cell indices (bx, by), bx = floor((x + 0.5) / h) */
+  const uint32_t* bin_count;     /* [B] members per bin */
+  const double* dummy;           /* [5][bin_stride] dummy states (mean state of each bin) */
+  const double* bin_loglik;      /* [B] log-likelihood of each dummy */
+  const double* loglik;          /* SIR: [N] log-likelihood of each propagated particle */
+  const uint32_t* particle_bin;  /* [N] bin index of each particle (PCSIR_KEEP_PARTICLE_BIN) */
+  const int32_t* ancestor;       /* [N] s(i) for each output particle i (PCSIR_KEEP_ANCESTORS) */
+  const double* weight;          /* [N] normalised weights (PCSIR_KEEP_WEIGHTS) */
+} pcsir_outputs;
+
+/* Create a context on the current CUDA device: validates cfg and allocates
+   all workspace for up to cfg->max_particles particles.  On success *out
+   receives the context; on failure *out is set to NULL.
+   Errors: PCSIR_EINVAL (bad cfg or NULL out), PCSIR_ENOMEM, PCSIR_ECUDA. */
+pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out);
+
+/* Release a context and its workspace (synchronises the device first).
+   NULL is accepted and ignored. */
+pcsir_status pcsir_destroy(pcsir_ctx* ctx);
+
+/*
+ * One pcSIR step (Algorithm 2, resampling every step).
+ *   state  device [5][N], state dtype, read-write: on entry the states
+ *          x_{k-1} (all weights equal, as after resampling), on return the
+ *          resampled states x_k.
+ *   N      particles, 1 .. max_particles.
+ *   image  device float32 [H][W], the observation z_k, read-only.
+ *   h      cell edge in pixels, 0 < h <= 8.  Cells are [b h - 0.5, (b+1) h - 0.5)
+ *          on each axis, so h = 1 cells are the image pixels (pcSIR-1x1) and
+ *          h = 0.5 quarters them (pcSIR-2x2) (Section 4.2).
+ *   noise  device [5][N] in the state dtype: the process noise e added by the
+ *          nearly-constant-velocity transition (Section 5.1),
+ *          x += vx + e_x, y += vy + e_y, vx += e_vx, vy += e_vy, I0 += e_I0.
+ *   u0     systematic-resampling offset in [0, 1): output particle i takes
+ *          the first particle l whose inclusive cumulative weight exceeds
+ *          (i + u0) / N of the total.
+ *   stream cudaStream_t (as void*).
+ *   result_host  NULL, or host memory (page-locked for a truly asynchronous
+ *          copy) that receives the step's pcsir_result once the stream has
+ *          reached the end of the step.
+ * Steps: propagate, cell index, per-cell centre of mass (the dummy),
+ * likelihood of the dummies only, the dummy's weight copied to its members,
+ * normalisation, ESS, posterior mean, systematic resampling.
+ * Errors: PCSIR_EINVAL (NULL pointers, N or h out of range, W or H < 1,
+ * u0 outside [0,1)), PCSIR_ERANGE (N > max_particles), PCSIR_ECUDA,
+ * PCSIR_ESTATE.
+ */
+pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image,
+                        int32_t W, int32_t H, double h, const void* noise, double u0,
+                        void* stream, pcsir_result* result_host);
+
+/* One SIR step (Algorithm 1, bootstrap proposal, resampling every step): as
+   pcsir_step without the bins; the likelihood is evaluated for every particle. */
+pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image,
+                      int32_t W, int32_t H, const void* noise, double u0,
+                      void* stream, pcsir_result* result_host);
+
+/* Log-likelihood (Eq. likelihood with the context's model) of n positions:
+   x, y, I0 device float64 [n], out device float64 [n].  The same device code
+   the steps use; exposed for tests and for labelling likelihood data. */
+pcsir_status pcsir_loglik(pcsir_ctx* ctx, const double* x, const double* y, const double* I0,
+                          int64_t n, const float* image, int32_t W, int32_t H, double* out,
+                          void* stream);
+
+/* Systematic resampling alone (Algorithm 1 resampling step): ancestors of N
+   outputs from N log-weights.  logw device float64 [N] (weights are
+   exp(logw - max logw)); ancestors device int32 [N].  Uses the step's scan
+   and resampling kernels; N <= max_particles. */
+pcsir_status pcsir_resample(pcsir_ctx* ctx, const double* logw, int64_t N, double u0,
+                            int32_t* ancestors, void* stream);
+
+/* Per-stage timing.  pcsir_timing_enable(ctx, max_steps) creates CUDA events
+   for max_steps steps (max_steps = 0 disables timing and frees them); every
+   later step records an event before its first kernel and after each of its
+   four kernel stages, into slot (step count mod max_steps), without any
+   synchronisation.  pcsir_timing_read(ctx, ms, capacity, &n_steps) waits for
+   the recorded steps (since enable or the previous read, at most max_steps)
+   and writes, for step s, the durations in milliseconds of stage j = 0..3 to
+   ms[4 s + j]: pcSIR = (propagate + cells + centre-of-mass sums, dummies +
+   likelihood, weight reduction, scan + resample), SIR = (propagate +
+   likelihood, weight reduction, 0, scan + resample).  capacity is the length
+   of ms in floats.  Errors: PCSIR_EINVAL, PCSIR_ESTATE (timing not enabled),
+   PCSIR_ECUDA. */
+pcsir_status pcsir_timing_enable(pcsir_ctx* ctx, int32_t max_steps);
+pcsir_status pcsir_timing_read(pcsir_ctx* ctx, float* ms, int32_t capacity, int32_t* n_steps);
+
+/* Intermediates of the last step (see pcsir_outputs).  Host call, no sync. */
+pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* out);
+
+/* Copy of the last step's pcsir_result kept by the context in page-locked
+   memory (valid after the stream of that step is synchronised). */
+pcsir_status pcsir_last_result(pcsir_ctx* ctx, pcsir_result* out);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* pcsir_last_error(pcsir_ctx* ctx);
+
+/* Library version string. */
+const char* pcsir_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCSIR_H_ */

@@ -232,7 +232,7 @@ def sir_step(state, image, noise, u0, model, lik=None, prior_logw=None):
     w, m, T = normalise(logw)
     anc = systematic_resample(w, u0)
     return dict(prop=prop, ll=ll, w=w, max_logw=m, ess=ess(w),
-                estimate=posterior_mean(w, prop), ancestors=anc, new_state=prop[:, anc])
+                estimate=posterior_mean(w, prop), ancestors=anc, new_state=np.ascontiguousarray(prop[:, anc]))
 
 
 def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None):
@@ -255,7 +255,7 @@ def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None):
     anc = systematic_resample(w, u0)
     return dict(prop=prop, bin_keys=keys, bin_counts=counts, member_bin=member,
                 dummies=dum, ll_bins=ll_bins, ll=ll, w=w, max_logw=m, ess=ess(w),
-                estimate=posterior_mean(w, prop), ancestors=anc, new_state=prop[:, anc])
+                estimate=posterior_mean(w, prop), ancestors=anc, new_state=np.ascontiguousarray(prop[:, anc]))
 
 
 def run_filter(kind, seq_images, gt0, N, noise_fn, u0_fn, model, h=None, dtype=np.float64,

@@ -1,0 +1,343 @@
+// Host side of the C ABI declared in include/pcsir.h: context lifetime,
+// argument checks, workspace, and the kernel sequence of one filter step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pcsir_internal.h"
+
+using namespace pcsir;
+
+struct pcsir_ctx {
+  pcsir_config cfg{};
+  int device = 0;
+  int num_sms = 0;
+  StepBuffers b{};
+  ModelParams m{};
+  pcsir_result* host_res = nullptr;  // page-locked copy of the last result
+  std::vector<void*> allocs;
+  std::string err = "no error";
+  bool failed = false;
+  int last_kind = -1;
+  int64_t last_N = 0;
+  // stage timing: 5 events per step slot
+  std::vector<cudaEvent_t> events;
+  int timing_slots = 0;
+  int64_t timing_count = 0;  // steps recorded since enable / last read
+};
+
+namespace {
+
+pcsir_status fail(pcsir_ctx* c, pcsir_status st, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (st == PCSIR_ECUDA) c->failed = true;
+  }
+  return st;
+}
+
+pcsir_status cuda_fail(pcsir_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, PCSIR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+bool dev_alloc(pcsir_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+void free_events(pcsir_ctx* c) {
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  c->events.clear();
+  c->timing_slots = 0;
+  c->timing_count = 0;
+}
+
+// events of the step about to be enqueued (nullptr when timing is off)
+StageEvents step_events(pcsir_ctx* c) {
+  if (c->timing_slots == 0) return StageEvents{nullptr};
+  const int slot = (int)(c->timing_count % c->timing_slots);
+  c->timing_count++;
+  return StageEvents{c->events.data() + 5 * slot};
+}
+
+void free_all(pcsir_ctx* c) {
+  free_events(c);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->host_res) cudaFreeHost(c->host_res);
+  c->host_res = nullptr;
+}
+
+size_t state_size(const pcsir_ctx* c) { return c->cfg.state_dtype == PCSIR_F64 ? 8 : 4; }
+
+pcsir_status check_step_args(pcsir_ctx* c, const void* state, int64_t N, const float* image, int32_t W, int32_t H,
+                             const void* noise, double u0) {
+  if (!c) return PCSIR_EINVAL;
+  if (c->failed) return fail(c, PCSIR_ESTATE, "context failed earlier: " + c->err);
+  if (!state || !image) return fail(c, PCSIR_EINVAL, "state and image must be non-NULL device pointers");
+  if (!noise) return fail(c, PCSIR_ENOTSUP, "noise must be a device array; in-kernel noise is not supported");
+  if (N < 1) return fail(c, PCSIR_EINVAL, "N must be >= 1");
+  if (N > c->cfg.max_particles) return fail(c, PCSIR_ERANGE, "N exceeds max_particles of the context");
+  if (W < 1 || H < 1) return fail(c, PCSIR_EINVAL, "image width and height must be >= 1");
+  if (!(u0 >= 0.0 && u0 < 1.0)) return fail(c, PCSIR_EINVAL, "u0 must lie in [0, 1)");
+  return PCSIR_OK;
+}
+
+pcsir_status finish_step(pcsir_ctx* c, cudaStream_t s, pcsir_result* result_host, int kind, int64_t N) {
+  cudaError_t e = cudaMemcpyAsync(c->host_res, c->b.dres, sizeof(pcsir_result), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy of step result");
+  if (result_host && result_host != c->host_res) {
+    e = cudaMemcpyAsync(result_host, c->b.dres, sizeof(pcsir_result), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy of step result");
+  }
+  c->last_kind = kind;
+  c->last_N = N;
+  return PCSIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pcsir_version(void) { return "pcsir-gb300 0.1 (sm_103a)"; }
+
+const char* pcsir_last_error(pcsir_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
+  if (!out) return PCSIR_EINVAL;
+  *out = nullptr;
+  if (!cfg) return PCSIR_EINVAL;
+  if (cfg->state_dtype != PCSIR_F32 && cfg->state_dtype != PCSIR_F64) return PCSIR_EINVAL;
+  if (cfg->lik_kind != PCSIR_LIK_POISSON && cfg->lik_kind != PCSIR_LIK_SSE) return PCSIR_EINVAL;
+  if (cfg->patch < 1 || cfg->patch > 63 || (cfg->patch & 1) == 0) return PCSIR_EINVAL;
+  if (!(cfg->psf_sigma > 0.0) || !std::isfinite(cfg->psf_sigma)) return PCSIR_EINVAL;
+  if (cfg->lik_kind == PCSIR_LIK_POISSON && !(cfg->bg > 0.0)) return PCSIR_EINVAL;
+  if (cfg->lik_kind == PCSIR_LIK_SSE && !(cfg->sigma_xi > 0.0)) return PCSIR_EINVAL;
+  if (!std::isfinite(cfg->bg)) return PCSIR_EINVAL;
+  if (cfg->max_particles < 1 || cfg->max_particles > MAX_PARTICLES) return PCSIR_EINVAL;
+  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN)) return PCSIR_EINVAL;
+
+  pcsir_ctx* c = new (std::nothrow) pcsir_ctx();
+  if (!c) return PCSIR_ENOMEM;
+  c->cfg = *cfg;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    cudaGetLastError();
+    return PCSIR_ECUDA;
+  }
+  c->m.P = cfg->patch;
+  c->m.kind = cfg->lik_kind;
+  c->m.sigma = cfg->psf_sigma;
+  c->m.bg = cfg->bg;
+  c->m.sigma_xi = cfg->sigma_xi > 0.0 ? cfg->sigma_xi : 1.0;
+
+  const int64_t nmax = cfg->max_particles;
+  int hbits = 1;
+  while ((int64_t(1) << hbits) < 2 * nmax) ++hbits;
+  if (hbits < 10) hbits = 10;
+  const size_t hcap = size_t(1) << hbits;
+  StepBuffers& b = c->b;
+  b.hbits = hbits;
+  b.bin_stride = nmax;
+  b.max_tiles = (nmax + SCAN_TILE - 1) / SCAN_TILE;
+  bool ok = dev_alloc(c, &b.hkey, hcap) && dev_alloc(c, &b.hcnt, hcap) && dev_alloc(c, &b.hsum, 5 * hcap) &&
+            dev_alloc(c, &b.hrank, hcap) && dev_alloc(c, &b.hq, hcap) && dev_alloc(c, &b.hw, hcap) &&
+            dev_alloc(c, &b.occ, (size_t)nmax) && dev_alloc(c, &b.bin_xy, 2 * (size_t)nmax) &&
+            dev_alloc(c, &b.bin_cnt, (size_t)nmax) && dev_alloc(c, &b.dummy, 5 * (size_t)nmax) &&
+            dev_alloc(c, &b.bin_ll, (size_t)nmax) && dev_alloc(c, &b.pslot, (size_t)nmax) &&
+            dev_alloc(c, &b.ll, (size_t)nmax) && dev_alloc(c, &b.tile_status, (size_t)b.max_tiles) &&
+            dev_alloc(c, &b.ctl, 1) && dev_alloc(c, &b.dres, 1);
+  if (ok) {
+    unsigned char* p = nullptr;
+    ok = dev_alloc(c, &p, 5 * (size_t)nmax * state_size(c));
+    b.prop = p;
+  }
+  if (ok && (cfg->keep & PCSIR_KEEP_ANCESTORS)) ok = dev_alloc(c, &b.anc, (size_t)nmax);
+  if (ok && (cfg->keep & PCSIR_KEEP_WEIGHTS)) ok = dev_alloc(c, &b.wout, (size_t)nmax);
+  if (ok && (cfg->keep & PCSIR_KEEP_PARTICLE_BIN)) ok = dev_alloc(c, &b.pbin, (size_t)nmax);
+  if (!ok) {
+    free_all(c);
+    delete c;
+    return PCSIR_ENOMEM;
+  }
+  e = prepare_kernels(cfg->state_dtype, &b.prop_bin_per_sm);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result));
+  if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b.hcnt, 0, hcap * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b.hsum, 0, 5 * hcap * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(b.tile_status, 0, (size_t)b.max_tiles * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b.dres, 0, sizeof(pcsir_result));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return e == cudaErrorMemoryAllocation ? PCSIR_ENOMEM : PCSIR_ECUDA;
+  }
+  std::memset(c->host_res, 0, sizeof(pcsir_result));
+  *out = c;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_destroy(pcsir_ctx* ctx) {
+  if (!ctx) return PCSIR_OK;
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H, double h,
+                        const void* noise, double u0, void* stream, pcsir_result* result_host) {
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StageEvents se = step_events(ctx);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  e = launch_pcsir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, h, image, W, H, ctx->num_sms, s,
+                         se);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels");
+  e = launch_resample(ctx->b, ctx->cfg.state_dtype, state, N, u0, WSRC_BINS, ctx->cfg.keep, ctx->num_sms, s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
+  return finish_step(ctx, s, result_host, 1, N);
+}
+
+pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H,
+                      const void* noise, double u0, void* stream, pcsir_result* result_host) {
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StageEvents se = step_events(ctx);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  e = launch_sir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, image, W, H, ctx->num_sms, s, se);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "SIR front kernels");
+  e = launch_resample(ctx->b, ctx->cfg.state_dtype, state, N, u0, WSRC_PARTICLES,
+                      ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN, ctx->num_sms, s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
+  return finish_step(ctx, s, result_host, 0, N);
+}
+
+pcsir_status pcsir_loglik(pcsir_ctx* ctx, const double* x, const double* y, const double* I0, int64_t n,
+                          const float* image, int32_t W, int32_t H, double* out, void* stream) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (n < 0) return fail(ctx, PCSIR_EINVAL, "n must be >= 0");
+  if (n == 0) return PCSIR_OK;
+  if (!x || !y || !I0 || !image || !out) return fail(ctx, PCSIR_EINVAL, "NULL device pointer");
+  if (W < 1 || H < 1) return fail(ctx, PCSIR_EINVAL, "image width and height must be >= 1");
+  cudaError_t e = launch_loglik(ctx->m, x, y, I0, n, image, W, H, out, ctx->num_sms, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "likelihood kernel");
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_resample(pcsir_ctx* ctx, const double* logw, int64_t N, double u0, int32_t* ancestors,
+                            void* stream) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (!logw || !ancestors) return fail(ctx, PCSIR_EINVAL, "NULL device pointer");
+  if (N < 1) return fail(ctx, PCSIR_EINVAL, "N must be >= 1");
+  if (N > ctx->cfg.max_particles) return fail(ctx, PCSIR_ERANGE, "N exceeds max_particles of the context");
+  if (!(u0 >= 0.0 && u0 < 1.0)) return fail(ctx, PCSIR_EINVAL, "u0 must lie in [0, 1)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  e = launch_logw_front(ctx->b, logw, N, ctx->num_sms, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "weight reduction");
+  e = launch_resample_logw(ctx->b, logw, ancestors, N, u0, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
+  ctx->last_kind = -1;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_timing_enable(pcsir_ctx* ctx, int32_t max_steps) {
+  if (!ctx || max_steps < 0 || max_steps > 100000) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  free_events(ctx);
+  if (max_steps == 0) return PCSIR_OK;
+  ctx->events.resize(5 * (size_t)max_steps, nullptr);
+  for (auto& ev : ctx->events) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      ev = nullptr;
+      free_events(ctx);
+      return cuda_fail(ctx, e, "event creation");
+    }
+  }
+  ctx->timing_slots = max_steps;
+  ctx->timing_count = 0;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_timing_read(pcsir_ctx* ctx, float* ms, int32_t capacity, int32_t* n_steps) {
+  if (!ctx || !ms || !n_steps || capacity < 0) return PCSIR_EINVAL;
+  if (ctx->timing_slots == 0) return fail(ctx, PCSIR_ESTATE, "timing is not enabled");
+  const int64_t n = ctx->timing_count < ctx->timing_slots ? ctx->timing_count : ctx->timing_slots;
+  const int64_t first = ctx->timing_count - n;
+  int32_t written = 0;
+  for (int64_t k = 0; k < n && 4 * (written + 1) <= capacity; ++k) {
+    const int slot = (int)((first + k) % ctx->timing_slots);
+    cudaEvent_t* ev = ctx->events.data() + 5 * slot;
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event synchronisation");
+    for (int j = 0; j < 4; ++j) {
+      float t = 0.0f;
+      e = cudaEventElapsedTime(&t, ev[j], ev[j + 1]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed time");
+      ms[4 * written + j] = t;
+    }
+    ++written;
+  }
+  *n_steps = written;
+  ctx->timing_count = 0;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* o) {
+  if (!ctx || !o) return PCSIR_EINVAL;
+  if (ctx->last_kind < 0) return fail(ctx, PCSIR_ESTATE, "no step has run on this context");
+  std::memset(o, 0, sizeof(*o));
+  const StepBuffers& b = ctx->b;
+  o->n_particles = ctx->last_N;
+  o->n_bins = ctx->last_kind == 1 ? ctx->host_res->n_bins : 0;
+  o->bin_stride = b.bin_stride;
+  o->prop_state = b.prop;
+  if (ctx->last_kind == 1) {
+    o->bin_xy = b.bin_xy;
+    o->bin_count = b.bin_cnt;
+    o->dummy = b.dummy;
+    o->bin_loglik = b.bin_ll;
+    o->particle_bin = b.pbin;
+  } else {
+    o->loglik = b.ll;
+  }
+  o->ancestor = b.anc;
+  o->weight = b.wout;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_last_result(pcsir_ctx* ctx, pcsir_result* out) {
+  if (!ctx || !out) return PCSIR_EINVAL;
+  std::memcpy(out, ctx->host_res, sizeof(*out));
+  return PCSIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+// Device helpers shared by the pcSIR / SIR kernels: double-float arithmetic,
+// fixed-point accumulation, ordered max of doubles, hashing, and the
+// warp-cooperative patch likelihood of Eq. (likelihood).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pcsir_internal.h"
+
+namespace pcsir {
+
+// ---------------------------------------------------------------------------
+// Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <=
+// ulp(hi)/2.  Error-free transformations after Knuth (TwoSum) and Dekker
+// (Fast2Sum), products through one FMA.  Every operation uses the _rn
+// intrinsics so no contraction or reassociation can change the rounding.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ df df_from_double(double v) {
+  float hi = __double2float_rn(v);
+  float lo = __double2float_rn(__dsub_rn(v, (double)hi));
+  return {hi, lo};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// exp of a double-float argument a <= 0, relative error about 1e-13.
+// Range reduction a = k ln2 + r (|r| <= ln2/2) with ln2 as a double-float,
+// then r' = r / 16, a degree-6 Taylor polynomial of exp(r') (the terms from
+// r'^3 on are below 2^-24 of the result and are summed in float), four
+// squarings, and the 2^k scale applied exactly to both parts.
+__device__ __forceinline__ df df_exp_neg(df a) {
+  if (a.hi < -87.0f) return {0.0f, 0.0f};
+  const float LOG2E = 1.44269504088896341f;
+  const df LN2 = {0.693147182464599609375f, -1.904654323148236017e-09f};
+  float k = rintf(__fmul_rn(a.hi, LOG2E));
+  df r = df_add(a, df_mul_f(LN2, -k));
+  r.hi = __fmul_rn(r.hi, 0.0625f);
+  r.lo = __fmul_rn(r.lo, 0.0625f);
+  // 1 + r + r^2/2 in double-float, the rest in float
+  df r2 = df_mul(r, r);
+  r2.hi = __fmul_rn(r2.hi, 0.5f);
+  r2.lo = __fmul_rn(r2.lo, 0.5f);
+  float x = r.hi;
+  float tail = x * x * x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))));
+  df p = df_add(r, r2);
+  p = df_add_f(p, tail);
+  p = df_add_f(p, 1.0f);
+  p = df_mul(p, p);
+  p = df_mul(p, p);
+  p = df_mul(p, p);
+  p = df_mul(p, p);
+  int ki = (int)k;
+  return {ldexpf(p.hi, ki), ldexpf(p.lo, ki)};
+}
+
+// phi(u) = u - log(1 + u) >= 0 for u > -1, computed without cancellation.
+// For -1/2 <= u <= 1, with s = u / (2 + u) (|s| <= 1/3) and
+// log(1+u) = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), u - 2 s = u s exactly,
+// so phi = u s - 2 s^3 (1/3 + s^2/5 + ... + s^14/17); truncation error below
+// 1e-9 relative.  Outside that range phi is O(1) and the direct difference
+// with log1pf is accurate.
+__device__ __forceinline__ float phi_log1p(float u) {
+  if (u >= -0.5f && u <= 1.0f) {
+    float s = __fdiv_rn(u, __fadd_rn(2.0f, u));
+    float s2 = s * s;
+    float p = 1.0f / 17.0f;
+    p = fmaf(p, s2, 1.0f / 15.0f);
+    p = fmaf(p, s2, 1.0f / 13.0f);
+    p = fmaf(p, s2, 1.0f / 11.0f);
+    p = fmaf(p, s2, 1.0f / 9.0f);
+    p = fmaf(p, s2, 1.0f / 7.0f);
+    p = fmaf(p, s2, 1.0f / 5.0f);
+    p = fmaf(p, s2, 1.0f / 3.0f);
+    return fmaf(u, s, -2.0f * s * s2 * p);
+  }
+  return u - log1pf(u);
+}
+
+// Kahan-compensated accumulator in float.
+struct kahan {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    float y = __fsub_rn(v, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+};
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Likelihood of one position, computed by a whole warp (Eq. object, Eq.
+// likelihood).  The PSF factorises, lambda = I0 gx(px) gy(py) + bg, so the
+// 2P one-dimensional factors are computed once in double-float (scratch in
+// shared memory, 4P floats per warp) and each of the P^2 pixels costs one
+// double-float product.  For the Poisson term the difference d = lambda - z
+// is rounded once to float and the term -z phi(d / z) is summed with Kahan
+// compensation per lane, then across the warp in double-float.
+// All lanes of the warp must call this with the same arguments; every lane
+// returns the result.
+// ---------------------------------------------------------------------------
+struct LikParams {
+  int P;          // odd patch side
+  int kind;       // PCSIR_LIK_*
+  float bg;       // background
+  df c2;          // 1 / (2 sigma^2) as double-float
+  float inv2sxi2; // 1 / (2 sigma_xi^2)
+};
+
+__device__ __forceinline__ double warp_loglik(const float* __restrict__ img, int W, int H,
+                                              double x, double y, double i0,
+                                              const LikParams& lp, float* __restrict__ scratch) {
+  const int lane = threadIdx.x & 31;
+  const int P = lp.P;
+  const int R = P >> 1;
+  const double cxd = floor(x + 0.5);
+  const double cyd = floor(y + 0.5);
+  const int cx = (int)cxd;
+  const int cy = (int)cyd;
+  const df I0 = df_from_double(i0 > 0.0 ? i0 : 0.0);
+  float* gxh = scratch;
+  float* gxl = scratch + P;
+  float* gyh = scratch + 2 * P;
+  float* gyl = scratch + 3 * P;
+  // one-dimensional factors: column j -> I0 * exp(-(px - x)^2 c2), row j -> exp(-(py - y)^2 c2)
+  for (int j = lane; j < 2 * P; j += 32) {
+    const bool col = j < P;
+    const int jj = col ? j : j - P;
+    const double off = (double)(jj - R);
+    // px - x = (c - x) + off, with |c - x| <= 1/2 and off an integer: exact in double
+    const double dd = col ? (cxd - x) + off : (cyd - y) + off;
+    const df d = df_from_double(dd);
+    df e = df_mul(df_mul(d, d), lp.c2);
+    e.hi = -e.hi;
+    e.lo = -e.lo;
+    df g = df_exp_neg(e);
+    if (col) {
+      g = df_mul(g, I0);
+      gxh[jj] = g.hi;
+      gxl[jj] = g.lo;
+    } else {
+      gyh[jj] = g.hi;
+      gyl[jj] = g.lo;
+    }
+  }
+  __syncwarp();
+  kahan acc;
+  const int PP = P * P;
+  for (int p = lane; p < PP; p += 32) {
+    const int r = p / P;
+    const int c = p - r * P;
+    const int px = cx - R + c;
+    const int py = cy - R + r;
+    if (px < 0 || px >= W || py < 0 || py >= H) continue;
+    const float z = __ldg(img + (size_t)py * W + px);
+    const df prod = df_mul({gxh[c], gxl[c]}, {gyh[r], gyl[r]});  // I0 gx gy
+    if (lp.kind == PCSIR_LIK_POISSON) {
+      if (z > 0.0f) {
+        // d = prod + (bg - z), rounded once
+        const df s = two_sum(prod.hi, __fsub_rn(lp.bg, z));
+        const float d = __fadd_rn(s.hi, __fadd_rn(s.lo, prod.lo));
+        const float u = __fdiv_rn(d, z);
+        acc.add(-z * phi_log1p(u));
+      } else {
+        const df lam = df_add_f(prod, lp.bg);
+        acc.add(-lam.hi);
+        acc.add(-lam.lo);
+      }
+    } else {
+      // e = z - lambda = (z - bg) - prod, rounded once
+      const df s = two_sum(__fsub_rn(z, lp.bg), -prod.hi);
+      const float e = __fadd_rn(s.hi, __fsub_rn(s.lo, prod.lo));
+      acc.add(-(e * e) * lp.inv2sxi2);
+    }
+  }
+  df tot = two_sum(acc.s, -acc.c);
+  tot = warp_sum_df(tot);
+  __syncwarp();
+  return df_to_double(tot);
+}
+
+// ---------------------------------------------------------------------------
+// Order-preserving 64-bit encoding of doubles (for atomicMax).  0 encodes
+// "nothing yet" and sorts below every real value.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ord_encode(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_decode(unsigned long long o) {
+  unsigned long long b = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
+  return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------------------
+// Cell keys and hashing.  A cell (bx, by), |bx|,|by| < 2^30, is packed into a
+// 64-bit key; all-ones never occurs and marks an empty hash slot.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long EMPTY_KEY = 0xffffffffffffffffull;
+
+__device__ __forceinline__ unsigned long long pack_key(int bx, int by) {
+  return ((unsigned long long)(unsigned)(by + 0x40000000) << 32) | (unsigned)(bx + 0x40000000);
+}
+__device__ __forceinline__ int key_bx(unsigned long long k) { return (int)(unsigned)(k & 0xffffffffu) - 0x40000000; }
+__device__ __forceinline__ int key_by(unsigned long long k) { return (int)(unsigned)(k >> 32) - 0x40000000; }
+
+__device__ __forceinline__ unsigned hash_bits(unsigned long long k, int bits) {
+  return (unsigned)((k * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+// Fixed-point scales of the centre-of-mass sums (see pcsir_internal.h).
+constexpr double POS_SCALE = 4294967296.0;      // 2^32
+constexpr double POS_INV = 1.0 / 4294967296.0;
+constexpr double VAL_SCALE = 4194304.0;         // 2^22
+constexpr double VAL_INV = 1.0 / 4194304.0;
+
+__device__ __forceinline__ long long to_fixed(float v, float scale) {
+  return __float2ll_rn(__fmul_rn(v, scale));
+}
+__device__ __forceinline__ long long to_fixed(double v, double scale) {
+  return __double2ll_rn(__dmul_rn(v, scale));
+}
+
+// Per-particle weight w = exp(ll - max) <= 1 in double-float (relative error
+// about 1e-13, so the integer weights below carry the scale's resolution) and
+// its integer weight q = rint(w 2^sq), computed as the sum of the rounded
+// scaled parts.  The weight reduction and the scan both call these, so both
+// see identical q.
+__device__ __forceinline__ df wtilde_df(double ll, double m) {
+  if (ll == -INFINITY) return {0.0f, 0.0f};
+  double a = ll - m;
+  if (a > 0.0) a = 0.0;
+  return df_exp_neg(df_from_double(a));
+}
+__device__ __forceinline__ long long q_of_wtilde(df w, int sq) {
+  const float scale = __int_as_float((127 + sq) << 23);  // 2^sq, exact
+  return __float2ll_rn(__fmul_rn(w.hi, scale)) + __float2ll_rn(__fmul_rn(w.lo, scale));
+}
+
+// Atomic OR of an error flag into the control block.
+__device__ __forceinline__ void raise_flag(Control* ctl, unsigned f) { atomicOr(&ctl->err, f); }
+
+}  // namespace pcsir

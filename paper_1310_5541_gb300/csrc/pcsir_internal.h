@@ -1,0 +1,111 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pcsir.h"
+
+namespace pcsir {
+
+// Per-step control block in device memory, zeroed at the start of every step.
+struct Control {
+  unsigned int nocc;          // occupied cells found so far (hash slots listed in occ[])
+  unsigned int tile_ticket;   // next tile of the scan/resample kernel
+  unsigned int done_blocks;   // last-block-done counter of the weight reduction
+  unsigned int err;           // PCSIR_DERR_* flags
+  unsigned long long max_ll;  // ordered encoding of the maximum log-likelihood
+  long long T_int;            // sum of the integer weights q_i (exact)
+  double T_f;                 // sum of exp(ll_i - max)
+  double T2_f;                // sum of exp(ll_i - max)^2
+  double est[5];              // sum of exp(ll_i - max) * state_i
+  unsigned long long delta_hi, delta_lo;  // T_int / N as 64.64 fixed point
+  unsigned long long u0_hi, u0_lo;        // u0 * T_int / N as 64.64 fixed point
+  long long anchor[5];        // fixed-point anchors of the non-position components
+  unsigned int tiles_done;    // finished tiles of the scan/resample kernel
+  unsigned int pad;
+};
+
+// Limits of the fixed-point centre-of-mass sums.  Position offsets from the
+// cell origin are < 9 * 2^32 (h <= 8) and other components are anchored at
+// particle 0's value with |v - anchor| < 2^14; with N <= 2^26 no sum exceeds
+// 2^62.
+constexpr int64_t MAX_PARTICLES = int64_t(1) << 26;
+constexpr double MAX_H = 8.0;
+constexpr long long VAL_SPREAD_LIMIT = 1ll << 36;   // 2^14 in units of 2^-22
+constexpr long long POS_OFFSET_LIMIT = 1ll << 36;   // 16 px in units of 2^-32
+
+// Tile of the scan / resampling kernel.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+struct StepBuffers {
+  // hash table over occupied cells (capacity hcap = 2^hbits >= 2 max_particles)
+  unsigned long long* hkey;
+  unsigned int* hcnt;
+  long long* hsum;          // [5][hcap]
+  unsigned int* hrank;      // hash slot -> bin index
+  long long* hq;            // hash slot -> integer weight q
+  double* hw;               // hash slot -> exp(ll - max)
+  int hbits;
+  // occupied bins, in discovery order (bin index)
+  unsigned int* occ;        // bin -> hash slot
+  int32_t* bin_xy;          // [2][max]
+  uint32_t* bin_cnt;
+  double* dummy;            // [5][max]
+  double* bin_ll;
+  // per particle
+  void* prop;               // [5][max] state dtype
+  unsigned int* pslot;      // particle -> hash slot
+  double* ll;               // SIR per-particle log-likelihood
+  int32_t* anc;
+  double* wout;
+  uint32_t* pbin;
+  int64_t bin_stride;       // row stride of bin_xy / dummy (= max particles)
+  // scan
+  unsigned long long* tile_status;
+  int64_t max_tiles;
+  Control* ctl;
+  pcsir_result* dres;
+  int prop_bin_per_sm;      // resident blocks per SM of the propagate/bin kernel
+};
+
+struct ModelParams {
+  int P;
+  int kind;
+  double sigma;
+  double bg;
+  double sigma_xi;
+};
+
+// Optional stage events: when ev != nullptr the launchers record ev[1..] after
+// their kernels (ev[0] is recorded by the caller before the first kernel).
+struct StageEvents {
+  cudaEvent_t* ev;  // 5 events of the current step, or nullptr
+};
+
+// Kernel launchers (pcsir_kernels.cu / pcsir_resample.cu).
+cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
+                               const void* noise, int64_t N, double h, const float* img, int W, int H,
+                               int num_sms, cudaStream_t s, StageEvents se);
+cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
+                             const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
+                             cudaStream_t s, StageEvents se);
+cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms,
+                              cudaStream_t s);
+cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm);
+// integer-weight scale: q = rint(exp(ll - max) * 2^sq) with N * 2^sq <= 2^61
+int weight_scale_bits(int64_t N);
+cudaError_t launch_resample(const StepBuffers& b, int dtype, void* state_out, int64_t N, double u0,
+                            int mode, int keep, int num_sms, cudaStream_t s);
+cudaError_t launch_resample_logw(const StepBuffers& b, const double* logw, int32_t* anc_out, int64_t N, double u0,
+                                 cudaStream_t s);
+cudaError_t launch_loglik(const ModelParams& m, const double* x, const double* y, const double* i0,
+                          int64_t n, const float* img, int W, int H, double* out, int num_sms,
+                          cudaStream_t s);
+
+// resampling weight sources
+enum { WSRC_BINS = 0, WSRC_PARTICLES = 1 };
+
+}  // namespace pcsir

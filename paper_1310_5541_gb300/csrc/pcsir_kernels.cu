@@ -1,0 +1,618 @@
+// Front half of a filter step: propagation, cells, dummies, likelihood and the
+// weight reductions (Algorithm 1 / Algorithm 2 up to the resampling step).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "pcsir_device.cuh"
+
+namespace pcsir {
+
+// ---------------------------------------------------------------------------
+// State-precision arithmetic with explicit rounding (no contraction), so the
+// propagated states and the cell indices are the IEEE results of the exact
+// operation sequence x + vx + e and floor((x + 0.5) / h).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float floor_t(float a) { return floorf(a); }
+__device__ __forceinline__ double floor_t(double a) { return floor(a); }
+template <typename T> struct Scales;
+template <> struct Scales<float> {
+  static constexpr float POS = 4294967296.0f;
+  static constexpr float VAL = 4194304.0f;
+};
+template <> struct Scales<double> {
+  static constexpr double POS = 4294967296.0;
+  static constexpr double VAL = 4194304.0;
+};
+
+// Nearly-constant-velocity transition of one particle (Section 5.1).
+template <typename T>
+__device__ __forceinline__ void propagate1(const T* __restrict__ st, const T* __restrict__ nz, int64_t N,
+                                           int64_t i, T v[5]) {
+  const T x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
+  const T ex = nz[i], ey = nz[N + i], evx = nz[2 * N + i], evy = nz[3 * N + i], ea = nz[4 * N + i];
+  v[0] = add_rn(add_rn(x, vx), ex);
+  v[1] = add_rn(add_rn(y, vy), ey);
+  v[2] = add_rn(vx, evx);
+  v[3] = add_rn(vy, evy);
+  v[4] = add_rn(a, ea);
+}
+
+__device__ __forceinline__ float abs_t(float a) { return fabsf(a); }
+__device__ __forceinline__ double abs_t(double a) { return fabs(a); }
+
+template <typename T>
+__device__ __forceinline__ bool finite_state(const T v[5]) {
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) ok &= (abs_t(v[c]) < T(1.0e9));  // false for NaN / Inf too
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Global hash table over occupied cells.  Linear probing; a slot is claimed
+// by CAS on its key and appended to the occupied list.  Capacity is at least
+// twice the particle count, so the probe loop always terminates.
+// ---------------------------------------------------------------------------
+__device__ unsigned global_find_or_insert(const StepBuffers& b, unsigned long long key) {
+  const unsigned mask = (1u << b.hbits) - 1u;
+  unsigned h = hash_bits(key, b.hbits);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const unsigned long long k = *(volatile unsigned long long*)&b.hkey[h];
+    if (k == key) return h;
+    if (k == EMPTY_KEY) {
+      const unsigned long long old = atomicCAS(&b.hkey[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY) {
+        const unsigned idx = atomicAdd(&b.ctl->nocc, 1u);
+        b.occ[idx] = h;
+        return h;
+      }
+      if (old == key) return h;
+    }
+    h = (h + 1u) & mask;
+  }
+  raise_flag(b.ctl, PCSIR_DERR_RANGE);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// propagate + cell + centre-of-mass sums (pcSIR front, Algorithm 2).
+// Each block keeps a private hash table of cells in shared memory holding
+// the member count and the fixed-point sums of the five state components, so
+// most updates are shared-memory atomics; the table is merged into the global
+// one (integer atomics, exact and order-independent) when it fills and at
+// the end.  Positions are summed as offsets from the cell origin in units of
+// 2^-32 px (exact for |x| >= 2^-9), the other components as offsets from
+// particle 0's input value in units of 2^-22.
+// ---------------------------------------------------------------------------
+constexpr int PB_THREADS = 256;
+constexpr int PB_ITEMS = 8;
+constexpr int PB_CHUNK = PB_THREADS * PB_ITEMS;
+constexpr int LT_BITS = 10;
+constexpr int LT = 1 << LT_BITS;
+constexpr unsigned LT_CAP = 640;
+
+struct LocalTable {
+  unsigned long long key[LT];
+  long long sum[5][LT];
+  unsigned int gslot[LT];
+  unsigned int cnt[LT];
+  unsigned int fill;
+};
+
+__device__ __forceinline__ int local_find_or_insert(LocalTable& t, unsigned long long key, bool& created) {
+  created = false;
+  unsigned h = hash_bits(key, LT_BITS);
+  for (int probe = 0; probe < LT; ++probe) {
+    const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
+    if (k == key) return (int)h;
+    if (k == EMPTY_KEY) {
+      if (atomicAdd(&t.fill, 1u) >= LT_CAP) return -1;
+      const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY) {
+        created = true;
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1u) & (LT - 1u);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void local_flush(LocalTable& t, const StepBuffers& b) {
+  const size_t hcap = size_t(1) << b.hbits;
+  for (int j = threadIdx.x; j < LT; j += blockDim.x) {
+    if (t.key[j] != EMPTY_KEY) {
+      const unsigned g = t.gslot[j];
+      atomicAdd(&b.hcnt[g], t.cnt[j]);
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)t.sum[c][j]);
+      t.key[j] = EMPTY_KEY;
+      t.cnt[j] = 0u;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) t.sum[c][j] = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) t.fill = 0u;
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PB_THREADS)
+k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LocalTable& tab = *reinterpret_cast<LocalTable*>(smem_raw);
+  T* __restrict__ prop = static_cast<T*>(b.prop);
+  const size_t hcap = size_t(1) << b.hbits;
+  for (int j = threadIdx.x; j < LT; j += blockDim.x) {
+    tab.key[j] = EMPTY_KEY;
+    tab.cnt[j] = 0u;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) tab.sum[c][j] = 0;
+  }
+  if (threadIdx.x == 0) tab.fill = 0u;
+  // anchors of vx, vy, I0: particle 0's input value in fixed point
+  long long anc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) anc[c] = to_fixed(st[(2 + c) * N], Scales<T>::VAL);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b.ctl->anchor[2 + c] = anc[c];
+  }
+  __syncthreads();
+  const T half = T(0.5);
+  const T lim = T(1073741823.0);  // 2^30 - 1
+  const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
+  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int64_t base = chunk * PB_CHUNK;
+    T v[PB_ITEMS][5];
+    unsigned long long key[PB_ITEMS];
+    int ls[PB_ITEMS];
+    int cbx[PB_ITEMS];
+    int cby[PB_ITEMS];
+#pragma unroll
+    for (int r = 0; r < PB_ITEMS; ++r) {
+      const int64_t i = base + r * PB_THREADS + threadIdx.x;
+      ls[r] = -2;
+      if (i < N) propagate1(st, nz, N, i, v[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < PB_ITEMS; ++r) {
+      const int64_t i = base + r * PB_THREADS + threadIdx.x;
+      if (i >= N) continue;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) prop[c * N + i] = v[r][c];
+      T fx = floor_t(div_rn(add_rn(v[r][0], half), h));
+      T fy = floor_t(div_rn(add_rn(v[r][1], half), h));
+      if (!(finite_state(v[r]) && abs_t(fx) < lim && abs_t(fy) < lim)) {
+        raise_flag(b.ctl, PCSIR_DERR_RANGE);
+        fx = T(0);
+        fy = T(0);
+        v[r][0] = T(0);
+        v[r][1] = T(0);
+      }
+      cbx[r] = (int)fx;
+      cby[r] = (int)fy;
+      key[r] = pack_key(cbx[r], cby[r]);
+      bool created;
+      ls[r] = local_find_or_insert(tab, key[r], created);
+      if (created) tab.gslot[ls[r]] = global_find_or_insert(b, key[r]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PB_ITEMS; ++r) {
+      if (ls[r] == -2) continue;
+      const int64_t i = base + r * PB_THREADS + threadIdx.x;
+      long long off[5];
+      off[0] = to_fixed(v[r][0], Scales<T>::POS) - (long long)cbx[r] * hq;
+      off[1] = to_fixed(v[r][1], Scales<T>::POS) - (long long)cby[r] * hq;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) off[2 + c] = to_fixed(v[r][2 + c], Scales<T>::VAL) - anc[c];
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) bad |= (off[c] >= POS_OFFSET_LIMIT || off[c] <= -POS_OFFSET_LIMIT);
+#pragma unroll
+      for (int c = 2; c < 5; ++c) bad |= (off[c] >= VAL_SPREAD_LIMIT || off[c] <= -VAL_SPREAD_LIMIT);
+      if (bad) {
+        raise_flag(b.ctl, PCSIR_DERR_RANGE);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) off[c] = 0;
+      }
+      unsigned g;
+      if (ls[r] >= 0) {
+        const int s = ls[r];
+        g = tab.gslot[s];
+        atomicAdd(&tab.cnt[s], 1u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) atomicAdd((unsigned long long*)&tab.sum[c][s], (unsigned long long)off[c]);
+      } else {
+        g = global_find_or_insert(b, key[r]);
+        atomicAdd(&b.hcnt[g], 1u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)off[c]);
+      }
+      b.pslot[i] = g;
+    }
+    __syncthreads();
+    if (tab.fill >= LT_CAP) local_flush(tab, b);
+  }
+  local_flush(tab, b);
+}
+
+// ---------------------------------------------------------------------------
+// Dummies and their likelihood (Algorithm 2: mean state of each bin, weight
+// update of the dummy only).  One warp per occupied bin.
+// ---------------------------------------------------------------------------
+constexpr int BIN_THREADS = 256;
+constexpr int MAXP = 63;
+
+__device__ __forceinline__ void block_max_to_global(double v, Control* ctl) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = -INFINITY;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) m = fmax(m, red[j]);
+    if (m > -INFINITY) atomicMax(&ctl->max_ll, ord_encode(m));
+  }
+}
+
+__global__ void __launch_bounds__(BIN_THREADS)
+k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq) {
+  __shared__ float scratch[BIN_THREADS / 32][4 * MAXP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned B = b.ctl->nocc;
+  const size_t hcap = size_t(1) << b.hbits;
+  const int64_t bs = b.bin_stride;
+  double mymax = -INFINITY;
+  for (unsigned bi = blockIdx.x * (BIN_THREADS / 32) + w; bi < B; bi += gridDim.x * (BIN_THREADS / 32)) {
+    const unsigned g = b.occ[bi];
+    const unsigned long long key = b.hkey[g];
+    const int bx = key_bx(key), by = key_by(key);
+    const unsigned n = b.hcnt[g];
+    const double dn = (double)n;
+    double mean[5];
+    mean[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] / dn) * POS_INV;
+    mean[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
+#pragma unroll
+    for (int c = 2; c < 5; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    if (lane == 0) {
+      b.bin_xy[bi] = bx;
+      b.bin_xy[bs + bi] = by;
+      b.bin_cnt[bi] = n;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = mean[c];
+      b.hrank[g] = bi;
+    }
+    double ll = warp_loglik(img, W, H, mean[0], mean[1], mean[4], lp, scratch[w]);
+    if (!isfinite(ll)) {
+      if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      ll = -INFINITY;
+    }
+    if (lane == 0) b.bin_ll[bi] = ll;
+    mymax = fmax(mymax, ll);
+  }
+  block_max_to_global(mymax, b.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Weight reductions.  w~ = exp(ll - max) per bin (pcSIR) or per particle
+// (SIR); integer weights q = rint(w~ 2^sq) for the exact scan; sums for the
+// normaliser, the ESS and the posterior mean.  The last block to finish
+// writes the step's scalar results.
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+
+struct RedAcc {
+  double Tf, T2, est[5];
+  long long Tint;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, int kind, bool with_est) {
+  __shared__ double sd[7][RED_THREADS / 32];
+  __shared__ long long sl[RED_THREADS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double vals[7] = {a.Tf, a.T2, a.est[0], a.est[1], a.est[2], a.est[3], a.est[4]};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) vals[k] = warp_sum_d(vals[k]);
+  const long long ti = warp_sum_ll(a.Tint);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sd[k][w] = vals[k];
+    sl[w] = ti;
+  }
+  __syncthreads();
+  Control* ctl = b.ctl;
+  if (threadIdx.x == 0) {
+    double t[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long tt = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) t[k] += sd[k][j];
+      tt += sl[j];
+    }
+    atomicAdd(&ctl->T_f, t[0]);
+    atomicAdd(&ctl->T2_f, t[1]);
+    if (with_est) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) atomicAdd(&ctl->est[c], t[2 + c]);
+    }
+    atomicAdd((unsigned long long*)&ctl->T_int, (unsigned long long)tt);
+    __threadfence();
+    last = (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    volatile Control* vc = ctl;
+    const double Tf = vc->T_f, T2 = vc->T2_f;
+    pcsir_result* r = b.dres;
+    for (int c = 0; c < 5; ++c) r->estimate[c] = with_est ? vc->est[c] / Tf : 0.0;
+    r->ess = Tf * Tf / T2;
+    r->max_loglik = ord_decode(vc->max_ll);
+    r->sum_wtilde = Tf;
+    r->n_particles = N;
+    r->n_bins = kind == 1 ? (int64_t)vc->nocc : 0;
+    r->kind = kind;
+    if (vc->T_int <= 0) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N, int sq) {
+  const unsigned B = b.ctl->nocc;
+  const double m = ord_decode(b.ctl->max_ll);
+  const int64_t bs = b.bin_stride;
+  RedAcc a = {0.0, 0.0, {0.0, 0.0, 0.0, 0.0, 0.0}, 0};
+  const unsigned gstride = gridDim.x * blockDim.x;
+  for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < B; bi += gstride) {
+    const unsigned g = b.occ[bi];
+    const double n = (double)b.bin_cnt[bi];
+    const double ll = b.bin_ll[bi];
+    const double wt = (ll == -INFINITY) ? 0.0 : exp(ll - m);
+    const long long q = __double2ll_rn(ldexp(wt, sq));
+    b.hq[g] = q;
+    b.hw[g] = wt;
+    a.Tf += n * wt;
+    a.T2 += n * wt * wt;
+    a.Tint += (long long)b.bin_cnt[bi] * q;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.est[c] += n * wt * b.dummy[c * bs + bi];
+  }
+  // the scan kernel's look-back status words start from zero every step
+  for (int64_t t = blockIdx.x * blockDim.x + threadIdx.x; t < b.max_tiles; t += gstride) b.tile_status[t] = 0ull;
+  block_reduce_commit(a, b, N, 1, true);
+}
+
+// ---------------------------------------------------------------------------
+// SIR: propagate and evaluate the likelihood of every particle.
+// ---------------------------------------------------------------------------
+constexpr int SL_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(SL_THREADS)
+k_sir_prop_lik(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, LikParams lp,
+               const float* __restrict__ img, int W, int H) {
+  __shared__ double sx[SL_THREADS], sy[SL_THREADS], si[SL_THREADS];
+  __shared__ float scratch[SL_THREADS / 32][4 * MAXP];
+  T* __restrict__ prop = static_cast<T*>(b.prop);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * SL_THREADS;
+  const int64_t i = base + threadIdx.x;
+  if (i < N) {
+    T v[5];
+    propagate1(st, nz, N, i, v);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) prop[c * N + i] = v[c];
+    if (!finite_state(v)) {
+      raise_flag(b.ctl, PCSIR_DERR_RANGE);
+      v[0] = v[1] = v[4] = T(0);
+    }
+    sx[threadIdx.x] = (double)v[0];
+    sy[threadIdx.x] = (double)v[1];
+    si[threadIdx.x] = (double)v[4];
+  }
+  __syncthreads();
+  const int cnt = (int)((N - base) < SL_THREADS ? (N - base) : SL_THREADS);
+  double mymax = -INFINITY;
+  for (int j = w; j < cnt; j += SL_THREADS / 32) {
+    double ll = warp_loglik(img, W, H, sx[j], sy[j], si[j], lp, scratch[w]);
+    if (!isfinite(ll)) {
+      if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      ll = -INFINITY;
+    }
+    if (lane == 0) b.ll[base + j] = ll;
+    mymax = fmax(mymax, ll);
+  }
+  block_max_to_global(mymax, b.ctl);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const double* __restrict__ lls, int64_t N,
+                                                       int sq, int with_est) {
+  const double m = ord_decode(b.ctl->max_ll);
+  const T* __restrict__ prop = static_cast<const T*>(b.prop);
+  kahan kt, k2, ke[5];
+  long long tint = 0;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
+    const df wd = wtilde_df(lls[i], m);
+    const float wt = wd.hi;
+    tint += q_of_wtilde(wd, sq);
+    kt.add(wt);
+    k2.add(wt * wt);
+    if (with_est) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) ke[c].add(wt * (float)prop[c * N + i]);
+    }
+  }
+  RedAcc a;
+  a.Tf = (double)kt.s - (double)kt.c;
+  a.T2 = (double)k2.s - (double)k2.c;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) a.est[c] = (double)ke[c].s - (double)ke[c].c;
+  a.Tint = tint;
+  if (blockIdx.x == 0) {
+    for (int64_t t = threadIdx.x; t < b.max_tiles; t += blockDim.x) b.tile_status[t] = 0ull;
+  }
+  block_reduce_commit(a, b, N, 0, with_est != 0);
+}
+
+// max of caller-given log-weights (standalone resampling)
+__global__ void __launch_bounds__(RED_THREADS) k_logw_max(StepBuffers b, const double* __restrict__ lw, int64_t N) {
+  double m = -INFINITY;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
+    const double v = lw[i];
+    if (isfinite(v)) m = fmax(m, v);
+  }
+  block_max_to_global(m, b.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Standalone likelihood of given positions: one warp per position.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BIN_THREADS)
+k_loglik(LikParams lp, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ a,
+         int64_t n, const float* __restrict__ img, int W, int H, double* __restrict__ out) {
+  __shared__ float scratch[BIN_THREADS / 32][4 * MAXP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t j = (int64_t)blockIdx.x * (BIN_THREADS / 32) + w; j < n; j += (int64_t)gridDim.x * (BIN_THREADS / 32)) {
+    const double ll = warp_loglik(img, W, H, x[j], y[j], a[j], lp, scratch[w]);
+    if (lane == 0) out[j] = ll;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static LikParams make_lik(const ModelParams& m) {
+  LikParams lp;
+  lp.P = m.P;
+  lp.kind = m.kind;
+  lp.bg = (float)m.bg;
+  const double c2 = 1.0 / (2.0 * m.sigma * m.sigma);
+  lp.c2.hi = (float)c2;
+  lp.c2.lo = (float)(c2 - (double)lp.c2.hi);
+  lp.inv2sxi2 = (float)(1.0 / (2.0 * m.sigma_xi * m.sigma_xi));
+  return lp;
+}
+
+int weight_scale_bits(int64_t N) {
+  int lg = 0;
+  while ((int64_t(1) << lg) < N) ++lg;
+  return 61 - lg;
+}
+
+// One-time kernel attributes and occupancy, queried at context creation so
+// that step calls only enqueue work (and stay legal inside a stream capture).
+template <typename T>
+static cudaError_t prop_bin_prepare(int* per_sm) {
+  const size_t smem = sizeof(LocalTable);
+  cudaError_t e = cudaFuncSetAttribute(k_prop_bin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T>, PB_THREADS, smem);
+  if (*per_sm < 1) *per_sm = 1;
+  return e;
+}
+
+cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
+  return dtype == PCSIR_F32 ? prop_bin_prepare<float>(prop_bin_per_sm) : prop_bin_prepare<double>(prop_bin_per_sm);
+}
+
+template <typename T>
+static cudaError_t prop_bin_launch(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
+                                   int num_sms, cudaStream_t s, long long hq) {
+  const size_t smem = sizeof(LocalTable);
+  const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
+  const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * b.prop_bin_per_sm);
+  k_prop_bin<T><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state), static_cast<const T*>(noise), N,
+                                               (T)h, hq);
+  return cudaGetLastError();
+}
+
+static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
+  return se.ev ? cudaEventRecord(se.ev[j], s) : cudaSuccess;
+}
+
+cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
+                               const void* noise, int64_t N, double h, const float* img, int W, int H,
+                               int num_sms, cudaStream_t s, StageEvents se) {
+  const long long hq = llrint(h * 4294967296.0);
+  cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
+                                     : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
+  if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
+  const LikParams lp = make_lik(m);
+  k_bins<<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
+  k_binred<<<num_sms * 2, RED_THREADS, 0, s>>>(b, N, weight_scale_bits(N));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return mark(se, 3, s);
+}
+
+cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
+                             const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
+                             cudaStream_t s, StageEvents se) {
+  const LikParams lp = make_lik(m);
+  const int64_t nb = (N + SL_THREADS - 1) / SL_THREADS;
+  const int sq = weight_scale_bits(N);
+  const int rgrid = (int)std::min<int64_t>((N + RED_THREADS - 1) / RED_THREADS, (int64_t)num_sms * 4);
+  if (dtype == PCSIR_F32) {
+    k_sir_prop_lik<float><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const float*>(state),
+                                                             static_cast<const float*>(noise), N, lp, img, W, H);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
+    k_sir_w<float><<<rgrid, RED_THREADS, 0, s>>>(b, b.ll, N, sq, 1);
+  } else {
+    k_sir_prop_lik<double><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const double*>(state),
+                                                              static_cast<const double*>(noise), N, lp, img, W, H);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
+    k_sir_w<double><<<rgrid, RED_THREADS, 0, s>>>(b, b.ll, N, sq, 1);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
+  return mark(se, 3, s);
+}
+
+cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms, cudaStream_t s) {
+  const int rgrid = (int)std::min<int64_t>((N + RED_THREADS - 1) / RED_THREADS, (int64_t)num_sms * 4);
+  k_logw_max<<<rgrid, RED_THREADS, 0, s>>>(b, logw, N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sir_w<float><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loglik(const ModelParams& m, const double* x, const double* y, const double* i0, int64_t n,
+                          const float* img, int W, int H, double* out, int num_sms, cudaStream_t s) {
+  const LikParams lp = make_lik(m);
+  const int64_t want = (n + (BIN_THREADS / 32) - 1) / (BIN_THREADS / 32);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
+  k_loglik<<<grid, BIN_THREADS, 0, s>>>(lp, x, y, i0, n, img, W, H, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pcsir

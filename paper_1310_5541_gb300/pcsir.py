@@ -1,0 +1,247 @@
+"""Thin ctypes binding of ``libpcsir.so`` (see ``include/pcsir.h``).
+
+Only argument marshalling happens here: every step of the filter runs in the
+library's CUDA kernels.  Tensors are torch CUDA tensors (torch provides device
+memory and streams); the current torch stream is used unless one is given.
+Importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcsir.so")
+
+# enums of pcsir.h
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, ENOTSUP, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+LIK_POISSON, LIK_SSE = 0, 1
+KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN = 1, 2, 4
+DERR_RANGE, DERR_TIMEOUT, DERR_NONFINITE, DERR_ZEROSUM = 1, 2, 4, 8
+
+_STATUS_NAMES = {0: "PCSIR_OK", -1: "PCSIR_EINVAL", -2: "PCSIR_ENOMEM", -3: "PCSIR_ECUDA",
+                 -4: "PCSIR_ETIMEDOUT", -5: "PCSIR_ESTATE", -6: "PCSIR_ENOTSUP", -7: "PCSIR_ERANGE"}
+
+
+class pcsir_config(ctypes.Structure):
+    _fields_ = [("state_dtype", ctypes.c_int32), ("lik_kind", ctypes.c_int32), ("patch", ctypes.c_int32),
+                ("keep", ctypes.c_int32), ("psf_sigma", ctypes.c_double), ("bg", ctypes.c_double),
+                ("sigma_xi", ctypes.c_double), ("max_particles", ctypes.c_int64)]
+
+
+class pcsir_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double * 5), ("ess", ctypes.c_double), ("max_loglik", ctypes.c_double),
+                ("sum_wtilde", ctypes.c_double), ("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64),
+                ("device_error", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+
+class pcsir_outputs(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("bin_stride", ctypes.c_int64),
+                ("prop_state", ctypes.c_void_p), ("bin_xy", ctypes.c_void_p), ("bin_count", ctypes.c_void_p),
+                ("dummy", ctypes.c_void_p), ("bin_loglik", ctypes.c_void_p), ("loglik", ctypes.c_void_p),
+                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+
+
+class PcsirError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpcsir.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "pcsir_create": ([ctypes.POINTER(pcsir_config), ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir_destroy": ([P], I32),
+        "pcsir_step": ([P, P, I64, P, I32, I32, D, P, D, P, P], I32),
+        "sir_step": ([P, P, I64, P, I32, I32, P, D, P, P], I32),
+        "pcsir_loglik": ([P, P, P, P, I64, P, I32, I32, P, P], I32),
+        "pcsir_resample": ([P, P, I64, D, P, P], I32),
+        "pcsir_get_outputs": ([P, ctypes.POINTER(pcsir_outputs)], I32),
+        "pcsir_last_result": ([P, ctypes.POINTER(pcsir_result)], I32),
+        "pcsir_last_error": ([P], ctypes.c_char_p),
+        "pcsir_version": ([], ctypes.c_char_p),
+        "pcsir_timing_enable": ([P, I32], I32),
+        "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_cuda(t, name, dtype=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+
+
+class Context:
+    """Owns one ``pcsir_ctx`` (workspace for up to ``max_particles`` particles)."""
+
+    def __init__(self, max_particles, state_dtype=torch.float32, lik="poisson", patch=9, psf_sigma=1.5,
+                 bg=10.0, sigma_xi=20.0, keep=0):
+        self.torch_dtype = state_dtype
+        cfg = pcsir_config(state_dtype=F32 if state_dtype == torch.float32 else F64,
+                           lik_kind=LIK_POISSON if lik == "poisson" else LIK_SSE, patch=int(patch), keep=int(keep),
+                           psf_sigma=float(psf_sigma), bg=float(bg), sigma_xi=float(sigma_xi),
+                           max_particles=int(max_particles))
+        h = ctypes.c_void_p()
+        st = lib.pcsir_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise PcsirError(st, "pcsir_create failed")
+        self.handle = h
+        self.cfg = cfg
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pcsir_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        raise PcsirError(st, lib.pcsir_last_error(self.handle).decode())
+
+    def last_result(self):
+        """The last step's pcsir_result as a dict (synchronise the step's stream first)."""
+        r = pcsir_result()
+        lib.pcsir_last_result(self.handle, ctypes.byref(r))
+        return dict(estimate=list(r.estimate), ess=r.ess, max_loglik=r.max_loglik, sum_wtilde=r.sum_wtilde,
+                    n_particles=r.n_particles, n_bins=r.n_bins, device_error=r.device_error, kind=r.kind)
+
+    def timing_enable(self, max_steps):
+        st = lib.pcsir_timing_enable(self.handle, int(max_steps))
+        if st != OK:
+            self._raise(st)
+
+    def timing_read(self, max_steps):
+        """Per-step stage durations in ms, shape [n_steps, 4] (waits for the recorded steps)."""
+        buf = (ctypes.c_float * (4 * max_steps))()
+        n = ctypes.c_int32()
+        st = lib.pcsir_timing_read(self.handle, buf, 4 * max_steps, ctypes.byref(n))
+        if st != OK:
+            self._raise(st)
+        return [list(buf[4 * k:4 * k + 4]) for k in range(n.value)]
+
+    def outputs(self):
+        """Intermediates of the last step as torch tensors (views, valid until the next step)."""
+        o = pcsir_outputs()
+        st = lib.pcsir_get_outputs(self.handle, ctypes.byref(o))
+        if st != OK:
+            self._raise(st)
+        N, B, S = o.n_particles, o.n_bins, o.bin_stride
+        sd = self.torch_dtype
+
+        def view(ptr, shape, dtype):
+            if not ptr:
+                return None
+            return _from_ptr(ptr, shape, dtype)
+
+        out = dict(n_particles=N, n_bins=B,
+                   prop_state=view(o.prop_state, (5, N), sd),
+                   ancestor=view(o.ancestor, (N,), torch.int32),
+                   weight=view(o.weight, (N,), torch.float64))
+        if B > 0:
+            out.update(bin_xy=view(o.bin_xy, (2, S), torch.int32)[:, :B],
+                       bin_count=view(o.bin_count, (B,), torch.int32),
+                       dummy=view(o.dummy, (5, S), torch.float64)[:, :B],
+                       bin_loglik=view(o.bin_loglik, (B,), torch.float64),
+                       particle_bin=view(o.particle_bin, (N,), torch.int32))
+        if o.loglik:
+            out["loglik"] = view(o.loglik, (N,), torch.float64)
+        return out
+
+
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 2, "strides": None}
+
+
+_TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4"}
+
+
+def _from_ptr(ptr, shape, dtype):
+    return torch.as_tensor(_CudaArray(ptr, shape, _TYPESTR[dtype]), device="cuda")
+
+
+def pcsir_step(ctx, state, image, h, noise, u0, stream=None):
+    """One pcSIR step (Algorithm 2) on ``state`` [5, N] in place."""
+    _check_cuda(state, "state", ctx.torch_dtype)
+    _check_cuda(noise, "noise", ctx.torch_dtype)
+    _check_cuda(image, "image", torch.float32)
+    N = state.shape[1]
+    H, W = image.shape
+    st = lib.pcsir_step(ctx.handle, _ptr(state), N, _ptr(image), W, H, float(h), _ptr(noise), float(u0),
+                        _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def sir_step(ctx, state, image, noise, u0, stream=None):
+    """One SIR step (Algorithm 1) on ``state`` [5, N] in place."""
+    _check_cuda(state, "state", ctx.torch_dtype)
+    _check_cuda(noise, "noise", ctx.torch_dtype)
+    _check_cuda(image, "image", torch.float32)
+    N = state.shape[1]
+    H, W = image.shape
+    st = lib.sir_step(ctx.handle, _ptr(state), N, _ptr(image), W, H, _ptr(noise), float(u0),
+                      _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def pcsir_loglik(ctx, x, y, i0, image, out=None, stream=None):
+    """Log-likelihood of positions (float64 CUDA tensors) against ``image``."""
+    for t, n in ((x, "x"), (y, "y"), (i0, "I0")):
+        _check_cuda(t, n, torch.float64)
+    _check_cuda(image, "image", torch.float32)
+    if out is None:
+        out = torch.empty_like(x)
+    H, W = image.shape
+    st = lib.pcsir_loglik(ctx.handle, _ptr(x), _ptr(y), _ptr(i0), x.numel(), _ptr(image), W, H, _ptr(out),
+                          _stream_ptr(stream))
+    if st != OK:
+        ctx._raise(st)
+    return out
+
+
+def pcsir_resample(ctx, logw, u0, out=None, stream=None):
+    """Systematic-resampling ancestors (int32) of ``logw`` (float64 CUDA tensor)."""
+    _check_cuda(logw, "logw", torch.float64)
+    if out is None:
+        out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
+    st = lib.pcsir_resample(ctx.handle, _ptr(logw), logw.numel(), float(u0), _ptr(out), _stream_ptr(stream))
+    if st != OK:
+        ctx._raise(st)
+    return out
+
+
+def version():
+    return lib.pcsir_version().decode()

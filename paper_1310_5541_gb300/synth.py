@@ -61,7 +61,7 @@ class Sequence:
 
 
 def make_sequence(W: int, H: int, n_frames: int, model: Model, seed: int,
-                  start=None, vmax=None) -> Sequence:
+                  start=None, vmax=None, margin=None) -> Sequence:
     """Ground-truth track and its noisy image sequence.
 
     The track starts at ``start`` (default: image centre) with a speed drawn
@@ -72,7 +72,8 @@ def make_sequence(W: int, H: int, n_frames: int, model: Model, seed: int,
     keeps a straight track inside the image margin for the whole sequence.
     """
     rng = np.random.default_rng([seed, 0x5EED])
-    margin = model.patch
+    if margin is None:
+        margin = model.patch
     if start is None:
         start = ((W - 1) / 2.0, (H - 1) / 2.0)
     if vmax is None:

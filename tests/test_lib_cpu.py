@@ -1,0 +1,80 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point include/pcsir.h declares, its structs have the header's
+layout, and argument errors are rejected on the host."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcsir.h")
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1310_5541_gb300 import pcsir
+
+    return pcsir
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_entry_point(binding):
+    names = _declared_functions()
+    assert "pcsir_step" in names and "sir_step" in names and len(names) >= 10
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layout_matches_header(binding, tmp_path):
+    prog = tmp_path / "layout.c"
+    fields = {
+        "pcsir_config": [f[0] for f in binding.pcsir_config._fields_],
+        "pcsir_result": [f[0] for f in binding.pcsir_result._fields_],
+        "pcsir_outputs": [f[0] for f in binding.pcsir_outputs._fields_],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', "int main(void){"]
+    for s, fs in fields.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f in fs:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for s, fs in fields.items():
+        cls = getattr(binding, s)
+        assert int(out[s]) == ctypes.sizeof(cls), s
+        for f in fs:
+            assert int(out["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
+
+
+def test_invalid_configs_rejected_on_host(binding):
+    lib = binding.lib
+    base = dict(state_dtype=0, lik_kind=0, patch=9, keep=0, psf_sigma=1.5, bg=10.0, sigma_xi=20.0,
+                max_particles=1000)
+    bad = [dict(patch=8), dict(patch=0), dict(patch=65), dict(state_dtype=2), dict(lik_kind=5),
+           dict(psf_sigma=0.0), dict(bg=0.0), dict(max_particles=0), dict(max_particles=(1 << 26) + 1),
+           dict(keep=64), dict(lik_kind=1, sigma_xi=0.0)]
+    for upd in bad:
+        cfg = binding.pcsir_config(**{**base, **upd})
+        h = ctypes.c_void_p(123)
+        assert lib.pcsir_create(ctypes.byref(cfg), ctypes.byref(h)) == binding.EINVAL, upd
+        assert not h.value
+    assert lib.pcsir_create(None, None) == binding.EINVAL
+    assert lib.pcsir_step(None, None, 1, None, 1, 1, 0.5, None, 0.5, None, None) == binding.EINVAL
+    assert lib.sir_step(None, None, 1, None, 1, 1, None, 0.5, None, None) == binding.EINVAL
+    assert lib.pcsir_destroy(None) == binding.OK
+    assert b"pcsir" in lib.pcsir_version()
