@@ -234,7 +234,7 @@ def main():
     state = state0.clone()
     ctx = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG, keep=0)
     stream = torch.cuda.current_stream()
-    res_host = torch.zeros((n_frames, 12), dtype=torch.float64).pin_memory()  # 96-byte pcsir_result each
+    res_host = torch.zeros((n_frames, 11), dtype=torch.float64).pin_memory()  # 88-byte pcsir_result each
 
     def step(k, st):
         r = pcsir.lib.pcsir_step(ctx.handle, pcsir._ptr(st), N, pcsir._ptr(images[k]), W_IMG, H_IMG, float(h),
@@ -310,7 +310,7 @@ def main():
         pcsir.lib.pcsir_last_result(ctx.handle, pcsir.ctypes.byref(res1))
     e2e_s = time.perf_counter() - t0
     e2e = {"value": N * K_e2e * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": 96}
+           "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": 88}
 
     # plain SIR on the same workload (the comparison path; likelihood for every particle)
     sir = None

@@ -269,8 +269,8 @@ __device__ __forceinline__ unsigned hash_bits(unsigned long long k, int bits) {
 }
 
 // Fixed-point scales of the centre-of-mass sums (see pcsir_internal.h).
-constexpr double POS_SCALE = 4294967296.0;      // 2^32
-constexpr double POS_INV = 1.0 / 4294967296.0;
+constexpr double POS_SCALE = 2147483648.0;      // 2^31
+constexpr double POS_INV = 1.0 / 2147483648.0;
 constexpr double VAL_SCALE = 4194304.0;         // 2^22
 constexpr double VAL_INV = 1.0 / 4194304.0;
 

@@ -27,13 +27,11 @@ struct Control {
 };
 
 // Limits of the fixed-point centre-of-mass sums.  Position offsets from the
-// cell origin are < 9 * 2^32 (h <= 8) and other components are anchored at
-// particle 0's value with |v - anchor| < 2^14; with N <= 2^26 no sum exceeds
+// cell origin are < 8.5 * 2^31 (h <= 8) and other components are anchored at
+// particle 0's value with |v - anchor| < 2^12; with N <= 2^26 no sum exceeds
 // 2^62.
 constexpr int64_t MAX_PARTICLES = int64_t(1) << 26;
 constexpr double MAX_H = 8.0;
-constexpr long long VAL_SPREAD_LIMIT = 1ll << 36;   // 2^14 in units of 2^-22
-constexpr long long POS_OFFSET_LIMIT = 1ll << 36;   // 16 px in units of 2^-32
 
 // Tile of the scan / resampling kernel.
 constexpr int SCAN_THREADS = 256;

@@ -1,6 +1,7 @@
 // Front half of a filter step: propagation, cells, dummies, likelihood and the
 // weight reductions (Algorithm 1 / Algorithm 2 up to the resampling step).
 #include <algorithm>
+#include <type_traits>
 #include <cfloat>
 #include <cmath>
 
@@ -21,11 +22,11 @@ __device__ __forceinline__ float floor_t(float a) { return floorf(a); }
 __device__ __forceinline__ double floor_t(double a) { return floor(a); }
 template <typename T> struct Scales;
 template <> struct Scales<float> {
-  static constexpr float POS = 4294967296.0f;
-  static constexpr float VAL = 4194304.0f;
+  static constexpr float POS = 2147483648.0f;  // 2^31
+  static constexpr float VAL = 4194304.0f;     // 2^22
 };
 template <> struct Scales<double> {
-  static constexpr double POS = 4294967296.0;
+  static constexpr double POS = 2147483648.0;
   static constexpr double VAL = 4194304.0;
 };
 
@@ -81,26 +82,40 @@ __device__ unsigned global_find_or_insert(const StepBuffers& b, unsigned long lo
 
 // ---------------------------------------------------------------------------
 // propagate + cell + centre-of-mass sums (pcSIR front, Algorithm 2).
-// Each block keeps a private hash table of cells in shared memory holding
-// the member count and the fixed-point sums of the five state components, so
-// most updates are shared-memory atomics; the table is merged into the global
-// one (integer atomics, exact and order-independent) when it fills and at
-// the end.  Positions are summed as offsets from the cell origin in units of
-// 2^-32 px (exact for |x| >= 2^-9), the other components as offsets from
-// particle 0's input value in units of 2^-22.
+//
+// Each block keeps a private hash table of cells in shared memory.  For
+// every cell it accumulates the member count and exact fixed-point sums of
+// the five state components; the global table receives the block's partial
+// sums with 64-bit integer atomics (exact and order-independent).
+//   positions: offset from the cell origin in units of 2^-31 px (exact for
+//              |x| >= 2^-8), biased by 2^33;
+//   vx, vy, I0: offset from particle 0's input value in units of 2^-22,
+//              biased by 2^34 (spread limit 2^12).
+// A biased value is below 2^36 and is added as two 18-bit pieces to 32-bit
+// shared-memory counters (64-bit shared atomics are an order of magnitude
+// slower on this GPU); the counters are flushed to the global table at
+// least every 2^14 particles, so no 32-bit counter can overflow.
 // ---------------------------------------------------------------------------
-constexpr int PB_THREADS = 256;
-constexpr int PB_ITEMS = 8;
-constexpr int PB_CHUNK = PB_THREADS * PB_ITEMS;
+constexpr int PB_THREADS = 512;
+constexpr int PB_PER_THREAD = 4;
+constexpr int PB_CHUNK = PB_THREADS * PB_PER_THREAD;
 constexpr int LT_BITS = 10;
 constexpr int LT = 1 << LT_BITS;
-constexpr unsigned LT_CAP = 640;
+constexpr unsigned LT_CAP = 768;
+constexpr int PIECE_BITS = 18;
+constexpr unsigned PIECE_MASK = (1u << PIECE_BITS) - 1u;
+constexpr int FLUSH_PARTICLES = 1 << 14;
+constexpr long long POS_BIAS = 1ll << 33;
+constexpr long long VAL_BIAS = 1ll << 34;
+constexpr long long BIASED_LIMIT = 1ll << 36;
+constexpr int NACC = 11;  // count, then (lo, hi) of x, y, vx, vy, I0
 
 struct LocalTable {
   unsigned long long key[LT];
-  long long sum[5][LT];
+  unsigned int acc[NACC][LT];
   unsigned int gslot[LT];
-  unsigned int cnt[LT];
+  unsigned short list[LT];
+  unsigned int nlist;
   unsigned int fill;
 };
 
@@ -115,6 +130,7 @@ __device__ __forceinline__ int local_find_or_insert(LocalTable& t, unsigned long
       const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
       if (old == EMPTY_KEY) {
         created = true;
+        t.list[atomicAdd(&t.nlist, 1u)] = (unsigned short)h;
         return (int)h;
       }
       if (old == key) return (int)h;
@@ -124,28 +140,46 @@ __device__ __forceinline__ int local_find_or_insert(LocalTable& t, unsigned long
   return -1;
 }
 
-__device__ __forceinline__ void local_flush(LocalTable& t, const StepBuffers& b) {
+// Merge the block's counters into the global table and zero them; with
+// clear_keys the cells themselves are dropped as well (table full).
+__device__ __forceinline__ void local_flush(LocalTable& t, const StepBuffers& b, bool clear_keys) {
   const size_t hcap = size_t(1) << b.hbits;
-  for (int j = threadIdx.x; j < LT; j += blockDim.x) {
-    if (t.key[j] != EMPTY_KEY) {
+  const unsigned n = t.nlist;
+  for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
+    const unsigned j = t.list[e];
+    const unsigned cnt = t.acc[0][j];
+    if (cnt != 0u) {
       const unsigned g = t.gslot[j];
-      atomicAdd(&b.hcnt[g], t.cnt[j]);
+      atomicAdd(&b.hcnt[g], cnt);
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)t.sum[c][j]);
-      t.key[j] = EMPTY_KEY;
-      t.cnt[j] = 0u;
+      for (int c = 0; c < 5; ++c) {
+        const long long bias = c < 2 ? POS_BIAS : VAL_BIAS;
+        const long long sum = (long long)t.acc[1 + 2 * c][j] + ((long long)t.acc[2 + 2 * c][j] << PIECE_BITS) -
+                              (long long)cnt * bias;
+        atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)sum);
+      }
 #pragma unroll
-      for (int c = 0; c < 5; ++c) t.sum[c][j] = 0;
+      for (int a = 0; a < NACC; ++a) t.acc[a][j] = 0u;
     }
+    if (clear_keys) t.key[j] = EMPTY_KEY;
   }
   __syncthreads();
-  if (threadIdx.x == 0) t.fill = 0u;
+  if (clear_keys && threadIdx.x == 0) {
+    t.nlist = 0u;
+    t.fill = 0u;
+  }
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PB_THREADS)
+// i-th particle (0..3) of this thread in the chunk: four consecutive indices
+// when the rows allow 16-byte vector access, otherwise strided by the block.
+template <bool VEC>
+__device__ __forceinline__ int64_t pb_index(int64_t base, int k) {
+  return VEC ? base + 4 * threadIdx.x + k : base + (int64_t)k * PB_THREADS + threadIdx.x;
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(PB_THREADS, 2)
 k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LocalTable& tab = *reinterpret_cast<LocalTable*>(smem_raw);
@@ -153,11 +187,13 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
   const size_t hcap = size_t(1) << b.hbits;
   for (int j = threadIdx.x; j < LT; j += blockDim.x) {
     tab.key[j] = EMPTY_KEY;
-    tab.cnt[j] = 0u;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) tab.sum[c][j] = 0;
+    for (int a = 0; a < NACC; ++a) tab.acc[a][j] = 0u;
   }
-  if (threadIdx.x == 0) tab.fill = 0u;
+  if (threadIdx.x == 0) {
+    tab.nlist = 0u;
+    tab.fill = 0u;
+  }
   // anchors of vx, vy, I0: particle 0's input value in fixed point
   long long anc[3];
 #pragma unroll
@@ -170,81 +206,123 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
   const T half = T(0.5);
   const T lim = T(1073741823.0);  // 2^30 - 1
   const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
+  int since_flush = 0;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t base = chunk * PB_CHUNK;
-    T v[PB_ITEMS][5];
-    unsigned long long key[PB_ITEMS];
-    int ls[PB_ITEMS];
-    int cbx[PB_ITEMS];
-    int cby[PB_ITEMS];
+    T v[PB_PER_THREAD][5];
+    if (VEC && base + PB_CHUNK <= N) {
+      // 16-byte loads and stores of four consecutive particles per component
+      const int64_t i0 = base + 4 * threadIdx.x;
+      float4 sv[5], nv[5];
 #pragma unroll
-    for (int r = 0; r < PB_ITEMS; ++r) {
-      const int64_t i = base + r * PB_THREADS + threadIdx.x;
-      ls[r] = -2;
-      if (i < N) propagate1(st, nz, N, i, v[r]);
+      for (int c = 0; c < 5; ++c) {
+        sv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0);
+        nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
+      }
+      const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
+      const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k][0] = (T)add_rn(add_rn(sp[0][k], sp[2][k]), np[0][k]);
+        v[k][1] = (T)add_rn(add_rn(sp[1][k], sp[3][k]), np[1][k]);
+        v[k][2] = (T)add_rn(sp[2][k], np[2][k]);
+        v[k][3] = (T)add_rn(sp[3][k], np[3][k]);
+        v[k][4] = (T)add_rn(sp[4][k], np[4][k]);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        float4 o = make_float4((float)v[0][c], (float)v[1][c], (float)v[2][c], (float)v[3][c]);
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(prop) + c * N + i0) = o;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < PB_PER_THREAD; ++k) {
+        const int64_t i = pb_index<false>(base, k);
+        if (i < N) {
+          propagate1(st, nz, N, i, v[k]);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) prop[c * N + i] = v[k][c];
+        }
+      }
     }
+    const bool vec_chunk = VEC && base + PB_CHUNK <= N;
+    unsigned long long key[PB_PER_THREAD];
+    int ls[PB_PER_THREAD];
 #pragma unroll
-    for (int r = 0; r < PB_ITEMS; ++r) {
-      const int64_t i = base + r * PB_THREADS + threadIdx.x;
+    for (int k = 0; k < PB_PER_THREAD; ++k) {
+      const int64_t i = vec_chunk ? pb_index<true>(base, k) : pb_index<false>(base, k);
+      ls[k] = -2;
       if (i >= N) continue;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) prop[c * N + i] = v[r][c];
-      T fx = floor_t(div_rn(add_rn(v[r][0], half), h));
-      T fy = floor_t(div_rn(add_rn(v[r][1], half), h));
-      if (!(finite_state(v[r]) && abs_t(fx) < lim && abs_t(fy) < lim)) {
+      T fx = floor_t(div_rn(add_rn(v[k][0], half), h));
+      T fy = floor_t(div_rn(add_rn(v[k][1], half), h));
+      if (!(finite_state(v[k]) && abs_t(fx) < lim && abs_t(fy) < lim)) {
         raise_flag(b.ctl, PCSIR_DERR_RANGE);
         fx = T(0);
         fy = T(0);
-        v[r][0] = T(0);
-        v[r][1] = T(0);
+        v[k][0] = T(0);
+        v[k][1] = T(0);
       }
-      cbx[r] = (int)fx;
-      cby[r] = (int)fy;
-      key[r] = pack_key(cbx[r], cby[r]);
+      key[k] = pack_key((int)fx, (int)fy);
       bool created;
-      ls[r] = local_find_or_insert(tab, key[r], created);
-      if (created) tab.gslot[ls[r]] = global_find_or_insert(b, key[r]);
+      ls[k] = local_find_or_insert(tab, key[k], created);
+      if (created) tab.gslot[ls[k]] = global_find_or_insert(b, key[k]);
     }
     __syncthreads();
+    unsigned gs[PB_PER_THREAD];
 #pragma unroll
-    for (int r = 0; r < PB_ITEMS; ++r) {
-      if (ls[r] == -2) continue;
-      const int64_t i = base + r * PB_THREADS + threadIdx.x;
-      long long off[5];
-      off[0] = to_fixed(v[r][0], Scales<T>::POS) - (long long)cbx[r] * hq;
-      off[1] = to_fixed(v[r][1], Scales<T>::POS) - (long long)cby[r] * hq;
+    for (int k = 0; k < PB_PER_THREAD; ++k) {
+      gs[k] = 0u;
+      if (ls[k] == -2) continue;
+      long long bv[5];
+      const int bx = key_bx(key[k]), by = key_by(key[k]);
+      bv[0] = to_fixed(v[k][0], Scales<T>::POS) - (long long)bx * hq + POS_BIAS;
+      bv[1] = to_fixed(v[k][1], Scales<T>::POS) - (long long)by * hq + POS_BIAS;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) off[2 + c] = to_fixed(v[r][2 + c], Scales<T>::VAL) - anc[c];
+      for (int c = 0; c < 3; ++c) bv[2 + c] = to_fixed(v[k][2 + c], Scales<T>::VAL) - anc[c] + VAL_BIAS;
       bool bad = false;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) bad |= (off[c] >= POS_OFFSET_LIMIT || off[c] <= -POS_OFFSET_LIMIT);
-#pragma unroll
-      for (int c = 2; c < 5; ++c) bad |= (off[c] >= VAL_SPREAD_LIMIT || off[c] <= -VAL_SPREAD_LIMIT);
+      for (int c = 0; c < 5; ++c) bad |= (bv[c] < 0 || bv[c] >= BIASED_LIMIT);
       if (bad) {
         raise_flag(b.ctl, PCSIR_DERR_RANGE);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) off[c] = 0;
+        bv[0] = bv[1] = POS_BIAS;
+        bv[2] = bv[3] = bv[4] = VAL_BIAS;
       }
-      unsigned g;
-      if (ls[r] >= 0) {
-        const int s = ls[r];
-        g = tab.gslot[s];
-        atomicAdd(&tab.cnt[s], 1u);
+      if (ls[k] >= 0) {
+        const int s = ls[k];
+        gs[k] = tab.gslot[s];
+        atomicAdd(&tab.acc[0][s], 1u);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) atomicAdd((unsigned long long*)&tab.sum[c][s], (unsigned long long)off[c]);
+        for (int c = 0; c < 5; ++c) {
+          atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & PIECE_MASK));
+          atomicAdd(&tab.acc[2 + 2 * c][s], (unsigned)(bv[c] >> PIECE_BITS));
+        }
       } else {
-        g = global_find_or_insert(b, key[r]);
+        const unsigned g = global_find_or_insert(b, key[k]);
+        gs[k] = g;
         atomicAdd(&b.hcnt[g], 1u);
 #pragma unroll
-        for (int c = 0; c < 5; ++c)
-          atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)off[c]);
+        for (int c = 0; c < 5; ++c) {
+          const long long bias = c < 2 ? POS_BIAS : VAL_BIAS;
+          atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias));
+        }
       }
-      b.pslot[i] = g;
     }
+    if (vec_chunk) {
+      *reinterpret_cast<uint4*>(b.pslot + base + 4 * threadIdx.x) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < PB_PER_THREAD; ++k)
+        if (ls[k] != -2) b.pslot[pb_index<false>(base, k)] = gs[k];
+    }
+    since_flush += PB_CHUNK;
     __syncthreads();
-    if (tab.fill >= LT_CAP) local_flush(tab, b);
+    const bool full = tab.fill >= LT_CAP;
+    if (full || since_flush + PB_CHUNK > FLUSH_PARTICLES) {
+      local_flush(tab, b, full);
+      since_flush = 0;
+    }
   }
-  local_flush(tab, b);
+  local_flush(tab, b, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,18 +606,28 @@ int weight_scale_bits(int64_t N) {
 
 // One-time kernel attributes and occupancy, queried at context creation so
 // that step calls only enqueue work (and stay legal inside a stream capture).
-template <typename T>
-static cudaError_t prop_bin_prepare(int* per_sm) {
+template <typename T, bool VEC>
+static cudaError_t prop_bin_prepare1(int* per_sm) {
   const size_t smem = sizeof(LocalTable);
-  cudaError_t e = cudaFuncSetAttribute(k_prop_bin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_prop_bin<T, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T>, PB_THREADS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T, VEC>, PB_THREADS, smem);
   if (*per_sm < 1) *per_sm = 1;
   return e;
 }
 
 cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
-  return dtype == PCSIR_F32 ? prop_bin_prepare<float>(prop_bin_per_sm) : prop_bin_prepare<double>(prop_bin_per_sm);
+  int a = 1, c = 1;
+  cudaError_t e;
+  if (dtype == PCSIR_F32) {
+    e = prop_bin_prepare1<float, true>(&a);
+    if (e == cudaSuccess) e = prop_bin_prepare1<float, false>(&c);
+  } else {
+    e = prop_bin_prepare1<double, false>(&a);
+    c = a;
+  }
+  *prop_bin_per_sm = a < c ? a : c;
+  return e;
 }
 
 template <typename T>
@@ -548,8 +636,15 @@ static cudaError_t prop_bin_launch(const StepBuffers& b, const void* state, cons
   const size_t smem = sizeof(LocalTable);
   const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
   const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * b.prop_bin_per_sm);
-  k_prop_bin<T><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state), static_cast<const T*>(noise), N,
-                                               (T)h, hq);
+  const bool vec = std::is_same<T, float>::value && (N % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(noise) |
+                     reinterpret_cast<uintptr_t>(b.prop) | reinterpret_cast<uintptr_t>(b.pslot)) % 16 == 0);
+  if (vec)
+    k_prop_bin<T, true><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state), static_cast<const T*>(noise),
+                                                        N, (T)h, hq);
+  else
+    k_prop_bin<T, false><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state),
+                                                         static_cast<const T*>(noise), N, (T)h, hq);
   return cudaGetLastError();
 }
 
@@ -560,7 +655,7 @@ static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
                                int num_sms, cudaStream_t s, StageEvents se) {
-  const long long hq = llrint(h * 4294967296.0);
+  const long long hq = llrint(h * 2147483648.0);
   cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
                                      : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
   if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;

@@ -47,8 +47,44 @@ __device__ long long first_out(const Map64& mp, long long C, long long N) {
 
 __device__ __forceinline__ int pad_idx(int j) { return j + (j >> 4); }
 
+// Exclusive prefix of a tile by decoupled look-back, done by one warp: each
+// lane reads one predecessor's status word (waiting, with a bound, until it
+// is published), the nearest predecessor holding an inclusive prefix ends the
+// walk, and the aggregates in between are summed.
+__device__ __forceinline__ long long lookback_warp(unsigned long long* st, long long tile, Control* ctl) {
+  const int lane = threadIdx.x & 31;
+  long long excl = 0;
+  long long j = tile - 1;
+  while (j >= 0) {
+    const long long idx = j - lane;
+    unsigned long long s = ST_PREFIX;  // before tile 0: an inclusive prefix of 0
+    if (idx >= 0) {
+      int spins = 0;
+      while (true) {
+        s = *(volatile unsigned long long*)&st[idx];
+        if (s != 0ull) break;
+        if (++spins > LOOKBACK_SPIN_LIMIT) {
+          atomicOr(&ctl->err, (unsigned)PCSIR_DERR_TIMEOUT);
+          s = ST_PREFIX;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    const unsigned pmask = __ballot_sync(0xffffffffu, (s & ST_PREFIX) != 0ull);
+    const int first = pmask ? __ffs(pmask) - 1 : 32;
+    long long c = lane <= first ? (long long)(s & ST_VAL) : 0ll;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    excl += c;
+    if (pmask) break;
+    j -= 32;
+  }
+  return excl;
+}
+
 template <typename T, int WSRC>
-__global__ void __launch_bounds__(SCAN_THREADS)
+__global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, double u0,
                 int sq, int keep) {
   __shared__ long long Cs[SCAN_TILE + SCAN_TILE / 16];
@@ -86,20 +122,42 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
   const double m = ord_decode(ctl->max_ll);
   const size_t hcap = size_t(1) << b.hbits;
 
-  // 1. integer weights of the tile, coalesced, into padded shared memory
-#pragma unroll 4
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int j = k * SCAN_THREADS + tid;
-    long long q = 0;
-    if (j < cnt) {
-      const int64_t i = base + j;
-      if (WSRC == WSRC_BINS) {
-        q = b.hq[b.pslot[i]];
+  // 1. integer weights of the tile into padded shared memory; four
+  //    consecutive particles per thread and load, all loads issued together
+  if (WSRC == WSRC_BINS) {
+    const bool vec = cnt == SCAN_TILE && (base % 4 == 0);
+    unsigned g[SCAN_ITEMS];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+      const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
+      if (vec) {
+        const uint4 q4 = *reinterpret_cast<const uint4*>(b.pslot + base + j0);
+        g[4 * k] = q4.x;
+        g[4 * k + 1] = q4.y;
+        g[4 * k + 2] = q4.z;
+        g[4 * k + 3] = q4.w;
       } else {
-        q = q_of_wtilde(wtilde_df(lsrc[i], m), sq);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) g[4 * k + e] = (j0 + e < cnt) ? b.pslot[base + j0 + e] : 0xffffffffu;
       }
     }
-    Cs[pad_idx(j)] = q;
+    long long q[SCAN_ITEMS];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) q[k] = g[k] != 0xffffffffu ? b.hq[g[k]] : 0ll;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+      const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Cs[pad_idx(j0 + e)] = q[4 * k + e];
+    }
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      const int j = k * SCAN_THREADS + tid;
+      long long q = 0;
+      if (j < cnt) q = q_of_wtilde(wtilde_df(lsrc[base + j], m), sq);
+      Cs[pad_idx(j)] = q;
+    }
   }
   __syncthreads();
   // 2. each thread scans its ITEMS consecutive weights
@@ -128,36 +186,17 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
   }
   const long long texcl = woff + inc - run;
   // 4. decoupled look-back for the tile's exclusive prefix
-  if (tid == 0) {
-    long long excl = 0;
+  if (w == 0) {
     unsigned long long* st = b.tile_status;
-    if (tile == 0) {
-      atomicExch(&st[0], ST_PREFIX | (unsigned long long)agg);
-    } else {
-      atomicExch(&st[tile], ST_AGG | (unsigned long long)agg);
-      long long j = (long long)tile - 1;
-      while (j >= 0) {
-        unsigned long long s = 0;
-        int spins = 0;
-        while (true) {
-          s = *(volatile unsigned long long*)&st[j];
-          if (s != 0ull) break;
-          if (++spins > LOOKBACK_SPIN_LIMIT) {
-            atomicOr(&ctl->err, (unsigned)PCSIR_DERR_TIMEOUT);
-            s = ST_PREFIX;
-            break;
-          }
-          __nanosleep(32);
-        }
-        excl += (long long)(s & ST_VAL);
-        if (s & ST_PREFIX) break;
-        --j;
-      }
-      atomicExch(&st[tile], ST_PREFIX | (unsigned long long)(excl + agg));
+    if (lane == 0) atomicExch(&st[tile], (tile == 0 ? ST_PREFIX : ST_AGG) | (unsigned long long)agg);
+    long long excl = 0;
+    if (tile > 0) excl = lookback_warp(st, (long long)tile, ctl);
+    if (lane == 0) {
+      if (tile > 0) atomicExch(&st[tile], ST_PREFIX | (unsigned long long)(excl + agg));
+      s_excl = excl;
+      s_lo = first_out(s_map, excl, N);
+      s_hi = (base + cnt >= N) ? N : first_out(s_map, excl + agg, N);
     }
-    s_excl = excl;
-    s_lo = first_out(s_map, excl, N);
-    s_hi = (base + cnt >= N) ? N : first_out(s_map, excl + agg, N);
   }
   __syncthreads();
   const long long excl = s_excl;
@@ -165,21 +204,37 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) Cs[pad_idx(tid * SCAN_ITEMS + k)] = excl + texcl + loc[k];
   __syncthreads();
-  // 6. outputs owned by the tile: ancestor by binary search, gather its state
+  // 6. outputs owned by the tile: ancestor = first j with C_j > U_i, found from
+  //    a proportional guess and a short walk (binary search if the walk is long)
   const Map64 mp = s_map;
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   const long long lo = s_lo, hi = s_hi;
+  const long long nout = hi - lo;
+  const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
   for (long long i = lo + tid; i < hi; i += SCAN_THREADS) {
     const long long U = u_int(mp, i);
-    int a = 0, c = cnt;  // first j in [0, cnt) with C_j > U
-    while (a < c) {
-      const int mid = (a + c) >> 1;
-      if (Cs[pad_idx(mid)] > U) c = mid;
-      else a = mid + 1;
-    }
+    int a = (int)(((i - lo) * (long long)cnt) / (nout > 0 ? nout : 1));
     if (a >= cnt) a = cnt - 1;
+    int steps = 0;
+    while (a < cnt - 1 && Cs[pad_idx(a)] <= U && steps < 8) {
+      ++a;
+      ++steps;
+    }
+    while (a > 0 && Cs[pad_idx(a - 1)] > U && steps < 8) {
+      --a;
+      ++steps;
+    }
+    if (steps >= 8) {
+      int l = 0, r = cnt;
+      while (l < r) {
+        const int mid = (l + r) >> 1;
+        if (Cs[pad_idx(mid)] > U) r = mid;
+        else l = mid + 1;
+      }
+      a = l < cnt ? l : cnt - 1;
+    }
     // all weights zero (Delta = 0): no distribution to sample, keep every particle
-    const int64_t anc = (mp.dhi == 0ull && mp.dlo == 0ull) ? (int64_t)i : base + a;
+    const int64_t anc = zero_sum ? (int64_t)i : base + a;
     if (out != nullptr) {
 #pragma unroll
       for (int d = 0; d < 5; ++d) out[d * N + i] = prop[d * N + anc];
