@@ -44,9 +44,10 @@ SEED = 1310554100 + 200
 # algorithmic bytes per particle of the propagate + cell + centre-of-mass kernel (FP32 state):
 # read state 20 + noise 20, write propagated state 20 + cell slot 4
 PROP_BIN_BYTES = 64
-# scan + resample kernel: read cell slot 4, gather one propagated state 20 and write it 20 per output
-RESAMPLE_BYTES = 44
-KERNELS_PER_STEP = 4
+# tile sums + resample kernels: read cell slot 4 (twice), gather one propagated state 20 and write it 20
+# per output
+RESAMPLE_BYTES = 48
+KERNELS_PER_STEP = 5
 
 
 def workload_name(N, h):

@@ -157,7 +157,8 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
             dev_alloc(c, &b.occ, (size_t)nmax) && dev_alloc(c, &b.bin_xy, 2 * (size_t)nmax) &&
             dev_alloc(c, &b.bin_cnt, (size_t)nmax) && dev_alloc(c, &b.dummy, 5 * (size_t)nmax) &&
             dev_alloc(c, &b.bin_ll, (size_t)nmax) && dev_alloc(c, &b.pslot, (size_t)nmax) &&
-            dev_alloc(c, &b.ll, (size_t)nmax) && dev_alloc(c, &b.tile_status, (size_t)b.max_tiles) &&
+            dev_alloc(c, &b.ll, (size_t)nmax) && dev_alloc(c, &b.tile_sum, (size_t)b.max_tiles) &&
+            dev_alloc(c, &b.tile_excl, (size_t)b.max_tiles) &&
             dev_alloc(c, &b.ctl, 1) && dev_alloc(c, &b.dres, 1);
   if (ok) {
     unsigned char* p = nullptr;
@@ -173,11 +174,11 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
     return PCSIR_ENOMEM;
   }
   e = prepare_kernels(cfg->state_dtype, &b.prop_bin_per_sm);
+  if (e == cudaSuccess) e = prepare_resample();
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result));
   if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b.hcnt, 0, hcap * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b.hsum, 0, 5 * hcap * sizeof(long long));
-  if (e == cudaSuccess) e = cudaMemset(b.tile_status, 0, (size_t)b.max_tiles * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b.dres, 0, sizeof(pcsir_result));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {

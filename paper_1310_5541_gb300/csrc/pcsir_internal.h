@@ -11,7 +11,7 @@ namespace pcsir {
 // Per-step control block in device memory, zeroed at the start of every step.
 struct Control {
   unsigned int nocc;          // occupied cells found so far (hash slots listed in occ[])
-  unsigned int tile_ticket;   // next tile of the scan/resample kernel
+  unsigned int spare;
   unsigned int done_blocks;   // last-block-done counter of the weight reduction
   unsigned int err;           // PCSIR_DERR_* flags
   unsigned long long max_ll;  // ordered encoding of the maximum log-likelihood
@@ -22,8 +22,8 @@ struct Control {
   unsigned long long delta_hi, delta_lo;  // T_int / N as 64.64 fixed point
   unsigned long long u0_hi, u0_lo;        // u0 * T_int / N as 64.64 fixed point
   long long anchor[5];        // fixed-point anchors of the non-position components
-  unsigned int tiles_done;    // finished tiles of the scan/resample kernel
-  unsigned int pad;
+  unsigned int tiles_done;    // finished tiles of the resampling kernel
+  unsigned int tsum_done;     // finished tiles of the tile-sum kernel
 };
 
 // Limits of the fixed-point centre-of-mass sums.  Position offsets from the
@@ -33,7 +33,7 @@ struct Control {
 constexpr int64_t MAX_PARTICLES = int64_t(1) << 26;
 constexpr double MAX_H = 8.0;
 
-// Tile of the scan / resampling kernel.
+// Tile of the scan / resampling kernels.
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -61,8 +61,9 @@ struct StepBuffers {
   double* wout;
   uint32_t* pbin;
   int64_t bin_stride;       // row stride of bin_xy / dummy (= max particles)
-  // scan
-  unsigned long long* tile_status;
+  // scan: per-tile sums of the integer weights and their exclusive prefixes
+  long long* tile_sum;
+  long long* tile_excl;
   int64_t max_tiles;
   Control* ctl;
   pcsir_result* dres;
@@ -93,6 +94,7 @@ cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dty
 cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms,
                               cudaStream_t s);
 cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm);
+cudaError_t prepare_resample();
 // integer-weight scale: q = rint(exp(ll - max) * 2^sq) with N * 2^sq <= 2^61
 int weight_scale_bits(int64_t N);
 cudaError_t launch_resample(const StepBuffers& b, int dtype, void* state_out, int64_t N, double u0,

@@ -479,8 +479,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N
 #pragma unroll
     for (int c = 0; c < 5; ++c) a.est[c] += n * wt * b.dummy[c * bs + bi];
   }
-  // the scan kernel's look-back status words start from zero every step
-  for (int64_t t = blockIdx.x * blockDim.x + threadIdx.x; t < b.max_tiles; t += gstride) b.tile_status[t] = 0ull;
   block_reduce_commit(a, b, N, 1, true);
 }
 
@@ -552,9 +550,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const doub
 #pragma unroll
   for (int c = 0; c < 5; ++c) a.est[c] = (double)ke[c].s - (double)ke[c].c;
   a.Tint = tint;
-  if (blockIdx.x == 0) {
-    for (int64_t t = threadIdx.x; t < b.max_tiles; t += blockDim.x) b.tile_status[t] = 0ull;
-  }
   block_reduce_commit(a, b, N, 0, with_est != 0);
 }
 

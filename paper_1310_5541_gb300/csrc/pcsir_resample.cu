@@ -1,6 +1,6 @@
-// Systematic resampling (Algorithm 1/2 resampling step) as one pass over the
-// particles: integer weights, single-pass decoupled look-back prefix scan,
-// and the gather of the selected propagated states into the caller's buffer.
+// Systematic resampling (Algorithm 1/2 resampling step): integer weights, a
+// tile-level prefix scan, and the gather of the selected propagated states
+// into the caller's buffer.
 //
 // Weights enter as integers q_i = rint(exp(ll_i - max) 2^sq), so the
 // cumulative sums C_j are exact and independent of the summation order.
@@ -10,16 +10,18 @@
 // integer part is compared with the integer C_j, which decides C_j > U_i
 // exactly.  Each tile of particles owns the outputs whose U falls between its
 // exclusive and inclusive prefixes, so every output is written exactly once.
+//
+// Two kernels: k_tile_sums adds up each tile's integer weights and its last
+// block scans the tile sums and fixes the 64.64 map; k_resample then scans
+// within each tile and writes the tile's outputs.  No block ever waits for
+// another.
 #include <cmath>
 
 #include "pcsir_device.cuh"
 
 namespace pcsir {
 
-constexpr unsigned long long ST_AGG = 1ull << 62;
-constexpr unsigned long long ST_PREFIX = 1ull << 63;
-constexpr unsigned long long ST_VAL = (1ull << 62) - 1ull;
-constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;
+constexpr int RS_WINDOW = 5120;  // outputs mapped to ancestors per pass (a tile has ~4096)
 
 struct Map64 {
   unsigned long long dhi, dlo, uhi, ulo;
@@ -28,105 +30,53 @@ struct Map64 {
 
 // integer part of i * Delta + U0
 __device__ __forceinline__ long long u_int(const Map64& mp, long long i) {
-  const unsigned __int128 lo = (unsigned __int128)(unsigned long long)i * mp.dlo + mp.ulo;
-  return (long long)((unsigned long long)i * mp.dhi + mp.uhi + (unsigned long long)(lo >> 64));
+  const unsigned long long ui = (unsigned long long)i;
+  const unsigned long long plo = ui * mp.dlo;
+  const unsigned long long phi = __umul64hi(ui, mp.dlo);
+  const unsigned long long s = plo + mp.ulo;
+  const unsigned long long carry = s < plo ? 1ull : 0ull;
+  return (long long)(ui * mp.dhi + mp.uhi + phi + carry);
 }
 
 // first output index i in [0, N] with U_i >= C
 __device__ long long first_out(const Map64& mp, long long C, long long N) {
   if (C <= 0) return 0;
+  if (mp.dd <= 0.0) return N;
   double x = ((double)C - mp.ud) / mp.dd;
-  long long i = (long long)ceil(x);
-  if (i < 0) i = 0;
-  if (i > N) i = N;
+  long long i = x < 0.0 ? 0 : (x > (double)N ? N : (long long)ceil(x));
   int guard = 0;
   while (i > 0 && u_int(mp, i - 1) >= C && guard++ < 64) --i;
   while (i < N && u_int(mp, i) < C && guard++ < 128) ++i;
   return i;
 }
 
-__device__ __forceinline__ int pad_idx(int j) { return j + (j >> 4); }
-
-// Exclusive prefix of a tile by decoupled look-back, done by one warp: each
-// lane reads one predecessor's status word (waiting, with a bound, until it
-// is published), the nearest predecessor holding an inclusive prefix ends the
-// walk, and the aggregates in between are summed.
-__device__ __forceinline__ long long lookback_warp(unsigned long long* st, long long tile, Control* ctl) {
-  const int lane = threadIdx.x & 31;
-  long long excl = 0;
-  long long j = tile - 1;
-  while (j >= 0) {
-    const long long idx = j - lane;
-    unsigned long long s = ST_PREFIX;  // before tile 0: an inclusive prefix of 0
-    if (idx >= 0) {
-      int spins = 0;
-      while (true) {
-        s = *(volatile unsigned long long*)&st[idx];
-        if (s != 0ull) break;
-        if (++spins > LOOKBACK_SPIN_LIMIT) {
-          atomicOr(&ctl->err, (unsigned)PCSIR_DERR_TIMEOUT);
-          s = ST_PREFIX;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    const unsigned pmask = __ballot_sync(0xffffffffu, (s & ST_PREFIX) != 0ull);
-    const int first = pmask ? __ffs(pmask) - 1 : 32;
-    long long c = lane <= first ? (long long)(s & ST_VAL) : 0ll;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    excl += c;
-    if (pmask) break;
-    j -= 32;
-  }
-  return excl;
+__device__ __forceinline__ Map64 load_map(const Control* ctl) {
+  Map64 mp;
+  mp.dhi = ctl->delta_hi;
+  mp.dlo = ctl->delta_lo;
+  mp.uhi = ctl->u0_hi;
+  mp.ulo = ctl->u0_lo;
+  mp.dd = (double)mp.dhi + (double)mp.dlo * 5.421010862427522e-20;
+  mp.ud = (double)mp.uhi + (double)mp.ulo * 5.421010862427522e-20;
+  return mp;
 }
 
-template <typename T, int WSRC>
-__global__ void __launch_bounds__(SCAN_THREADS, 4)
-k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, double u0,
-                int sq, int keep) {
-  __shared__ long long Cs[SCAN_TILE + SCAN_TILE / 16];
-  __shared__ long long wtot[SCAN_THREADS / 32];
-  __shared__ unsigned s_tile;
-  __shared__ long long s_excl, s_lo, s_hi;
-  __shared__ Map64 s_map;
-  Control* ctl = b.ctl;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) {
-    s_tile = atomicAdd(&ctl->tile_ticket, 1u);
-    // Delta = T / N and U0 = u0 Delta in 64.64 fixed point
-    const unsigned long long T = (unsigned long long)*(volatile long long*)&ctl->T_int;
-    const unsigned long long n = (unsigned long long)N;
-    Map64 mp;
-    mp.dhi = T / n;
-    const unsigned long long rem = T % n;
-    mp.dlo = (unsigned long long)(((unsigned __int128)rem << 64) / n);
-    double uf = u0 * 18446744073709551616.0;
-    if (!(uf >= 0.0)) uf = 0.0;
-    const unsigned long long u0f = uf >= 18446744073709549568.0 ? 18446744073709549568ull : __double2ull_rz(uf);
-    const unsigned __int128 ph = (unsigned __int128)u0f * mp.dhi;
-    const unsigned __int128 pl = ((unsigned __int128)u0f * mp.dlo) >> 64;
-    const unsigned __int128 tot = ph + pl;
-    mp.uhi = (unsigned long long)(tot >> 64);
-    mp.ulo = (unsigned long long)tot;
-    mp.dd = (double)mp.dhi + (double)mp.dlo * 5.421010862427522e-20;
-    mp.ud = (double)mp.uhi + (double)mp.ulo * 5.421010862427522e-20;
-    s_map = mp;
-  }
-  __syncthreads();
-  const unsigned tile = s_tile;
-  const int64_t base = (int64_t)tile * SCAN_TILE;
-  const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
-  const double m = ord_decode(ctl->max_ll);
-  const size_t hcap = size_t(1) << b.hbits;
+__device__ __forceinline__ int pad_idx(int j) { return j + (j >> 4); }
 
-  // 1. integer weights of the tile into padded shared memory; four
-  //    consecutive particles per thread and load, all loads issued together
+// every map entry is written before it is read; the clamp only keeps a
+// gather inside the tile should that ever fail
+__device__ __forceinline__ int clamp_item(int a, int cnt) { return a < 0 ? 0 : (a >= cnt ? cnt - 1 : a); }
+
+// Integer weights of the tile's particles j = 1024 k + 4 t + e: WSRC_BINS reads
+// the particle's hash slot and the bin's q; otherwise q is computed from the
+// particle's log-weight.  Particles past the end weigh 0.
+template <int WSRC>
+__device__ __forceinline__ void tile_weights(const StepBuffers& b, const double* __restrict__ lsrc, int64_t base,
+                                             int cnt, double m, int sq, long long q[SCAN_ITEMS]) {
+  const int tid = threadIdx.x;
   if (WSRC == WSRC_BINS) {
-    const bool vec = cnt == SCAN_TILE && (base % 4 == 0);
     unsigned g[SCAN_ITEMS];
+    const bool vec = cnt == SCAN_TILE;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
       const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
@@ -141,22 +91,138 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
         for (int e = 0; e < 4; ++e) g[4 * k + e] = (j0 + e < cnt) ? b.pslot[base + j0 + e] : 0xffffffffu;
       }
     }
-    long long q[SCAN_ITEMS];
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) q[k] = g[k] != 0xffffffffu ? b.hq[g[k]] : 0ll;
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = k * (4 * SCAN_THREADS) + 4 * tid + e;
+        q[4 * k + e] = j < cnt ? q_of_wtilde(wtilde_df(lsrc[base + j], m), sq) : 0ll;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-tile sums of the integer weights; the last block scans them into the
+// tiles' exclusive prefixes and fixes Delta and U0.
+// ---------------------------------------------------------------------------
+template <int WSRC>
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0, int sq) {
+  __shared__ long long red[SCAN_THREADS / 32];
+  __shared__ long long wtot[SCAN_THREADS / 32];
+  __shared__ bool last;
+  Control* ctl = b.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
+  const double m = ord_decode(ctl->max_ll);
+  long long q[SCAN_ITEMS];
+  tile_weights<WSRC>(b, lsrc, base, cnt, m, sq, q);
+  long long t = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) t += q[k];
+  t = warp_sum_i64(t);
+  if (lane == 0) red[w] = t;
+  __syncthreads();
+  if (tid == 0) {
+    long long s = 0;
+    for (int j = 0; j < SCAN_THREADS / 32; ++j) s += red[j];
+    b.tile_sum[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(&ctl->tsum_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // exclusive scan of the tile sums (each thread a run of consecutive tiles)
+  const int nt = (int)gridDim.x;
+  const int per = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int t0 = tid * per;
+  long long run = 0;
+  for (int k = 0; k < per && t0 + k < nt; ++k) run += *(volatile long long*)&b.tile_sum[t0 + k];
+  long long inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wtot[w] = inc;
+  __syncthreads();
+  long long off = 0, total = 0;
+  for (int j = 0; j < SCAN_THREADS / 32; ++j) {
+    if (j < w) off += wtot[j];
+    total += wtot[j];
+  }
+  long long e = off + inc - run;
+  for (int k = 0; k < per && t0 + k < nt; ++k) {
+    const long long v = *(volatile long long*)&b.tile_sum[t0 + k];
+    b.tile_excl[t0 + k] = e;
+    e += v;
+  }
+  if (tid == 0) {
+    // Delta = T / N and U0 = u0 Delta in 64.64 fixed point
+    const unsigned long long T = (unsigned long long)total;
+    const unsigned long long n = (unsigned long long)N;
+    const unsigned long long dhi = T / n;
+    const unsigned long long rem = T % n;
+    const unsigned long long dlo = (unsigned long long)(((unsigned __int128)rem << 64) / n);
+    double uf = u0 * 18446744073709551616.0;
+    if (!(uf >= 0.0)) uf = 0.0;
+    const unsigned long long u0f = uf >= 18446744073709549568.0 ? 18446744073709549568ull : __double2ull_rz(uf);
+    const unsigned __int128 tot = (unsigned __int128)u0f * dhi + (((unsigned __int128)u0f * dlo) >> 64);
+    ctl->delta_hi = dhi;
+    ctl->delta_lo = dlo;
+    ctl->u0_hi = (unsigned long long)(tot >> 64);
+    ctl->u0_lo = (unsigned long long)tot;
+    if (T == 0ull) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Resampling of one tile: inclusive cumulative weights of the tile, then the
+// tile's outputs in windows of RS_WINDOW.  Each thread walks its consecutive
+// particles k and the outputs i from first_out(C_{k-1}) on, giving output i to
+// the particle k with C_{k-1} <= U_i < C_k (an ancestor map in shared
+// memory); then the outputs are written in order, each gathering its
+// ancestor's propagated state.
+// ---------------------------------------------------------------------------
+template <typename T, int WSRC>
+__global__ void __launch_bounds__(SCAN_THREADS, 4)
+k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  long long* Cs = reinterpret_cast<long long*>(rs_smem);                       // SCAN_TILE + SCAN_TILE / 16
+  int* amap = reinterpret_cast<int*>(rs_smem + sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16));  // RS_WINDOW
+  __shared__ long long wtot[SCAN_THREADS / 32];
+  __shared__ long long s_lo, s_hi;
+  Control* ctl = b.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned tile = blockIdx.x;
+  const int64_t base = (int64_t)tile * SCAN_TILE;
+  const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
+  const double m = ord_decode(ctl->max_ll);
+  const size_t hcap = size_t(1) << b.hbits;
+  const Map64 mp = load_map(ctl);
+  const long long excl = b.tile_excl[tile];
+
+  // 1. integer weights, into padded shared memory in particle order
+  {
+    long long q[SCAN_ITEMS];
+    tile_weights<WSRC>(b, lsrc, base, cnt, m, sq, q);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
       const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
 #pragma unroll
       for (int e = 0; e < 4; ++e) Cs[pad_idx(j0 + e)] = q[4 * k + e];
-    }
-  } else {
-#pragma unroll 4
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      const int j = k * SCAN_THREADS + tid;
-      long long q = 0;
-      if (j < cnt) q = q_of_wtilde(wtilde_df(lsrc[base + j], m), sq);
-      Cs[pad_idx(j)] = q;
     }
   }
   __syncthreads();
@@ -185,63 +251,72 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
     agg += t;
   }
   const long long texcl = woff + inc - run;
-  // 4. decoupled look-back for the tile's exclusive prefix
-  if (w == 0) {
-    unsigned long long* st = b.tile_status;
-    if (lane == 0) atomicExch(&st[tile], (tile == 0 ? ST_PREFIX : ST_AGG) | (unsigned long long)agg);
-    long long excl = 0;
-    if (tile > 0) excl = lookback_warp(st, (long long)tile, ctl);
-    if (lane == 0) {
-      if (tile > 0) atomicExch(&st[tile], ST_PREFIX | (unsigned long long)(excl + agg));
-      s_excl = excl;
-      s_lo = first_out(s_map, excl, N);
-      s_hi = (base + cnt >= N) ? N : first_out(s_map, excl + agg, N);
-    }
+  if (tid == 0) {
+    s_lo = first_out(mp, excl, N);
+    s_hi = (base + cnt >= N) ? N : first_out(mp, excl + agg, N);
   }
-  __syncthreads();
-  const long long excl = s_excl;
-  // 5. inclusive cumulative weights C_j of the tile
+  // 4. inclusive cumulative weights C_j of the tile
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) Cs[pad_idx(tid * SCAN_ITEMS + k)] = excl + texcl + loc[k];
   __syncthreads();
-  // 6. outputs owned by the tile: ancestor = first j with C_j > U_i, found from
-  //    a proportional guess and a short walk (binary search if the walk is long)
-  const Map64 mp = s_map;
+  // 5. the tile's outputs
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   const long long lo = s_lo, hi = s_hi;
-  const long long nout = hi - lo;
   const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
-  for (long long i = lo + tid; i < hi; i += SCAN_THREADS) {
-    const long long U = u_int(mp, i);
-    int a = (int)(((i - lo) * (long long)cnt) / (nout > 0 ? nout : 1));
-    if (a >= cnt) a = cnt - 1;
-    int steps = 0;
-    while (a < cnt - 1 && Cs[pad_idx(a)] <= U && steps < 8) {
-      ++a;
-      ++steps;
-    }
-    while (a > 0 && Cs[pad_idx(a - 1)] > U && steps < 8) {
-      --a;
-      ++steps;
-    }
-    if (steps >= 8) {
-      int l = 0, r = cnt;
-      while (l < r) {
-        const int mid = (l + r) >> 1;
-        if (Cs[pad_idx(mid)] > U) r = mid;
-        else l = mid + 1;
+  long long cur = first_out(mp, excl + texcl, N);  // first output of this thread's particles
+  // U_cur kept as integer part + 64-bit fraction and advanced by Delta per output
+  unsigned long long ufrac = (unsigned long long)cur * mp.dlo + mp.ulo;
+  long long uint_cur = u_int(mp, cur);
+  int kk = 0;
+  for (long long wlo = lo; wlo < hi; wlo += RS_WINDOW) {
+    const long long whi = (hi - wlo) < RS_WINDOW ? hi : wlo + RS_WINDOW;
+    if (!zero_sum) {
+      while (kk < SCAN_ITEMS && cur < whi) {
+        if (uint_cur < Cs[pad_idx(tid * SCAN_ITEMS + kk)]) {
+          if (cur >= wlo) amap[cur - wlo] = tid * SCAN_ITEMS + kk;
+          ++cur;
+          const unsigned long long f = ufrac + mp.dlo;
+          uint_cur += (long long)(mp.dhi + (f < ufrac ? 1ull : 0ull));
+          ufrac = f;
+        } else {
+          ++kk;
+        }
       }
-      a = l < cnt ? l : cnt - 1;
     }
-    // all weights zero (Delta = 0): no distribution to sample, keep every particle
-    const int64_t anc = zero_sum ? (int64_t)i : base + a;
-    if (out != nullptr) {
+    __syncthreads();
+    // row offsets fit 32 bits (N <= 2^26)
+    const unsigned wn = (unsigned)(whi - wlo);
+    const unsigned w0 = (unsigned)wlo;
+    const unsigned nb = (unsigned)N;
+    const unsigned ub = (unsigned)base;
+    for (unsigned r0 = tid; r0 < wn; r0 += 2 * SCAN_THREADS) {
+      const unsigned r1 = r0 + SCAN_THREADS;
+      const bool has1 = r1 < wn;
+      const unsigned i0 = w0 + r0, i1 = w0 + r1;
+      // all weights zero (Delta = 0): no distribution to sample, keep every particle
+      const unsigned a0 = zero_sum ? i0 : ub + (unsigned)clamp_item(amap[r0], cnt);
+      const unsigned a1 = has1 ? (zero_sum ? i1 : ub + (unsigned)clamp_item(amap[r1], cnt)) : a0;
+      if (out != nullptr) {
+        T v0[5], v1[5];
 #pragma unroll
-      for (int d = 0; d < 5; ++d) out[d * N + i] = prop[d * N + anc];
+        for (int d = 0; d < 5; ++d) {
+          v0[d] = prop[d * nb + a0];
+          v1[d] = prop[d * nb + a1];
+        }
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          out[d * nb + i0] = v0[d];
+          if (has1) out[d * nb + i1] = v1[d];
+        }
+      }
+      if (keep & PCSIR_KEEP_ANCESTORS) {
+        b.anc[i0] = (int32_t)a0;
+        if (has1) b.anc[i1] = (int32_t)a1;
+      }
     }
-    if (keep & PCSIR_KEEP_ANCESTORS) b.anc[i] = (int32_t)anc;
+    __syncthreads();
   }
-  // 7. optional per-particle outputs of the tile
+  // 6. optional per-particle outputs of the tile
   if (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN)) {
     const double Tf = *(volatile double*)&ctl->T_f;
     for (int j = tid; j < cnt; j += SCAN_THREADS) {
@@ -256,7 +331,7 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
       }
     }
   }
-  // 8. pcSIR: return the occupied hash slots to empty for the next step
+  // 7. pcSIR: return the occupied hash slots to empty for the next step
   if (WSRC == WSRC_BINS) {
     const unsigned B = ctl->nocc;
     for (unsigned bi = tile * SCAN_THREADS + tid; bi < B; bi += gridDim.x * SCAN_THREADS) {
@@ -267,7 +342,7 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
       for (int d = 0; d < 5; ++d) b.hsum[d * hcap + g] = 0;
     }
   }
-  // 9. the last tile to finish publishes the step's device error flags
+  // 8. the last tile to finish publishes the step's device error flags
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -278,20 +353,34 @@ k_scan_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ 
   }
 }
 
+constexpr size_t RS_SMEM = sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16) + sizeof(int) * RS_WINDOW;
+
+cudaError_t prepare_resample() {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_resample<float, WSRC_BINS>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_PARTICLES>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_BINS>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_PARTICLES>, a, (int)RS_SMEM);
+  return e;
+}
+
 template <typename T>
 static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, void* out, int64_t N, double u0,
                                    int mode, int keep, cudaStream_t s) {
   const unsigned ntiles = (unsigned)((N + SCAN_TILE - 1) / SCAN_TILE);
   const int sq = weight_scale_bits(N);
   T* o = static_cast<T*>(out);
-  switch (mode) {
-    case WSRC_BINS:
-      k_scan_resample<T, WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, o, N, u0, sq, keep);
-      break;
-    default:
-      k_scan_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc ? lsrc : b.ll, o, N, u0, sq,
-                                                                         keep);
-      break;
+  if (mode == WSRC_BINS) {
+    k_tile_sums<WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<T, WSRC_BINS><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
+  } else {
+    const double* src = lsrc ? lsrc : b.ll;
+    k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, src, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, src, o, N, sq, keep);
   }
   return cudaGetLastError();
 }
