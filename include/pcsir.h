@@ -206,6 +206,28 @@ pcsir_status pcsir_resample(pcsir_ctx* ctx, const double* logw, int64_t N, doubl
 pcsir_status pcsir_timing_enable(pcsir_ctx* ctx, int32_t max_steps);
 pcsir_status pcsir_timing_read(pcsir_ctx* ctx, float* ms, int32_t capacity, int32_t* n_steps);
 
+/* Systematic resampling for callers that cannot allocate device memory (the
+   paper has no counterpart: this is a property of the library, not of the
+   method).  Some callers may not call cudaMalloc: a host application whose
+   device-memory budget is fixed and handed out at start-up, a framework
+   whose caching allocator already owns the free memory, or a real-time loop
+   that must not take the device-wide synchronisation an allocation can
+   cause.  This entry point needs no context and allocates nothing: its
+   scratch is a fixed array of about 17 KB in the library's own device
+   memory, held by every GPU that loads the library until the process exits.
+     logw       device float64 [N] log-weights (weights exp(logw - max logw)).
+     N          1 .. 2^22 (4,194,304); larger N returns PCSIR_ERANGE.
+     u0         systematic offset in [0, 1).
+     ancestors  device int32 [N], receives s(i) for every output i; the same
+                values pcsir_resample returns for the same inputs.
+   The first call on each device (with that device current) looks up the
+   scratch array's address and sets a kernel attribute; make that first call
+   before any stream capture.  All calls on a device share the one scratch
+   array: calls whose work may overlap on the GPU (different streams without
+   ordering) race on it and must not be issued.  Errors: PCSIR_EINVAL,
+   PCSIR_ERANGE, PCSIR_ECUDA. */
+pcsir_status pcsir_resample_noalloc(const double* logw, int64_t N, double u0, int32_t* ancestors, void* stream);
+
 /* Intermediates of the last step (see pcsir_outputs).  Host call, no sync. */
 pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* out);
 

@@ -67,6 +67,7 @@ def _load():
         "pcsir_last_result": ([P, ctypes.POINTER(pcsir_result)], I32),
         "pcsir_last_error": ([P], ctypes.c_char_p),
         "pcsir_version": ([], ctypes.c_char_p),
+        "pcsir_resample_noalloc": ([P, I64, D, P, P], I32),
         "pcsir_timing_enable": ([P, I32], I32),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
     }
@@ -240,6 +241,19 @@ def pcsir_resample(ctx, logw, u0, out=None, stream=None):
     st = lib.pcsir_resample(ctx.handle, _ptr(logw), logw.numel(), float(u0), _ptr(out), _stream_ptr(stream))
     if st != OK:
         ctx._raise(st)
+    return out
+
+
+def pcsir_resample_noalloc(logw, u0, out=None, stream=None):
+    """Systematic-resampling ancestors without a context and without device allocation
+    (scratch in a fixed library-owned device array; N <= 2^22; calls must not overlap)."""
+    _check_cuda(logw, "logw", torch.float64)
+    if out is None:
+        out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
+    _check_cuda(out, "ancestors", torch.int32)
+    st = lib.pcsir_resample_noalloc(_ptr(logw), logw.numel(), float(u0), _ptr(out), _stream_ptr(stream))
+    if st != OK:
+        raise PcsirError(st, "pcsir_resample_noalloc failed")
     return out
 
 
