@@ -66,7 +66,8 @@ enum {
 enum {
   PCSIR_KEEP_ANCESTORS = 1,    /* int32 ancestor index s(i) of every output particle */
   PCSIR_KEEP_WEIGHTS = 2,      /* float64 normalised weight w_k^i of every propagated particle */
-  PCSIR_KEEP_PARTICLE_BIN = 4  /* uint32 bin index (into the bin arrays) of every particle */
+  PCSIR_KEEP_PARTICLE_BIN = 4, /* uint32 bin index (into the bin arrays) of every particle */
+  PCSIR_KEEP_LOGLIK = 8        /* SIR: float64 log-likelihood of every propagated particle */
 };
 
 /* bit flags of pcsir_result.device_error */
@@ -124,7 +125,7 @@ typedef struct pcsir_outputs {
   const uint32_t* bin_count;     /* [B] members per bin */
   const double* dummy;           /* [5][bin_stride] dummy states (mean state of each bin) */
   const double* bin_loglik;      /* [B] log-likelihood of each dummy */
-  const double* loglik;          /* SIR: [N] log-likelihood of each propagated particle */
+  const double* loglik;          /* SIR: [N] log-likelihood of each propagated particle (PCSIR_KEEP_LOGLIK) */
   const uint32_t* particle_bin;  /* [N] bin index of each particle (PCSIR_KEEP_PARTICLE_BIN) */
   const int32_t* ancestor;       /* [N] s(i) for each output particle i (PCSIR_KEEP_ANCESTORS) */
   const double* weight;          /* [N] normalised weights (PCSIR_KEEP_WEIGHTS) */

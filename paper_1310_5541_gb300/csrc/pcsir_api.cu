@@ -125,7 +125,8 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   if (cfg->lik_kind == PCSIR_LIK_SSE && !(cfg->sigma_xi > 0.0)) return PCSIR_EINVAL;
   if (!std::isfinite(cfg->bg)) return PCSIR_EINVAL;
   if (cfg->max_particles < 1 || cfg->max_particles > MAX_PARTICLES) return PCSIR_EINVAL;
-  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN)) return PCSIR_EINVAL;
+  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK))
+    return PCSIR_EINVAL;
 
   pcsir_ctx* c = new (std::nothrow) pcsir_ctx();
   if (!c) return PCSIR_ENOMEM;
@@ -157,7 +158,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
             dev_alloc(c, &b.occ, (size_t)nmax) && dev_alloc(c, &b.bin_xy, 2 * (size_t)nmax) &&
             dev_alloc(c, &b.bin_cnt, (size_t)nmax) && dev_alloc(c, &b.dummy, 5 * (size_t)nmax) &&
             dev_alloc(c, &b.bin_ll, (size_t)nmax) && dev_alloc(c, &b.pslot, (size_t)nmax) &&
-            dev_alloc(c, &b.ll, (size_t)nmax) && dev_alloc(c, &b.tile_sum, (size_t)b.max_tiles) &&
+            dev_alloc(c, &b.llq, (size_t)nmax) && dev_alloc(c, &b.tile_sum, (size_t)b.max_tiles) &&
             dev_alloc(c, &b.tile_excl, (size_t)b.max_tiles) &&
             dev_alloc(c, &b.ctl, 1) && dev_alloc(c, &b.dres, 1);
   if (ok) {
@@ -168,6 +169,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   if (ok && (cfg->keep & PCSIR_KEEP_ANCESTORS)) ok = dev_alloc(c, &b.anc, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_WEIGHTS)) ok = dev_alloc(c, &b.wout, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_PARTICLE_BIN)) ok = dev_alloc(c, &b.pbin, (size_t)nmax);
+  if (ok && (cfg->keep & PCSIR_KEEP_LOGLIK)) ok = dev_alloc(c, &b.ll, (size_t)nmax);
   if (!ok) {
     free_all(c);
     delete c;
@@ -228,7 +230,8 @@ pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image
   cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
-  e = launch_sir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, image, W, H, ctx->num_sms, s, se);
+  e = launch_sir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, image, W, H, ctx->num_sms, s, se,
+                       ctx->cfg.keep);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "SIR front kernels");
   e = launch_resample(ctx->b, ctx->cfg.state_dtype, state, N, u0, WSRC_PARTICLES,
                       ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN, ctx->num_sms, s);

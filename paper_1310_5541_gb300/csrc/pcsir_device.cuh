@@ -3,6 +3,7 @@
 // warp-cooperative patch likelihood of Eq. (likelihood).
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -149,15 +150,16 @@ __device__ __forceinline__ df warp_sum_df(df v) {
 }
 
 // ---------------------------------------------------------------------------
-// Likelihood of one position, computed by a whole warp (Eq. object, Eq.
-// likelihood).  The PSF factorises, lambda = I0 gx(px) gy(py) + bg, so the
-// 2P one-dimensional factors are computed once in double-float (scratch in
-// shared memory, 4P floats per warp) and each of the P^2 pixels costs one
-// double-float product.  For the Poisson term the difference d = lambda - z
-// is rounded once to float and the term -z phi(d / z) is summed with Kahan
-// compensation per lane, then across the warp in double-float.
-// All lanes of the warp must call this with the same arguments; every lane
-// returns the result.
+// Likelihood of one position, computed by a group of GS threads (a warp or
+// several; Eq. object, Eq. likelihood).  The PSF factorises,
+// lambda = I0 gx(px) gy(py) + bg, so the 2P one-dimensional factors are
+// computed once in double-float (scratch in shared memory, 4P floats per
+// group) and each of the P^2 pixels costs one double-float product.  For the
+// Poisson term the difference d = lambda - z is rounded once to float and the
+// term is -z phi(d / z).  Pixel terms are summed with Kahan compensation per
+// thread, then in double-float across the group in a fixed order.
+// All threads of the group must call this with the same arguments; every
+// thread returns the result.
 // ---------------------------------------------------------------------------
 struct LikParams {
   int P;          // odd patch side
@@ -167,29 +169,129 @@ struct LikParams {
   float inv2sxi2; // 1 / (2 sigma_xi^2)
 };
 
-__device__ __forceinline__ double warp_loglik(const float* __restrict__ img, int W, int H,
-                                              double x, double y, double i0,
-                                              const LikParams& lp, float* __restrict__ scratch) {
-  const int lane = threadIdx.x & 31;
+// Conversions between floats and 64-bit fixed-point integers done with
+// integer instructions: the hardware's 64-bit float <-> integer conversions
+// run on this GPU's (slow) FP64 pipe.
+
+// t * 2^32 truncated toward zero (|t| < 2^30; exact for |t| >= 2^-9)
+__device__ __forceinline__ long long f2fix32(float t) {
+  const unsigned b = __float_as_uint(t);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;
+  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 118;  // t * 2^32 = m * 2^(e - 150 + 32)
+  unsigned long long v;
+  if (sh >= 0) v = sh < 39 ? (m << sh) : (1ull << 61);
+  else v = sh > -24 ? (m >> -sh) : 0ull;
+  return (b >> 31) ? -(long long)v : (long long)v;
+}
+
+// |d| truncated to 24 significant bits as a float; *back = its integer value
+__device__ __forceinline__ float i64_trunc_float(long long d, long long* back) {
+  if (d == 0) {
+    *back = 0;
+    return 0.0f;
+  }
+  const bool neg = d < 0;
+  const unsigned long long a = neg ? 0ull - (unsigned long long)d : (unsigned long long)d;
+  const int top = 63 - __clzll((long long)a);
+  const int sh = top - 23;  // mantissa with its leading bit at position 23
+  const unsigned long long mt = sh >= 0 ? a >> sh : a << (-sh);
+  const unsigned long long tv = sh >= 0 ? mt << sh : a;
+  *back = neg ? -(long long)tv : (long long)tv;
+  return __uint_as_float((neg ? 0x80000000u : 0u) | ((unsigned)(top + 127) << 23) | (unsigned)(mt & 0x7fffffu));
+}
+
+// d * 2^-32 as a double-float (relative error below 2^-46)
+__device__ __forceinline__ df fix32_to_df(long long d) {
+  long long hb, lb;
+  const float hi = i64_trunc_float(d, &hb);
+  const float lo = i64_trunc_float(d - hb, &lb);
+  const float sc = 2.3283064365386963e-10f;  // 2^-32
+  return fast_two_sum(__fmul_rn(hi, sc), __fmul_rn(lo, sc));
+}
+
+// barrier over the GS threads of one group (GS = 32: the warp)
+template <int GS>
+__device__ __forceinline__ void group_sync(int group) {
+  if (GS == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(GS) : "memory");
+  }
+}
+
+// An evaluated position: coordinates and intensity as double-float, and the
+// pixel nearest to it, (floor(x + 0.5), floor(y + 0.5)), computed exactly.
+struct LikPos {
+  df x, y, i0;
+  int cx, cy;
+};
+
+// nearest pixel of a float coordinate without rounding x + 0.5: floor(x) and
+// the fraction x - floor(x), which is exact except for x in (-1, 0), where
+// its rounding cannot cross 1/2
+__device__ __forceinline__ int nearest_pixel(float x) {
+  const float f = floorf(x);
+  return (int)f + (__fsub_rn(x, f) >= 0.5f ? 1 : 0);
+}
+
+__device__ __forceinline__ LikPos lik_pos(float x, float y, float i0) {
+  LikPos q;
+  q.x = {x, 0.0f};
+  q.y = {y, 0.0f};
+  q.i0 = {i0 > 0.0f ? i0 : 0.0f, 0.0f};
+  q.cx = nearest_pixel(x);
+  q.cy = nearest_pixel(y);
+  return q;
+}
+
+__device__ __forceinline__ LikPos lik_pos(double x, double y, double i0) {
+  LikPos q;
+  q.x = df_from_double(x);
+  q.y = df_from_double(y);
+  q.i0 = df_from_double(i0 > 0.0 ? i0 : 0.0);
+  q.cx = (int)floor(x + 0.5);
+  q.cy = (int)floor(y + 0.5);
+  return q;
+}
+
+// (integer pixel coordinate) - (double-float position), exactly rounded to a double-float
+__device__ __forceinline__ df pixel_offset(int p, df x) {
+  df d = two_sum((float)p, -x.hi);
+  d.lo = __fsub_rn(d.lo, x.lo);
+  return fast_two_sum(d.hi, d.lo);
+}
+
+// Log-likelihood as a double-float sum; bad if a pixel term was not a number
+// (a non-finite image value).
+struct LLSum {
+  df sum;
+  bool bad;
+};
+
+__device__ __forceinline__ double ll_to_double(LLSum s) {
+  return s.bad ? -INFINITY : (double)s.sum.hi + (double)s.sum.lo;
+}
+
+template <int GS>
+__device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int W, int H, const LikPos& q,
+                                               const LikParams& lp, float* __restrict__ scratch,
+                                               int* __restrict__ red, int group, int gtid) {
   const int P = lp.P;
   const int R = P >> 1;
-  const double cxd = floor(x + 0.5);
-  const double cyd = floor(y + 0.5);
-  const int cx = (int)cxd;
-  const int cy = (int)cyd;
-  const df I0 = df_from_double(i0 > 0.0 ? i0 : 0.0);
+  const int cx = q.cx;
+  const int cy = q.cy;
+  const df I0 = q.i0;
   float* gxh = scratch;
   float* gxl = scratch + P;
   float* gyh = scratch + 2 * P;
   float* gyl = scratch + 3 * P;
   // one-dimensional factors: column j -> I0 * exp(-(px - x)^2 c2), row j -> exp(-(py - y)^2 c2)
-  for (int j = lane; j < 2 * P; j += 32) {
+  for (int j = gtid; j < 2 * P; j += GS) {
     const bool col = j < P;
     const int jj = col ? j : j - P;
-    const double off = (double)(jj - R);
-    // px - x = (c - x) + off, with |c - x| <= 1/2 and off an integer: exact in double
-    const double dd = col ? (cxd - x) + off : (cyd - y) + off;
-    const df d = df_from_double(dd);
+    const df d = col ? pixel_offset(cx - R + jj, q.x) : pixel_offset(cy - R + jj, q.y);
     df e = df_mul(df_mul(d, d), lp.c2);
     e.hi = -e.hi;
     e.lo = -e.lo;
@@ -203,10 +305,11 @@ __device__ __forceinline__ double warp_loglik(const float* __restrict__ img, int
       gyl[jj] = g.lo;
     }
   }
-  __syncwarp();
+  group_sync<GS>(group);
   kahan acc;
+  bool bad = false;
   const int PP = P * P;
-  for (int p = lane; p < PP; p += 32) {
+  for (int p = gtid; p < PP; p += GS) {
     const int r = p / P;
     const int c = p - r * P;
     const int px = cx - R + c;
@@ -220,9 +323,12 @@ __device__ __forceinline__ double warp_loglik(const float* __restrict__ img, int
         const df s = two_sum(prod.hi, __fsub_rn(lp.bg, z));
         const float d = __fadd_rn(s.hi, __fadd_rn(s.lo, prod.lo));
         const float u = __fdiv_rn(d, z);
-        acc.add(-z * phi_log1p(u));
+        const float t = -z * phi_log1p(u);
+        bad |= (t != t);
+        acc.add(t);
       } else {
         const df lam = df_add_f(prod, lp.bg);
+        bad |= (z != z);
         acc.add(-lam.hi);
         acc.add(-lam.lo);
       }
@@ -230,13 +336,36 @@ __device__ __forceinline__ double warp_loglik(const float* __restrict__ img, int
       // e = z - lambda = (z - bg) - prod, rounded once
       const df s = two_sum(__fsub_rn(z, lp.bg), -prod.hi);
       const float e = __fadd_rn(s.hi, __fsub_rn(s.lo, prod.lo));
-      acc.add(-(e * e) * lp.inv2sxi2);
+      const float t = -(e * e) * lp.inv2sxi2;
+      bad |= (t != t);
+      acc.add(t);
     }
   }
-  df tot = two_sum(acc.s, -acc.c);
-  tot = warp_sum_df(tot);
-  __syncwarp();
-  return df_to_double(tot);
+  bad = __any_sync(0xffffffffu, bad);
+  df tot = warp_sum_df(two_sum(acc.s, -acc.c));
+  if (GS > 32) {
+    // warps' partial sums in a fixed order
+    if ((gtid & 31) == 0) {
+      red[2 * (gtid >> 5)] = __float_as_int(tot.hi);
+      red[2 * (gtid >> 5) + 1] = bad ? 1 : 0;
+      reinterpret_cast<float*>(red)[2 * (GS / 32) + (gtid >> 5)] = tot.lo;
+    }
+    group_sync<GS>(group);
+    tot = {0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < GS / 32; ++k) {
+      tot = df_add(tot, {__int_as_float(red[2 * k]), reinterpret_cast<float*>(red)[2 * (GS / 32) + k]});
+      bad |= red[2 * k + 1] != 0;
+    }
+  }
+  group_sync<GS>(group);  // scratch and red may be reused after this
+  return {tot, bad};
+}
+
+// the warp version used per particle (SIR) and for stand-alone evaluations
+__device__ __forceinline__ LLSum warp_loglik(const float* __restrict__ img, int W, int H, const LikPos& q,
+                                             const LikParams& lp, float* __restrict__ scratch) {
+  return group_loglik<32>(img, W, H, q, lp, scratch, nullptr, 0, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -281,16 +410,38 @@ __device__ __forceinline__ long long to_fixed(double v, double scale) {
   return __double2ll_rn(__dmul_rn(v, scale));
 }
 
+// Per-particle log-likelihoods kept as exact fixed-point integers (units of
+// 2^-32, LLQ_NONE for "no weight"); max encoded for an unsigned atomicMax.
+constexpr long long LLQ_NONE = LLONG_MIN;
+constexpr long long LLQ_LIMIT = 1ll << 61;
+
+__device__ __forceinline__ long long llq_of(LLSum s) {
+  if (s.bad) return LLQ_NONE;
+  const float lim = 5.0e8f;  // |ll| beyond this carries no usable weight
+  if (!(fabsf(s.sum.hi) < lim)) return s.sum.hi > 0.0f ? f2fix32(lim) : -f2fix32(lim);
+  return f2fix32(s.sum.hi) + f2fix32(s.sum.lo);
+}
+// caller-given log-weight in fixed point (non-finite or -inf: no weight)
+__device__ __forceinline__ long long llq_of(double lw) {
+  if (!(lw > -2.0e9 && lw < 2.0e9)) return lw == lw && lw > 0.0 ? LLQ_LIMIT : LLQ_NONE;
+  return __double2ll_rn(lw * 4294967296.0);
+}
+__device__ __forceinline__ unsigned long long llq_enc(long long v) {
+  return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ long long llq_dec(unsigned long long e) { return (long long)(e ^ 0x8000000000000000ull); }
+
 // Per-particle weight w = exp(ll - max) <= 1 in double-float (relative error
-// about 1e-13, so the integer weights below carry the scale's resolution) and
-// its integer weight q = rint(w 2^sq), computed as the sum of the rounded
+// about 1e-13, so the integer weights below carry the scale's resolution),
+// from the fixed-point log-likelihood and maximum without any FP64 operation,
+// and its integer weight q = rint(w 2^sq), computed as the sum of the rounded
 // scaled parts.  The weight reduction and the scan both call these, so both
 // see identical q.
-__device__ __forceinline__ df wtilde_df(double ll, double m) {
-  if (ll == -INFINITY) return {0.0f, 0.0f};
-  double a = ll - m;
-  if (a > 0.0) a = 0.0;
-  return df_exp_neg(df_from_double(a));
+__device__ __forceinline__ df wtilde_q(long long llq, long long mq) {
+  if (llq == LLQ_NONE) return {0.0f, 0.0f};
+  long long d = llq - mq;  // <= 0; both lie within +-2^61
+  if (d > 0) d = 0;
+  return df_exp_neg(fix32_to_df(d));
 }
 __device__ __forceinline__ long long q_of_wtilde(df w, int sq) {
   const float scale = __int_as_float((127 + sq) << 23);  // 2^sq, exact

@@ -14,7 +14,8 @@ struct Control {
   unsigned int spare;
   unsigned int done_blocks;   // last-block-done counter of the weight reduction
   unsigned int err;           // PCSIR_DERR_* flags
-  unsigned long long max_ll;  // ordered encoding of the maximum log-likelihood
+  unsigned long long max_ll;  // ordered encoding of the maximum log-likelihood (bins)
+  unsigned long long max_llq; // encoded maximum fixed-point log-likelihood (particles), 0 = none
   long long T_int;            // sum of the integer weights q_i (exact)
   double T_f;                 // sum of exp(ll_i - max)
   double T2_f;                // sum of exp(ll_i - max)^2
@@ -56,7 +57,8 @@ struct StepBuffers {
   // per particle
   void* prop;               // [5][max] state dtype
   unsigned int* pslot;      // particle -> hash slot
-  double* ll;               // SIR per-particle log-likelihood
+  double* ll;               // SIR per-particle log-likelihood (kept on request)
+  long long* llq;           // SIR per-particle log-likelihood, fixed point 2^-32
   int32_t* anc;
   double* wout;
   uint32_t* pbin;
@@ -90,7 +92,7 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
                                int num_sms, cudaStream_t s, StageEvents se);
 cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                              const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
-                             cudaStream_t s, StageEvents se);
+                             cudaStream_t s, StageEvents se, int keep);
 cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms,
                               cudaStream_t s);
 cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm);
@@ -106,6 +108,6 @@ cudaError_t launch_loglik(const ModelParams& m, const double* x, const double* y
                           cudaStream_t s);
 
 // resampling weight sources
-enum { WSRC_BINS = 0, WSRC_PARTICLES = 1 };
+enum { WSRC_BINS = 0, WSRC_PARTICLES = 1, WSRC_LOGW = 2 };
 
 }  // namespace pcsir

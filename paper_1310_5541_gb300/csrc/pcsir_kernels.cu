@@ -346,15 +346,38 @@ __device__ __forceinline__ void block_max_to_global(double v, Control* ctl) {
   }
 }
 
+// threads evaluating one dummy: a warp, the same partition as the per-particle
+// SIR kernel, so a bin holding a single particle gives SIR's value bit for bit
+constexpr int BIN_GROUP = 32;
+
+__device__ __forceinline__ void block_max_llq_to_global(long long v, Control* ctl) {
+  __shared__ long long red[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = LLQ_NONE;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) m = red[j] > m ? red[j] : m;
+    if (m != LLQ_NONE) atomicMax(&ctl->max_llq, llq_enc(m));
+  }
+}
+
 __global__ void __launch_bounds__(BIN_THREADS)
 k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq) {
-  __shared__ float scratch[BIN_THREADS / 32][4 * MAXP];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int NG = BIN_THREADS / BIN_GROUP;
+  __shared__ float scratch[NG][4 * MAXP];
+  __shared__ int red[NG][3 * (BIN_GROUP / 32)];
+  const int group = threadIdx.x / BIN_GROUP, gtid = threadIdx.x % BIN_GROUP;
   const unsigned B = b.ctl->nocc;
   const size_t hcap = size_t(1) << b.hbits;
   const int64_t bs = b.bin_stride;
   double mymax = -INFINITY;
-  for (unsigned bi = blockIdx.x * (BIN_THREADS / 32) + w; bi < B; bi += gridDim.x * (BIN_THREADS / 32)) {
+  for (unsigned bi = blockIdx.x * NG + group; bi < B; bi += gridDim.x * NG) {
     const unsigned g = b.occ[bi];
     const unsigned long long key = b.hkey[g];
     const int bx = key_bx(key), by = key_by(key);
@@ -365,7 +388,7 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
     mean[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
 #pragma unroll
     for (int c = 2; c < 5; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
-    if (lane == 0) {
+    if (gtid == 0) {
       b.bin_xy[bi] = bx;
       b.bin_xy[bs + bi] = by;
       b.bin_cnt[bi] = n;
@@ -373,12 +396,13 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
       for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = mean[c];
       b.hrank[g] = bi;
     }
-    double ll = warp_loglik(img, W, H, mean[0], mean[1], mean[4], lp, scratch[w]);
+    double ll = ll_to_double(group_loglik<BIN_GROUP>(img, W, H, lik_pos(mean[0], mean[1], mean[4]), lp,
+                                                     scratch[group], red[group], group, gtid));
     if (!isfinite(ll)) {
-      if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      if (gtid == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
       ll = -INFINITY;
     }
-    if (lane == 0) b.bin_ll[bi] = ll;
+    if (gtid == 0) b.bin_ll[bi] = ll;
     mymax = fmax(mymax, ll);
   }
   block_max_to_global(mymax, b.ctl);
@@ -408,7 +432,9 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   return v;
 }
 
-__device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, int kind, bool with_est) {
+// nblocks: the number of blocks taking part (the last of them writes the results)
+__device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, int kind, bool with_est,
+                                    unsigned nblocks) {
   __shared__ double sd[7][RED_THREADS / 32];
   __shared__ long long sl[RED_THREADS / 32];
   __shared__ bool last;
@@ -440,7 +466,7 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
     }
     atomicAdd((unsigned long long*)&ctl->T_int, (unsigned long long)tt);
     __threadfence();
-    last = (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1);
+    last = (atomicAdd(&ctl->done_blocks, 1u) == nblocks - 1);
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
@@ -450,7 +476,12 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
     pcsir_result* r = b.dres;
     for (int c = 0; c < 5; ++c) r->estimate[c] = with_est ? vc->est[c] / Tf : 0.0;
     r->ess = Tf * Tf / T2;
-    r->max_loglik = ord_decode(vc->max_ll);
+    if (kind == 1) {
+      r->max_loglik = ord_decode(vc->max_ll);
+    } else {
+      const unsigned long long e = vc->max_llq;
+      r->max_loglik = e == 0ull ? -INFINITY : (double)llq_dec(e) * (1.0 / 4294967296.0);
+    }
     r->sum_wtilde = Tf;
     r->n_particles = N;
     r->n_bins = kind == 1 ? (int64_t)vc->nocc : 0;
@@ -461,6 +492,10 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
 
 __global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N, int sq) {
   const unsigned B = b.ctl->nocc;
+  // only as many blocks as there are bins to cover take part
+  const unsigned need = (B + blockDim.x - 1) / blockDim.x;
+  const unsigned active = need < 1u ? 1u : (need < gridDim.x ? need : gridDim.x);
+  if (blockIdx.x >= active) return;
   const double m = ord_decode(b.ctl->max_ll);
   const int64_t bs = b.bin_stride;
   RedAcc a = {0.0, 0.0, {0.0, 0.0, 0.0, 0.0, 0.0}, 0};
@@ -479,7 +514,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N
 #pragma unroll
     for (int c = 0; c < 5; ++c) a.est[c] += n * wt * b.dummy[c * bs + bi];
   }
-  block_reduce_commit(a, b, N, 1, true);
+  block_reduce_commit(a, b, N, 1, true, active);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,8 +525,8 @@ constexpr int SL_THREADS = 256;
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS)
 k_sir_prop_lik(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, LikParams lp,
-               const float* __restrict__ img, int W, int H) {
-  __shared__ double sx[SL_THREADS], sy[SL_THREADS], si[SL_THREADS];
+               const float* __restrict__ img, int W, int H, int keep) {
+  __shared__ T sx[SL_THREADS], sy[SL_THREADS], si[SL_THREADS];
   __shared__ float scratch[SL_THREADS / 32][4 * MAXP];
   T* __restrict__ prop = static_cast<T*>(b.prop);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -506,35 +541,42 @@ k_sir_prop_lik(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz
       raise_flag(b.ctl, PCSIR_DERR_RANGE);
       v[0] = v[1] = v[4] = T(0);
     }
-    sx[threadIdx.x] = (double)v[0];
-    sy[threadIdx.x] = (double)v[1];
-    si[threadIdx.x] = (double)v[4];
+    sx[threadIdx.x] = v[0];
+    sy[threadIdx.x] = v[1];
+    si[threadIdx.x] = v[4];
   }
   __syncthreads();
   const int cnt = (int)((N - base) < SL_THREADS ? (N - base) : SL_THREADS);
-  double mymax = -INFINITY;
+  long long mymax = LLQ_NONE;
   for (int j = w; j < cnt; j += SL_THREADS / 32) {
-    double ll = warp_loglik(img, W, H, sx[j], sy[j], si[j], lp, scratch[w]);
-    if (!isfinite(ll)) {
-      if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
-      ll = -INFINITY;
+    const LLSum ls = warp_loglik(img, W, H, lik_pos(sx[j], sy[j], si[j]), lp, scratch[w]);
+    const long long q = llq_of(ls);
+    if (lane == 0) {
+      if (ls.bad) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      b.llq[base + j] = q;
+      if (keep & PCSIR_KEEP_LOGLIK) b.ll[base + j] = ll_to_double(ls);
     }
-    if (lane == 0) b.ll[base + j] = ll;
-    mymax = fmax(mymax, ll);
+    mymax = q > mymax ? q : mymax;
   }
-  block_max_to_global(mymax, b.ctl);
+  block_max_llq_to_global(mymax, b.ctl);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const double* __restrict__ lls, int64_t N,
+// fixed-point log-likelihood of particle i: from the SIR kernel's array, or
+// converted from a caller's float64 log-weight
+__device__ __forceinline__ long long particle_llq(const long long* __restrict__ llq, int64_t i) { return llq[i]; }
+__device__ __forceinline__ long long particle_llq(const double* __restrict__ lw, int64_t i) { return llq_of(lw[i]); }
+
+template <typename T, typename SRC>
+__global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC* __restrict__ lls, int64_t N,
                                                        int sq, int with_est) {
-  const double m = ord_decode(b.ctl->max_ll);
+  const unsigned long long me = b.ctl->max_llq;
+  const long long mq = llq_dec(me);
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   kahan kt, k2, ke[5];
   long long tint = 0;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
-    const df wd = wtilde_df(lls[i], m);
+    const df wd = me == 0ull ? df{0.0f, 0.0f} : wtilde_q(particle_llq(lls, i), mq);
     const float wt = wd.hi;
     tint += q_of_wtilde(wd, sq);
     kt.add(wt);
@@ -550,18 +592,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const doub
 #pragma unroll
   for (int c = 0; c < 5; ++c) a.est[c] = (double)ke[c].s - (double)ke[c].c;
   a.Tint = tint;
-  block_reduce_commit(a, b, N, 0, with_est != 0);
+  block_reduce_commit(a, b, N, 0, with_est != 0, gridDim.x);
 }
 
 // max of caller-given log-weights (standalone resampling)
 __global__ void __launch_bounds__(RED_THREADS) k_logw_max(StepBuffers b, const double* __restrict__ lw, int64_t N) {
-  double m = -INFINITY;
+  long long m = LLQ_NONE;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
-    const double v = lw[i];
-    if (isfinite(v)) m = fmax(m, v);
+    const long long v = llq_of(lw[i]);
+    m = v > m ? v : m;
   }
-  block_max_to_global(m, b.ctl);
+  block_max_llq_to_global(m, b.ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +615,7 @@ k_loglik(LikParams lp, const double* __restrict__ x, const double* __restrict__ 
   __shared__ float scratch[BIN_THREADS / 32][4 * MAXP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t j = (int64_t)blockIdx.x * (BIN_THREADS / 32) + w; j < n; j += (int64_t)gridDim.x * (BIN_THREADS / 32)) {
-    const double ll = warp_loglik(img, W, H, x[j], y[j], a[j], lp, scratch[w]);
+    const double ll = ll_to_double(warp_loglik(img, W, H, lik_pos(x[j], y[j], a[j]), lp, scratch[w]));
     if (lane == 0) out[j] = ll;
   }
 }
@@ -664,23 +706,25 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
 
 cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                              const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
-                             cudaStream_t s, StageEvents se) {
+                             cudaStream_t s, StageEvents se, int keep) {
   const LikParams lp = make_lik(m);
   const int64_t nb = (N + SL_THREADS - 1) / SL_THREADS;
   const int sq = weight_scale_bits(N);
   const int rgrid = (int)std::min<int64_t>((N + RED_THREADS - 1) / RED_THREADS, (int64_t)num_sms * 4);
   if (dtype == PCSIR_F32) {
     k_sir_prop_lik<float><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const float*>(state),
-                                                             static_cast<const float*>(noise), N, lp, img, W, H);
+                                                             static_cast<const float*>(noise), N, lp, img, W, H,
+                                                             keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    k_sir_w<float><<<rgrid, RED_THREADS, 0, s>>>(b, b.ll, N, sq, 1);
+    k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1);
   } else {
     k_sir_prop_lik<double><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const double*>(state),
-                                                              static_cast<const double*>(noise), N, lp, img, W, H);
+                                                              static_cast<const double*>(noise), N, lp, img, W, H,
+                                                              keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    k_sir_w<double><<<rgrid, RED_THREADS, 0, s>>>(b, b.ll, N, sq, 1);
+    k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
@@ -692,7 +736,7 @@ cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t 
   k_logw_max<<<rgrid, RED_THREADS, 0, s>>>(b, logw, N);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sir_w<float><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0);
+  k_sir_w<float, double><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0);
   return cudaGetLastError();
 }
 

@@ -71,8 +71,13 @@ __device__ __forceinline__ int clamp_item(int a, int cnt) { return a < 0 ? 0 : (
 // the particle's hash slot and the bin's q; otherwise q is computed from the
 // particle's log-weight.  Particles past the end weigh 0.
 template <int WSRC>
+__device__ __forceinline__ long long src_llq(const StepBuffers& b, const double* __restrict__ lsrc, int64_t i) {
+  return WSRC == WSRC_LOGW ? llq_of(lsrc[i]) : b.llq[i];
+}
+
+template <int WSRC>
 __device__ __forceinline__ void tile_weights(const StepBuffers& b, const double* __restrict__ lsrc, int64_t base,
-                                             int cnt, double m, int sq, long long q[SCAN_ITEMS]) {
+                                             int cnt, long long mq, bool any, int sq, long long q[SCAN_ITEMS]) {
   const int tid = threadIdx.x;
   if (WSRC == WSRC_BINS) {
     unsigned g[SCAN_ITEMS];
@@ -99,7 +104,7 @@ __device__ __forceinline__ void tile_weights(const StepBuffers& b, const double*
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int j = k * (4 * SCAN_THREADS) + 4 * tid + e;
-        q[4 * k + e] = j < cnt ? q_of_wtilde(wtilde_df(lsrc[base + j], m), sq) : 0ll;
+        q[4 * k + e] = (j < cnt && any) ? q_of_wtilde(wtilde_q(src_llq<WSRC>(b, lsrc, base + j), mq), sq) : 0ll;
       }
     }
   }
@@ -125,9 +130,9 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
   const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
-  const double m = ord_decode(ctl->max_ll);
+  const unsigned long long me = ctl->max_llq;
   long long q[SCAN_ITEMS];
-  tile_weights<WSRC>(b, lsrc, base, cnt, m, sq, q);
+  tile_weights<WSRC>(b, lsrc, base, cnt, llq_dec(me), me != 0ull, sq, q);
   long long t = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) t += q[k];
@@ -209,7 +214,8 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   const unsigned tile = blockIdx.x;
   const int64_t base = (int64_t)tile * SCAN_TILE;
   const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
-  const double m = ord_decode(ctl->max_ll);
+  const unsigned long long me = ctl->max_llq;
+  const long long mq = llq_dec(me);
   const size_t hcap = size_t(1) << b.hbits;
   const Map64 mp = load_map(ctl);
   const long long excl = b.tile_excl[tile];
@@ -217,7 +223,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   // 1. integer weights, into padded shared memory in particle order
   {
     long long q[SCAN_ITEMS];
-    tile_weights<WSRC>(b, lsrc, base, cnt, m, sq, q);
+    tile_weights<WSRC>(b, lsrc, base, cnt, mq, me != 0ull, sq, q);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
       const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
@@ -326,8 +332,8 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
         if (keep & PCSIR_KEEP_WEIGHTS) b.wout[i] = b.hw[g] / Tf;
         if (keep & PCSIR_KEEP_PARTICLE_BIN) b.pbin[i] = b.hrank[g];
       } else if (keep & PCSIR_KEEP_WEIGHTS) {
-        const double ll = lsrc[i];
-        b.wout[i] = (ll == -INFINITY ? 0.0 : exp(ll - m)) / Tf;
+        const df wd = me == 0ull ? df{0.0f, 0.0f} : wtilde_q(src_llq<WSRC>(b, lsrc, i), mq);
+        b.wout[i] = ((double)wd.hi + (double)wd.lo) / Tf;
       }
     }
   }
@@ -359,8 +365,10 @@ cudaError_t prepare_resample() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(k_resample<float, WSRC_BINS>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_PARTICLES>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_LOGW>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_BINS>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_PARTICLES>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_LOGW>, a, (int)RS_SMEM);
   return e;
 }
 
@@ -375,12 +383,16 @@ static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, voi
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_resample<T, WSRC_BINS><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
-  } else {
-    const double* src = lsrc ? lsrc : b.ll;
-    k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, src, N, u0, sq);
+  } else if (mode == WSRC_PARTICLES) {
+    k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, src, o, N, sq, keep);
+    k_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, o, N, sq, keep);
+  } else {
+    k_tile_sums<WSRC_LOGW><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<T, WSRC_LOGW><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
   }
   return cudaGetLastError();
 }
@@ -397,7 +409,7 @@ cudaError_t launch_resample_logw(const StepBuffers& b, const double* logw, int32
   // ancestors only, no state gather
   StepBuffers bb = b;
   bb.anc = anc_out;
-  return resample_launch<float>(bb, logw, nullptr, N, u0, WSRC_PARTICLES, PCSIR_KEEP_ANCESTORS, s);
+  return resample_launch<float>(bb, logw, nullptr, N, u0, WSRC_LOGW, PCSIR_KEEP_ANCESTORS, s);
 }
 
 }  // namespace pcsir

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpcsir.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, ENOTSUP, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
 F32, F64 = 0, 1
 LIK_POISSON, LIK_SSE = 0, 1
-KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN = 1, 2, 4
+KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN, KEEP_LOGLIK = 1, 2, 4, 8
 DERR_RANGE, DERR_TIMEOUT, DERR_NONFINITE, DERR_ZEROSUM = 1, 2, 4, 8
 
 _STATUS_NAMES = {0: "PCSIR_OK", -1: "PCSIR_EINVAL", -2: "PCSIR_ENOMEM", -3: "PCSIR_ECUDA",

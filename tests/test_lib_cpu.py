@@ -67,7 +67,7 @@ def test_invalid_configs_rejected_on_host(binding):
                 max_particles=1000)
     bad = [dict(patch=8), dict(patch=0), dict(patch=65), dict(state_dtype=2), dict(lik_kind=5),
            dict(psf_sigma=0.0), dict(bg=0.0), dict(max_particles=0), dict(max_particles=(1 << 26) + 1),
-           dict(keep=64), dict(lik_kind=1, sigma_xi=0.0)]
+           dict(keep=64), dict(keep=16), dict(lik_kind=1, sigma_xi=0.0)]
     for upd in bad:
         cfg = binding.pcsir_config(**{**base, **upd})
         h = ctypes.c_void_p(123)
