@@ -239,6 +239,62 @@ pcsir_status pcsir_last_result(pcsir_ctx* ctx, pcsir_result* out);
 /* Human-readable description of the last error on ctx (never NULL). */
 const char* pcsir_last_error(pcsir_ctx* ctx);
 
+/*
+ * Batched multi-target filtering: T independent targets, each its own pcSIR
+ * filter (Algorithm 2) with its own particle count, PSF, patch and cell edge,
+ * observed in one shared image and advanced together by one persistent
+ * cooperative kernel launch per step.  FP32 state, Poisson likelihood.
+ * The particles of all targets are concatenated: target t owns particles
+ * [off_t, off_t + n_t) of the [5][sum n_t] state, in target order.
+ */
+typedef struct pcsir_batch pcsir_batch;
+
+typedef struct pcsir_target {
+  int64_t n_particles;  /* >= 1 */
+  double h;             /* cell edge, 0 < h <= 8 */
+  double psf_sigma;     /* > 0 */
+  double bg;            /* > 0 */
+  int32_t patch;        /* odd, 1 .. 63 */
+  int32_t pad;
+} pcsir_target;
+
+/* Create the workspace for T targets (1 .. 2047, sum of n_particles <= 2^26);
+   targets is a host array.  Errors: PCSIR_EINVAL, PCSIR_ERANGE, PCSIR_ENOMEM,
+   PCSIR_ENOTSUP (no cooperative launch), PCSIR_ECUDA. */
+pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_batch** out);
+pcsir_status pcsir_batch_destroy(pcsir_batch* batch);
+
+/* One step of every target.  state: device float32 [5][sum n_t], read-write
+   (resampled in place per target); image: device float32 [H][W]; noise:
+   device float32 [5][sum n_t] process noise (Section 5.1); u0: device float64
+   [T] systematic offsets in [0, 1).  Each target's particles are propagated,
+   binned (cells of that target's h), reduced to dummies, weighted by the
+   dummies' likelihood (that target's PSF and patch) and resampled within the
+   target, as pcsir_step does for one target.  The per-target pcsir_result
+   array is copied to page-locked memory owned by the batch; read it with
+   pcsir_batch_results after synchronising.  Capturable in a CUDA graph. */
+pcsir_status pcsir_batched_step(pcsir_batch* batch, float* state, const float* image, int32_t W, int32_t H,
+                                const float* noise, const double* u0, void* stream);
+
+/* Results of the last step, one per target (out: host array of T), and the
+   step's PCSIR_DERR_* flags (device_error may be NULL; reading them
+   synchronises the device). */
+pcsir_status pcsir_batch_results(pcsir_batch* batch, pcsir_result* out, int32_t T, int32_t* device_error);
+
+/* Device pointers of the last step's propagated states [5][sum n_t] and
+   per-particle cell slots (for inspection), and the total particle count. */
+pcsir_status pcsir_batch_outputs(pcsir_batch* batch, const float** prop_state, const unsigned int** particle_slot,
+                                 int64_t* n_total);
+
+/* Device pointers to the last step's occupied cells of all targets (n_bins of
+   them, in an unspecified order): keys (target << 52 | (by + 2^25) << 26 |
+   (bx + 2^25)), member counts and dummy log-likelihoods.  Reading n_bins
+   synchronises the device. */
+pcsir_status pcsir_batch_bins(pcsir_batch* batch, const uint64_t** keys, const uint32_t** counts,
+                              const double** loglik, int64_t* n_bins);
+
+const char* pcsir_batch_last_error(pcsir_batch* batch);
+
 /* Library version string. */
 const char* pcsir_version(void);
 

@@ -1,0 +1,847 @@
+// Batched multi-target pcSIR: many independent targets (each its own
+// Algorithm 2 filter, with its own particle count, PSF, patch and cell edge)
+// advance by one step in a single persistent cooperative launch.  The phases
+//   A  propagate + cell + centre-of-mass sums (cells keyed by target),
+//   B  dummies and their likelihood,
+//   C  per-target weights, normaliser, ESS, posterior mean,
+//   D  per-(target, tile) sums of the integer weights,
+//   E  per-target scan of its tile sums and the 64.64 resampling map,
+//   F  per-(target, tile) systematic resampling and state gather
+// are separated by grid-wide barriers whose waits are bounded: a wait that
+// runs out sets PCSIR_DERR_TIMEOUT and every block leaves the kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pcsir_device.cuh"
+
+namespace pcsir {
+
+struct BatchTarget {
+  long long off;     // first particle of the target in the concatenated arrays
+  long long n;       // particles of the target
+  long long hq;      // cell edge in units of 2^-31 px
+  double h;          // cell edge (px)
+  double sigma;      // PSF std
+  float bg;          // background
+  int patch;         // odd patch side
+  int sq;            // integer-weight scale bits (n 2^sq <= 2^61)
+  int tile0;         // first global tile of the target
+  int ntiles;        // tiles of the target
+  int pad;
+};
+
+struct BatchStats {  // per target, zeroed every step
+  unsigned long long max_ll;
+  long long T_int;
+  double T_f, T2_f, est[5];
+  unsigned long long dhi, dlo, uhi, ulo;
+  long long anchor[3];
+  unsigned int nbins;
+  unsigned int pad;
+};
+
+struct BatchCtl {  // zeroed every step
+  unsigned int nocc;
+  unsigned int err;
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int abort;
+  unsigned int pad;
+};
+
+struct BatchBufs {
+  const BatchTarget* tg;
+  BatchStats* st;
+  BatchCtl* ctl;
+  const long long* offs;  // [T + 1]
+  int T;
+  int ntiles_total;
+  long long ntot;
+  // hash table over (target, cell)
+  unsigned long long* hkey;
+  unsigned int* hcnt;
+  long long* hsum;
+  long long* hq;
+  int hbits;
+  unsigned int* occ;
+  double* bin_ll;
+  unsigned int* bin_cnt;
+  unsigned long long* bin_key;
+  unsigned int* pslot;
+  float* prop;
+  long long* tile_sum;
+  long long* tile_excl;
+  pcsir_result* res;  // [T]
+};
+
+constexpr int BT_THREADS = 512;
+constexpr int BT_PER_THREAD = 4;
+constexpr int BT_CHUNK = BT_THREADS * BT_PER_THREAD;
+constexpr int BT_LT_BITS = 10;
+constexpr int BT_LT = 1 << BT_LT_BITS;
+constexpr unsigned BT_LT_CAP = 768;
+constexpr int BT_PIECE_BITS = 18;
+constexpr unsigned BT_PIECE_MASK = (1u << BT_PIECE_BITS) - 1u;
+constexpr int BT_FLUSH = 1 << 14;
+constexpr long long BT_POS_BIAS = 1ll << 33;
+constexpr long long BT_VAL_BIAS = 1ll << 34;
+constexpr long long BT_BIASED_LIMIT = 1ll << 36;
+constexpr int BT_NACC = 11;
+constexpr int BT_MAX_TARGETS = 2047;
+constexpr int BT_TILE = 4096;
+constexpr int BT_ITEMS = BT_TILE / BT_THREADS;  // 8
+constexpr int BT_WINDOW = 4608;
+constexpr int BT_BARRIER_SPINS = 1 << 22;
+
+// cell key: target (11 bits) | by + 2^25 (26 bits) | bx + 2^25 (26 bits)
+__device__ __forceinline__ unsigned long long bkey(int t, int bx, int by) {
+  return ((unsigned long long)t << 52) | ((unsigned long long)(unsigned)(by + (1 << 25)) << 26) |
+         (unsigned long long)(unsigned)(bx + (1 << 25));
+}
+__device__ __forceinline__ int bkey_t(unsigned long long k) { return (int)(k >> 52); }
+__device__ __forceinline__ int bkey_by(unsigned long long k) { return (int)((k >> 26) & 0x3ffffffu) - (1 << 25); }
+__device__ __forceinline__ int bkey_bx(unsigned long long k) { return (int)(k & 0x3ffffffu) - (1 << 25); }
+
+struct BatchLocal {
+  unsigned long long key[BT_LT];
+  unsigned int acc[BT_NACC][BT_LT];
+  unsigned int gslot[BT_LT];
+  unsigned short list[BT_LT];
+  unsigned int nlist;
+  unsigned int fill;
+};
+
+struct BatchResampleSmem {
+  long long Cs[BT_TILE + BT_TILE / 16];
+  int amap[BT_WINDOW];
+  long long wtot[BT_THREADS / 32];
+  long long s_lo, s_hi;
+};
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t BT_SMEM_UNION = cmax(sizeof(BatchLocal), sizeof(BatchResampleSmem));
+constexpr size_t BT_SMEM = BT_SMEM_UNION + sizeof(long long) * (BT_MAX_TARGETS + 1);
+
+// ---------------------------------------------------------------------------
+// bounded grid-wide barrier (all blocks are co-resident: cooperative launch)
+// ---------------------------------------------------------------------------
+__device__ bool grid_barrier(BatchCtl* c) {
+  __shared__ unsigned s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1u;
+    volatile BatchCtl* vc = c;
+    const unsigned gen = vc->bar_gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      c->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      int spins = 0;
+      while (vc->bar_gen == gen) {
+        if (vc->abort) break;
+        if (++spins > BT_BARRIER_SPINS) {
+          atomicOr(&c->err, (unsigned)PCSIR_DERR_TIMEOUT);
+          atomicExch(&c->abort, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (vc->abort) s_ok = 0u;
+  }
+  __syncthreads();
+  return s_ok != 0u;
+}
+
+__device__ unsigned bglobal_insert(const BatchBufs& b, unsigned long long key) {
+  const unsigned mask = (1u << b.hbits) - 1u;
+  unsigned h = hash_bits(key, b.hbits);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const unsigned long long k = *(volatile unsigned long long*)&b.hkey[h];
+    if (k == key) return h;
+    if (k == EMPTY_KEY) {
+      const unsigned long long old = atomicCAS(&b.hkey[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY) {
+        const unsigned idx = atomicAdd(&b.ctl->nocc, 1u);
+        b.occ[idx] = h;
+        return h;
+      }
+      if (old == key) return h;
+    }
+    h = (h + 1u) & mask;
+  }
+  atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_RANGE);
+  return 0;
+}
+
+__device__ int blocal_insert(BatchLocal& t, unsigned long long key, bool& created) {
+  created = false;
+  unsigned h = hash_bits(key, BT_LT_BITS);
+  for (int probe = 0; probe < BT_LT; ++probe) {
+    const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
+    if (k == key) return (int)h;
+    if (k == EMPTY_KEY) {
+      if (atomicAdd(&t.fill, 1u) >= BT_LT_CAP) return -1;
+      const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY) {
+        created = true;
+        t.list[atomicAdd(&t.nlist, 1u)] = (unsigned short)h;
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1u) & (BT_LT - 1u);
+  }
+  return -1;
+}
+
+__device__ void blocal_flush(BatchLocal& t, const BatchBufs& b, bool clear_keys) {
+  const size_t hcap = size_t(1) << b.hbits;
+  const unsigned n = t.nlist;
+  for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
+    const unsigned j = t.list[e];
+    const unsigned cnt = t.acc[0][j];
+    if (cnt != 0u) {
+      const unsigned g = t.gslot[j];
+      atomicAdd(&b.hcnt[g], cnt);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const long long bias = c < 2 ? BT_POS_BIAS : BT_VAL_BIAS;
+        const long long sum = (long long)t.acc[1 + 2 * c][j] + ((long long)t.acc[2 + 2 * c][j] << BT_PIECE_BITS) -
+                              (long long)cnt * bias;
+        atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)sum);
+      }
+#pragma unroll
+      for (int a = 0; a < BT_NACC; ++a) t.acc[a][j] = 0u;
+    }
+    if (clear_keys) t.key[j] = EMPTY_KEY;
+  }
+  __syncthreads();
+  if (clear_keys && threadIdx.x == 0) {
+    t.nlist = 0u;
+    t.fill = 0u;
+  }
+  __syncthreads();
+}
+
+// target owning particle i (offsets in shared memory, T + 1 entries)
+__device__ __forceinline__ int target_of(const long long* offs, int T, long long i) {
+  int lo = 0, hi = T;  // offs[lo] <= i < offs[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Phase A: propagate, cell, centre-of-mass sums (cf. k_prop_bin)
+// ---------------------------------------------------------------------------
+__device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st, const float* __restrict__ nz,
+                               BatchLocal& tab, const long long* offs) {
+  const long long N = b.ntot;
+  const size_t hcap = size_t(1) << b.hbits;
+  for (int j = threadIdx.x; j < BT_LT; j += blockDim.x) {
+    tab.key[j] = EMPTY_KEY;
+#pragma unroll
+    for (int a = 0; a < BT_NACC; ++a) tab.acc[a][j] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    tab.nlist = 0u;
+    tab.fill = 0u;
+  }
+  __syncthreads();
+  const long long nchunks = (N + BT_CHUNK - 1) / BT_CHUNK;
+  int since_flush = 0;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long base = chunk * BT_CHUNK;
+    float v[BT_PER_THREAD][5];
+    int tg[BT_PER_THREAD];
+    unsigned long long key[BT_PER_THREAD];
+    int ls[BT_PER_THREAD];
+    const long long i0 = base + (long long)BT_PER_THREAD * threadIdx.x;
+    int t = i0 < N ? target_of(offs, b.T, i0) : 0;
+#pragma unroll
+    for (int k = 0; k < BT_PER_THREAD; ++k) {
+      const long long i = i0 + k;
+      ls[k] = -2;
+      tg[k] = 0;
+      if (i >= N) continue;
+      while (t + 1 < b.T && offs[t + 1] <= i) ++t;
+      tg[k] = t;
+      const float x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
+      v[k][0] = __fadd_rn(__fadd_rn(x, vx), nz[i]);
+      v[k][1] = __fadd_rn(__fadd_rn(y, vy), nz[N + i]);
+      v[k][2] = __fadd_rn(vx, nz[2 * N + i]);
+      v[k][3] = __fadd_rn(vy, nz[3 * N + i]);
+      v[k][4] = __fadd_rn(a, nz[4 * N + i]);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) b.prop[c * N + i] = v[k][c];
+      const float h = (float)b.tg[t].h;
+      float fx = floorf(__fdiv_rn(__fadd_rn(v[k][0], 0.5f), h));
+      float fy = floorf(__fdiv_rn(__fadd_rn(v[k][1], 0.5f), h));
+      bool ok = fabsf(fx) < 33554431.0f && fabsf(fy) < 33554431.0f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) ok &= fabsf(v[k][c]) < 1.0e9f;
+      if (!ok) {
+        atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_RANGE);
+        fx = fy = 0.0f;
+        v[k][0] = v[k][1] = 0.0f;
+      }
+      key[k] = bkey(t, (int)fx, (int)fy);
+      bool created;
+      ls[k] = blocal_insert(tab, key[k], created);
+      if (created) tab.gslot[ls[k]] = bglobal_insert(b, key[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BT_PER_THREAD; ++k) {
+      if (ls[k] == -2) continue;
+      const long long i = i0 + k;
+      const BatchTarget& T_ = b.tg[tg[k]];
+      const BatchStats& S_ = b.st[tg[k]];
+      long long bv[5];
+      bv[0] = to_fixed(v[k][0], 2147483648.0f) - (long long)bkey_bx(key[k]) * T_.hq + BT_POS_BIAS;
+      bv[1] = to_fixed(v[k][1], 2147483648.0f) - (long long)bkey_by(key[k]) * T_.hq + BT_POS_BIAS;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) bv[2 + c] = to_fixed(v[k][2 + c], 4194304.0f) - S_.anchor[c] + BT_VAL_BIAS;
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) bad |= (bv[c] < 0 || bv[c] >= BT_BIASED_LIMIT);
+      if (bad) {
+        atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_RANGE);
+        bv[0] = bv[1] = BT_POS_BIAS;
+        bv[2] = bv[3] = bv[4] = BT_VAL_BIAS;
+      }
+      unsigned g;
+      if (ls[k] >= 0) {
+        const int s = ls[k];
+        g = tab.gslot[s];
+        atomicAdd(&tab.acc[0][s], 1u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & BT_PIECE_MASK));
+          atomicAdd(&tab.acc[2 + 2 * c][s], (unsigned)(bv[c] >> BT_PIECE_BITS));
+        }
+      } else {
+        g = bglobal_insert(b, key[k]);
+        atomicAdd(&b.hcnt[g], 1u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const long long bias = c < 2 ? BT_POS_BIAS : BT_VAL_BIAS;
+          atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias));
+        }
+      }
+      b.pslot[i] = g;
+    }
+    since_flush += BT_CHUNK;
+    __syncthreads();
+    const bool full = tab.fill >= BT_LT_CAP;
+    if (full || since_flush + BT_CHUNK > BT_FLUSH) {
+      blocal_flush(tab, b, full);
+      since_flush = 0;
+    }
+  }
+  blocal_flush(tab, b, false);
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: dummies and their likelihood, one warp per occupied cell
+// ---------------------------------------------------------------------------
+__device__ void phase_bins(const BatchBufs& b, const float* __restrict__ img, int W, int H, float* scratch_all) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
+  const size_t hcap = size_t(1) << b.hbits;
+  float* scratch = scratch_all + w * 4 * 64;
+  const unsigned nw = gridDim.x * (blockDim.x >> 5);
+  for (unsigned bi = blockIdx.x * (blockDim.x >> 5) + w; bi < B; bi += nw) {
+    const unsigned g = b.occ[bi];
+    const unsigned long long key = b.hkey[g];
+    const int t = bkey_t(key);
+    const BatchTarget& T_ = b.tg[t];
+    const BatchStats& S_ = b.st[t];
+    const unsigned n = b.hcnt[g];
+    const double dn = (double)n;
+    const double inv = 1.0 / 2147483648.0;
+    const double mx = ((double)((long long)bkey_bx(key) * T_.hq) + (double)b.hsum[g] / dn) * inv;
+    const double my = ((double)((long long)bkey_by(key) * T_.hq) + (double)b.hsum[hcap + g] / dn) * inv;
+    const double mi = ((double)S_.anchor[2] + (double)b.hsum[4 * hcap + g] / dn) * (1.0 / 4194304.0);
+    LikParams lp;
+    lp.P = T_.patch;
+    lp.kind = PCSIR_LIK_POISSON;
+    lp.bg = T_.bg;
+    const double c2 = 1.0 / (2.0 * T_.sigma * T_.sigma);
+    lp.c2 = df_from_double(c2);
+    lp.inv2sxi2 = 0.0f;
+    const LLSum ls = warp_loglik(img, W, H, lik_pos(mx, my, mi), lp, scratch);
+    double ll = ll_to_double(ls);
+    if (lane == 0) {
+      if (ls.bad) atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_NONFINITE);
+      b.bin_ll[bi] = ll;
+      b.bin_cnt[bi] = n;
+      b.bin_key[bi] = key;
+      if (!ls.bad) atomicMax(&b.st[t].max_ll, ord_encode(ll));
+      atomicAdd(&b.st[t].nbins, 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase C: per-target weights of the cells, integer weights, sums
+// ---------------------------------------------------------------------------
+__device__ void phase_weights(const BatchBufs& b) {
+  const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
+  const size_t hcap = size_t(1) << b.hbits;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < B; bi += stride) {
+    const unsigned g = b.occ[bi];
+    const unsigned long long key = b.hkey[g];
+    const int t = bkey_t(key);
+    BatchStats& S_ = b.st[t];
+    const double m = ord_decode(*(volatile unsigned long long*)&S_.max_ll);
+    const double ll = b.bin_ll[bi];
+    const double wt = (ll == -INFINITY) ? 0.0 : exp(ll - m);
+    const long long q = __double2ll_rn(ldexp(wt, b.tg[t].sq));
+    b.hq[g] = q;
+    const unsigned n = b.bin_cnt[bi];
+    atomicAdd(&S_.T_f, n * wt);
+    atomicAdd(&S_.T2_f, n * wt * wt);
+    atomicAdd((unsigned long long*)&S_.T_int, (unsigned long long)((long long)n * q));
+    const double inv = 1.0 / 2147483648.0;
+    const double sx = (double)((long long)bkey_bx(key) * b.tg[t].hq) * inv * n + (double)b.hsum[g] * inv;
+    const double sy = (double)((long long)bkey_by(key) * b.tg[t].hq) * inv * n + (double)b.hsum[hcap + g] * inv;
+    atomicAdd(&S_.est[0], wt * sx);
+    atomicAdd(&S_.est[1], wt * sy);
+#pragma unroll
+    for (int c = 2; c < 5; ++c) {
+      const double sc = ((double)S_.anchor[c - 2] * n + (double)b.hsum[c * hcap + g]) * (1.0 / 4194304.0);
+      atomicAdd(&S_.est[c], wt * sc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phases D-F: resampling per (target, tile) item
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int item_target(const BatchBufs& b, int item) {
+  int lo = 0, hi = b.T;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.tg[mid].tile0 <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ long long bu_int(unsigned long long dhi, unsigned long long dlo, unsigned long long uhi,
+                                            unsigned long long ulo, long long i) {
+  const unsigned long long ui = (unsigned long long)i;
+  const unsigned long long plo = ui * dlo;
+  const unsigned long long phi = __umul64hi(ui, dlo);
+  const unsigned long long s = plo + ulo;
+  return (long long)(ui * dhi + uhi + phi + (s < plo ? 1ull : 0ull));
+}
+
+__device__ long long bfirst_out(const BatchStats& S, long long C, long long N) {
+  if (C <= 0) return 0;
+  const double dd = (double)S.dhi + (double)S.dlo * 5.421010862427522e-20;
+  if (dd <= 0.0) return N;
+  const double ud = (double)S.uhi + (double)S.ulo * 5.421010862427522e-20;
+  const double x = ((double)C - ud) / dd;
+  long long i = x < 0.0 ? 0 : (x > (double)N ? N : (long long)ceil(x));
+  int guard = 0;
+  while (i > 0 && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i - 1) >= C && guard++ < 64) --i;
+  while (i < N && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i) < C && guard++ < 128) ++i;
+  return i;
+}
+
+__device__ void phase_tile_sums(const BatchBufs& b) {
+  __shared__ long long red[BT_THREADS / 32];
+  for (int item = blockIdx.x; item < b.ntiles_total; item += gridDim.x) {
+    const int t = item_target(b, item);
+    const BatchTarget& T_ = b.tg[t];
+    const long long base = T_.off + (long long)(item - T_.tile0) * BT_TILE;
+    const long long end = T_.off + T_.n;
+    long long s = 0;
+    for (int j = threadIdx.x; j < BT_TILE; j += blockDim.x) {
+      const long long i = base + j;
+      if (i < end) s += b.hq[b.pslot[i]];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tot = 0;
+      for (int k = 0; k < BT_THREADS / 32; ++k) tot += red[k];
+      b.tile_sum[item] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// one thread per target: scan of its tile sums, the resampling map, the results
+__device__ void phase_target_scan(const BatchBufs& b, const double* __restrict__ u0s) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
+    const BatchTarget& T_ = b.tg[t];
+    BatchStats& S_ = b.st[t];
+    long long e = 0;
+    for (int k = 0; k < T_.ntiles; ++k) {
+      const long long v = *(volatile long long*)&b.tile_sum[T_.tile0 + k];
+      b.tile_excl[T_.tile0 + k] = e;
+      e += v;
+    }
+    const unsigned long long Tq = (unsigned long long)e;
+    const unsigned long long n = (unsigned long long)T_.n;
+    S_.dhi = Tq / n;
+    S_.dlo = (unsigned long long)(((unsigned __int128)(Tq % n) << 64) / n);
+    double uf = u0s[t] * 18446744073709551616.0;
+    if (!(uf >= 0.0)) uf = 0.0;
+    const unsigned long long u0f = uf >= 18446744073709549568.0 ? 18446744073709549568ull : __double2ull_rz(uf);
+    const unsigned __int128 tot = (unsigned __int128)u0f * S_.dhi + (((unsigned __int128)u0f * S_.dlo) >> 64);
+    S_.uhi = (unsigned long long)(tot >> 64);
+    S_.ulo = (unsigned long long)tot;
+    pcsir_result& r = b.res[t];
+    const double Tf = S_.T_f;
+    for (int c = 0; c < 5; ++c) r.estimate[c] = S_.est[c] / Tf;
+    r.ess = Tf * Tf / S_.T2_f;
+    r.max_loglik = ord_decode(S_.max_ll);
+    r.sum_wtilde = Tf;
+    r.n_particles = T_.n;
+    r.n_bins = S_.nbins;
+    r.kind = 1;
+    r.device_error = Tq == 0ull ? PCSIR_DERR_ZEROSUM : 0;
+  }
+}
+
+__device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, BatchResampleSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long long Ntot = b.ntot;
+  for (int item = blockIdx.x; item < b.ntiles_total; item += gridDim.x) {
+    const int t = item_target(b, item);
+    const BatchTarget& T_ = b.tg[t];
+    const BatchStats& S_ = b.st[t];
+    const long long lbase = (long long)(item - T_.tile0) * BT_TILE;  // within the target
+    const long long N = T_.n;
+    const int cnt = (int)((N - lbase) < BT_TILE ? (N - lbase) : BT_TILE);
+    const long long excl = b.tile_excl[item];
+    long long loc[BT_ITEMS];
+    long long run = 0;
+#pragma unroll
+    for (int k = 0; k < BT_ITEMS; ++k) {
+      const int j = tid * BT_ITEMS + k;
+      const long long q = j < cnt ? b.hq[b.pslot[T_.off + lbase + j]] : 0ll;
+      run += q;
+      loc[k] = run;
+    }
+    long long inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) sm.wtot[w] = inc;
+    __syncthreads();
+    long long woff = 0, agg = 0;
+#pragma unroll
+    for (int j = 0; j < BT_THREADS / 32; ++j) {
+      const long long v = sm.wtot[j];
+      if (j < w) woff += v;
+      agg += v;
+    }
+    const long long texcl = woff + inc - run;
+#pragma unroll
+    for (int k = 0; k < BT_ITEMS; ++k) sm.Cs[(tid * BT_ITEMS + k) + ((tid * BT_ITEMS + k) >> 4)] = excl + texcl + loc[k];
+    if (tid == 0) {
+      sm.s_lo = bfirst_out(S_, excl, N);
+      sm.s_hi = (lbase + cnt >= N) ? N : bfirst_out(S_, excl + agg, N);
+    }
+    __syncthreads();
+    const long long lo = sm.s_lo, hi = sm.s_hi;
+    const bool zero_sum = (S_.dhi == 0ull && S_.dlo == 0ull);
+    long long cur = bfirst_out(S_, excl + texcl, N);
+    unsigned long long ufrac = (unsigned long long)cur * S_.dlo + S_.ulo;
+    long long uint_cur = bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, cur);
+    int kk = 0;
+    for (long long wlo = lo; wlo < hi; wlo += BT_WINDOW) {
+      const long long whi = (hi - wlo) < BT_WINDOW ? hi : wlo + BT_WINDOW;
+      if (!zero_sum) {
+        while (kk < BT_ITEMS && cur < whi) {
+          const int jj = tid * BT_ITEMS + kk;
+          if (uint_cur < sm.Cs[jj + (jj >> 4)]) {
+            if (cur >= wlo) sm.amap[cur - wlo] = jj;
+            ++cur;
+            const unsigned long long f = ufrac + S_.dlo;
+            uint_cur += (long long)(S_.dhi + (f < ufrac ? 1ull : 0ull));
+            ufrac = f;
+          } else {
+            ++kk;
+          }
+        }
+      }
+      __syncthreads();
+      for (long long i = wlo + tid; i < whi; i += BT_THREADS) {
+        int a = sm.amap[i - wlo];
+        a = a < 0 ? 0 : (a >= cnt ? cnt - 1 : a);
+        // all weights zero: no distribution to sample, keep every particle
+        const long long src = zero_sum ? T_.off + i : T_.off + lbase + a;
+        const long long dst = T_.off + i;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) out[d * Ntot + dst] = b.prop[d * Ntot + src];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 2)
+k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restrict__ nz, float* __restrict__ out,
+               const float* __restrict__ img, int W, int H, const double* __restrict__ u0s) {
+  extern __shared__ __align__(16) unsigned char bt_smem[];
+  long long* offs = reinterpret_cast<long long*>(bt_smem + BT_SMEM_UNION);
+  for (int t = threadIdx.x; t <= b.T; t += blockDim.x) offs[t] = b.offs[t];
+  // anchors of vx, vy, I0 per target: the target's first particle's input value
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
+    const long long i = b.tg[t].off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b.st[t].anchor[c] = to_fixed(st[(2 + c) * b.ntot + i], 4194304.0f);
+  }
+  if (!grid_barrier(b.ctl)) return;
+  phase_prop_bin(b, st, nz, *reinterpret_cast<BatchLocal*>(bt_smem), offs);
+  if (!grid_barrier(b.ctl)) return;
+  phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
+  if (!grid_barrier(b.ctl)) return;
+  phase_weights(b);
+  // the cells are not needed any more: return their hash slots to empty
+  // after the tile sums, which still read the slots' integer weights
+  if (!grid_barrier(b.ctl)) return;
+  phase_tile_sums(b);
+  if (!grid_barrier(b.ctl)) return;
+  phase_target_scan(b, u0s);
+  {
+    const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
+    const size_t hcap = size_t(1) << b.hbits;
+    for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < B; bi += gridDim.x * blockDim.x) {
+      const unsigned g = b.occ[bi];
+      b.hkey[g] = EMPTY_KEY;
+      b.hcnt[g] = 0u;
+#pragma unroll
+      for (int d = 0; d < 5; ++d) b.hsum[d * hcap + g] = 0;
+    }
+  }
+  if (!grid_barrier(b.ctl)) return;
+  phase_resample(b, out, *reinterpret_cast<BatchResampleSmem*>(bt_smem));
+}
+
+}  // namespace pcsir
+
+// ---------------------------------------------------------------------------
+// Host API
+// ---------------------------------------------------------------------------
+using namespace pcsir;
+
+struct pcsir_batch {
+  int T = 0;
+  long long ntot = 0;
+  int ntiles = 0;
+  int grid = 0;
+  BatchBufs b{};
+  std::vector<void*> allocs;
+  pcsir_result* host_res = nullptr;
+  std::string err = "no error";
+  bool failed = false;
+};
+
+namespace {
+template <typename X>
+bool balloc(pcsir_batch* c, X** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(X) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<X*>(q);
+  return true;
+}
+void bfree(pcsir_batch* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->host_res) cudaFreeHost(c->host_res);
+  c->host_res = nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_batch** out) {
+  if (!out) return PCSIR_EINVAL;
+  *out = nullptr;
+  if (!targets || T < 1 || T > BT_MAX_TARGETS) return PCSIR_EINVAL;
+  long long ntot = 0;
+  int ntiles = 0;
+  std::vector<BatchTarget> tg(T);
+  for (int t = 0; t < T; ++t) {
+    const pcsir_target& x = targets[t];
+    if (x.n_particles < 1 || !(x.h > 0.0 && x.h <= MAX_H) || !(x.psf_sigma > 0.0) || !(x.bg > 0.0) ||
+        x.patch < 1 || x.patch > 63 || (x.patch & 1) == 0)
+      return PCSIR_EINVAL;
+    tg[t].off = ntot;
+    tg[t].n = x.n_particles;
+    tg[t].h = (double)(float)x.h;
+    tg[t].hq = llrint(x.h * 2147483648.0);
+    tg[t].sigma = x.psf_sigma;
+    tg[t].bg = (float)x.bg;
+    tg[t].patch = x.patch;
+    tg[t].sq = weight_scale_bits(x.n_particles);
+    tg[t].tile0 = ntiles;
+    tg[t].ntiles = (int)((x.n_particles + BT_TILE - 1) / BT_TILE);
+    tg[t].pad = 0;
+    ntot += x.n_particles;
+    ntiles += tg[t].ntiles;
+  }
+  if (ntot > MAX_PARTICLES) return PCSIR_ERANGE;
+  pcsir_batch* c = new (std::nothrow) pcsir_batch();
+  if (!c) return PCSIR_ENOMEM;
+  c->T = T;
+  c->ntot = ntot;
+  c->ntiles = ntiles;
+  int hbits = 10;
+  while ((1ll << hbits) < 2 * ntot) ++hbits;
+  const size_t hcap = size_t(1) << hbits;
+  BatchBufs& b = c->b;
+  b.T = T;
+  b.ntot = ntot;
+  b.ntiles_total = ntiles;
+  b.hbits = hbits;
+  BatchTarget* dtg = nullptr;
+  long long* doffs = nullptr;
+  bool ok = balloc(c, &dtg, T) && balloc(c, &b.st, T) && balloc(c, &b.ctl, 1) && balloc(c, &doffs, T + 1) &&
+            balloc(c, &b.hkey, hcap) && balloc(c, &b.hcnt, hcap) && balloc(c, &b.hsum, 5 * hcap) &&
+            balloc(c, &b.hq, hcap) && balloc(c, &b.occ, (size_t)ntot) && balloc(c, &b.bin_ll, (size_t)ntot) &&
+            balloc(c, &b.bin_cnt, (size_t)ntot) && balloc(c, &b.bin_key, (size_t)ntot) &&
+            balloc(c, &b.pslot, (size_t)ntot) &&
+            balloc(c, &b.prop, 5 * (size_t)ntot) && balloc(c, &b.tile_sum, (size_t)ntiles) &&
+            balloc(c, &b.tile_excl, (size_t)ntiles) && balloc(c, &b.res, (size_t)T);
+  if (!ok) {
+    bfree(c);
+    delete c;
+    return PCSIR_ENOMEM;
+  }
+  b.tg = dtg;
+  b.offs = doffs;
+  std::vector<long long> offs(T + 1);
+  for (int t = 0; t < T; ++t) offs[t] = tg[t].off;
+  offs[T] = ntot;
+  cudaError_t e = cudaMemcpy(dtg, tg.data(), sizeof(BatchTarget) * T, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(doffs, offs.data(), sizeof(long long) * (T + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b.hcnt, 0, hcap * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b.hsum, 0, 5 * hcap * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result) * T);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batched_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_SMEM);
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, BT_THREADS, BT_SMEM);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess || !coop || per_sm < 1) {
+    cudaGetLastError();
+    bfree(c);
+    delete c;
+    return e == cudaErrorMemoryAllocation ? PCSIR_ENOMEM : (e != cudaSuccess ? PCSIR_ECUDA : PCSIR_ENOTSUP);
+  }
+  c->grid = sms * per_sm;
+  *out = c;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_destroy(pcsir_batch* c) {
+  if (!c) return PCSIR_OK;
+  cudaDeviceSynchronize();
+  bfree(c);
+  delete c;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batched_step(pcsir_batch* c, float* state, const float* image, int32_t W, int32_t H,
+                                const float* noise, const double* u0, void* stream) {
+  if (!c) return PCSIR_EINVAL;
+  if (c->failed) return PCSIR_ESTATE;
+  if (!state || !image || !noise || !u0 || W < 1 || H < 1) {
+    c->err = "NULL pointer or empty image";
+    return PCSIR_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BatchBufs b = c->b;
+  cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(BatchCtl), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.st, 0, sizeof(BatchStats) * c->T, s);
+  if (e == cudaSuccess) {
+    const float* st_in = state;
+    const float* nz = noise;
+    float* out = state;
+    const float* img = image;
+    int w = W, h = H;
+    const double* u0s = u0;
+    void* args[] = {&b, &st_in, &nz, &out, &img, &w, &h, &u0s};
+    e = cudaLaunchCooperativeKernel((const void*)k_batched_step, dim3(c->grid), dim3(BT_THREADS), args, BT_SMEM, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->host_res, b.res, sizeof(pcsir_result) * c->T, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) {
+    c->err = std::string("batched step: ") + cudaGetErrorString(e);
+    c->failed = true;
+    return PCSIR_ECUDA;
+  }
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_results(pcsir_batch* c, pcsir_result* out, int32_t T, int32_t* device_error) {
+  if (!c || !out || T != c->T) return PCSIR_EINVAL;
+  std::memcpy(out, c->host_res, sizeof(pcsir_result) * T);
+  if (device_error) {
+    BatchCtl ctl;
+    if (cudaMemcpy(&ctl, c->b.ctl, sizeof(ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return PCSIR_ECUDA;
+    *device_error = (int32_t)ctl.err;
+  }
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_outputs(pcsir_batch* c, const float** prop_state, const unsigned int** particle_slot,
+                                 int64_t* n_total) {
+  if (!c) return PCSIR_EINVAL;
+  if (prop_state) *prop_state = c->b.prop;
+  if (particle_slot) *particle_slot = c->b.pslot;
+  if (n_total) *n_total = c->ntot;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_bins(pcsir_batch* c, const uint64_t** keys, const uint32_t** counts, const double** loglik,
+                              int64_t* n_bins) {
+  if (!c) return PCSIR_EINVAL;
+  if (keys) *keys = reinterpret_cast<const uint64_t*>(c->b.bin_key);
+  if (counts) *counts = c->b.bin_cnt;
+  if (loglik) *loglik = c->b.bin_ll;
+  if (n_bins) {
+    BatchCtl ctl;
+    if (cudaMemcpy(&ctl, c->b.ctl, sizeof(ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return PCSIR_ECUDA;
+    *n_bins = ctl.nocc;
+  }
+  return PCSIR_OK;
+}
+
+const char* pcsir_batch_last_error(pcsir_batch* c) { return c ? c->err.c_str() : "NULL batch"; }
+
+}  // extern "C"

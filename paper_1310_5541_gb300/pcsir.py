@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +46,11 @@ class pcsir_outputs(ctypes.Structure):
                 ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
 
 
+class pcsir_target(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("h", ctypes.c_double), ("psf_sigma", ctypes.c_double),
+                ("bg", ctypes.c_double), ("patch", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class PcsirError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
@@ -69,6 +75,15 @@ def _load():
         "pcsir_version": ([], ctypes.c_char_p),
         "pcsir_resample_noalloc": ([P, I64, D, P, P], I32),
         "pcsir_timing_enable": ([P, I32], I32),
+        "pcsir_batch_create": ([ctypes.POINTER(pcsir_target), I32, ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir_batch_destroy": ([P], I32),
+        "pcsir_batched_step": ([P, P, P, I32, I32, P, P, P], I32),
+        "pcsir_batch_results": ([P, ctypes.POINTER(pcsir_result), I32, ctypes.POINTER(ctypes.c_int32)], I32),
+        "pcsir_batch_outputs": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                 ctypes.POINTER(ctypes.c_int64)], I32),
+        "pcsir_batch_bins": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                              ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
+        "pcsir_batch_last_error": ([P], ctypes.c_char_p),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
     }
     for name, (args, res) in sig.items():
@@ -185,7 +200,7 @@ class _CudaArray:
                                          "version": 2, "strides": None}
 
 
-_TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4"}
+_TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.int64: "<i8"}
 
 
 def _from_ptr(ptr, shape, dtype):
@@ -255,6 +270,69 @@ def pcsir_resample_noalloc(logw, u0, out=None, stream=None):
     if st != OK:
         raise PcsirError(st, "pcsir_resample_noalloc failed")
     return out
+
+
+class Batch:
+    """Owns one ``pcsir_batch``: T targets filtered together (FP32 state, Poisson likelihood)."""
+
+    def __init__(self, n, h, psf_sigma, bg, patch):
+        T = len(n)
+        arr = (pcsir_target * T)()
+        for t in range(T):
+            arr[t] = pcsir_target(int(n[t]), float(h[t]), float(psf_sigma[t]), float(bg if np.isscalar(bg) else bg[t]),
+                                  int(patch[t]), 0)
+        hdl = ctypes.c_void_p()
+        st = lib.pcsir_batch_create(arr, T, ctypes.byref(hdl))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_create failed")
+        self.handle = hdl
+        self.T = T
+        self.n_total = int(sum(int(x) for x in n))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pcsir_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, state, image, noise, u0, stream=None):
+        """One step of every target (state [5, sum N] float32 in place; u0 float64 [T] on the device)."""
+        _check_cuda(state, "state", torch.float32)
+        _check_cuda(noise, "noise", torch.float32)
+        _check_cuda(image, "image", torch.float32)
+        _check_cuda(u0, "u0", torch.float64)
+        H, W = image.shape
+        st = lib.pcsir_batched_step(self.handle, _ptr(state), _ptr(image), W, H, _ptr(noise), _ptr(u0),
+                                    _stream_ptr(stream))
+        if st != OK:
+            raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def results(self):
+        """Per-target results of the last step and the step's device error flags (synchronises)."""
+        arr = (pcsir_result * self.T)()
+        err = ctypes.c_int32()
+        st = lib.pcsir_batch_results(self.handle, arr, self.T, ctypes.byref(err))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_results failed")
+        out = [dict(estimate=list(r.estimate), ess=r.ess, n_bins=r.n_bins, n_particles=r.n_particles,
+                    device_error=r.device_error) for r in arr]
+        return out, err.value
+
+    def outputs(self):
+        prop, slot, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        lib.pcsir_batch_outputs(self.handle, ctypes.byref(prop), ctypes.byref(slot), ctypes.byref(n))
+        keys, cnts, ll, nb = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        lib.pcsir_batch_bins(self.handle, ctypes.byref(keys), ctypes.byref(cnts), ctypes.byref(ll), ctypes.byref(nb))
+        B = nb.value
+        return dict(prop_state=_from_ptr(prop.value, (5, n.value), torch.float32),
+                    bin_key=_from_ptr(keys.value, (B,), torch.int64) if B else None,
+                    bin_count=_from_ptr(cnts.value, (B,), torch.int32) if B else None,
+                    bin_loglik=_from_ptr(ll.value, (B,), torch.float64) if B else None)
 
 
 def version():

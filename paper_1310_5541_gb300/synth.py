@@ -131,3 +131,91 @@ def random_weights_case(N: int, seed: int):
     """Random positive log-weights for resampling tests (no filter arithmetic)."""
     rng = np.random.default_rng([seed, 3])
     return rng.normal(size=N) * 3.0
+
+
+@dataclasses.dataclass
+class Batch:
+    """Many independent targets in one frame sequence."""
+
+    n: np.ndarray          # [T] particles per target
+    sigma: np.ndarray      # [T] PSF std per target
+    i0: np.ndarray         # [T] peak intensity per target
+    patch: np.ndarray      # [T] odd likelihood patch side per target
+    h: np.ndarray          # [T] cell edge per target
+    bg: float
+    gt: np.ndarray         # [K+1, T, 5] ground-truth states
+    images: np.ndarray     # [K, H, W] float32 Poisson images with every target's spot
+
+
+def make_batch(T: int, W: int, H: int, n_frames: int, seed: int, n_range=(1000, 100000), sigma_range=(1.2, 2.0),
+               snr_range=(2.0, 8.0), bg: float = 10.0, min_sep: float = 16.0, h_of_sigma=None, q=None,
+               n_values=None) -> Batch:
+    """Multi-target workload: positions by dart throwing with a minimum separation,
+    particle counts log-uniform in n_range (or given), PSF std uniform in sigma_range,
+    SNR uniform in snr_range (I0 from the Poisson SNR), patch side 2 ceil(3 sigma) + 1,
+    slow nearly-constant-velocity tracks."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    q = q or (0.5, 0.5, 0.1, 0.1, 1.0)
+    margin = 24.0
+    pos = []
+    for _ in range(T * 200):
+        if len(pos) == T:
+            break
+        p = rng.uniform([margin, margin], [W - 1 - margin, H - 1 - margin])
+        if all((p[0] - a) ** 2 + (p[1] - b) ** 2 >= min_sep ** 2 for a, b in pos):
+            pos.append(p)
+    if len(pos) < T:
+        raise ValueError("cannot place %d targets with separation %g in %dx%d" % (T, min_sep, W, H))
+    if n_values is None:
+        n = np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]), T)).astype(np.int64)
+    else:
+        n = np.asarray(n_values, dtype=np.int64)
+    sigma = rng.uniform(sigma_range[0], sigma_range[1], T)
+    i0 = np.array([i0_from_snr(s, bg) for s in rng.uniform(snr_range[0], snr_range[1], T)])
+    patch = (2 * np.ceil(3.0 * sigma) + 1).astype(np.int64)
+    h = np.full(T, 0.5) if h_of_sigma is None else np.asarray([h_of_sigma(s) for s in sigma])
+    gt = np.zeros((n_frames + 1, T, 5))
+    ang = rng.uniform(0, 2 * math.pi, T)
+    speed = rng.uniform(0.05, 0.3, T)
+    gt[0, :, 0] = [p[0] for p in pos]
+    gt[0, :, 1] = [p[1] for p in pos]
+    gt[0, :, 2] = speed * np.cos(ang)
+    gt[0, :, 3] = speed * np.sin(ang)
+    gt[0, :, 4] = i0
+    for k in range(n_frames):
+        s = gt[k].copy()
+        s[:, 0] += s[:, 2]
+        s[:, 1] += s[:, 3]
+        s[:, 2] += rng.normal(size=T) * q[2] * 0.1
+        s[:, 3] += rng.normal(size=T) * q[3] * 0.1
+        gt[k + 1] = s
+    images = np.empty((n_frames, H, W), dtype=np.float32)
+    xs = np.arange(W, dtype=np.float64)
+    ys = np.arange(H, dtype=np.float64)
+    for k in range(n_frames):
+        lam = np.full((H, W), bg)
+        for t in range(T):
+            x0, y0, a = gt[k + 1, t, 0], gt[k + 1, t, 1], gt[k + 1, t, 4]
+            r = int(np.ceil(5 * sigma[t]))
+            cx, cy = int(round(x0)), int(round(y0))
+            xa, xb = max(0, cx - r), min(W, cx + r + 1)
+            ya, yb = max(0, cy - r), min(H, cy + r + 1)
+            gx = np.exp(-((xs[xa:xb] - x0) ** 2) / (2 * sigma[t] ** 2))
+            gy = np.exp(-((ys[ya:yb] - y0) ** 2) / (2 * sigma[t] ** 2))
+            lam[ya:yb, xa:xb] += a * np.outer(gy, gx)
+        images[k] = rng.poisson(lam).astype(np.float32)
+    return Batch(n=n, sigma=sigma, i0=i0, patch=patch, h=h, bg=bg, gt=gt, images=images)
+
+
+def batch_initial_state(batch: Batch, dtype=np.float32) -> np.ndarray:
+    """Concatenated [5, sum N_t] state with each target's particles at its ground truth."""
+    parts = [initial_state(batch.gt[0, t], int(batch.n[t]), dtype) for t in range(len(batch.n))]
+    return np.ascontiguousarray(np.concatenate(parts, axis=1))
+
+
+def batch_noise(batch: Batch, q, seed: int, frame: int, dtype=np.float32) -> np.ndarray:
+    return make_noise(int(batch.n.sum()), q, seed, frame, dtype)
+
+
+def batch_u0(T: int, seed: int, frame: int) -> np.ndarray:
+    return np.random.default_rng([seed, 4, frame]).random(T)

@@ -1,0 +1,144 @@
+"""GPU parity of the batched multi-target step against the oracle run per target.
+
+Each target is an independent pcSIR filter (Algorithm 2) with its own particle
+count, PSF, patch and cell edge; the oracle runs ``pcsir_step`` on each
+target's slice of the state and noise with that target's model.  Tolerances
+are those of the single-target parity tests: propagated states and cells
+(with member counts) bit-exact, posterior means and ESS relative 1e-5, every
+resampled particle one of its own target's propagated particles, and the
+number of outputs that differ from the oracle's reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pcsir_oracle as O
+from paper_1310_5541_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SEED = 1310554300
+
+
+@pytest.fixture(scope="module")
+def pc():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1310_5541_gb300 import pcsir
+
+    return pcsir
+
+
+def _model(batch, t):
+    return synth.Model(sigma_psf=float(batch.sigma[t]), I0=float(batch.i0[t]), bg=batch.bg,
+                       patch=int(batch.patch[t]))
+
+
+def _warm(batch, frames):
+    """Per-target oracle runs for a few frames: realistic clouds for every target."""
+    st = synth.batch_initial_state(batch, np.float32)
+    offs = np.concatenate([[0], np.cumsum(batch.n)])
+    for k in range(frames):
+        nz = synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), SEED + 1, k)
+        u0 = synth.batch_u0(len(batch.n), SEED + 1, k)
+        for t in range(len(batch.n)):
+            sl = slice(offs[t], offs[t + 1])
+            r = O.pcsir_step(np.ascontiguousarray(st[:, sl]), batch.images[k], np.ascontiguousarray(nz[:, sl]),
+                             u0[t], batch.h[t], _model(batch, t))
+            st[:, sl] = r["new_state"]
+    return st
+
+
+def _decode(keys):
+    k = keys.astype(np.uint64)
+    t = (k >> np.uint64(52)).astype(np.int64)
+    by = ((k >> np.uint64(26)) & np.uint64(0x3FFFFFF)).astype(np.int64) - (1 << 25)
+    bx = (k & np.uint64(0x3FFFFFF)).astype(np.int64) - (1 << 25)
+    return t, bx, by
+
+
+def _compare(pc, batch, st, frame, noise_seed):
+    T = len(batch.n)
+    offs = np.concatenate([[0], np.cumsum(batch.n)])
+    nz = synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), noise_seed, frame)
+    u0 = synth.batch_u0(T, noise_seed, frame)
+    bt = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    d_st = torch.from_numpy(np.ascontiguousarray(st)).cuda()
+    bt.step(d_st, torch.from_numpy(batch.images[frame]).cuda(), torch.from_numpy(nz).cuda(),
+            torch.from_numpy(u0).cuda())
+    torch.cuda.synchronize()
+    res, derr = bt.results()
+    assert derr == 0
+    out = bt.outputs()
+    prop = out["prop_state"].cpu().numpy()
+    new = d_st.cpu().numpy()
+    tk, bx, by = _decode(out["bin_key"].cpu().numpy())
+    cnt = out["bin_count"].cpu().numpy()
+    mism_total = 0
+    for t in range(T):
+        sl = slice(offs[t], offs[t + 1])
+        ref = O.pcsir_step(np.ascontiguousarray(st[:, sl]), batch.images[frame], np.ascontiguousarray(nz[:, sl]),
+                           u0[t], batch.h[t], _model(batch, t))
+        np.testing.assert_array_equal(prop[:, sl], ref["prop"])
+        sel = tk == t
+        order = np.lexsort((bx[sel], by[sel]))
+        np.testing.assert_array_equal(np.stack([bx[sel][order], by[sel][order]], 1), ref["bin_keys"])
+        np.testing.assert_array_equal(cnt[sel][order], ref["bin_counts"])
+        assert res[t]["n_bins"] == ref["bin_keys"].shape[0]
+        est = np.array(res[t]["estimate"])
+        assert np.all(np.abs(est - ref["estimate"]) <= 1e-5 * np.abs(ref["estimate"]) + 1e-6), (t, est)
+        assert abs(res[t]["ess"] - ref["ess"]) <= 1e-5 * ref["ess"]
+        # every output is one of the target's propagated particles; count differences from the oracle
+        P = prop[:, sl]
+        cols = {tuple(c) for c in P.T}
+        assert all(tuple(c) in cols for c in new[:, sl].T)
+        mism_total += int(np.sum(np.any(new[:, sl] != ref["new_state"], axis=0)))
+    bt.close()
+    return mism_total
+
+
+def test_batched_step_matches_per_target_oracle(pc):
+    n = [1, 3000, 4096, 4097, 9000, 777, 20000]
+    batch = synth.make_batch(len(n), 192, 160, 3, seed=SEED, n_values=n, min_sep=30.0,
+                             h_of_sigma=None)
+    batch.h[:] = [0.25, 0.5, 1.0, 0.5, 2.0, 0.5, 0.25]
+    st = _warm(batch, 2)
+    mism = _compare(pc, batch, st, 2, SEED + 2)
+    print("batched: outputs differing from the oracle:", mism, "of", int(batch.n.sum()))
+    assert mism <= 0.01 * batch.n.sum()
+
+
+def test_batched_many_small_targets(pc):
+    rng = np.random.default_rng(4)
+    n = list(rng.integers(50, 3000, 40))
+    batch = synth.make_batch(len(n), 320, 320, 2, seed=SEED + 10, n_values=n, min_sep=24.0)
+    st = synth.batch_initial_state(batch, np.float32)
+    mism = _compare(pc, batch, st, 0, SEED + 11)
+    assert mism <= 0.01 * batch.n.sum()
+
+
+def test_batched_step_graph_capture_replays(pc):
+    n = [5000, 7000, 123]
+    batch = synth.make_batch(len(n), 128, 128, 1, seed=SEED + 20, n_values=n, min_sep=30.0)
+    st0 = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
+    nz = torch.from_numpy(synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), SEED, 0)).cuda()
+    img = torch.from_numpy(batch.images[0]).cuda()
+    u0 = torch.from_numpy(synth.batch_u0(3, SEED, 0)).cuda()
+    bt = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    s = torch.cuda.Stream()
+    st = st0.clone()
+    with torch.cuda.stream(s):
+        bt.step(st, img, nz, u0, stream=s)
+    torch.cuda.synchronize()
+    ref = st.clone()
+    g = torch.cuda.CUDAGraph()
+    st.copy_(st0)
+    with torch.cuda.graph(g, stream=s):
+        bt.step(st, img, nz, u0, stream=s)
+    st.copy_(st0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(st, ref)
+    bt.close()
