@@ -264,6 +264,11 @@ typedef struct pcsir_target {
 pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_batch** out);
 pcsir_status pcsir_batch_destroy(pcsir_batch* batch);
 
+/* Blocks per SM of the persistent kernel (default: the most that fit, 2).
+   A launch-shape knob for the autotuner; results do not depend on it.
+   Errors: PCSIR_EINVAL, PCSIR_ERANGE (more than fit), PCSIR_ECUDA. */
+pcsir_status pcsir_batch_set_grid(pcsir_batch* batch, int32_t blocks_per_sm);
+
 /* One step of every target.  state: device float32 [5][sum n_t], read-write
    (resampled in place per target); image: device float32 [H][W]; noise:
    device float32 [5][sum n_t] process noise (Section 5.1); u0: device float64

@@ -1,0 +1,109 @@
+"""Autotuner of the batched multi-target step: cell edge per target and launch shape.
+
+The cell edge h trades accuracy for speed (Section 4.2: the piecewise-constant
+likelihood converges to SIR's as h shrinks; larger cells mean fewer dummies).
+For each PSF width the tuner runs the GPU filter on a short synthetic
+sequence with h = c * sigma for several c and keeps the largest c whose
+tracking RMSE stays within ``tol`` of the finest c's (the "matched RMSE"
+criterion), then times the persistent kernel with each number of blocks per
+SM and keeps the fastest.  Results are cached as JSON; ``cell_edges`` reads
+the cache and falls back to h = sigma / 3.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+DEFAULT_C = 1.0 / 3.0
+CANDIDATES = (1.0 / 8.0, 1.0 / 6.0, 1.0 / 4.0, 1.0 / 3.0, 1.0 / 2.0, 1.0)
+
+
+def cache_path():
+    return os.environ.get("PCSIR_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "pcsir_gb300", "autotune.json"))
+
+
+def load():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cell_edges(sigma, table=None):
+    """Cell edge per target from the tuned multiplier of its PSF width."""
+    table = load() if table is None else table
+    c = float(table.get("c", DEFAULT_C))
+    return np.clip(np.asarray(sigma, dtype=np.float64) * c, 0.02, 8.0)
+
+
+def _track_rmse(pcsir, synth, c, n_targets, frames, seed, n_particles):
+    import torch
+
+    batch = synth.make_batch(n_targets, 256, 256, frames, seed, n_values=[n_particles] * n_targets, min_sep=40.0)
+    batch.h[:] = np.clip(batch.sigma * c, 0.02, 8.0)
+    st = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
+    bt = pcsir.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    err = []
+    for k in range(frames):
+        nz = torch.from_numpy(synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), seed, k)).cuda()
+        u0 = torch.from_numpy(synth.batch_u0(n_targets, seed, k)).cuda()
+        bt.step(st, torch.from_numpy(batch.images[k]).cuda(), nz, u0)
+        res, _ = bt.results()
+        est = np.array([r["estimate"][:2] for r in res])
+        err.append(np.sum((est - batch.gt[k + 1, :, :2]) ** 2, axis=1))
+    bt.close()
+    return float(np.sqrt(np.mean(err)))
+
+
+def tune(tol=0.05, n_targets=16, frames=12, n_particles=20000, seed=1310554400, write=True, verbose=False):
+    """Pick the cell-edge multiplier and the blocks per SM; returns (and caches) the table."""
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    rmse = {c: _track_rmse(pcsir, synth, c, n_targets, frames, seed, n_particles) for c in CANDIDATES}
+    finest = rmse[min(CANDIDATES)]
+    ok = [c for c in CANDIDATES if rmse[c] <= (1.0 + tol) * finest]
+    c_best = max(ok)
+    # launch shape: time the persistent step with each number of blocks per SM
+    batch = synth.make_batch(64, 1024, 1024, 4, seed + 1)
+    batch.h[:] = np.clip(batch.sigma * c_best, 0.02, 8.0)
+    st = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
+    nz = torch.from_numpy(synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), seed, 0)).cuda()
+    img = torch.from_numpy(batch.images[0]).cuda()
+    u0 = torch.from_numpy(synth.batch_u0(64, seed, 0)).cuda()
+    bt = pcsir.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    times = {}
+    for bps in (1, 2):
+        try:
+            bt.set_grid(bps)
+        except pcsir.PcsirError:
+            continue
+        for _ in range(2):
+            bt.step(st, img, nz, u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            bt.step(st, img, nz, u0)
+        torch.cuda.synchronize()
+        times[bps] = (time.perf_counter() - t0) / 5
+    bt.close()
+    table = {"c": c_best, "blocks_per_sm": min(times, key=times.get) if times else 2,
+             "rmse": {str(k): v for k, v in rmse.items()}, "step_s": {str(k): v for k, v in times.items()},
+             "tol": tol}
+    if verbose:
+        print(json.dumps(table, indent=1))
+    if write:
+        os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
+        with open(cache_path(), "w") as f:
+            json.dump(table, f, indent=1)
+    return table
+
+
+if __name__ == "__main__":
+    tune(verbose=True)

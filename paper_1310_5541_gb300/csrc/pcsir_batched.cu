@@ -768,6 +768,18 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   return PCSIR_OK;
 }
 
+pcsir_status pcsir_batch_set_grid(pcsir_batch* c, int32_t blocks_per_sm) {
+  if (!c || blocks_per_sm < 1) return PCSIR_EINVAL;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, BT_THREADS, BT_SMEM);
+  if (e != cudaSuccess) return PCSIR_ECUDA;
+  if (blocks_per_sm > per_sm) return PCSIR_ERANGE;
+  c->grid = sms * blocks_per_sm;
+  return PCSIR_OK;
+}
+
 pcsir_status pcsir_batch_destroy(pcsir_batch* c) {
   if (!c) return PCSIR_OK;
   cudaDeviceSynchronize();

@@ -77,6 +77,7 @@ def _load():
         "pcsir_timing_enable": ([P, I32], I32),
         "pcsir_batch_create": ([ctypes.POINTER(pcsir_target), I32, ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_batch_destroy": ([P], I32),
+        "pcsir_batch_set_grid": ([P, I32], I32),
         "pcsir_batched_step": ([P, P, P, I32, I32, P, P, P], I32),
         "pcsir_batch_results": ([P, ctypes.POINTER(pcsir_result), I32, ctypes.POINTER(ctypes.c_int32)], I32),
         "pcsir_batch_outputs": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -311,6 +312,11 @@ class Batch:
                                     _stream_ptr(stream))
         if st != OK:
             raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def set_grid(self, blocks_per_sm):
+        st = lib.pcsir_batch_set_grid(self.handle, int(blocks_per_sm))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_set_grid failed")
 
     def results(self):
         """Per-target results of the last step and the step's device error flags (synchronises)."""

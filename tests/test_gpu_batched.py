@@ -142,3 +142,14 @@ def test_batched_step_graph_capture_replays(pc):
     torch.cuda.synchronize()
     assert torch.equal(st, ref)
     bt.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches(pc, tmp_path, monkeypatch):
+    from paper_1310_5541_gb300 import autotune
+
+    monkeypatch.setenv("PCSIR_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    table = autotune.tune(n_targets=4, frames=4, n_particles=4000)
+    assert table["c"] in autotune.CANDIDATES and table["blocks_per_sm"] in (1, 2)
+    assert autotune.load()["c"] == table["c"]
+    h = autotune.cell_edges(np.array([1.2, 2.0]))
+    np.testing.assert_allclose(h, np.array([1.2, 2.0]) * table["c"])

@@ -78,3 +78,13 @@ def test_invalid_configs_rejected_on_host(binding):
     assert lib.sir_step(None, None, 1, None, 1, 1, None, 0.5, None, None) == binding.EINVAL
     assert lib.pcsir_destroy(None) == binding.OK
     assert b"pcsir" in lib.pcsir_version()
+
+
+def test_autotune_defaults_without_cache(tmp_path, monkeypatch):
+    import numpy as np
+
+    from paper_1310_5541_gb300 import autotune
+
+    monkeypatch.setenv("PCSIR_AUTOTUNE_CACHE", str(tmp_path / "absent.json"))
+    assert autotune.load() == {}
+    np.testing.assert_allclose(autotune.cell_edges([1.5, 3.0]), [0.5, 1.0])
