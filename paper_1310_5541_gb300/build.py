@@ -68,7 +68,7 @@ def build(verbose: bool = False, extra=()) -> str:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr[-8000:]))
         os.replace(tmp, LIB)
     if verbose:
-        print("built", LIB)
+        print("built", LIB, file=sys.stderr)
     return LIB
 
 

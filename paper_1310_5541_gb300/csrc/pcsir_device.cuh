@@ -112,7 +112,7 @@ __device__ __forceinline__ df df_exp_neg(df a) {
 // with log1pf is accurate.
 __device__ __forceinline__ float phi_log1p(float u) {
   if (u >= -0.5f && u <= 1.0f) {
-    float s = __fdiv_rn(u, __fadd_rn(2.0f, u));
+    float s = __fdividef(u, __fadd_rn(2.0f, u));  // 2 ulp, 2 + u in [1.5, 3]
     float s2 = s * s;
     float p = 1.0f / 17.0f;
     p = fmaf(p, s2, 1.0f / 15.0f);
@@ -309,9 +309,14 @@ __device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int
   kahan acc;
   bool bad = false;
   const int PP = P * P;
-  for (int p = gtid; p < PP; p += GS) {
-    const int r = p / P;
-    const int c = p - r * P;
+  // pixel p = r P + c, advanced by GS per iteration without integer division
+  const int step_r = GS / P, step_c = GS - (GS / P) * P;
+  int r = gtid / P, c = gtid - (gtid / P) * P;
+  for (int p = gtid; p < PP; p += GS, r += step_r, c += step_c) {
+    if (c >= P) {
+      c -= P;
+      ++r;
+    }
     const int px = cx - R + c;
     const int py = cy - R + r;
     if (px < 0 || px >= W || py < 0 || py >= H) continue;
@@ -322,7 +327,7 @@ __device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int
         // d = prod + (bg - z), rounded once
         const df s = two_sum(prod.hi, __fsub_rn(lp.bg, z));
         const float d = __fadd_rn(s.hi, __fadd_rn(s.lo, prod.lo));
-        const float u = __fdiv_rn(d, z);
+        const float u = __fdividef(d, z);  // 2 ulp; z is a photon count, far inside the normal range
         const float t = -z * phi_log1p(u);
         bad |= (t != t);
         acc.add(t);

@@ -4,6 +4,8 @@ Tolerances (FP32/double-float GPU arithmetic against the FP64 oracle):
   * propagated states, cells, member counts, member -> cell map: bit-exact;
   * dummies: positions 1e-9 px, other components 2.5e-7 (fixed-point sums
     round velocities and intensities to 2^-22 per particle);
+  * log-likelihoods: absolute 1e-4 + 4e-7 |ll| (a few float ulps per pixel
+    term, summed over the patch);
   * normalised weights: relative 1e-5 for every weight carrying mass
     (w >= 1e-3 max w), absolute 1e-5 max w below;
   * ESS and posterior mean: relative 1e-5 (plus 1e-6 absolute for
@@ -123,7 +125,7 @@ def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model):
     np.testing.assert_allclose(dum[:2], ref["dummies"][:2], rtol=0, atol=1e-9)
     np.testing.assert_allclose(dum[2:], ref["dummies"][2:], rtol=0, atol=2.5e-7)
     ll = out["bin_loglik"][order]
-    assert np.all(np.abs(ll - ref["ll_bins"]) <= 1e-4 + 1e-7 * np.abs(ref["ll_bins"]))
+    assert np.all(np.abs(ll - ref["ll_bins"]) <= 1e-4 + 4e-7 * np.abs(ref["ll_bins"]))
     werr = check_weights(out["weight"], ref["w"])
     check_scalars(res, ref)
     mism = check_resampling(new, out["prop_state"], out["ancestor"], out["weight"], u0, ref["ancestors"])
@@ -136,7 +138,7 @@ def compare_sir(pc, ctx, st_np, img, nz, u0, model):
     assert res["device_error"] == 0 and res["kind"] == 0
     np.testing.assert_array_equal(out["prop_state"], ref["prop"])
     ll = out["loglik"]
-    assert np.all(np.abs(ll - ref["ll"]) <= 1e-4 + 1e-7 * np.abs(ref["ll"]))
+    assert np.all(np.abs(ll - ref["ll"]) <= 1e-4 + 4e-7 * np.abs(ref["ll"]))
     werr = check_weights(out["weight"], ref["w"])
     check_scalars(res, ref)
     mism = check_resampling(new, out["prop_state"], out["ancestor"], out["weight"], u0, ref["ancestors"])
@@ -245,7 +247,7 @@ def test_loglik_entry_point(pc):
     ll = pc.pcsir_loglik(ctx, t(x), t(y), t(a), t(img)).cpu().numpy()
     ref = O.loglik(img, x, y, a, MODEL_BIG)
     err = ll - ref
-    assert np.abs(err).max() <= 1e-4 + 1e-7 * np.abs(ref).max()
+    assert np.abs(err).max() <= 1e-4 + 4e-7 * np.abs(ref).max()
     w = np.exp(ref - ref.max())
     sig = w >= 1e-3
     assert np.abs(err[sig] - err[sig].mean()).max() <= 1e-5
