@@ -408,8 +408,23 @@ constexpr double POS_INV = 1.0 / 2147483648.0;
 constexpr double VAL_SCALE = 4194304.0;         // 2^22
 constexpr double VAL_INV = 1.0 / 4194304.0;
 
+// v * 2^shift rounded to the nearest integer (ties away from zero), by integer
+// instructions (|v| 2^shift < 2^62); exact whenever v * 2^shift is an integer.
+template <int SHIFT>
+__device__ __forceinline__ long long fix_round(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;
+  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 150 + SHIFT;  // v 2^SHIFT = m 2^sh
+  unsigned long long r;
+  if (sh >= 0) r = sh < 39 ? (m << sh) : (1ull << 62);
+  else r = sh > -25 ? ((m + (1ull << (-sh - 1))) >> (-sh)) : 0ull;
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
 __device__ __forceinline__ long long to_fixed(float v, float scale) {
-  return __float2ll_rn(__fmul_rn(v, scale));
+  // the two scales used: 2^31 (positions) and 2^22 (other components)
+  return scale > 4194304.0f ? fix_round<31>(v) : fix_round<22>(v);
 }
 __device__ __forceinline__ long long to_fixed(double v, double scale) {
   return __double2ll_rn(__dmul_rn(v, scale));

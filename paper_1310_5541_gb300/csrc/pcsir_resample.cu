@@ -50,6 +50,21 @@ __device__ long long first_out(const Map64& mp, long long C, long long N) {
   return i;
 }
 
+// first_out without FP64: a float guess of (C - U0) / Delta, then the exact
+// integer correction of first_out
+__device__ long long first_out_f(const Map64& mp, long long C, long long N, float inv_delta) {
+  if (C <= 0) return 0;
+  if (mp.dhi == 0ull && mp.dlo == 0ull) return N;
+  long long back;
+  const float cf = i64_trunc_float(C - (long long)mp.uhi, &back);
+  float xf = __fmul_rn(cf, inv_delta);
+  long long i = xf <= 0.0f ? 0 : (xf >= (float)N ? N : (long long)__float2int_rn(xf));
+  int guard = 0;
+  while (i > 0 && u_int(mp, i - 1) >= C && guard++ < 256) --i;
+  while (i < N && u_int(mp, i) < C && guard++ < 512) ++i;
+  return i;
+}
+
 __device__ __forceinline__ Map64 load_map(const Control* ctl) {
   Map64 mp;
   mp.dhi = ctl->delta_hi;
@@ -269,7 +284,8 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   const long long lo = s_lo, hi = s_hi;
   const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
-  long long cur = first_out(mp, excl + texcl, N);  // first output of this thread's particles
+  const float inv_delta = (float)(1.0 / mp.dd);
+  long long cur = first_out_f(mp, excl + texcl, N, inv_delta);  // first output of this thread's particles
   // U_cur kept as integer part + 64-bit fraction and advanced by Delta per output
   unsigned long long ufrac = (unsigned long long)cur * mp.dlo + mp.ulo;
   long long uint_cur = u_int(mp, cur);
