@@ -300,6 +300,15 @@ pcsir_status pcsir_batch_bins(pcsir_batch* batch, const uint64_t** keys, const u
 
 const char* pcsir_batch_last_error(pcsir_batch* batch);
 
+/* BF16 tensor-core GEMM (tcgen05, FP32 accumulation), the building block of
+   the likelihood surrogate (the paper has no counterpart; exposed for tests).
+   C[m * ldc + n] (+)= sum_k A[m * sam + k * sak] * B[n * sbn + k * sbk] for
+   m < M, n < N, k < K; A and B device bf16 (as uint16_t), C device float32.
+   accumulate != 0 adds to C.  Errors: PCSIR_EINVAL, PCSIR_ENOMEM, PCSIR_ECUDA. */
+pcsir_status pcsir_gemm_bf16(const uint16_t* A, int64_t sam, int64_t sak, const uint16_t* B, int64_t sbn,
+                             int64_t sbk, float* C, int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t accumulate,
+                             void* stream);
+
 /* Library version string. */
 const char* pcsir_version(void);
 

@@ -85,6 +85,7 @@ def _load():
         "pcsir_batch_bins": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
+        "pcsir_gemm_bf16": ([P, I64, I64, P, I64, I64, P, I64, I32, I32, I32, I32, P], I32),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
     }
     for name, (args, res) in sig.items():
@@ -339,6 +340,21 @@ class Batch:
                     bin_key=_from_ptr(keys.value, (B,), torch.int64) if B else None,
                     bin_count=_from_ptr(cnts.value, (B,), torch.int32) if B else None,
                     bin_loglik=_from_ptr(ll.value, (B,), torch.float64) if B else None)
+
+
+def gemm_bf16(A, B, C=None, accumulate=False, stream=None):
+    """C (+)= A @ B.T on the tensor cores (A [M, K], B [N, K] bfloat16 views with any strides;
+    C [M, N] float32)."""
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    st = lib.pcsir_gemm_bf16(_ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0), B.stride(1), _ptr(C),
+                             C.stride(0), M, N, K, int(bool(accumulate)), _stream_ptr(stream))
+    if st != OK:
+        raise PcsirError(st, "pcsir_gemm_bf16 failed")
+    return C
 
 
 def version():
