@@ -1,0 +1,152 @@
+"""Pins of the surrogate oracle against what its definitions fix (CPU only).
+
+* network inputs: a pure-Python loop over a small hand-built image;
+* backpropagation: central finite differences of the loss in FP64 at the
+  network's real sizes (445 -> 256 -> 256 -> 1);
+* silu and its derivative at closed-form points;
+* Adam: the first bias-corrected step is -lr g / (|g| + eps) exactly, the
+  second follows the recursion written out for one scalar;
+* splitmix64: the published first outputs of the generator seeded with 0;
+* held-out check: hand-made cases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_oracle as S
+
+
+def _rand_params(rng, scale=0.3):
+    p = {}
+    for k, s in S.PARAM_SHAPES:
+        fan_in = s[1] if len(s) == 2 else S.HIDDEN
+        p[k] = rng.standard_normal(s) * scale / math.sqrt(fan_in) * (3.0 if k == "w3" else 1.0)
+    return p
+
+
+def test_features_match_pixel_loop():
+    rng = np.random.default_rng(1)
+    H, W = 40, 37
+    img = rng.uniform(0, 50, (H, W)).astype(np.float32)
+    xs = np.array([18.2, 10.49, 10.5, 25.0, 3.0, 35.9])
+    ys = np.array([20.7, 10.51, 11.49, 29.2, 20.0, 1.0])
+    i0 = np.array([90.0, 100.0, 110.0, 5.0, 70.0, 100.0])
+    bg, i0_ref, s_ref = 10.0, 100.0, 2.0
+    X, clipped = S.features(img, xs, ys, i0, 1.5, bg, i0_ref, s_ref)
+    for n in range(len(xs)):
+        cx = math.floor(xs[n] + 0.5)
+        cy = math.floor(ys[n] + 0.5)
+        clip = not (cx - 10 >= 0 and cx + 10 <= W - 1 and cy - 10 >= 0 and cy + 10 <= H - 1)
+        assert clipped[n] == clip
+        k = 0
+        for r in range(cy - 10, cy + 11):
+            for c in range(cx - 10, cx + 11):
+                z = float(img[r, c]) if (0 <= r < H and 0 <= c < W) else bg
+                assert X[n, k] == (z - bg) / i0_ref
+                k += 1
+        assert X[n, 441] == 2 * (xs[n] - cx) and X[n, 442] == 2 * (ys[n] - cy)
+        assert X[n, 443] == i0[n] / i0_ref and X[n, 444] == 1.5 / s_ref
+    # exact ties go up, as the exact likelihood's nearest pixel does
+    assert X[2, 441] == -1.0 and X[1, 441] == 2 * (10.49 - 10)
+    assert not clipped[0] and clipped[4] and clipped[5]
+
+
+def test_silu_closed_forms():
+    assert S.silu(0.0) == 0.0 and S.silu_grad(0.0) == 0.5
+    t = np.array([-3.0, -0.5, 0.7, 4.0])
+    np.testing.assert_allclose(S.silu(t), t / (1 + np.exp(-t)), rtol=0)
+    h = 1e-6
+    np.testing.assert_allclose(S.silu_grad(t), (S.silu(t + h) - S.silu(t - h)) / (2 * h), rtol=1e-8)
+    # maximum of the derivative, used by the error bounds of the GPU tests
+    grid = np.linspace(-10, 10, 200001)
+    assert S.silu_grad(grid).max() < 1.0999
+
+
+def test_backprop_matches_central_differences():
+    rng = np.random.default_rng(7)
+    p = _rand_params(rng)
+    X = rng.standard_normal((16, S.N_IN)) * 0.5
+    t = rng.standard_normal(16)
+    loss, g = S.loss_and_grads(p, X, t)
+    eps = 1e-6
+    for k, shape in S.PARAM_SHAPES:
+        flat = p[k].reshape(-1)
+        idx = rng.choice(flat.size, size=min(12, flat.size), replace=False)
+        for j in idx:
+            old = flat[j]
+            flat[j] = old + eps
+            lp = S.loss_and_grads(p, X, t)[0]
+            flat[j] = old - eps
+            lm = S.loss_and_grads(p, X, t)[0]
+            flat[j] = old
+            fd = (lp - lm) / (2 * eps)
+            an = g[k].reshape(-1)[j]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9, (k, j, fd, an)
+    assert loss > 0
+
+
+def test_gradient_vanishes_at_a_perfect_fit():
+    rng = np.random.default_rng(8)
+    p = _rand_params(rng)
+    X = rng.standard_normal((9, S.N_IN))
+    out, _ = S.forward(p, X)
+    loss, g = S.loss_and_grads(p, X, out)
+    assert loss == 0.0
+    for k, _ in S.PARAM_SHAPES:
+        assert np.all(g[k] == 0.0)
+
+
+def test_adam_first_and_second_step():
+    p = {k: np.zeros(s) for k, s in S.PARAM_SHAPES}
+    g = {k: np.full(s, 0.25) for k, s in S.PARAM_SHAPES}
+    g["b3"] = np.array([-2.0])
+    st = {}
+    S.adam_step(p, g, st, lr=0.01)
+    # bias-corrected first step: m^ = g, v^ = g^2
+    np.testing.assert_allclose(p["W1"], -0.01 * 0.25 / (0.25 + 1e-8), rtol=1e-15)
+    np.testing.assert_allclose(p["b3"], 0.01 * 2.0 / (2.0 + 1e-8), rtol=1e-15)
+    g2 = {k: np.full(s, -1.0) for k, s in S.PARAM_SHAPES}
+    S.adam_step(p, g2, st, lr=0.01)
+    m = 0.9 * (0.1 * 0.25) + 0.1 * (-1.0)
+    v = 0.999 * (0.001 * 0.0625) + 0.001 * 1.0
+    want = -0.01 * 0.25 / (0.25 + 1e-8) - 0.01 * (m / (1 - 0.81)) / (math.sqrt(v / (1 - 0.999 ** 2)) + 1e-8)
+    np.testing.assert_allclose(p["W2"], want, rtol=1e-13)
+
+
+def test_splitmix64_published_outputs():
+    # the generator seeded with 0: its first two outputs (Steele, Lea and Flood 2014)
+    assert S.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert S.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+def test_holdout_mask_fraction_and_determinism():
+    rng = np.random.default_rng(3)
+    bx = rng.integers(-5000, 5000, 40000)
+    by = rng.integers(-5000, 5000, 40000)
+    m = S.holdout_mask(bx, by, 17, 0.02)
+    assert abs(m.mean() - 0.02) < 5 * math.sqrt(0.02 * 0.98 / 40000)
+    assert np.array_equal(m, S.holdout_mask(bx, by, 17, 0.02))
+    assert not np.array_equal(m, S.holdout_mask(bx, by, 18, 0.02))
+    assert not S.holdout_mask(bx, by, 17, 0.0).any() and S.holdout_mask(bx, by, 17, 1.0).all()
+
+
+def test_holdout_check_cases():
+    r = S.holdout_check([-10.0, -50.0, -12.0], [-10.2, -80.0, -11.0], max_pred=-9.0, window=20.0, max_err=0.5)
+    # the second dummy is far below the maximum on both sides: not significant
+    assert r["n_significant"] == 2 and r["max_abs_err"] == pytest.approx(1.0) and r["fallback"]
+    r = S.holdout_check([-10.0, -12.0], [-10.1, -12.2], max_pred=-10.0, window=20.0, max_err=0.5)
+    assert not r["fallback"] and r["max_abs_err"] == pytest.approx(0.2)
+    assert S.holdout_check([np.nan], [-1.0], -1.0, 20.0, 0.5)["fallback"]
+    e = S.holdout_check([], [], -1.0, 20.0, 0.5)
+    assert e["n_holdout"] == 0 and not e["fallback"]
+
+
+def test_pack_roundtrip():
+    rng = np.random.default_rng(2)
+    p = _rand_params(rng)
+    flat = S.pack(p)
+    assert flat.size == S.N_PARAMS == 256 * 445 + 256 + 256 * 256 + 256 + 256 + 1
+    q = S.unpack(flat)
+    for k, _ in S.PARAM_SHAPES:
+        assert np.array_equal(p[k], q[k])
