@@ -19,13 +19,28 @@ likelihood stays the judge of its error.  Definitions written out here:
   leaves the image is "clipped": the exact likelihood drops the outside
   pixels, which the network cannot see, so clipped dummies always take the
   exact likelihood.
+* Exact window term.  With lambda_j = bg + I0 g_j (Eq. object) the Poisson
+  term of Eq. likelihood splits, pixel by pixel, into
+  ``z log(lambda/z) - (lambda - z) = [z - z log z + z log bg - bg]
+  + [z log(1 + I0 g / bg) - I0 g]``.  The first bracket depends on the image
+  alone; summed over the window it is ``T(cx, cy) = sum (z - z log z) +
+  log(bg) sum z - P^2 bg`` (0 log 0 = 0), which a box filter gives for every
+  window of a frame.  The network learns only the second bracket, the
+  residual ``r = ll - T``, which involves the pixels near the spot alone;
+  the part of ll that sums noise over all 441 pixels is computed exactly.
 * Network: ``z1 = W1 x + b1, a1 = silu(z1), z2 = W2 a1 + b2, a2 = silu(z2),
   out = w3 . a2 + b3`` with ``silu(t) = t / (1 + exp(-t))``; W1 is 256 x 445,
-  W2 256 x 256.  The prediction of the log-likelihood is ``mean + scale * out``
-  with the label mean and standard deviation of the training rows.
-* Training: mean squared error of ``out`` against the standardised label
-  ``(ll - mean) / scale`` over a minibatch; gradients by backpropagation; the
-  Adam update (Kingma and Ba, 2015) with bias-corrected moments.
+  W2 256 x 256.  The prediction of the log-likelihood is
+  ``T + mean + scale * out`` with the mean and standard deviation of the
+  training rows' residual labels.
+* Training: squared error of ``out`` against the standardised label
+  ``(r - mean) / scale``, averaged over a minibatch; gradients by
+  backpropagation; the Adam update (Kingma and Ba, 2015) with bias-corrected
+  moments.  A "censored" row carries a floor instead of its log-likelihood
+  (the exact value lies below it, so far below the step's best dummy that its
+  weight is negligible; the label is ``floor - T``): its error counts only
+  where ``out`` exceeds the label, ``max(out - label, 0)^2``, the one-sided
+  loss of censored regression.
 * Held-out check: a dummy is held out when a splitmix64 hash (Steele, Lea
   and Flood, 2014) of its cell index and the step's salt falls below the
   requested fraction; its exact likelihood is computed beside the
@@ -91,6 +106,18 @@ def features(image: np.ndarray, x, y, i0, sigma, bg: float, i0_ref: float, sigma
     return X, clipped
 
 
+def window_term(image: np.ndarray, x, y, bg: float) -> np.ndarray:
+    """T(cx, cy) of the windows around the states' nearest pixels (windows inside the image)."""
+    z = image.astype(np.float64)
+    e = np.where(z > 0, z - z * np.log(np.where(z > 0, z, 1.0)), 0.0) + np.log(bg) * z
+    cx = np.floor(np.asarray(x, np.float64) + 0.5).astype(np.int64)
+    cy = np.floor(np.asarray(y, np.float64) + 0.5).astype(np.int64)
+    out = np.empty(cx.shape[0])
+    for i in range(cx.shape[0]):
+        out[i] = e[cy[i] - R:cy[i] + R + 1, cx[i] - R:cx[i] + R + 1].sum() - P * P * bg
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Forward and backward passes
 # ----------------------------------------------------------------------------
@@ -113,15 +140,19 @@ def forward(params: dict, X: np.ndarray):
     return out, {"X": X, "z1": z1, "a1": a1, "z2": z2, "a2": a2}
 
 
-def predict_ll(params: dict, mean: float, scale: float, X: np.ndarray) -> np.ndarray:
-    return mean + scale * forward(params, X)[0]
+def predict_ll(params: dict, mean: float, scale: float, X: np.ndarray, T) -> np.ndarray:
+    """Predicted log-likelihood: the exact window term plus the network's residual."""
+    return np.asarray(T, np.float64) + mean + scale * forward(params, X)[0]
 
 
-def loss_and_grads(params: dict, X: np.ndarray, t: np.ndarray):
-    """Mean squared error L = mean((out - t)^2) and its gradient with respect to every parameter."""
+def loss_and_grads(params: dict, X: np.ndarray, t: np.ndarray, censored=None):
+    """Mean squared error L = mean(d^2), d = out - t (0 where a censored row has out <= t), and its
+    gradient with respect to every parameter."""
     out, c = forward(params, X)
     n = X.shape[0]
     d = out - t
+    if censored is not None:
+        d = np.where(np.asarray(censored, bool) & (d < 0), 0.0, d)
     loss = float(np.mean(d * d))
     g_out = 2.0 * d / n                                  # dL/d out
     g = {"w3": c["a2"].T @ g_out, "b3": np.array([g_out.sum()])}

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/pcsir.h: context lifetime,
 // argument checks, workspace, and the kernel sequence of one filter step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,11 @@ struct pcsir_ctx {
   bool failed = false;
   int last_kind = -1;
   int64_t last_N = 0;
+  // attached likelihood surrogate: per-step held-out list and statistics
+  SurStep sur{};
+  bool sur_on = false;
+  bool sur_ran = false;          // the last pcSIR step used the surrogate
+  unsigned long long sur_steps = 0;
   // stage timing: 5 events per step slot
   std::vector<cudaEvent_t> events;
   int timing_slots = 0;
@@ -212,9 +218,20 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
   cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  SurStep sp{};
+  if (ctx->sur_on && (int64_t)W * H > sur_max_pixels(ctx->sur.sur))
+    return fail(ctx, PCSIR_ERANGE, "image larger than the surrogate's max_pixels");
+  if (ctx->sur_on) {
+    sp = ctx->sur;
+    sp.salt = ctx->sur_steps;
+    e = cudaMemsetAsync(sp.stats, 0, sizeof(SurStats), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of surrogate statistics");
+  }
   e = launch_pcsir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, h, image, W, H, ctx->num_sms, s,
-                         se);
+                         se, ctx->sur_on ? &sp : nullptr);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels");
+  if (ctx->sur_on) ctx->sur_steps++;
+  ctx->sur_ran = ctx->sur_on;
   e = launch_resample(ctx->b, ctx->cfg.state_dtype, state, N, u0, WSRC_BINS, ctx->cfg.keep, ctx->num_sms, s);
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
@@ -335,6 +352,60 @@ pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* o) {
   }
   o->ancestor = b.anc;
   o->weight = b.wout;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_attach_surrogate(pcsir_ctx* ctx, pcsir_surrogate* sur, double holdout_frac, int32_t min_holdout,
+                                    double window, double max_err) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (!sur) {
+    ctx->sur_on = false;
+    return PCSIR_OK;
+  }
+  if (!(holdout_frac >= 0.0 && holdout_frac <= 1.0) || min_holdout < 0 || !(window >= 0.0) || !(max_err >= 0.0))
+    return fail(ctx, PCSIR_EINVAL, "invalid held-out fraction, window or error threshold");
+  if (ctx->cfg.patch != PCSIR_SUR_PATCH || ctx->cfg.lik_kind != PCSIR_LIK_POISSON)
+    return fail(ctx, PCSIR_EINVAL, "the surrogate models the Poisson likelihood over a 21 x 21 patch");
+  SurStep& sp = ctx->sur;
+  if (!sp.stats) {
+    constexpr int HO_CAP = 1 << 16;
+    if (!(dev_alloc(ctx, &sp.ho_bin, HO_CAP) && dev_alloc(ctx, &sp.ho_ll, HO_CAP) && dev_alloc(ctx, &sp.stats, 1))) {
+      sp.stats = nullptr;
+      return fail(ctx, PCSIR_ENOMEM, "held-out list allocation");
+    }
+    sp.ho_cap = HO_CAP;
+    cudaError_t e = cudaMemset(sp.stats, 0, sizeof(SurStats));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "held-out statistics");
+  }
+  sp.sur = sur;
+  sp.frac = holdout_frac;
+  sp.min_holdout = min_holdout;
+  sp.window = window;
+  sp.max_err = max_err;
+  ctx->sur_on = true;
+  ctx->sur_steps = 0;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_surrogate_last_check(pcsir_ctx* ctx, pcsir_surrogate_check* out) {
+  if (!ctx || !out) return PCSIR_EINVAL;
+  if (!ctx->sur_ran || ctx->last_kind != 1) return fail(ctx, PCSIR_ESTATE, "the last step did not use a surrogate");
+  SurStats st{};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ctx->sur.stats, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading surrogate statistics");
+  std::memset(out, 0, sizeof(*out));
+  const int64_t nb = ctx->host_res->n_bins;
+  const int64_t nho = std::min<int64_t>(st.n_ho, ctx->sur.ho_cap);
+  out->n_dummies = nb;
+  out->n_holdout = nho;
+  out->n_significant = st.n_sig;
+  out->n_clipped = st.n_clipped;
+  out->fallback = st.fallback ? 1 : 0;
+  out->n_exact = st.fallback ? nb : (int64_t)st.n_ho + (int64_t)st.n_clipped;
+  out->max_abs_err = st.max_err;
+  out->rms_err = nho > 0 ? std::sqrt(st.sum_sq / (double)nho) : 0.0;
   return PCSIR_OK;
 }
 

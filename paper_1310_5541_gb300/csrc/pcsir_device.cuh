@@ -471,4 +471,42 @@ __device__ __forceinline__ long long q_of_wtilde(df w, int sq) {
 // Atomic OR of an error flag into the control block.
 __device__ __forceinline__ void raise_flag(Control* ctl, unsigned f) { atomicOr(&ctl->err, f); }
 
+// ---------------------------------------------------------------------------
+// Likelihood surrogate: the input patch and the held-out selection.
+// ---------------------------------------------------------------------------
+constexpr int SUR_R = PCSIR_SUR_PATCH / 2;
+
+// Nearest pixel (cx, cy) = (floor(x + 0.5), floor(y + 0.5)); false when the
+// 21 x 21 patch around it leaves the image (or the position is not finite).
+__device__ __forceinline__ bool sur_origin(double x, double y, int W, int H, int* cx, int* cy) {
+  const double fx = floor(x + 0.5), fy = floor(y + 0.5);
+  if (!(fx - SUR_R >= 0.0 && fx + SUR_R <= (double)(W - 1) && fy - SUR_R >= 0.0 && fy + SUR_R <= (double)(H - 1)))
+    return false;
+  *cx = (int)fx;
+  *cy = (int)fy;
+  return true;
+}
+
+// One output of the splitmix64 generator (Steele, Lea and Flood, 2014) whose
+// state has just become x - 0x9E3779B97F4A7C15.
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Held-out threshold floor(max(frac, min_holdout / B) * 2^24) (2^24: every cell).
+__device__ __forceinline__ unsigned sur_holdout_threshold(double frac, int min_holdout, unsigned B) {
+  double f = frac;
+  if (B > 0u) f = fmax(f, (double)min_holdout / (double)B);
+  return f >= 1.0 ? (1u << 24) : (unsigned)floor(f * 16777216.0);
+}
+
+__device__ __forceinline__ bool sur_held(int bx, int by, unsigned long long salt, unsigned thr) {
+  const unsigned long long key = (unsigned long long)(unsigned)bx | ((unsigned long long)(unsigned)by << 32);
+  const unsigned long long h = splitmix64(key + salt * 0x9E3779B97F4A7C15ull);
+  return (unsigned)(h >> 40) < thr;
+}
+
 }  // namespace pcsir

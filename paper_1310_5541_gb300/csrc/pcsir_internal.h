@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pcsir.h"
+#include "../../include/pcsir_surrogate.h"
 
 namespace pcsir {
 
@@ -86,10 +87,43 @@ struct StageEvents {
   cudaEvent_t* ev;  // 5 events of the current step, or nullptr
 };
 
+// Surrogate-assisted dummy likelihoods of one pcSIR step (pcsir_surrogate.cu):
+// per-step counters and the held-out check's result, zeroed with the control
+// block.
+struct SurStats {
+  unsigned int n_ho;       // held-out dummies found (entries past the list capacity are dropped)
+  unsigned int n_clipped;  // dummies whose patch leaves the image
+  unsigned int n_sig;      // significant held-out dummies
+  unsigned int fallback;   // 1: every dummy takes the exact likelihood
+  unsigned int bad;        // a prediction was not finite
+  unsigned int n_nonfinite_err;
+  double max_err;          // largest error over the significant held-out dummies
+  double sum_sq;           // sum of squared errors over the held-out dummies
+};
+
+struct SurStep {
+  const pcsir_surrogate* sur;
+  unsigned long long salt;  // step counter since the attach
+  double frac;              // held-out fraction
+  int min_holdout;          // at least this many held-out dummies (when there are enough)
+  int ho_cap;               // capacity of the held-out list
+  double window;            // significance window below the maximum prediction
+  double max_err;           // fallback threshold
+  int* ho_bin;              // held-out list: bin index and exact log-likelihood
+  double* ho_ll;
+  SurStats* stats;
+};
+
 // Kernel launchers (pcsir_kernels.cu / pcsir_resample.cu).
+// sur == nullptr: exact likelihood of every dummy.
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
-                               int num_sms, cudaStream_t s, StageEvents se);
+                               int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur = nullptr);
+// largest image the surrogate's window-term buffer holds (pcsir_surrogate.cu)
+int64_t sur_max_pixels(const pcsir_surrogate* s);
+// surrogate predictions of the non-clipped dummies and the held-out check (pcsir_surrogate.cu)
+cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const ModelParams& m, const float* img, int W,
+                            int H, cudaStream_t s);
 cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                              const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
                              cudaStream_t s, StageEvents se, int keep);

@@ -367,8 +367,23 @@ __device__ __forceinline__ void block_max_llq_to_global(long long v, Control* ct
   }
 }
 
+// With SUR (a likelihood surrogate is attached) the exact likelihood is
+// evaluated only for dummies whose surrogate patch leaves the image (their
+// value is final) and for held-out dummies (their value goes to the held-out
+// list, and the surrogate's prediction to bin_ll).
+struct SurBins {
+  unsigned long long salt;
+  double frac;
+  int min_holdout;
+  int ho_cap;
+  int* ho_bin;
+  double* ho_ll;
+  SurStats* stats;
+};
+
+template <bool SUR>
 __global__ void __launch_bounds__(BIN_THREADS)
-k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq) {
+k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq, SurBins sb) {
   constexpr int NG = BIN_THREADS / BIN_GROUP;
   __shared__ float scratch[NG][4 * MAXP];
   __shared__ int red[NG][3 * (BIN_GROUP / 32)];
@@ -376,6 +391,7 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
   const unsigned B = b.ctl->nocc;
   const size_t hcap = size_t(1) << b.hbits;
   const int64_t bs = b.bin_stride;
+  const unsigned thr = SUR ? sur_holdout_threshold(sb.frac, sb.min_holdout, B) : 0u;
   double mymax = -INFINITY;
   for (unsigned bi = blockIdx.x * NG + group; bi < B; bi += gridDim.x * NG) {
     const unsigned g = b.occ[bi];
@@ -396,8 +412,54 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
       for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = mean[c];
       b.hrank[g] = bi;
     }
+    bool clipped = false, held = false;
+    if (SUR) {
+      int cx, cy;
+      clipped = !sur_origin(mean[0], mean[1], W, H, &cx, &cy);
+      held = !clipped && sur_held(bx, by, sb.salt, thr);
+      if (!clipped && !held) continue;  // uniform over the group: the surrogate predicts this dummy
+    }
     double ll = ll_to_double(group_loglik<BIN_GROUP>(img, W, H, lik_pos(mean[0], mean[1], mean[4]), lp,
                                                      scratch[group], red[group], group, gtid));
+    if (!isfinite(ll)) {
+      if (gtid == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      ll = -INFINITY;
+    }
+    if (SUR && held) {
+      if (gtid == 0) {
+        const unsigned slot = atomicAdd(&sb.stats->n_ho, 1u);
+        if (slot < (unsigned)sb.ho_cap) {
+          sb.ho_bin[slot] = (int)bi;
+          sb.ho_ll[slot] = ll;
+        }
+      }
+      continue;
+    }
+    if (SUR && gtid == 0) atomicAdd(&sb.stats->n_clipped, 1u);
+    if (gtid == 0) b.bin_ll[bi] = ll;
+    mymax = fmax(mymax, ll);
+  }
+  block_max_to_global(mymax, b.ctl);
+}
+
+// Exact likelihood of every dummy when the held-out check rejected the
+// surrogate's predictions (stats->fallback); otherwise returns at once.  The
+// dummy states are those k_bins stored, so the values equal the plain step's.
+__global__ void __launch_bounds__(BIN_THREADS)
+k_bins_fallback(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
+                const SurStats* __restrict__ stats) {
+  if (*(volatile const unsigned*)&stats->fallback == 0u) return;
+  constexpr int NG = BIN_THREADS / BIN_GROUP;
+  __shared__ float scratch[NG][4 * MAXP];
+  __shared__ int red[NG][3 * (BIN_GROUP / 32)];
+  const int group = threadIdx.x / BIN_GROUP, gtid = threadIdx.x % BIN_GROUP;
+  const unsigned B = b.ctl->nocc;
+  const int64_t bs = b.bin_stride;
+  double mymax = -INFINITY;
+  for (unsigned bi = blockIdx.x * NG + group; bi < B; bi += gridDim.x * NG) {
+    const double x = b.dummy[bi], y = b.dummy[bs + bi], a = b.dummy[4 * bs + bi];
+    double ll = ll_to_double(group_loglik<BIN_GROUP>(img, W, H, lik_pos(x, y, a), lp, scratch[group], red[group],
+                                                     group, gtid));
     if (!isfinite(ll)) {
       if (gtid == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
       ll = -INFINITY;
@@ -691,14 +753,26 @@ static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
 
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
-                               int num_sms, cudaStream_t s, StageEvents se) {
+                               int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur) {
   const long long hq = llrint(h * 2147483648.0);
   cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
                                      : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
   if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
   const LikParams lp = make_lik(m);
-  k_bins<<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq);
-  if ((e = cudaGetLastError()) != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
+  if (sur == nullptr) {
+    k_bins<false><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, SurBins{});
+    e = cudaGetLastError();
+  } else {
+    const SurBins sb{sur->salt, sur->frac, sur->min_holdout, sur->ho_cap, sur->ho_bin, sur->ho_ll, sur->stats};
+    k_bins<true><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, sb);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_sur_step(*sur, b, m, img, W, H, s);
+    if (e == cudaSuccess) {
+      k_bins_fallback<<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, sur->stats);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
   k_binred<<<num_sms * 2, RED_THREADS, 0, s>>>(b, N, weight_scale_bits(N));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return mark(se, 3, s);

@@ -8,6 +8,7 @@ Importing this module fails loudly when the library has not been built.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -51,6 +52,23 @@ class pcsir_target(ctypes.Structure):
                 ("bg", ctypes.c_double), ("patch", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class pcsir_surrogate_config(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("i0_ref", ctypes.c_double), ("sigma_ref", ctypes.c_double), ("max_pixels", ctypes.c_int64)]
+
+
+class pcsir_surrogate_check(ctypes.Structure):
+    _fields_ = [("n_dummies", ctypes.c_int64), ("n_exact", ctypes.c_int64), ("n_holdout", ctypes.c_int64),
+                ("n_significant", ctypes.c_int64), ("n_clipped", ctypes.c_int64), ("max_abs_err", ctypes.c_double),
+                ("rms_err", ctypes.c_double), ("fallback", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# sizes of pcsir_surrogate.h
+SUR_PATCH, SUR_INPUTS, SUR_HIDDEN = 21, 445, 256
+SUR_NPARAMS = 256 * 445 + 256 + 256 * 256 + 256 + 256 + 1
+SUR_ROW = 448  # stored inputs per dataset row
+
+
 class PcsirError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
@@ -87,6 +105,24 @@ def _load():
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
         "pcsir_gemm_bf16": ([P, I64, I64, P, I64, I64, P, I64, I32, I32, I32, I32, P], I32),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
+        "pcsir_surrogate_create": ([ctypes.POINTER(pcsir_surrogate_config), ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir_surrogate_destroy": ([P], I32),
+        "pcsir_surrogate_last_error": ([P], ctypes.c_char_p),
+        "pcsir_surrogate_init": ([P, ctypes.c_uint64, P], I32),
+        "pcsir_surrogate_set_params": ([P, P, D, D], I32),
+        "pcsir_surrogate_get_params": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+        "pcsir_surrogate_add": ([P, P, I64, I64, P, D, P, I32, I32, D, D, P], I32),
+        "pcsir_surrogate_rows": ([P, ctypes.POINTER(ctypes.c_int64)], I32),
+        "pcsir_surrogate_clear": ([P, P], I32),
+        "pcsir_surrogate_dataset": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                     ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir_surrogate_fit_scale": ([P, I64, I64], I32),
+        "pcsir_surrogate_train": ([P, I64, I64, I32, D, ctypes.c_uint64, P, P], I32),
+        "pcsir_surrogate_grads": ([P, I64, I32, P, ctypes.POINTER(ctypes.c_double)], I32),
+        "pcsir_surrogate_predict_rows": ([P, I64, I64, P, P], I32),
+        "pcsir_surrogate_predict": ([P, P, I64, I64, P, I32, I32, D, D, P, P], I32),
+        "pcsir_attach_surrogate": ([P, P, D, I32, D, D], I32),
+        "pcsir_surrogate_last_check": ([P, ctypes.POINTER(pcsir_surrogate_check)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -202,7 +238,8 @@ class _CudaArray:
                                          "version": 2, "strides": None}
 
 
-_TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.int64: "<i8"}
+_TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.int64: "<i8",
+            torch.int16: "<i2", torch.uint8: "|u1"}
 
 
 def _from_ptr(ptr, shape, dtype):
@@ -359,3 +396,127 @@ def gemm_bf16(A, B, C=None, accumulate=False, stream=None):
 
 def version():
     return lib.pcsir_version().decode()
+
+
+class Surrogate:
+    """Owns one ``pcsir_surrogate``: the likelihood network, its training state and its dataset."""
+
+    def __init__(self, capacity, batch=4096, i0_ref=128.0, sigma_ref=1.5, max_pixels=1 << 20):
+        cfg = pcsir_surrogate_config(capacity=int(capacity), batch=int(batch), reserved=0, i0_ref=float(i0_ref),
+                                     sigma_ref=float(sigma_ref), max_pixels=int(max_pixels))
+        h = ctypes.c_void_p()
+        st = lib.pcsir_surrogate_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise PcsirError(st, "pcsir_surrogate_create failed")
+        self.handle = h
+        self.cfg = cfg
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pcsir_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise PcsirError(st, lib.pcsir_surrogate_last_error(self.handle).decode())
+
+    def init(self, seed, stream=None):
+        self._check(lib.pcsir_surrogate_init(self.handle, int(seed), _stream_ptr(stream)))
+
+    def set_params(self, flat, label_mean=0.0, label_scale=1.0):
+        a = np.ascontiguousarray(np.asarray(flat, np.float32))
+        assert a.size == SUR_NPARAMS
+        self._check(lib.pcsir_surrogate_set_params(self.handle, a.ctypes.data, float(label_mean), float(label_scale)))
+
+    def get_params(self):
+        a = np.empty(SUR_NPARAMS, np.float32)
+        m, s = ctypes.c_double(), ctypes.c_double()
+        self._check(lib.pcsir_surrogate_get_params(self.handle, a.ctypes.data, ctypes.byref(m), ctypes.byref(s)))
+        return a, m.value, s.value
+
+    def add(self, dummy, ll, image, bg, psf_sigma, label_floor=-math.inf, stream=None):
+        """Append rows for the states ``dummy`` [5, n] (float64 view with unit column stride) with labels
+        max(``ll``, ``label_floor``)."""
+        assert dummy.dtype == torch.float64 and dummy.is_cuda and dummy.stride(1) == 1
+        _check_cuda(ll, "ll", torch.float64)
+        _check_cuda(image, "image", torch.float32)
+        n = dummy.shape[1]
+        H, W = image.shape
+        self._check(lib.pcsir_surrogate_add(self.handle, _ptr(dummy), dummy.stride(0), n, _ptr(ll),
+                                            float(label_floor), _ptr(image), W, H, float(bg), float(psf_sigma),
+                                            _stream_ptr(stream)))
+
+    def rows(self):
+        n = ctypes.c_int64()
+        self._check(lib.pcsir_surrogate_rows(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def clear(self, stream=None):
+        self._check(lib.pcsir_surrogate_clear(self.handle, _stream_ptr(stream)))
+
+    def dataset(self):
+        """(inputs [rows, 448] as int16 bit patterns of bf16, labels [rows] float32, censored [rows] uint8) views."""
+        xp, yp, cp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(lib.pcsir_surrogate_dataset(self.handle, ctypes.byref(xp), ctypes.byref(yp), ctypes.byref(cp)))
+        n = self.rows()
+        if n == 0:
+            return None, None, None
+        return (_from_ptr(xp.value, (n, SUR_ROW), torch.int16), _from_ptr(yp.value, (n,), torch.float32),
+                _from_ptr(cp.value, (n,), torch.uint8))
+
+    def fit_scale(self, begin, end):
+        self._check(lib.pcsir_surrogate_fit_scale(self.handle, int(begin), int(end)))
+
+    def train(self, begin, end, steps, lr, seed, loss=None, stream=None):
+        if loss is not None:
+            _check_cuda(loss, "loss", torch.float32)
+            assert loss.numel() >= steps
+        self._check(lib.pcsir_surrogate_train(self.handle, int(begin), int(end), int(steps), float(lr), int(seed),
+                                              _ptr(loss), _stream_ptr(stream)))
+
+    def grads(self, begin, n):
+        g = np.empty(SUR_NPARAMS, np.float32)
+        loss = ctypes.c_double()
+        self._check(lib.pcsir_surrogate_grads(self.handle, int(begin), int(n), g.ctypes.data, ctypes.byref(loss)))
+        return g, loss.value
+
+    def predict_rows(self, begin, end, out=None, stream=None):
+        """Predictions of dataset rows in label units (the residual, without the window term)."""
+        if out is None:
+            out = torch.empty(end - begin, dtype=torch.float64, device="cuda")
+        self._check(lib.pcsir_surrogate_predict_rows(self.handle, int(begin), int(end), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def predict(self, dummy, image, bg, psf_sigma, out=None, stream=None):
+        assert dummy.dtype == torch.float64 and dummy.is_cuda and dummy.stride(1) == 1
+        _check_cuda(image, "image", torch.float32)
+        n = dummy.shape[1]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=dummy.device)
+        H, W = image.shape
+        self._check(lib.pcsir_surrogate_predict(self.handle, _ptr(dummy), dummy.stride(0), n, _ptr(image), W, H,
+                                                float(bg), float(psf_sigma), _ptr(out), _stream_ptr(stream)))
+        return out
+
+
+def attach_surrogate(ctx, sur, holdout_frac=0.02, min_holdout=32, window=20.0, max_err=1.0):
+    """Let ``pcsir_step`` on ``ctx`` use ``sur`` for the dummies' log-likelihoods (``sur=None`` detaches)."""
+    st = lib.pcsir_attach_surrogate(ctx.handle, sur.handle if sur is not None else None, float(holdout_frac),
+                                    int(min_holdout), float(window), float(max_err))
+    if st != OK:
+        ctx._raise(st)
+    ctx.surrogate = sur
+
+
+def surrogate_last_check(ctx):
+    c = pcsir_surrogate_check()
+    st = lib.pcsir_surrogate_last_check(ctx.handle, ctypes.byref(c))
+    if st != OK:
+        ctx._raise(st)
+    return {k: getattr(c, k) for k, _ in pcsir_surrogate_check._fields_ if k != "reserved"}

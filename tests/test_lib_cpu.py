@@ -1,7 +1,8 @@
 """Host-side checks of the C-ABI library that need no GPU: it loads, exports
-every entry point include/pcsir.h declares, its structs have the header's
-layout, and argument errors are rejected on the host."""
+every entry point the headers in include/ declare, its structs have the
+headers' layout, and argument errors are rejected on the host."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -9,7 +10,7 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "pcsir.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -23,14 +24,14 @@ def binding():
 
 
 def _declared_functions():
-    src = open(HEADER).read()
+    src = "\n".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
 
 
 def test_exports_every_declared_entry_point(binding):
     names = _declared_functions()
-    assert "pcsir_step" in names and "sir_step" in names and len(names) >= 10
+    assert "pcsir_step" in names and "sir_step" in names and "pcsir_surrogate_train" in names and len(names) >= 30
     lib = ctypes.CDLL(binding.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
@@ -42,8 +43,12 @@ def test_struct_layout_matches_header(binding, tmp_path):
         "pcsir_config": [f[0] for f in binding.pcsir_config._fields_],
         "pcsir_result": [f[0] for f in binding.pcsir_result._fields_],
         "pcsir_outputs": [f[0] for f in binding.pcsir_outputs._fields_],
+        "pcsir_target": [f[0] for f in binding.pcsir_target._fields_],
+        "pcsir_surrogate_config": [f[0] for f in binding.pcsir_surrogate_config._fields_],
+        "pcsir_surrogate_check": [f[0] for f in binding.pcsir_surrogate_check._fields_],
     }
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', "int main(void){"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', '#include "pcsir_surrogate.h"',
+             "int main(void){", 'printf("NPARAMS %d\\n", PCSIR_SUR_NPARAMS);']
     for s, fs in fields.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
         for f in fs:
@@ -54,6 +59,7 @@ def test_struct_layout_matches_header(binding, tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                  check=True).stdout.splitlines())
+    assert int(out["NPARAMS"]) == binding.SUR_NPARAMS
     for s, fs in fields.items():
         cls = getattr(binding, s)
         assert int(out[s]) == ctypes.sizeof(cls), s
@@ -78,6 +84,21 @@ def test_invalid_configs_rejected_on_host(binding):
     assert lib.sir_step(None, None, 1, None, 1, 1, None, 0.5, None, None) == binding.EINVAL
     assert lib.pcsir_destroy(None) == binding.OK
     assert b"pcsir" in lib.pcsir_version()
+
+
+def test_invalid_surrogate_configs_rejected_on_host(binding):
+    lib = binding.lib
+    base = dict(capacity=1000, batch=256, reserved=0, i0_ref=128.0, sigma_ref=1.5, max_pixels=4096)
+    for upd in [dict(capacity=0), dict(batch=100), dict(batch=0), dict(batch=65536 + 128), dict(reserved=1),
+                dict(i0_ref=0.0), dict(sigma_ref=-1.0), dict(i0_ref=float("nan")), dict(max_pixels=0)]:
+        cfg = binding.pcsir_surrogate_config(**{**base, **upd})
+        h = ctypes.c_void_p(123)
+        assert lib.pcsir_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)) == binding.EINVAL, upd
+        assert not h.value
+    assert lib.pcsir_surrogate_create(None, None) == binding.EINVAL
+    assert lib.pcsir_surrogate_destroy(None) == binding.OK
+    assert lib.pcsir_attach_surrogate(None, None, 0.02, 32, 30.0, 1.0) == binding.EINVAL
+    assert lib.pcsir_surrogate_train(None, 0, 1, 1, 1e-3, 1, None, None) == binding.EINVAL
 
 
 def test_autotune_defaults_without_cache(tmp_path, monkeypatch):

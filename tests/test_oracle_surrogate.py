@@ -52,6 +52,33 @@ def test_features_match_pixel_loop():
     assert not clipped[0] and clipped[4] and clipped[5]
 
 
+def test_window_term_splits_the_poisson_likelihood():
+    # ll - T equals the spot-only sum  sum_j z_j log(1 + I0 g_j / bg) - I0 g_j  (closed form, pixel loop)
+    from oracle import pcsir_oracle as O
+    from paper_1310_5541_gb300 import synth
+
+    rng = np.random.default_rng(5)
+    H, W = 40, 44
+    img = rng.poisson(synth.render(W, H, 21.3, 19.6, 100.0, 10.0, 1.5)).astype(np.float32)
+    img[5, 7] = 0.0  # a zero count inside some windows
+    xs = np.array([21.3, 20.6, 14.2, 23.9])
+    ys = np.array([19.6, 20.4, 15.1, 12.5])
+    i0 = np.array([100.0, 90.0, 120.0, 0.0])
+    m = synth.Model(patch=21)
+    ll = O.loglik(img, xs, ys, i0, m)
+    T = S.window_term(img, xs, ys, 10.0)
+    for n in range(len(xs)):
+        cx, cy = math.floor(xs[n] + 0.5), math.floor(ys[n] + 0.5)
+        r = 0.0
+        for py in range(cy - 10, cy + 11):
+            for px in range(cx - 10, cx + 11):
+                g = math.exp(-((px - xs[n]) ** 2 + (py - ys[n]) ** 2) / (2 * 1.5 ** 2))
+                r += float(img[py, px]) * math.log1p(i0[n] * g / 10.0) - i0[n] * g
+        assert ll[n] - T[n] == pytest.approx(r, rel=1e-9, abs=1e-8)
+    # I0 = 0: the prediction lambda = bg everywhere, and ll is the window term itself
+    assert ll[3] == pytest.approx(T[3], rel=1e-12)
+
+
 def test_silu_closed_forms():
     assert S.silu(0.0) == 0.0 and S.silu_grad(0.0) == 0.5
     t = np.array([-3.0, -0.5, 0.7, 4.0])
@@ -84,6 +111,34 @@ def test_backprop_matches_central_differences():
             an = g[k].reshape(-1)[j]
             assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9, (k, j, fd, an)
     assert loss > 0
+
+
+def test_censored_rows_count_only_above_their_floor():
+    rng = np.random.default_rng(9)
+    p = _rand_params(rng)
+    X = rng.standard_normal((16, S.N_IN)) * 0.5
+    out, _ = S.forward(p, X)
+    t = out + np.where(np.arange(16) % 2 == 0, 0.3, -0.3)  # even rows: output below the label
+    cens = np.arange(16) % 4 < 2                           # rows 0, 1, 4, 5, ...
+    loss, g = S.loss_and_grads(p, X, t, cens)
+    # censored rows with out below the floor (rows 0, 4, 8, 12) contribute nothing
+    keep = ~(cens & (np.arange(16) % 2 == 0))
+    assert loss == pytest.approx(np.sum(keep * 0.09) / 16, rel=1e-12)
+    # the same gradient as the plain loss over the counted rows, rescaled to the full batch
+    l2, g2 = S.loss_and_grads(p, X[keep], t[keep])
+    for k, _ in S.PARAM_SHAPES:
+        np.testing.assert_allclose(g[k], g2[k] * keep.sum() / 16, rtol=1e-12, atol=1e-15)
+    # and central differences agree with it
+    eps = 1e-6
+    flat = p["W2"].reshape(-1)
+    for j in rng.choice(flat.size, 6, replace=False):
+        old = flat[j]
+        flat[j] = old + eps
+        lp = S.loss_and_grads(p, X, t, cens)[0]
+        flat[j] = old - eps
+        lm = S.loss_and_grads(p, X, t, cens)[0]
+        flat[j] = old
+        assert abs((lp - lm) / (2 * eps) - g["W2"].reshape(-1)[j]) <= 1e-6 * max(1e-3, abs(g["W2"].reshape(-1)[j]))
 
 
 def test_gradient_vanishes_at_a_perfect_fit():
