@@ -244,6 +244,123 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
             "device_error": derr, "autotune": {"c": table.get("c"), "blocks_per_sm": table.get("blocks_per_sm")}}
 
 
+def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_cap=None):
+    """SIR vs pcSIR vs surrogate-pcSIR on the single-target workload at matched tracking RMSE.
+
+    The surrogate is trained first on pairs its own method generates: exact pcSIR
+    steps (N = 2^20, cells h in {0.02, 0.05, 0.1, 0.2, 0.5} px) over further
+    512 x 512 sequences of the same model, until ``rows_target`` (dummy inputs,
+    exact log-likelihood) rows are stored.  Then every method filters the same
+    ``n_seq`` sequences of ``n_frames`` frames with N particles and identical
+    noise and resampling uniforms; per method the tracking RMSE against the
+    ground truth and the device time per step (CUDA events around each step)
+    are reported.  At matched RMSE (within 5% of SIR's) the fastest cell size of
+    each pcSIR variant is picked.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, surrogate, synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    model = synth.Model(sigma_psf=SIGMA, I0=I0, bg=BG, patch=PATCH, q=Q)
+    out = {}
+    # training pairs from exact pcSIR runs
+    t0 = time.perf_counter()
+    Nc = 1 << 20
+    hs_c = (0.02, 0.05, 0.1, 0.2, 0.5)
+    pool_c = [torch.from_numpy(synth.make_noise(Nc, Q, seed + 9, j, np.float32)).to(dev) for j in range(4)]
+    sur = pcsir.Surrogate(capacity=rows_target + (1 << 20), batch=4096, i0_ref=128.0, sigma_ref=SIGMA,
+                          max_pixels=W_IMG * H_IMG)
+    ctx_c = pcsir.Context(Nc, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG)
+    i = 0
+    while sur.rows() < rows_target and i < 100000:
+        sq = synth.make_sequence(W_IMG, H_IMG, 10, model, seed + 500 + i)
+        st = torch.from_numpy(synth.initial_state(sq.gt[0], Nc, np.float32)).to(dev)
+        frames = ((torch.from_numpy(sq.images[k]).to(dev), pool_c[(i + k) % 4], synth.make_u0(seed + 500 + i, k))
+                  for k in range(sq.images.shape[0]))
+        surrogate.collect(ctx_c, sur, st, frames, hs_c[i % len(hs_c)], BG, SIGMA)
+        i += 1
+    ctx_c.close()
+    rows = sur.rows()
+    t1 = time.perf_counter()
+    sur.init(seed)
+    fit = surrogate.fit(sur, steps=train_steps, lr=2e-3, seed=3, val_frac=0.02, chunk=2000)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out["surrogate_training"] = {
+        "rows": rows, "sequences": i, "train_steps": train_steps, "batch": 4096, "collect_s": t1 - t0,
+        "train_s": t2 - t1, "val_rmse_nats": fit["val_rmse"], "val_max_nats": fit["val_max"],
+        "val_label_std_nats": fit["val_label_std"], "val_censored_above": fit["val_censored_above"],
+        "final_loss": float(fit["loss"][-500:].mean())}
+
+    # the comparison sequences
+    seqs = [synth.make_sequence(W_IMG, H_IMG, n_frames, model, seed + 90000 + r) for r in range(n_seq)]
+    imgs = [torch.from_numpy(sq.images).to(dev) for sq in seqs]
+    pool = [torch.from_numpy(synth.make_noise(N, Q, seed + 7, j, np.float32)).to(dev) for j in range(NOISE_POOL)]
+    ctx = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG)
+    ctx_s = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG)
+    pcsir.attach_surrogate(ctx_s, sur, holdout_frac=0.02, min_holdout=32, window=20.0, max_err=3.0)
+    stream = torch.cuda.current_stream()
+
+    def run(kind, h, frames_cap=None):
+        errs, ms, exact, dummies, fallbacks = [], [], 0, 0, 0
+        c = ctx_s if kind == "surrogate" else ctx
+        c.timing_enable(n_seq * n_frames)
+        for r, sq in enumerate(seqs):
+            st = torch.from_numpy(synth.initial_state(sq.gt[0], N, np.float32)).to(dev)
+            K = n_frames if frames_cap is None else min(n_frames, frames_cap)
+            for k in range(K):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                u0 = synth.make_u0(seed + 90000 + r, k)
+                a.record(stream)
+                if kind == "sir":
+                    pcsir.sir_step(c, st, imgs[r][k], pool[k % NOISE_POOL], u0, stream)
+                else:
+                    pcsir.pcsir_step(c, st, imgs[r][k], h, pool[k % NOISE_POOL], u0, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                res = c.last_result()
+                if res["device_error"]:
+                    raise RuntimeError("device error %d in %s h=%s" % (res["device_error"], kind, h))
+                if k >= 2:  # the first steps include one-time work
+                    ms.append(a.elapsed_time(b))
+                errs.append(np.array(res["estimate"][:2]) - sq.gt[k + 1, :2])
+                if kind == "surrogate":
+                    chk = pcsir.surrogate_last_check(c)
+                    exact += chk["n_exact"]
+                    dummies += chk["n_dummies"]
+                    fallbacks += chk["fallback"]
+        stages = np.array(c.timing_read(n_seq * n_frames))[2:].mean(axis=0)
+        c.timing_enable(0)
+        e = np.array(errs)
+        d = {"method": kind, "h": h, "rmse_px": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1)))),
+             "ms_per_step": float(np.mean(ms)), "steps_per_s": 1e3 / float(np.mean(ms)),
+             "particles_per_s": N * 1e3 / float(np.mean(ms)), "frames": len(errs),
+             "stages_ms": [float(x) for x in stages]}
+        if kind == "surrogate":
+            d.update(exact_fraction=exact / max(1, dummies), fallbacks=fallbacks, mean_dummies=dummies / len(errs))
+        return d
+
+    results = [run("sir", None, sir_steps_cap)]
+    for h in (0.5, 0.2, 0.1, 0.05, 0.02):
+        results.append(run("pcsir", h))
+    for h in (0.2, 0.1, 0.05, 0.02):
+        results.append(run("surrogate", h))
+    ctx.close()
+    ctx_s.close()
+    sur.close()
+    target = 1.05 * results[0]["rmse_px"]
+
+    def best(kind):
+        ok = [r for r in results if r["method"] == kind and r["rmse_px"] <= target]
+        return max(ok, key=lambda r: r["steps_per_s"]) if ok else None
+
+    out.update(N=N, sequences=n_seq, frames=n_frames, target_rmse_px=target, runs=results,
+               matched={"sir": results[0], "pcsir": best("pcsir"), "surrogate_pcsir": best("surrogate")})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,6 +373,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-targets", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--matched-frames", type=int, default=30, help="frames per sequence of the matched-RMSE "
+                    "comparison (0 skips it and the surrogate training)")
+    ap.add_argument("--matched-seqs", type=int, default=2)
+    ap.add_argument("--surrogate-rows", type=int, default=10_000_000)
+    ap.add_argument("--surrogate-steps", type=int, default=100_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -393,6 +515,11 @@ def main():
     if args.batched_steps > 0:
         batched = run_batched(args.batched_targets, args.batched_steps, 3, SEED + 77 + 1000 * rank, world)
 
+    matched = None
+    if args.matched_frames > 0:
+        matched = run_matched(N, args.surrogate_rows, args.surrogate_steps, args.matched_seqs, args.matched_frames,
+                              SEED + 31 + 1000 * rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_s = 1 << 18
@@ -414,7 +541,8 @@ def main():
                           "scan_resample": st_mean[3], "share": [float(s) for s in share],
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
-            "e2e": e2e, "sir": sir, "batched": batched, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "cpu_baseline": cpu,
+            "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),
             "device_error": derr,
         }

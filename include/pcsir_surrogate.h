@@ -26,8 +26,9 @@
  *   z log(lambda / z) - (lambda - z)
  *     = [z - z log z + z log bg - bg] + [z log(1 + I0 g / bg) - I0 g].
  * The first part summed over the window, T(cx, cy) = sum (z - z log z) +
- * log(bg) sum z - 441 bg (0 log 0 = 0), is computed exactly for every window
- * of a frame by a box filter (per-pixel terms in FP32, sums in FP64).  The
+ * log(bg) sum z - 441 bg (0 log 0 = 0), is computed for every window of a
+ * frame by a box filter (per-pixel terms in FP32, sums in double-float,
+ * result rounded to FP32).  The
  * network learns the residual r = ll - T from the training labels; the
  * predicted log-likelihood is T + label_mean + label_scale * out, where out
  * is the network output.  Weights W1 (256 x 445) and W2 (256 x 256) enter the

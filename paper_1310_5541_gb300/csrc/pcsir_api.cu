@@ -181,7 +181,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
     delete c;
     return PCSIR_ENOMEM;
   }
-  e = prepare_kernels(cfg->state_dtype, &b.prop_bin_per_sm);
+  e = prepare_kernels(cfg->state_dtype, b.prop_bin_per_sm);
   if (e == cudaSuccess) e = prepare_resample();
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result));
   if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
@@ -218,6 +218,12 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
   cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  // Cell-table size of the propagate/bin kernel (results do not depend on it):
+  // the large table once the previous step found more cells than the small
+  // table holds comfortably, else from the cell size alone.  The previous
+  // count is read from the page-locked result copy of that step.
+  const int64_t prev_bins = ctx->last_kind == 1 ? ((volatile pcsir_result*)ctx->host_res)->n_bins : -1;
+  ctx->b.big_table = prev_bins >= 0 ? (prev_bins > 1200 ? 1 : 0) : (h < 0.15 ? 1 : 0);
   SurStep sp{};
   if (ctx->sur_on && (int64_t)W * H > sur_max_pixels(ctx->sur.sur))
     return fail(ctx, PCSIR_ERANGE, "image larger than the surrogate's max_pixels");

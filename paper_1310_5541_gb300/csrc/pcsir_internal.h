@@ -70,7 +70,8 @@ struct StepBuffers {
   int64_t max_tiles;
   Control* ctl;
   pcsir_result* dres;
-  int prop_bin_per_sm;      // resident blocks per SM of the propagate/bin kernel
+  int prop_bin_per_sm[2];   // resident blocks per SM of the propagate/bin kernel (small, large cell table)
+  int big_table;            // 1: the propagate/bin kernel uses the large cell table
 };
 
 struct ModelParams {
@@ -129,7 +130,7 @@ cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dty
                              cudaStream_t s, StageEvents se, int keep);
 cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms,
                               cudaStream_t s);
-cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm);
+cudaError_t prepare_kernels(int dtype, int prop_bin_per_sm[2]);
 cudaError_t prepare_resample();
 // integer-weight scale: q = rint(exp(ll - max) * 2^sq) with N * 2^sq <= 2^61
 int weight_scale_bits(int64_t N);

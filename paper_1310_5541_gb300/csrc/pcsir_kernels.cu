@@ -99,9 +99,6 @@ __device__ unsigned global_find_or_insert(const StepBuffers& b, unsigned long lo
 constexpr int PB_THREADS = 512;
 constexpr int PB_PER_THREAD = 4;
 constexpr int PB_CHUNK = PB_THREADS * PB_PER_THREAD;
-constexpr int LT_BITS = 10;
-constexpr int LT = 1 << LT_BITS;
-constexpr unsigned LT_CAP = 768;
 constexpr int PIECE_BITS = 18;
 constexpr unsigned PIECE_MASK = (1u << PIECE_BITS) - 1u;
 constexpr int FLUSH_PARTICLES = 1 << 14;
@@ -110,27 +107,34 @@ constexpr long long VAL_BIAS = 1ll << 34;
 constexpr long long BIASED_LIMIT = 1ll << 36;
 constexpr int NACC = 11;  // count, then (lo, hi) of x, y, vx, vy, I0
 
+// The block's table of cells: 2^LTB slots, filled to 3/4 at most.  Two sizes:
+// 2^10 slots (56 KB, two blocks per SM) for cells that hold many particles,
+// and 2^12 slots (224 KB, one block per SM) for small cells, where a block
+// meets thousands of distinct cells and the small table would overflow into
+// per-particle global atomics.
+template <int LTB>
 struct LocalTable {
+  static constexpr int LT = 1 << LTB;
+  static constexpr unsigned CAP = 3u << (LTB - 2);
   unsigned long long key[LT];
   unsigned int acc[NACC][LT];
   unsigned int gslot[LT];
-  unsigned short list[LT];
-  unsigned int nlist;
   unsigned int fill;
 };
 
-__device__ __forceinline__ int local_find_or_insert(LocalTable& t, unsigned long long key, bool& created) {
+template <int LTB>
+__device__ __forceinline__ int local_find_or_insert(LocalTable<LTB>& t, unsigned long long key, bool& created) {
+  constexpr int LT = LocalTable<LTB>::LT;
   created = false;
-  unsigned h = hash_bits(key, LT_BITS);
+  unsigned h = hash_bits(key, LTB);
   for (int probe = 0; probe < LT; ++probe) {
     const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
     if (k == key) return (int)h;
     if (k == EMPTY_KEY) {
-      if (atomicAdd(&t.fill, 1u) >= LT_CAP) return -1;
+      if (atomicAdd(&t.fill, 1u) >= LocalTable<LTB>::CAP) return -1;
       const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
       if (old == EMPTY_KEY) {
         created = true;
-        t.list[atomicAdd(&t.nlist, 1u)] = (unsigned short)h;
         return (int)h;
       }
       if (old == key) return (int)h;
@@ -142,11 +146,11 @@ __device__ __forceinline__ int local_find_or_insert(LocalTable& t, unsigned long
 
 // Merge the block's counters into the global table and zero them; with
 // clear_keys the cells themselves are dropped as well (table full).
-__device__ __forceinline__ void local_flush(LocalTable& t, const StepBuffers& b, bool clear_keys) {
+template <int LTB>
+__device__ __forceinline__ void local_flush(LocalTable<LTB>& t, const StepBuffers& b, bool clear_keys) {
   const size_t hcap = size_t(1) << b.hbits;
-  const unsigned n = t.nlist;
-  for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
-    const unsigned j = t.list[e];
+  for (unsigned j = threadIdx.x; j < (unsigned)LocalTable<LTB>::LT; j += blockDim.x) {
+    if (t.key[j] == EMPTY_KEY) continue;
     const unsigned cnt = t.acc[0][j];
     if (cnt != 0u) {
       const unsigned g = t.gslot[j];
@@ -164,36 +168,40 @@ __device__ __forceinline__ void local_flush(LocalTable& t, const StepBuffers& b,
     if (clear_keys) t.key[j] = EMPTY_KEY;
   }
   __syncthreads();
-  if (clear_keys && threadIdx.x == 0) {
-    t.nlist = 0u;
-    t.fill = 0u;
-  }
+  if (clear_keys && threadIdx.x == 0) t.fill = 0u;
   __syncthreads();
 }
 
+// Threads per block of the propagate/bin kernel: 512 with the small cell
+// table (two blocks per SM), 1024 with the large one (one block per SM).
+template <int LTB>
+struct PbShape {
+  static constexpr int THREADS = LTB == 10 ? PB_THREADS : 2 * PB_THREADS;
+  static constexpr int CHUNK = THREADS * PB_PER_THREAD;
+};
+
 // i-th particle (0..3) of this thread in the chunk: four consecutive indices
 // when the rows allow 16-byte vector access, otherwise strided by the block.
-template <bool VEC>
+template <bool VEC, int THREADS>
 __device__ __forceinline__ int64_t pb_index(int64_t base, int k) {
-  return VEC ? base + 4 * threadIdx.x + k : base + (int64_t)k * PB_THREADS + threadIdx.x;
+  return VEC ? base + 4 * threadIdx.x + k : base + (int64_t)k * THREADS + threadIdx.x;
 }
 
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(PB_THREADS, 2)
+template <typename T, bool VEC, int LTB>
+__global__ void __launch_bounds__(PbShape<LTB>::THREADS, LTB == 10 ? 2 : 1)
 k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq) {
+  constexpr int THR = PbShape<LTB>::THREADS;
+  constexpr int CHUNK = PbShape<LTB>::CHUNK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LocalTable& tab = *reinterpret_cast<LocalTable*>(smem_raw);
+  LocalTable<LTB>& tab = *reinterpret_cast<LocalTable<LTB>*>(smem_raw);
   T* __restrict__ prop = static_cast<T*>(b.prop);
   const size_t hcap = size_t(1) << b.hbits;
-  for (int j = threadIdx.x; j < LT; j += blockDim.x) {
+  for (int j = threadIdx.x; j < LocalTable<LTB>::LT; j += blockDim.x) {
     tab.key[j] = EMPTY_KEY;
 #pragma unroll
     for (int a = 0; a < NACC; ++a) tab.acc[a][j] = 0u;
   }
-  if (threadIdx.x == 0) {
-    tab.nlist = 0u;
-    tab.fill = 0u;
-  }
+  if (threadIdx.x == 0) tab.fill = 0u;
   // anchors of vx, vy, I0: particle 0's input value in fixed point
   long long anc[3];
 #pragma unroll
@@ -205,12 +213,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
   __syncthreads();
   const T half = T(0.5);
   const T lim = T(1073741823.0);  // 2^30 - 1
-  const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
+  const int64_t nchunks = (N + CHUNK - 1) / CHUNK;
   int since_flush = 0;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    const int64_t base = chunk * PB_CHUNK;
+    const int64_t base = chunk * CHUNK;
     T v[PB_PER_THREAD][5];
-    if (VEC && base + PB_CHUNK <= N) {
+    if (VEC && base + CHUNK <= N) {
       // 16-byte loads and stores of four consecutive particles per component
       const int64_t i0 = base + 4 * threadIdx.x;
       float4 sv[5], nv[5];
@@ -237,7 +245,7 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
     } else {
 #pragma unroll
       for (int k = 0; k < PB_PER_THREAD; ++k) {
-        const int64_t i = pb_index<false>(base, k);
+        const int64_t i = pb_index<false, THR>(base, k);
         if (i < N) {
           propagate1(st, nz, N, i, v[k]);
 #pragma unroll
@@ -245,12 +253,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
         }
       }
     }
-    const bool vec_chunk = VEC && base + PB_CHUNK <= N;
+    const bool vec_chunk = VEC && base + CHUNK <= N;
     unsigned long long key[PB_PER_THREAD];
     int ls[PB_PER_THREAD];
 #pragma unroll
     for (int k = 0; k < PB_PER_THREAD; ++k) {
-      const int64_t i = vec_chunk ? pb_index<true>(base, k) : pb_index<false>(base, k);
+      const int64_t i = vec_chunk ? pb_index<true, THR>(base, k) : pb_index<false, THR>(base, k);
       ls[k] = -2;
       if (i >= N) continue;
       T fx = floor_t(div_rn(add_rn(v[k][0], half), h));
@@ -312,12 +320,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
     } else {
 #pragma unroll
       for (int k = 0; k < PB_PER_THREAD; ++k)
-        if (ls[k] != -2) b.pslot[pb_index<false>(base, k)] = gs[k];
+        if (ls[k] != -2) b.pslot[pb_index<false, THR>(base, k)] = gs[k];
     }
-    since_flush += PB_CHUNK;
+    since_flush += CHUNK;
     __syncthreads();
-    const bool full = tab.fill >= LT_CAP;
-    if (full || since_flush + PB_CHUNK > FLUSH_PARTICLES) {
+    const bool full = tab.fill >= LocalTable<LTB>::CAP;
+    if (full || since_flush + CHUNK > FLUSH_PARTICLES) {
       local_flush(tab, b, full);
       since_flush = 0;
     }
@@ -705,46 +713,63 @@ int weight_scale_bits(int64_t N) {
 
 // One-time kernel attributes and occupancy, queried at context creation so
 // that step calls only enqueue work (and stay legal inside a stream capture).
-template <typename T, bool VEC>
+template <typename T, bool VEC, int LTB>
 static cudaError_t prop_bin_prepare1(int* per_sm) {
-  const size_t smem = sizeof(LocalTable);
-  cudaError_t e = cudaFuncSetAttribute(k_prop_bin<T, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(LocalTable<LTB>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_prop_bin<T, VEC, LTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T, VEC>, PB_THREADS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T, VEC, LTB>, PbShape<LTB>::THREADS, smem);
   if (*per_sm < 1) *per_sm = 1;
   return e;
 }
 
-cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
+template <int LTB>
+static cudaError_t prop_bin_prepare(int dtype, int* per_sm) {
   int a = 1, c = 1;
   cudaError_t e;
   if (dtype == PCSIR_F32) {
-    e = prop_bin_prepare1<float, true>(&a);
-    if (e == cudaSuccess) e = prop_bin_prepare1<float, false>(&c);
+    e = prop_bin_prepare1<float, true, LTB>(&a);
+    if (e == cudaSuccess) e = prop_bin_prepare1<float, false, LTB>(&c);
   } else {
-    e = prop_bin_prepare1<double, false>(&a);
+    e = prop_bin_prepare1<double, false, LTB>(&a);
     c = a;
   }
-  *prop_bin_per_sm = a < c ? a : c;
+  *per_sm = a < c ? a : c;
   return e;
+}
+
+cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
+  cudaError_t e = prop_bin_prepare<10>(dtype, &prop_bin_per_sm[0]);
+  if (e == cudaSuccess) e = prop_bin_prepare<12>(dtype, &prop_bin_per_sm[1]);
+  return e;
+}
+
+template <typename T, int LTB>
+static cudaError_t prop_bin_launch_t(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
+                                     int num_sms, int per_sm, cudaStream_t s, long long hq) {
+  const size_t smem = sizeof(LocalTable<LTB>);
+  constexpr int THR = PbShape<LTB>::THREADS;
+  const int64_t nchunks = (N + PbShape<LTB>::CHUNK - 1) / PbShape<LTB>::CHUNK;
+  const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * per_sm);
+  const bool vec = std::is_same<T, float>::value && (N % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(noise) |
+                     reinterpret_cast<uintptr_t>(b.prop) | reinterpret_cast<uintptr_t>(b.pslot)) % 16 == 0);
+  if (vec)
+    k_prop_bin<T, true, LTB><<<grid, THR, smem, s>>>(b, static_cast<const T*>(state),
+                                                      static_cast<const T*>(noise), N, (T)h, hq);
+  else
+    k_prop_bin<T, false, LTB><<<grid, THR, smem, s>>>(b, static_cast<const T*>(state),
+                                                       static_cast<const T*>(noise), N, (T)h, hq);
+  return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t prop_bin_launch(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
                                    int num_sms, cudaStream_t s, long long hq) {
-  const size_t smem = sizeof(LocalTable);
-  const int64_t nchunks = (N + PB_CHUNK - 1) / PB_CHUNK;
-  const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * b.prop_bin_per_sm);
-  const bool vec = std::is_same<T, float>::value && (N % 4 == 0) &&
-                   ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(noise) |
-                     reinterpret_cast<uintptr_t>(b.prop) | reinterpret_cast<uintptr_t>(b.pslot)) % 16 == 0);
-  if (vec)
-    k_prop_bin<T, true><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state), static_cast<const T*>(noise),
-                                                        N, (T)h, hq);
-  else
-    k_prop_bin<T, false><<<grid, PB_THREADS, smem, s>>>(b, static_cast<const T*>(state),
-                                                         static_cast<const T*>(noise), N, (T)h, hq);
-  return cudaGetLastError();
+  if (b.big_table)
+    return prop_bin_launch_t<T, 12>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[1], s, hq);
+  return prop_bin_launch_t<T, 10>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[0], s, hq);
 }
 
 static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {

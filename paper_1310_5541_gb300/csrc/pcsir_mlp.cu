@@ -19,7 +19,8 @@ constexpr int MM_THREADS = 128;  // four warps: one TMEM lane quarter each
 // One CTA: rows [m0, m0 + 128) x columns [n0, n0 + NT), K chunks of its slice.
 template <int NT>
 __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
-  extern __shared__ __align__(1024) uint8_t mm_smem[];
+  extern __shared__ __align__(1024) uint8_t mm_smem_raw[];
+  uint8_t* mm_smem = align1024(mm_smem_raw);
   uint8_t* sA = mm_smem;                    // 128 x 64 bf16 = 16 KB
   uint8_t* sB = mm_smem + MM_M * MM_K * 2;  // NT x 64 bf16
   uint64_t* bar = reinterpret_cast<uint64_t*>(mm_smem + MM_M * MM_K * 2 + NT * MM_K * 2);

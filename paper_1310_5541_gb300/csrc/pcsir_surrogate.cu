@@ -76,17 +76,20 @@ __device__ __forceinline__ float sur_input(const float* __restrict__ img, const 
 // ---------------------------------------------------------------------------
 // Window term T(cx, cy) = sum over the 21 x 21 window of
 // (z - z log z + log(bg) z) - 441 bg, for every window inside the image
-// (NaN elsewhere).  Per-pixel terms in FP32, window sums in FP64; one block
-// per 32 x 32 tile of window centres, the (32 + 20)^2 input pixels staged in
-// shared memory, a horizontal then a vertical pass of 21-wide sums.
+// (NaN elsewhere).  Per-pixel terms in FP32, window sums in double-float
+// (pairs of FP32 with error-free additions: GB300's FP64 pipe would make this
+// pass cost more than the network), stored rounded to FP32 (relative error
+// 2^-24, 1e-4 nats for |T| ~ 1e3).  One block per 32 x 32 tile of window
+// centres, the (32 + 20)^2 input pixels staged in shared memory, a
+// horizontal then a vertical pass of 21-wide sums.
 // ---------------------------------------------------------------------------
 constexpr int WT_TILE = 32;
 constexpr int WT_IN = WT_TILE + 2 * SUR_R;  // 52
 
 __global__ void __launch_bounds__(256)
-k_sur_window(const float* __restrict__ img, int W, int H, float log_bg, double pbg, double* __restrict__ T) {
+k_sur_window(const float* __restrict__ img, int W, int H, float log_bg, df pbg, float* __restrict__ T) {
   __shared__ float s_v[WT_IN][WT_IN];
-  __shared__ double s_h[WT_IN][WT_TILE];
+  __shared__ float s_hh[WT_IN][WT_TILE], s_hl[WT_IN][WT_TILE];
   const int x0 = blockIdx.x * WT_TILE, y0 = blockIdx.y * WT_TILE;
   for (int i = threadIdx.x; i < WT_IN * WT_IN; i += blockDim.x) {
     const int yy = y0 - SUR_R + i / WT_IN, xx = x0 - SUR_R + i % WT_IN;
@@ -100,21 +103,23 @@ k_sur_window(const float* __restrict__ img, int W, int H, float log_bg, double p
   __syncthreads();
   for (int i = threadIdx.x; i < WT_IN * WT_TILE; i += blockDim.x) {
     const int r = i / WT_TILE, c = i % WT_TILE;
-    double a = 0.0;
+    df a{0.0f, 0.0f};
 #pragma unroll
-    for (int k = 0; k < 2 * SUR_R + 1; ++k) a += (double)s_v[r][c + k];
-    s_h[r][c] = a;
+    for (int k = 0; k < 2 * SUR_R + 1; ++k) a = df_add_f(a, s_v[r][c + k]);
+    s_hh[r][c] = a.hi;
+    s_hl[r][c] = a.lo;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < WT_TILE * WT_TILE; i += blockDim.x) {
     const int r = i / WT_TILE, c = i % WT_TILE;
     const int x = x0 + c, y = y0 + r;
     if (x >= W || y >= H) continue;
-    double a = 0.0;
+    df a{0.0f, 0.0f};
 #pragma unroll
-    for (int k = 0; k < 2 * SUR_R + 1; ++k) a += s_h[r + k][c];
+    for (int k = 0; k < 2 * SUR_R + 1; ++k) a = df_add(a, df{s_hh[r + k][c], s_hl[r + k][c]});
+    a = df_add(a, df{-pbg.hi, -pbg.lo});
     const bool inside = x >= SUR_R && x + SUR_R <= W - 1 && y >= SUR_R && y + SUR_R <= H - 1;
-    T[(long long)y * W + x] = inside ? a - pbg : __longlong_as_double(0x7ff8000000000000ll);
+    T[(long long)y * W + x] = inside ? a.hi + a.lo : __int_as_float(0x7fc00000);
   }
 }
 
@@ -177,7 +182,7 @@ k_sur_add_count(const double* __restrict__ dummy, long long stride, long long n,
 
 __global__ void __launch_bounds__(ADD_THREADS)
 k_sur_add_write(const double* __restrict__ dummy, long long stride, long long n, const double* __restrict__ ll,
-                double label_floor, const double* __restrict__ T, const float* __restrict__ img, int W, int H, SurFeat sf, const unsigned* __restrict__ blk_cnt,
+                double label_floor, const float* __restrict__ T, const float* __restrict__ img, int W, int H, SurFeat sf, const unsigned* __restrict__ blk_cnt,
                 const unsigned long long* __restrict__ base, unsigned long long* __restrict__ count,
                 unsigned* __restrict__ done, long long capacity, __nv_bfloat16* __restrict__ X,
                 float* __restrict__ y, uint8_t* __restrict__ cens) {
@@ -226,7 +231,7 @@ k_sur_add_write(const double* __restrict__ dummy, long long stride, long long n,
     if (lane == 0) {
       const double v = ll[s_src[r]];
       const bool below = v < label_floor;
-      y[row] = (float)((below ? label_floor : v) - T[sur_tindex(q.base, W)]);
+      y[row] = (float)((below ? label_floor : v) - (double)T[sur_tindex(q.base, W)]);
       cens[row] = below ? 1 : 0;
     }
   }
@@ -430,7 +435,7 @@ struct SurInfer {
   const float* img;
   int W, H;
   SurFeat sf;
-  const double* T;                // window terms of img (states), or null (rows: label units)
+  const float* T;                 // window terms of img (states), or null (rows: label units)
   double* out;
   int nan_clipped;                // write NaN for clipped states
   unsigned long long* max_ll;     // ordered maximum of the written predictions, or null
@@ -440,8 +445,8 @@ struct SurInfer {
 
 template <int SRC>
 __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
-  extern __shared__ __align__(1024) uint8_t si_smem[];
-  uint8_t* sX = si_smem;
+  extern __shared__ __align__(1024) uint8_t si_smem_raw[];
+  uint8_t* sX = align1024(si_smem_raw);
   uint8_t* sW = sX + SI_X;
   uint8_t* sA = sW + SI_W;
   int* poff = reinterpret_cast<int*>(sA + SI_A);
@@ -561,7 +566,7 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
       for (int i = 0; i < 8; ++i) acc = fmaf(silu_f(v[i] + __ldg(b2 + c + i)), __ldg(w3 + c + i), acc);
     }
     double ll = mean + scale * (double)(acc + b3);
-    if (SRC == SRC_STATES && rowi[tid].valid) ll += a.T[sur_tindex(rowi[tid].base, a.W)];
+    if (SRC == SRC_STATES && rowi[tid].valid) ll += (double)a.T[sur_tindex(rowi[tid].base, a.W)];
     if (rowi[tid].valid) {
       if (!isfinite(ll) && a.bad) atomicOr(a.bad, 1u);
       a.out[d] = ll;
@@ -679,7 +684,7 @@ struct pcsir_surrogate {
   float* y = nullptr;
   uint8_t* cens = nullptr;
   uint8_t* cb = nullptr;
-  double* T = nullptr;  // window terms of the current image (max_pixels)
+  float* T = nullptr;  // window terms of the current image (max_pixels)
   unsigned long long* count = nullptr;
   unsigned long long* add_base = nullptr;
   unsigned* add_cnt = nullptr;
@@ -741,7 +746,9 @@ SurNet net_of(const pcsir_surrogate* s) { return SurNet{s->W1b, s->W2b, s->P, s-
 cudaError_t launch_window(const pcsir_surrogate* s, const float* img, int W, int H, double bg, cudaStream_t st) {
   if ((long long)W * H > s->cfg.max_pixels) return cudaErrorInvalidValue;
   dim3 grid((W + WT_TILE - 1) / WT_TILE, (H + WT_TILE - 1) / WT_TILE);
-  k_sur_window<<<grid, 256, 0, st>>>(img, W, H, (float)std::log(bg), (double)(SUR_NPIX) * bg, s->T);
+  const double pbg = (double)SUR_NPIX * bg;
+  const df pbg_df{(float)pbg, (float)(pbg - (double)(float)pbg)};
+  k_sur_window<<<grid, 256, 0, st>>>(img, W, H, (float)std::log(bg), pbg_df, s->T);
   return cudaGetLastError();
 }
 

@@ -2,14 +2,15 @@
 // memory matrix descriptors, the instruction descriptor of kind::f16 with
 // FP32 accumulation, TMEM allocation, MMA issue and commit to an mbarrier,
 // bounded mbarrier waits, TMEM loads, and the staging of bf16 operands into
-// the no-swizzle K-major core-matrix layout.
+// the 128-byte-swizzled K-major layout.
 //
-// Operand layout in shared memory (no swizzle, K-major): 8 x 8 bf16 "core
-// matrices" of 128 contiguous bytes (8 rows of 16 bytes); cores adjacent
-// along K are LBO = 128 bytes apart, 8-row groups SBO = 1024 bytes apart, so
-// a 64-wide K chunk of R rows takes R * 128 bytes.  One tcgen05.mma consumes
-// K = 16 (two cores along K), so the descriptor of the s-th K = 16 step of a
-// chunk starts 2 * s * LBO bytes after the chunk.
+// Operand layout in shared memory (K-major, 128-byte swizzle): a 64-wide K
+// chunk of R rows is R rows of 128 bytes; within each group of 8 rows (1024
+// bytes, SBO) the 16-byte pieces of row r are permuted by XOR with r mod 8,
+// so that the eight rows of a core matrix fall in different banks.  A chunk
+// starts on a 1024-byte boundary.  One tcgen05.mma consumes K = 16, and the
+// descriptor of the s-th K = 16 step of a chunk starts 32 * s bytes after it
+// (the swizzle is applied to the computed addresses).
 #pragma once
 
 #include <cstdint>
@@ -20,16 +21,17 @@
 namespace pcsir {
 
 constexpr int MM_K = 64;  // K per staged chunk
-constexpr uint32_t MM_LBO = 128;
 constexpr uint32_t MM_SBO = 1024;
 constexpr int MM_WAIT_SPINS = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1, no swizzle
+// shared-memory matrix descriptor: start >> 4, leading offset 1 (unused for
+// swizzled K-major operands), SBO >> 4, version 1, base offset 0, 128-byte
+// swizzle (mode 2)
 __device__ __forceinline__ uint64_t mm_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(MM_LBO >> 4) << 16) | ((uint64_t)(MM_SBO >> 4) << 32) |
-         (1ull << 46);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(MM_SBO >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
 }
 
 // instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N
@@ -39,7 +41,13 @@ __host__ __device__ constexpr uint32_t mm_idesc(int M, int N) {
 
 // byte offset of element (r, k) of a staged K chunk
 __device__ __forceinline__ uint32_t mm_off(int r, int k) {
-  return (uint32_t)((r >> 3) * MM_SBO + (k >> 3) * MM_LBO + (r & 7) * 16 + (k & 7) * 2);
+  return (uint32_t)(r * 128 + ((((k >> 3) ^ r) & 7) << 4) + (k & 7) * 2);
+}
+
+// first 1024-byte boundary at or after p (shared memory)
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  const uint32_t a = smem_u32(p);
+  return p + (((a + 1023u) & ~1023u) - a);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -104,7 +112,7 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float v[8]) {
 __device__ __forceinline__ void tc_mma_chunk(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t idesc, bool first) {
 #pragma unroll
   for (int s = 0; s < MM_K / 16; ++s)
-    tc_mma(tmem, mm_desc(a0 + s * 2 * MM_LBO), mm_desc(b0 + s * 2 * MM_LBO), idesc, (!first || s > 0) ? 1u : 0u);
+    tc_mma(tmem, mm_desc(a0 + s * 32), mm_desc(b0 + s * 32), idesc, (!first || s > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ uint4 pack_bf16x8(const float v[8]) {
@@ -127,7 +135,7 @@ __device__ __forceinline__ float silu_grad_f(float t) {
 }
 
 // Stage a rows x 64 chunk of an operand, element (r, k) = src[(r0 + r) srow +
-// (k0 + k) sk], into the core-matrix layout; rows >= rows_valid and k >= K
+// (k0 + k) sk], into the swizzled layout; rows >= rows_valid and k >= K
 // are zero.  Three access patterns: K contiguous (sk == 1, 16-byte loads),
 // rows contiguous (srow == 1, lanes over rows), and any other strides.
 template <int NTHREADS>

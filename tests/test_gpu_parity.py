@@ -203,6 +203,36 @@ def test_pcsir_fp32_big_image(pc, big_case, h):
     ctx.close()
 
 
+def test_cell_table_size_does_not_change_the_step(pc, big_case):
+    """The propagate/bin kernel has a small and a large shared-memory cell table, chosen per step
+    from the previous step's cell count; both must give the same step bit for bit."""
+    seq, N, st = big_case
+    nz = torch.from_numpy(synth.make_noise(N, MODEL_BIG.q, SEED + 5, 2, np.float32)).cuda()
+    img = torch.from_numpy(seq.images[2]).cuda()
+    outs = []
+    for prime_h in (None, 4.0, 0.03):
+        ctx = _ctx(pc, N, torch.float32, MODEL_BIG)
+        if prime_h is not None:  # a previous step with few (large table off) or many cells (on)
+            s0 = torch.from_numpy(st).cuda()
+            pc.pcsir_step(ctx, s0, img, prime_h, nz, 0.5)
+            torch.cuda.synchronize()
+        s1 = torch.from_numpy(st).cuda()
+        pc.pcsir_step(ctx, s1, img, 0.1, nz, 0.3)
+        torch.cuda.synchronize()
+        o = ctx.outputs()
+        order = np.lexsort((o["bin_xy"][0].cpu().numpy(), o["bin_xy"][1].cpu().numpy()))
+        outs.append((s1.cpu().numpy(), o["dummy"].cpu().numpy()[:, order], o["bin_count"].cpu().numpy()[order],
+                     o["weight"].cpu().numpy(), ctx.last_result()["estimate"]))
+        ctx.close()
+    for other in outs[1:]:
+        np.testing.assert_array_equal(outs[0][0], other[0])
+        np.testing.assert_array_equal(outs[0][1], other[1])
+        np.testing.assert_array_equal(outs[0][2], other[2])
+        # normalised weights divide by a sum accumulated with atomics: equal up to its rounding order
+        np.testing.assert_allclose(outs[0][3], other[3], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(outs[0][4], other[4], rtol=1e-12)
+
+
 def test_sir_fp32_big_image(pc, big_case):
     seq, N, st = big_case
     N2 = 40_000 + 123

@@ -87,12 +87,15 @@ def states_near(rng, n, x0, y0, spread, W, H, n_edge=0):
 
 
 def window_bound(img, x, y):
-    """Bound on |T_gpu - T| from the FP32 per-pixel terms: a few roundings of size 2^-24 per term."""
+    """Bound on |T_gpu - T|: a few roundings of size 2^-24 per FP32 per-pixel term, and the final
+    rounding of the (double-float) sum to FP32."""
     z = img.astype(np.float64)
     mag = z + np.where(z > 0, z * np.abs(np.log(np.where(z > 0, z, 1.0))), 0.0) + np.log(10.0) * z
     cx = np.floor(np.asarray(x) + 0.5).astype(int)
     cy = np.floor(np.asarray(y) + 0.5).astype(int)
-    return np.array([16 * 2.0 ** -24 * mag[b - 10:b + 11, a - 10:a + 11].sum() + 1e-9 for a, b in zip(cx, cy)])
+    T = np.abs(S.window_term(img, x, y, 10.0))
+    return np.array([16 * 2.0 ** -24 * mag[b - 10:b + 11, a - 10:a + 11].sum() for a, b in zip(cx, cy)]) \
+        + 2.0 ** -23 * T + 1e-9
 
 
 def forward_bound(p, X):
