@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   uint32_t phase = 0;
   bool ok = true;
   for (int kc = kc0; kc < kc1 && ok; ++kc) {
-    mm_stage<MM_THREADS>(sA, g.A, g.sam, g.sak, m0, MM_M, g.M, kc * MM_K, g.K);
-    mm_stage<MM_THREADS>(sB, g.B, g.sbn, g.sbk, n0, NT, g.N, kc * MM_K, g.K);
+    mm_stage<MM_THREADS, MM_M>(sA, g.A, g.sam, g.sak, m0, g.M, kc * MM_K, g.K);
+    mm_stage<MM_THREADS, NT>(sB, g.B, g.sbn, g.sbk, n0, g.N, kc * MM_K, g.K);
     proxy_fence();
     __syncthreads();
     if (tid == 0) {
@@ -58,8 +58,9 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
       tc_mma_chunk(tmem, smem_u32(sA), smem_u32(sB), idesc, kc == kc0);
       tc_commit(bar);
     }
-    // every thread waits; the block continues only if all saw the phase complete
-    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    // thread 0 polls the mbarrier (polling by every warp would compete with the
+    // tensor core for shared memory); the block barrier releases the others
+    ok = __syncthreads_and(tid != 0 || mbar_wait(bar, phase)) != 0;
     phase ^= 1u;
     tc_fence_after();
   }

@@ -405,22 +405,31 @@ __global__ void k_sur_adam(float* __restrict__ P, float* __restrict__ G, float* 
 }
 
 // ---------------------------------------------------------------------------
-// Fused inference: per tile of 128 states, the inputs are built from the
-// image straight into the shared-memory operand layout, layer 1 (K = 448 in
-// seven chunks) and layer 2 (K = 256, the bf16 activations of layer 1 kept in
-// shared memory) accumulate in the same 256 TMEM columns, and the output
-// layer runs in FP32 on each thread's TMEM lane.
+// Fused inference.  Per tile of 128 states the inputs are built from the
+// image straight into the shared-memory operand layout; layer 1 (K = 448,
+// seven chunks of 64) and layer 2 (K = 256, four chunks, the bf16
+// activations of layer 1 kept in shared memory) accumulate in the same 256
+// TMEM columns, and the output layer runs in FP32 on the TMEM lanes.
+//
+// The eleven weight chunks (32 KB each) are stored pre-arranged in the
+// swizzled shared-memory layout, so one thread fetches a chunk with a single
+// bulk asynchronous copy completing on an mbarrier.  Input and weight
+// buffers are doubled: the copy and the input build of chunk q overlap the
+// MMAs of chunk q - 1.  Eight warps: all build inputs; for the epilogues the
+// warps w and w + 4 share TMEM lanes 32 (w mod 4) .. + 31 and split the 256
+// columns in halves.
 // ---------------------------------------------------------------------------
-constexpr int SI_THREADS = 128;
+constexpr int SI_THREADS = 256;
+constexpr int SI_CHUNKS = SUR_K1 / MM_K + SUR_HID / MM_K;  // 7 + 4
 constexpr int SI_X = 128 * MM_K * 2;      // 16 KB: one input chunk
 constexpr int SI_W = SUR_HID * MM_K * 2;  // 32 KB: one weight chunk
 constexpr int SI_A = 128 * SUR_HID * 2;   // 64 KB: layer-1 activations (four chunks)
-constexpr int SI_SMEM = SI_X + SI_W + SI_A + SUR_K1 * 4 + SI_THREADS * (int)sizeof(SurRowInfo) + 16;
+constexpr int SI_SMEM = 2 * SI_X + 2 * SI_W + SI_A + SUR_K1 * 4 + 128 * (int)sizeof(SurRowInfo) +
+                        2 * 128 * 4 + 64;
 enum { SRC_STATES = 0, SRC_ROWS = 1 };
 
 struct SurNet {
-  const __nv_bfloat16* W1b;
-  const __nv_bfloat16* W2b;
+  const uint8_t* Wsw;   // SI_CHUNKS weight chunks in the shared-memory layout
   const float* P;       // FP32 parameters (biases, output layer)
   const double* norm;   // label mean and scale
 };
@@ -443,18 +452,60 @@ struct SurInfer {
   unsigned* err;
 };
 
+// weight chunk q (W1 for q < 7, W2 after) rearranged into the shared-memory layout
+__global__ void k_sur_pack(const __nv_bfloat16* __restrict__ W1b, const __nv_bfloat16* __restrict__ W2b,
+                           uint8_t* __restrict__ Wsw) {
+  const int total = SI_CHUNKS * SUR_HID * 8;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const int q = g / (SUR_HID * 8), rem = g % (SUR_HID * 8);
+    const int r = rem >> 3, kg = (rem & 7) * 8;
+    const uint4 v = q < SUR_K1 / MM_K
+                        ? *reinterpret_cast<const uint4*>(W1b + (long long)r * SUR_K1 + q * MM_K + kg)
+                        : *reinterpret_cast<const uint4*>(W2b + (long long)r * SUR_HID + (q - SUR_K1 / MM_K) * MM_K + kg);
+    *reinterpret_cast<uint4*>(Wsw + (long long)q * SI_W + mm_off(r, kg)) = v;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint8_t* dst, const uint8_t* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// 4 x 8 consecutive fp32 columns of this thread's TMEM lane, one wait
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[8 * j]), "=r"(r[8 * j + 1]), "=r"(r[8 * j + 2]), "=r"(r[8 * j + 3]), "=r"(r[8 * j + 4]),
+          "=r"(r[8 * j + 5]), "=r"(r[8 * j + 6]), "=r"(r[8 * j + 7])
+        : "r"(taddr + 8u * j)
+        : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int SRC>
 __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
   extern __shared__ __align__(1024) uint8_t si_smem_raw[];
-  uint8_t* sX = align1024(si_smem_raw);
-  uint8_t* sW = sX + SI_X;
-  uint8_t* sA = sW + SI_W;
+  uint8_t* sX = align1024(si_smem_raw);  // two input chunks
+  uint8_t* sW = sX + 2 * SI_X;           // two weight chunks
+  uint8_t* sA = sW + 2 * SI_W;           // layer-1 activations
   int* poff = reinterpret_cast<int*>(sA + SI_A);
   SurRowInfo* rowi = reinterpret_cast<SurRowInfo*>(poff + SUR_K1);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(rowi + SI_THREADS);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  __shared__ double s_max[SI_THREADS / 32];
+  float* part = reinterpret_cast<float*>(rowi + 128);  // [2][128] partial output sums
+  uint64_t* bar_w = reinterpret_cast<uint64_t*>(part + 2 * 128);
+  uint64_t* bar_m = bar_w + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_m + 2);
+  __shared__ double s_max[4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = 32 * (warp & 3) + lane;  // TMEM lane of this thread
+  const int half = warp >> 2;               // column half of the epilogues
   const long long n = a.n_dev ? (long long)*a.n_dev : a.n;
   const long long ntiles = (n + 127) / 128;
   if ((long long)blockIdx.x >= ntiles) return;
@@ -462,130 +513,166 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
     poff[f] = f < SUR_NPIX ? (f / PCSIR_SUR_PATCH) * a.W + (f % PCSIR_SUR_PATCH) : 0;
   if (warp == 0) tc_alloc(tslot, SUR_HID);
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_w[i], 1);
+      mbar_init(&bar_m[i], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * 128);
   const uint32_t idesc = mm_idesc(128, SUR_HID);
   const float* b1 = a.net.P + OFF_B1;
   const float* b2 = a.net.P + OFF_B2;
   const float* w3 = a.net.P + OFF_W3;
   const float b3 = a.net.P[OFF_B3];
   const double mean = a.net.norm[0], scale = a.net.norm[1];
-  uint32_t phase = 0;
+  uint32_t ph_w[2] = {0u, 0u}, ph_m[2] = {0u, 0u};
+  bool out_w[2] = {false, false}, out_m[2] = {false, false};  // copy / MMA in flight on buffer b
   bool ok = true;
   double mymax = -INFINITY;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long d = t * 128 + tid;
-    if (SRC == SRC_STATES) {
-      SurRowInfo ri{0, 0.f, 0.f, 0.f, 0};
-      if (d < n) ri = sur_row_info(a.dummy, a.stride, d, a.W, a.H, a.sf);
-      rowi[tid] = ri;
-    } else {
-      rowi[tid] = SurRowInfo{0, 0.f, 0.f, 0.f, d < n ? 1 : 0};
+  unsigned q = 0;  // running chunk counter: buffer q & 1
+
+  // bounded wait for the MMA last committed on buffer b (uniform over the block)
+  auto wait_mma = [&](int b) {
+    if (!out_m[b]) return;
+    ok = ok && __syncthreads_and(tid != 0 || mbar_wait(&bar_m[b], ph_m[b])) != 0;
+    ph_m[b] ^= 1u;
+    out_m[b] = false;
+    tc_fence_after();
+  };
+
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long long d = t * 128 + (tid & 127);
+    if (tid < 128) {
+      if (SRC == SRC_STATES) {
+        SurRowInfo ri{0, 0.f, 0.f, 0.f, 0};
+        if (d < n) ri = sur_row_info(a.dummy, a.stride, d, a.W, a.H, a.sf);
+        rowi[tid] = ri;
+      } else {
+        rowi[tid] = SurRowInfo{0, 0.f, 0.f, 0.f, d < n ? 1 : 0};
+      }
     }
     __syncthreads();
-    // layer 1
-    for (int kc = 0; kc < SUR_K1 / MM_K && ok; ++kc) {
-      for (int g = tid; g < 128 * 8; g += SI_THREADS) {
-        const int r = g >> 3, kg = (g & 7) * 8;
-        const SurRowInfo ri = rowi[r];
-        uint4 u = make_uint4(0u, 0u, 0u, 0u);
-        if (ri.valid) {
+    for (int c = 0; c < SI_CHUNKS && ok; ++c, ++q) {
+      const int b = q & 1;
+      wait_mma(b);  // buffers b free again
+      if (!ok) break;
+      if (tid == 0) {
+        bulk_load(sW + b * SI_W, a.net.Wsw + (long long)c * SI_W, SI_W, &bar_w[b]);
+        out_w[b] = true;
+      }
+      if (c < SUR_K1 / MM_K) {
+        // inputs of chunk c: 128 rows x 8 groups of 8, four groups per thread, loads first
+        float v[4][8];
+        uint4 u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int g = tid + j * SI_THREADS;
+          const int r = g >> 3, kg = (g & 7) * 8;
+          const SurRowInfo ri = rowi[r];
           if (SRC == SRC_ROWS) {
-            u = __ldg(reinterpret_cast<const uint4*>(a.rows + (t * 128 + r) * SUR_K1 + kc * MM_K + kg));
+            u[j] = ri.valid ? __ldg(reinterpret_cast<const uint4*>(a.rows + (t * 128 + r) * SUR_K1 + c * MM_K + kg))
+                            : make_uint4(0u, 0u, 0u, 0u);
           } else {
-            float v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const int f = kc * MM_K + kg + i;
-              v[i] = sur_input(a.img, ri, f, poff[f], a.sf);
+              const int f = c * MM_K + kg + i;
+              v[j][i] = ri.valid ? sur_input(a.img, ri, f, poff[f], a.sf) : 0.0f;
             }
-            u = pack_bf16x8(v);
           }
         }
-        *reinterpret_cast<uint4*>(sX + mm_off(r, kg)) = u;
-      }
-      for (int g = tid; g < SUR_HID * 8; g += SI_THREADS) {
-        const int r = g >> 3, kg = (g & 7) * 8;
-        *reinterpret_cast<uint4*>(sW + mm_off(r, kg)) =
-            __ldg(reinterpret_cast<const uint4*>(a.net.W1b + (long long)r * SUR_K1 + kc * MM_K + kg));
-      }
-      proxy_fence();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        tc_mma_chunk(tmem, smem_u32(sX), smem_u32(sW), idesc, kc == 0);
-        tc_commit(bar);
-      }
-      ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
-      phase ^= 1u;
-      tc_fence_after();
-    }
-    if (!ok) break;
-    // layer-1 epilogue: bias, SiLU, bf16 into the layer-2 operand
-    for (int c = 0; c < SUR_HID; c += 8) {
-      float v[8];
-      tc_ld8(tmem + lane_base + (uint32_t)c, v);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = silu_f(v[i] + __ldg(b1 + c + i));
-      *reinterpret_cast<uint4*>(sA + (c / MM_K) * SI_X + mm_off(tid, c % MM_K)) = pack_bf16x8(v);
-    }
-    tc_fence_before();
-    proxy_fence();
-    __syncthreads();
-    // layer 2
-    for (int kc = 0; kc < SUR_HID / MM_K && ok; ++kc) {
-      for (int g = tid; g < SUR_HID * 8; g += SI_THREADS) {
-        const int r = g >> 3, kg = (g & 7) * 8;
-        *reinterpret_cast<uint4*>(sW + mm_off(r, kg)) =
-            __ldg(reinterpret_cast<const uint4*>(a.net.W2b + (long long)r * SUR_HID + kc * MM_K + kg));
+        for (int j = 0; j < 4; ++j) {
+          const int g = tid + j * SI_THREADS;
+          const int r = g >> 3, kg = (g & 7) * 8;
+          if (SRC == SRC_STATES) u[j] = pack_bf16x8(v[j]);
+          *reinterpret_cast<uint4*>(sX + b * SI_X + mm_off(r, kg)) = u[j];
+        }
+      } else if (c == SUR_K1 / MM_K) {
+        // layer-1 epilogue: all layer-1 MMAs done (the other buffer's too), then bias, SiLU, bf16
+        wait_mma(b ^ 1);
+        if (!ok) break;
+#pragma unroll 1
+        for (int cc = 0; cc < 128; cc += 32) {
+          float v[32];
+          tc_ld32(taddr + (uint32_t)cc, v);
+          const int col0 = half * 128 + cc;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = silu_f(v[8 * j + i] + __ldg(b1 + col0 + 8 * j + i));
+            const int col = col0 + 8 * j;
+            *reinterpret_cast<uint4*>(sA + (col / MM_K) * SI_X + mm_off(row, col % MM_K)) = pack_bf16x8(w);
+          }
+        }
+        tc_fence_before();
       }
       proxy_fence();
       __syncthreads();
+      // weights of chunk c present
+      ok = ok && __syncthreads_and(tid != 0 || mbar_wait(&bar_w[b], ph_w[b])) != 0;
+      ph_w[b] ^= 1u;
+      out_w[b] = false;
+      if (!ok) break;
       if (tid == 0) {
         tc_fence_after();
-        tc_mma_chunk(tmem, smem_u32(sA + kc * SI_X), smem_u32(sW), idesc, kc == 0);
-        tc_commit(bar);
+        const uint32_t a0 = c < SUR_K1 / MM_K ? smem_u32(sX + b * SI_X)
+                                              : smem_u32(sA + (c - SUR_K1 / MM_K) * SI_X);
+        tc_mma_chunk(tmem, a0, smem_u32(sW + b * SI_W), idesc, c == 0 || c == SUR_K1 / MM_K);
+        tc_commit(&bar_m[b]);
       }
-      ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
-      phase ^= 1u;
-      tc_fence_after();
+      out_m[b] = true;
     }
     if (!ok) break;
-    // output layer in FP32
+    wait_mma(0);
+    wait_mma(1);
+    if (!ok) break;
+    // output layer in FP32: each half sums its 128 columns
     float acc = 0.0f;
-    for (int c = 0; c < SUR_HID; c += 8) {
-      float v[8];
-      tc_ld8(tmem + lane_base + (uint32_t)c, v);
+#pragma unroll 1
+    for (int cc = 0; cc < 128; cc += 32) {
+      float v[32];
+      tc_ld32(taddr + (uint32_t)cc, v);
+      const int col0 = half * 128 + cc;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) acc = fmaf(silu_f(v[i] + __ldg(b2 + c + i)), __ldg(w3 + c + i), acc);
+      for (int i = 0; i < 32; ++i) acc = fmaf(silu_f(v[i] + __ldg(b2 + col0 + i)), __ldg(w3 + col0 + i), acc);
     }
-    double ll = mean + scale * (double)(acc + b3);
-    if (SRC == SRC_STATES && rowi[tid].valid) ll += (double)a.T[sur_tindex(rowi[tid].base, a.W)];
-    if (rowi[tid].valid) {
-      if (!isfinite(ll) && a.bad) atomicOr(a.bad, 1u);
-      a.out[d] = ll;
-      mymax = fmax(mymax, ll);
-    } else if (a.nan_clipped && d < n) {
-      a.out[d] = __longlong_as_double(0x7ff8000000000000ll);
-    }
+    part[half * 128 + row] = acc;
     tc_fence_before();
+    __syncthreads();
+    if (tid < 128) {
+      const long long dd = t * 128 + tid;
+      double ll = mean + scale * (double)(part[tid] + part[128 + tid] + b3);
+      if (SRC == SRC_STATES && rowi[tid].valid) ll += (double)a.T[sur_tindex(rowi[tid].base, a.W)];
+      if (rowi[tid].valid) {
+        if (!isfinite(ll) && a.bad) atomicOr(a.bad, 1u);
+        a.out[dd] = ll;
+        mymax = fmax(mymax, ll);
+      } else if (a.nan_clipped && dd < n) {
+        a.out[dd] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+    }
     __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(a.err, (unsigned)PCSIR_DERR_TIMEOUT);
+  if (!ok) {
+    if (tid == 0) atomicOr(a.err, (unsigned)PCSIR_DERR_TIMEOUT);
+    // let copies still in flight land before the block's shared memory goes away
+    for (int b = 0; b < 2; ++b)
+      if (out_w[b]) mbar_wait(&bar_w[b], ph_w[b]);
+  }
   if (a.max_ll) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
-    if (lane == 0) s_max[warp] = mymax;
+    if (lane == 0 && warp < 4) s_max[warp] = mymax;
     __syncthreads();
     if (tid == 0) {
       double m = -INFINITY;
-      for (int w = 0; w < SI_THREADS / 32; ++w) m = fmax(m, s_max[w]);
+      for (int w = 0; w < 4; ++w) m = fmax(m, s_max[w]);
       if (m > -INFINITY) atomicMax(a.max_ll, ord_encode(m));
     }
   }
@@ -678,6 +765,7 @@ struct pcsir_surrogate {
   int num_sms = 0;
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *V = nullptr;
   __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+  uint8_t* Wsw = nullptr;  // SI_CHUNKS x 32 KB, inference layout
   double* norm = nullptr;  // device: label mean, scale
   double host_mean = 0.0, host_scale = 1.0;
   __nv_bfloat16* X = nullptr;
@@ -741,7 +829,13 @@ SurFeat make_feat(const pcsir_surrogate* s, double bg, double sigma) {
   return f;
 }
 
-SurNet net_of(const pcsir_surrogate* s) { return SurNet{s->W1b, s->W2b, s->P, s->norm}; }
+SurNet net_of(const pcsir_surrogate* s) { return SurNet{s->Wsw, s->P, s->norm}; }
+
+// inference copy of the weights in the shared-memory layout (after any change of W1b / W2b)
+cudaError_t pack_weights(const pcsir_surrogate* s, cudaStream_t st) {
+  k_sur_pack<<<2 * s->num_sms, 256, 0, st>>>(s->W1b, s->W2b, s->Wsw);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_window(const pcsir_surrogate* s, const float* img, int W, int H, double bg, cudaStream_t st) {
   if ((long long)W * H > s->cfg.max_pixels) return cudaErrorInvalidValue;
@@ -879,6 +973,7 @@ pcsir_status pcsir_surrogate_create(const pcsir_surrogate_config* cfg, pcsir_sur
   s->add_max_blocks = 1 << 12;  // up to 2^20 states per add call
   bool ok = salloc(s, &s->P, NDEV) && salloc(s, &s->G, NDEV) && salloc(s, &s->Mo, NDEV) && salloc(s, &s->V, NDEV) &&
             salloc(s, &s->W1b, (size_t)SUR_HID * SUR_K1) && salloc(s, &s->W2b, (size_t)SUR_HID * SUR_HID) &&
+            salloc(s, &s->Wsw, (size_t)SI_CHUNKS * SI_W) &&
             salloc(s, &s->norm, 2) && salloc(s, &s->X, cap * SUR_K1) && salloc(s, &s->y, cap) && salloc(s, &s->cens, cap) &&
             salloc(s, &s->cb, bt) &&
             salloc(s, &s->count, 1) && salloc(s, &s->add_base, 1) && salloc(s, &s->add_cnt, (size_t)s->add_max_blocks) &&
@@ -898,6 +993,7 @@ pcsir_status pcsir_surrogate_create(const pcsir_surrogate_config* cfg, pcsir_sur
   if (e == cudaSuccess) e = cudaMemset(s->V, 0, NDEV * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(s->W1b, 0, (size_t)SUR_HID * SUR_K1 * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMemset(s->W2b, 0, (size_t)SUR_HID * SUR_HID * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMemset(s->Wsw, 0, (size_t)SI_CHUNKS * SI_W);
   if (e == cudaSuccess) e = cudaMemcpy(s->norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->count, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(s->add_done, 0, sizeof(unsigned));
@@ -931,6 +1027,7 @@ pcsir_status pcsir_surrogate_init(pcsir_surrogate* s, uint64_t seed, void* strea
                                                                                                      s->W2b);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = pack_weights(s, st);
   const double norm0[2] = {0.0, 1.0};
   if (e == cudaSuccess) e = cudaMemsetAsync(s->G, 0, NDEV * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->Mo, 0, NDEV * sizeof(float), st);
@@ -963,6 +1060,7 @@ pcsir_status pcsir_surrogate_set_params(pcsir_surrogate* s, const float* params,
     k_sur_tobf16<<<grid_for((long long)SUR_HID * (SUR_K1 + SUR_HID), 256, s->num_sms), 256>>>(s->P, s->W1b, s->W2b);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = pack_weights(s, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return scuda(s, e, "setting surrogate parameters");
   s->host_mean = label_mean;
@@ -1110,6 +1208,7 @@ pcsir_status pcsir_surrogate_train(pcsir_surrogate* s, int64_t begin, int64_t en
                                                                s->W2b);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && steps > 0) e = pack_weights(s, st);
   if (e != cudaSuccess) return scuda(s, e, "training step");
   return PCSIR_OK;
 }

@@ -135,44 +135,56 @@ __device__ __forceinline__ float silu_grad_f(float t) {
 }
 
 // Stage a rows x 64 chunk of an operand, element (r, k) = src[(r0 + r) srow +
-// (k0 + k) sk], into the swizzled layout; rows >= rows_valid and k >= K
-// are zero.  Three access patterns: K contiguous (sk == 1, 16-byte loads),
-// rows contiguous (srow == 1, lanes over rows), and any other strides.
-template <int NTHREADS>
+// (k0 + k) sk], into the swizzled layout; rows >= rows_valid and k >= K are
+// zero.  Three access patterns: K contiguous (sk == 1, 16-byte loads), rows
+// contiguous (srow == 1, lanes over rows), and any other strides.  Each
+// thread issues all its loads before its shared-memory stores, so their
+// latencies overlap.
+__device__ __forceinline__ uint4 mm_load8(const __nv_bfloat16* src, long long srow, long long sk, int row,
+                                          int rows_valid, int kk, int K) {
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (row < rows_valid) {
+    const __nv_bfloat16* p = src + (long long)row * srow + (long long)kk * sk;
+    if (sk == 1 && kk + 8 <= K && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0u)) {
+      v = __ldg(reinterpret_cast<const uint4*>(p));
+    } else {
+      unsigned short e[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        e[i] = (kk + i < K) ? __bfloat16_as_ushort(p[(long long)i * sk]) : (unsigned short)0;
+      v.x = e[0] | ((unsigned)e[1] << 16);
+      v.y = e[2] | ((unsigned)e[3] << 16);
+      v.z = e[4] | ((unsigned)e[5] << 16);
+      v.w = e[6] | ((unsigned)e[7] << 16);
+    }
+  }
+  return v;
+}
+
+template <int NTHREADS, int NROWS>
 __device__ __forceinline__ void mm_stage(uint8_t* dst, const __nv_bfloat16* src, long long srow, long long sk,
-                                         int r0, int nrows_tile, int rows_valid, int k0, int K) {
-  const int tid = threadIdx.x;
-  const int total = nrows_tile * (MM_K / 8);  // 8-element groups along K
+                                         int r0, int rows_valid, int k0, int K) {
+  constexpr int PER = NROWS * (MM_K / 8) / NTHREADS;  // 8-element groups per thread
+  static_assert(PER * NTHREADS == NROWS * (MM_K / 8), "tile not divisible among threads");
   const bool mn_major = (srow == 1 && sk != 1);
-  for (int g = tid; g < total; g += NTHREADS) {
+  uint4 v[PER];
+  int off[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int g = threadIdx.x + j * NTHREADS;
     int r, kg;
     if (mn_major) {
-      r = g % nrows_tile;
-      kg = (g / nrows_tile) * 8;
+      r = g % NROWS;
+      kg = (g / NROWS) * 8;
     } else {
       r = g / (MM_K / 8);
       kg = (g % (MM_K / 8)) * 8;
     }
-    const int row = r0 + r;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (row < rows_valid) {
-      const int kk = k0 + kg;
-      const __nv_bfloat16* p = src + (long long)row * srow + (long long)kk * sk;
-      if (sk == 1 && kk + 8 <= K && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0u)) {
-        v = *reinterpret_cast<const uint4*>(p);
-      } else {
-        unsigned short e[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          e[i] = (kk + i < K) ? __bfloat16_as_ushort(p[(long long)i * sk]) : (unsigned short)0;
-        v.x = e[0] | ((unsigned)e[1] << 16);
-        v.y = e[2] | ((unsigned)e[3] << 16);
-        v.z = e[4] | ((unsigned)e[5] << 16);
-        v.w = e[6] | ((unsigned)e[7] << 16);
-      }
-    }
-    *reinterpret_cast<uint4*>(dst + mm_off(r, kg)) = v;
+    off[j] = (int)mm_off(r, kg);
+    v[j] = mm_load8(src, srow, sk, r0 + r, rows_valid, k0 + kg, K);
   }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) *reinterpret_cast<uint4*>(dst + off[j]) = v[j];
 }
 
 // ---------------------------------------------------------------------------
