@@ -378,6 +378,8 @@ def main():
     ap.add_argument("--matched-seqs", type=int, default=2)
     ap.add_argument("--surrogate-rows", type=int, default=10_000_000)
     ap.add_argument("--surrogate-steps", type=int, default=100_000)
+    ap.add_argument("--pseudo-reps", type=int, default=100, help="repetitions of the pseudo-tracking experiment "
+                    "(Section 5.4; 0 skips it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -520,6 +522,16 @@ def main():
         matched = run_matched(N, args.surrogate_rows, args.surrogate_steps, args.matched_seqs, args.matched_frames,
                               SEED + 31 + 1000 * rank)
 
+    pseudo = None
+    if args.pseudo_reps > 0:
+        from paper_1310_5541_gb300 import pseudo_tracking
+
+        t0 = time.perf_counter()
+        pseudo = pseudo_tracking.run(counts=(1000, 10000, 100000), reps=args.pseudo_reps, seed=SEED + 41 + rank)
+        pseudo["sir_slope"] = {p: pseudo_tracking.convergence_slope(pseudo["counts"], t["sir"])
+                               for p, t in pseudo["rmse_px"].items()}
+        pseudo["seconds"] = time.perf_counter() - t0
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_s = 1 << 18
@@ -541,7 +553,8 @@ def main():
                           "scan_resample": st_mean[3], "share": [float(s) for s in share],
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
-            "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "cpu_baseline": cpu,
+            "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
+            "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),
             "device_error": derr,

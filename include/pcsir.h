@@ -97,7 +97,16 @@ typedef struct pcsir_config {
   double bg;             /* background intensity; > 0 for PCSIR_LIK_POISSON */
   double sigma_xi;       /* > 0; used by PCSIR_LIK_SSE only */
   int64_t max_particles; /* 1 .. 2^26 */
+  int32_t dummy;         /* PCSIR_DUMMY_COM (0) or PCSIR_DUMMY_COC (1), see below */
+  int32_t reserved;      /* must be 0 */
 } pcsir_config;
+
+/* Placement of the dummy particle of a cell (Section 5.4): at the centre of
+   mass of its members (pcSIR-CoM, Algorithm 2), or at the cell's geometric
+   centre ((bx + 1/2) h - 1/2, (by + 1/2) h - 1/2) for the binned position
+   with the members' mean for the other components (pcSIR-CoC). */
+#define PCSIR_DUMMY_COM 0
+#define PCSIR_DUMMY_COC 1
 
 /* Scalars of one step, in host memory (see result_host below). */
 typedef struct pcsir_result {

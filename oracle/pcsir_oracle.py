@@ -235,8 +235,20 @@ def sir_step(state, image, noise, u0, model, lik=None, prior_logw=None):
                 estimate=posterior_mean(w, prop), ancestors=anc, new_state=np.ascontiguousarray(prop[:, anc]))
 
 
-def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None):
+def cell_centres(keys: np.ndarray, h: float) -> np.ndarray:
+    """Geometric centres of cells (bx, by): the cell [b h - 1/2, (b + 1) h - 1/2) has its
+    centre at (b + 1/2) h - 1/2 (Section 5.4, pcSIR-CoC).  FP64, [2, B]."""
+    k = np.asarray(keys, np.float64)
+    return np.stack([(k[:, 0] + 0.5) * h - 0.5, (k[:, 1] + 0.5) * h - 0.5])
+
+
+def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None, dummy="com"):
     """Algorithm 2, one time step k, with resampling at every step.
+
+    ``dummy``: "com" places each dummy at the centre of mass of its members
+    (pcSIR-CoM); "coc" at the geometric centre of its cell for the binned
+    components (x, y), the members' mean for the others (pcSIR-CoC,
+    Section 5.4).
 
     Returns the same keys as ``sir_step`` plus the bins (keys [B, 2] as
     (bx, by) in ascending (by, bx) order, counts), the member -> bin map, the
@@ -248,6 +260,10 @@ def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None):
     keys, member, counts = segment(bx, by)
     prior_w = None if prior_logw is None else np.exp(prior_logw - np.max(prior_logw))
     dum = dummies(prop, member, keys.shape[0], prior_w)
+    if dummy == "coc":
+        dum[[X, Y]] = cell_centres(keys, h)
+    elif dummy != "com":
+        raise ValueError(dummy)
     ll_bins = lik(dum[X], dum[Y], dum[I0])
     ll = ll_bins[member]
     logw = ll if prior_logw is None else prior_logw + ll

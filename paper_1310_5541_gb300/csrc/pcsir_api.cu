@@ -133,6 +133,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   if (cfg->max_particles < 1 || cfg->max_particles > MAX_PARTICLES) return PCSIR_EINVAL;
   if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK))
     return PCSIR_EINVAL;
+  if ((cfg->dummy != PCSIR_DUMMY_COM && cfg->dummy != PCSIR_DUMMY_COC) || cfg->reserved != 0) return PCSIR_EINVAL;
 
   pcsir_ctx* c = new (std::nothrow) pcsir_ctx();
   if (!c) return PCSIR_ENOMEM;
@@ -149,6 +150,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   c->m.sigma = cfg->psf_sigma;
   c->m.bg = cfg->bg;
   c->m.sigma_xi = cfg->sigma_xi > 0.0 ? cfg->sigma_xi : 1.0;
+  c->m.coc = cfg->dummy == PCSIR_DUMMY_COC ? 1 : 0;
 
   const int64_t nmax = cfg->max_particles;
   int hbits = 1;

@@ -41,7 +41,7 @@ struct BatchStats {  // per target, zeroed every step
   unsigned long long dhi, dlo, uhi, ulo;
   long long anchor[3];
   unsigned int nbins;
-  unsigned int pad;
+  float inv_delta;  // 1 / Delta rounded to FP32 (first guesses of output indices)
 };
 
 struct BatchCtl {  // zeroed every step
@@ -464,6 +464,20 @@ __device__ long long bfirst_out(const BatchStats& S, long long C, long long N) {
   return i;
 }
 
+// bfirst_out without FP64: a float guess of (C - U0) / Delta, then the exact integer correction
+__device__ long long bfirst_out_f(const BatchStats& S, long long C, long long N) {
+  if (C <= 0) return 0;
+  if (S.dhi == 0ull && S.dlo == 0ull) return N;
+  long long back;
+  const float cf = i64_trunc_float(C - (long long)S.uhi, &back);
+  const float xf = __fmul_rn(cf, S.inv_delta);
+  long long i = xf <= 0.0f ? 0 : (xf >= (float)N ? N : (long long)__float2int_rn(xf));
+  int guard = 0;
+  while (i > 0 && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i - 1) >= C && guard++ < 256) --i;
+  while (i < N && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i) < C && guard++ < 512) ++i;
+  return i;
+}
+
 __device__ void phase_tile_sums(const BatchBufs& b) {
   __shared__ long long red[BT_THREADS / 32];
   for (int item = blockIdx.x; item < b.ntiles_total; item += gridDim.x) {
@@ -504,6 +518,8 @@ __device__ void phase_target_scan(const BatchBufs& b, const double* __restrict__
     const unsigned long long n = (unsigned long long)T_.n;
     S_.dhi = Tq / n;
     S_.dlo = (unsigned long long)(((unsigned __int128)(Tq % n) << 64) / n);
+    const double dd = (double)S_.dhi + (double)S_.dlo * 5.421010862427522e-20;
+    S_.inv_delta = dd > 0.0 ? (float)(1.0 / dd) : 0.0f;
     double uf = u0s[t] * 18446744073709551616.0;
     if (!(uf >= 0.0)) uf = 0.0;
     const unsigned long long u0f = uf >= 18446744073709549568.0 ? 18446744073709549568ull : __double2ull_rz(uf);
@@ -568,7 +584,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
     __syncthreads();
     const long long lo = sm.s_lo, hi = sm.s_hi;
     const bool zero_sum = (S_.dhi == 0ull && S_.dlo == 0ull);
-    long long cur = bfirst_out(S_, excl + texcl, N);
+    long long cur = bfirst_out_f(S_, excl + texcl, N);
     unsigned long long ufrac = (unsigned long long)cur * S_.dlo + S_.ulo;
     long long uint_cur = bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, cur);
     int kk = 0;

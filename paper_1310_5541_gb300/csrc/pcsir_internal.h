@@ -26,6 +26,8 @@ struct Control {
   long long anchor[5];        // fixed-point anchors of the non-position components
   unsigned int tiles_done;    // finished tiles of the resampling kernel
   unsigned int tsum_done;     // finished tiles of the tile-sum kernel
+  float inv_delta;            // 1 / Delta rounded to FP32 (first guesses of output indices)
+  float spare_f;
 };
 
 // Limits of the fixed-point centre-of-mass sums.  Position offsets from the
@@ -80,6 +82,7 @@ struct ModelParams {
   double sigma;
   double bg;
   double sigma_xi;
+  int coc;  // 1: dummies at cell centres (pcSIR-CoC)
 };
 
 // Optional stage events: when ev != nullptr the launchers record ev[1..] after

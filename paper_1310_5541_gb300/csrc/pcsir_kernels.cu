@@ -391,7 +391,8 @@ struct SurBins {
 
 template <bool SUR>
 __global__ void __launch_bounds__(BIN_THREADS)
-k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq, SurBins sb) {
+k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H, long long hq, double h, int coc,
+       SurBins sb) {
   constexpr int NG = BIN_THREADS / BIN_GROUP;
   __shared__ float scratch[NG][4 * MAXP];
   __shared__ int red[NG][3 * (BIN_GROUP / 32)];
@@ -412,6 +413,10 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
     mean[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
 #pragma unroll
     for (int c = 2; c < 5; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    if (coc) {  // pcSIR-CoC: the cell's geometric centre
+      mean[0] = ((double)bx + 0.5) * h - 0.5;
+      mean[1] = ((double)by + 0.5) * h - 0.5;
+    }
     if (gtid == 0) {
       b.bin_xy[bi] = bx;
       b.bin_xy[bs + bi] = by;
@@ -560,7 +565,11 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
   }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N, int sq) {
+// The posterior mean (Alg. 1) is the weighted mean over particles: per bin,
+// weight x member count x centre of mass.  With pcSIR-CoC the dummy sits at
+// the cell centre, so the centre of mass of the position is recomputed from
+// the exact sums here.
+__global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N, int sq, long long hq, int coc) {
   const unsigned B = b.ctl->nocc;
   // only as many blocks as there are bins to cover take part
   const unsigned need = (B + blockDim.x - 1) / blockDim.x;
@@ -581,8 +590,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_binred(StepBuffers b, int64_t N
     a.Tf += n * wt;
     a.T2 += n * wt * wt;
     a.Tint += (long long)b.bin_cnt[bi] * q;
+    double pos[2] = {b.dummy[bi], b.dummy[bs + bi]};
+    if (coc) {
+      const size_t hcap = size_t(1) << b.hbits;
+      const unsigned long long key = b.hkey[g];
+      pos[0] = ((double)((long long)key_bx(key) * hq) + (double)b.hsum[g] / n) * POS_INV;
+      pos[1] = ((double)((long long)key_by(key) * hq) + (double)b.hsum[hcap + g] / n) * POS_INV;
+    }
+    a.est[0] += n * wt * pos[0];
+    a.est[1] += n * wt * pos[1];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.est[c] += n * wt * b.dummy[c * bs + bi];
+    for (int c = 2; c < 5; ++c) a.est[c] += n * wt * b.dummy[c * bs + bi];
   }
   block_reduce_commit(a, b, N, 1, true, active);
 }
@@ -785,11 +803,11 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
   if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
   const LikParams lp = make_lik(m);
   if (sur == nullptr) {
-    k_bins<false><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, SurBins{});
+    k_bins<false><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, h, m.coc, SurBins{});
     e = cudaGetLastError();
   } else {
     const SurBins sb{sur->salt, sur->frac, sur->min_holdout, sur->ho_cap, sur->ho_bin, sur->ho_ll, sur->stats};
-    k_bins<true><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, sb);
+    k_bins<true><<<num_sms * 4, BIN_THREADS, 0, s>>>(b, lp, img, W, H, hq, h, m.coc, sb);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_sur_step(*sur, b, m, img, W, H, s);
     if (e == cudaSuccess) {
@@ -798,7 +816,7 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
     }
   }
   if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
-  k_binred<<<num_sms * 2, RED_THREADS, 0, s>>>(b, N, weight_scale_bits(N));
+  k_binred<<<num_sms * 2, RED_THREADS, 0, s>>>(b, N, weight_scale_bits(N), hq, m.coc);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return mark(se, 3, s);
 }

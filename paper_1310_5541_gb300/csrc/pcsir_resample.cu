@@ -25,7 +25,6 @@ constexpr int RS_WINDOW = 5120;  // outputs mapped to ancestors per pass (a tile
 
 struct Map64 {
   unsigned long long dhi, dlo, uhi, ulo;
-  double dd, ud;
 };
 
 // integer part of i * Delta + U0
@@ -38,11 +37,13 @@ __device__ __forceinline__ long long u_int(const Map64& mp, long long i) {
   return (long long)(ui * mp.dhi + mp.uhi + phi + carry);
 }
 
-// first output index i in [0, N] with U_i >= C
+// first output index i in [0, N] with U_i >= C (FP64 first guess: one thread per block)
 __device__ long long first_out(const Map64& mp, long long C, long long N) {
   if (C <= 0) return 0;
-  if (mp.dd <= 0.0) return N;
-  double x = ((double)C - mp.ud) / mp.dd;
+  const double dd = (double)mp.dhi + (double)mp.dlo * 5.421010862427522e-20;
+  const double ud = (double)mp.uhi + (double)mp.ulo * 5.421010862427522e-20;
+  if (dd <= 0.0) return N;
+  double x = ((double)C - ud) / dd;
   long long i = x < 0.0 ? 0 : (x > (double)N ? N : (long long)ceil(x));
   int guard = 0;
   while (i > 0 && u_int(mp, i - 1) >= C && guard++ < 64) --i;
@@ -71,8 +72,6 @@ __device__ __forceinline__ Map64 load_map(const Control* ctl) {
   mp.dlo = ctl->delta_lo;
   mp.uhi = ctl->u0_hi;
   mp.ulo = ctl->u0_lo;
-  mp.dd = (double)mp.dhi + (double)mp.dlo * 5.421010862427522e-20;
-  mp.ud = (double)mp.uhi + (double)mp.ulo * 5.421010862427522e-20;
   return mp;
 }
 
@@ -204,6 +203,8 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
     ctl->delta_lo = dlo;
     ctl->u0_hi = (unsigned long long)(tot >> 64);
     ctl->u0_lo = (unsigned long long)tot;
+    const double dd = (double)dhi + (double)dlo * 5.421010862427522e-20;
+    ctl->inv_delta = dd > 0.0 ? (float)(1.0 / dd) : 0.0f;
     if (T == 0ull) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
   }
 }
@@ -284,7 +285,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   const long long lo = s_lo, hi = s_hi;
   const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
-  const float inv_delta = (float)(1.0 / mp.dd);
+  const float inv_delta = ctl->inv_delta;
   long long cur = first_out_f(mp, excl + texcl, N, inv_delta);  // first output of this thread's particles
   // U_cur kept as integer part + 64-bit fraction and advanced by Delta per output
   unsigned long long ufrac = (unsigned long long)cur * mp.dlo + mp.ulo;

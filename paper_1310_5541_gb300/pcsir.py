@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, ENOTSUP, ERANGE = 0, -1, -2, -3, -
 F32, F64 = 0, 1
 LIK_POISSON, LIK_SSE = 0, 1
 KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN, KEEP_LOGLIK = 1, 2, 4, 8
+DUMMY_COM, DUMMY_COC = 0, 1
 DERR_RANGE, DERR_TIMEOUT, DERR_NONFINITE, DERR_ZEROSUM = 1, 2, 4, 8
 
 _STATUS_NAMES = {0: "PCSIR_OK", -1: "PCSIR_EINVAL", -2: "PCSIR_ENOMEM", -3: "PCSIR_ECUDA",
@@ -31,7 +32,8 @@ _STATUS_NAMES = {0: "PCSIR_OK", -1: "PCSIR_EINVAL", -2: "PCSIR_ENOMEM", -3: "PCS
 class pcsir_config(ctypes.Structure):
     _fields_ = [("state_dtype", ctypes.c_int32), ("lik_kind", ctypes.c_int32), ("patch", ctypes.c_int32),
                 ("keep", ctypes.c_int32), ("psf_sigma", ctypes.c_double), ("bg", ctypes.c_double),
-                ("sigma_xi", ctypes.c_double), ("max_particles", ctypes.c_int64)]
+                ("sigma_xi", ctypes.c_double), ("max_particles", ctypes.c_int64), ("dummy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class pcsir_result(ctypes.Structure):
@@ -155,12 +157,13 @@ class Context:
     """Owns one ``pcsir_ctx`` (workspace for up to ``max_particles`` particles)."""
 
     def __init__(self, max_particles, state_dtype=torch.float32, lik="poisson", patch=9, psf_sigma=1.5,
-                 bg=10.0, sigma_xi=20.0, keep=0):
+                 bg=10.0, sigma_xi=20.0, keep=0, dummy="com"):
         self.torch_dtype = state_dtype
         cfg = pcsir_config(state_dtype=F32 if state_dtype == torch.float32 else F64,
                            lik_kind=LIK_POISSON if lik == "poisson" else LIK_SSE, patch=int(patch), keep=int(keep),
                            psf_sigma=float(psf_sigma), bg=float(bg), sigma_xi=float(sigma_xi),
-                           max_particles=int(max_particles))
+                           max_particles=int(max_particles), dummy=DUMMY_COC if dummy == "coc" else DUMMY_COM,
+                           reserved=0)
         h = ctypes.c_void_p()
         st = lib.pcsir_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:

@@ -41,9 +41,9 @@ def pc():
 KEEP_ALL = 1 | 2 | 4 | 8
 
 
-def _ctx(pc, N, dtype, model, keep=KEEP_ALL):
+def _ctx(pc, N, dtype, model, keep=KEEP_ALL, dummy="com"):
     return pc.Context(N, dtype, lik=model.lik, patch=model.patch, psf_sigma=model.sigma_psf, bg=model.bg,
-                      sigma_xi=model.sigma_xi, keep=keep)
+                      sigma_xi=model.sigma_xi, keep=keep, dummy=dummy)
 
 
 def _warm_state(seq, N, model, dtype, frames, h=None):
@@ -105,8 +105,8 @@ def run_sir(pc, ctx, st_np, img_np, nz_np, u0):
     return st.cpu().numpy(), res, out
 
 
-def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model):
-    ref = O.pcsir_step(st_np, img, nz, u0, h, model)
+def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model, dummy="com"):
+    ref = O.pcsir_step(st_np, img, nz, u0, h, model, dummy=dummy)
     new, res, out = run_pcsir(pc, ctx, st_np, img, nz, u0, h)
     assert res["device_error"] == 0 and res["kind"] == 1
     np.testing.assert_array_equal(out["prop_state"], ref["prop"])
@@ -151,18 +151,19 @@ def compare_sir(pc, ctx, st_np, img, nz, u0, model):
 MODEL_SMALL = synth.Model(sigma_psf=1.5, I0=100.0, bg=10.0, patch=9)
 
 
-@pytest.mark.parametrize("h", [0.5, 1.0, 0.1])
-def test_pcsir_fp64_small_image(pc, h):
+@pytest.mark.parametrize("h,dummy", [(0.5, "com"), (1.0, "com"), (0.1, "com"), (1.0, "coc"), (0.3, "coc")])
+def test_pcsir_fp64_small_image(pc, h, dummy):
     seq = synth.make_sequence(64, 64, 4, MODEL_SMALL, seed=SEED + 1)
     N = 10_000
     st = _warm_state(seq, N, MODEL_SMALL, np.float64, 2, h=0.5)
-    ctx = _ctx(pc, N, torch.float64, MODEL_SMALL)
+    ctx = _ctx(pc, N, torch.float64, MODEL_SMALL, dummy=dummy)
     for k in (2, 3):
         nz = synth.make_noise(N, MODEL_SMALL.q, SEED + 1, k, np.float64)
-        r = compare_pcsir(pc, ctx, st, seq.images[k], nz, synth.make_u0(SEED + 1, k), h, MODEL_SMALL)
-        print("pcSIR fp64 h=%g frame %d: %s" % (h, k, r))
+        r = compare_pcsir(pc, ctx, st, seq.images[k], nz, synth.make_u0(SEED + 1, k), h, MODEL_SMALL, dummy=dummy)
+        print("pcSIR-%s fp64 h=%g frame %d: %s" % (dummy, h, k, r))
         assert r["mismatches"] <= 0.01 * N
-        st = O.pcsir_step(st, seq.images[k], nz, synth.make_u0(SEED + 1, k), h, MODEL_SMALL)["new_state"]
+        st = O.pcsir_step(st, seq.images[k], nz, synth.make_u0(SEED + 1, k), h, MODEL_SMALL,
+                          dummy=dummy)["new_state"]
     ctx.close()
 
 
@@ -231,6 +232,18 @@ def test_cell_table_size_does_not_change_the_step(pc, big_case):
         # normalised weights divide by a sum accumulated with atomics: equal up to its rounding order
         np.testing.assert_allclose(outs[0][3], other[3], rtol=1e-12, atol=0)
         np.testing.assert_allclose(outs[0][4], other[4], rtol=1e-12)
+
+
+@pytest.mark.parametrize("h", [0.25, 1.0])
+def test_pcsir_coc_fp32_big_image(pc, big_case, h):
+    """pcSIR-CoC (Section 5.4): dummies at the cells' geometric centres."""
+    seq, N, st = big_case
+    ctx = _ctx(pc, N, torch.float32, MODEL_BIG, dummy="coc")
+    nz = synth.make_noise(N, MODEL_BIG.q, SEED + 6, 2, np.float32)
+    r = compare_pcsir(pc, ctx, st, seq.images[2], nz, synth.make_u0(SEED + 6, 2), h, MODEL_BIG, dummy="coc")
+    print("pcSIR-CoC fp32 h=%g: %s" % (h, r))
+    assert r["mismatches"] <= 0.05 * N
+    ctx.close()
 
 
 def test_sir_fp32_big_image(pc, big_case):

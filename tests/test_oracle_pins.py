@@ -407,3 +407,41 @@ def test_monte_carlo_rate_is_inverse_sqrt_n():
         rmse.append(math.sqrt(np.mean(e2)))
     slope = np.polyfit(np.log(Ns), np.log(rmse), 1)[0]
     assert -0.65 < slope < -0.35
+
+
+def test_coc_dummies_sit_at_cell_centres():
+    """pcSIR-CoC (Section 5.4): the binned components of each dummy are its cell's geometric
+    centre, checked by a loop over the cells; the other components stay the members' mean, and
+    with particles on a lattice centred in each cell CoC and CoM coincide."""
+    rng = np.random.default_rng(21)
+    m = synth.Model(patch=9)
+    img = rng.poisson(synth.render(32, 32, 15.2, 14.7, 100.0, 10.0, 1.5)).astype(np.float32)
+    N = 500
+    st = np.zeros((5, N))
+    st[0] = 15.0 + rng.normal(0, 1.0, N)
+    st[1] = 15.0 + rng.normal(0, 1.0, N)
+    st[4] = 100.0 + rng.normal(0, 3.0, N)
+    nz = np.zeros_like(st)
+    for h in (0.5, 1.0, 0.3):
+        r = O.pcsir_step(st, img, nz, 0.4, h, m, dummy="coc")
+        com = O.pcsir_step(st, img, nz, 0.4, h, m)
+        for j, (bx, by) in enumerate(r["bin_keys"]):
+            lo_x, lo_y = bx * h - 0.5, by * h - 0.5
+            assert r["dummies"][0, j] == pytest.approx(lo_x + h / 2, abs=1e-12)
+            assert r["dummies"][1, j] == pytest.approx(lo_y + h / 2, abs=1e-12)
+        np.testing.assert_array_equal(r["dummies"][2:], com["dummies"][2:])
+    # a 2 x 2 lattice centred in every cell: centre of mass = cell centre
+    h = 1.0
+    cx, cy = np.meshgrid(np.arange(10, 20), np.arange(12, 18))
+    pts = []
+    for dx in (-0.25, 0.25):
+        for dy in (-0.25, 0.25):
+            pts.append(np.stack([cx.ravel() + dx, cy.ravel() + dy]))
+    P2 = np.concatenate(pts, axis=1)
+    lat = np.zeros((5, P2.shape[1]))
+    lat[:2] = P2
+    lat[4] = 100.0
+    a = O.pcsir_step(lat, img, np.zeros_like(lat), 0.4, h, m, dummy="coc")
+    b = O.pcsir_step(lat, img, np.zeros_like(lat), 0.4, h, m)
+    np.testing.assert_allclose(a["dummies"], b["dummies"], atol=1e-12)
+    np.testing.assert_allclose(a["estimate"], b["estimate"], rtol=1e-12)
