@@ -361,6 +361,55 @@ def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_ca
     return out
 
 
+def run_large_object(counts, n_frames, seed):
+    """The paper's large-object regime (Section 5.3): 512 x 512 frames, PSF sigma 13 px, SNR 2, speed
+    U[2, 7] px/frame, Gaussian (SSE) likelihood over a 65 x 65 kernel.  SIR, pcSIR-1x1 (h = 1) and
+    pcSIR-2x2 (h = 0.5) filter the same sequence with the same noise; per method and particle count
+    the device time per step (CUDA events around each step) and the tracking RMSE."""
+    import numpy as np
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m = synth.large_object_model()
+    seq = synth.large_object_sequence(n_frames, seed)
+    imgs = torch.from_numpy(seq.images).to(dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in counts:
+        pool = [torch.from_numpy(synth.make_noise(N, m.q, seed + 3, j, np.float32)).to(dev) for j in range(NOISE_POOL)]
+        ctx = pcsir.Context(N, torch.float32, lik="sse", patch=m.patch, psf_sigma=m.sigma_psf, bg=m.bg,
+                            sigma_xi=m.sigma_xi)
+        for name, h in (("sir", None), ("pcsir-1x1", 1.0), ("pcsir-2x2", 0.5)):
+            st = torch.from_numpy(synth.initial_state(seq.gt[0], N, np.float32)).to(dev)
+            ms, errs = [], []
+            for k in range(n_frames):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                u0 = synth.make_u0(seed + 5, k)
+                a.record(stream)
+                if h is None:
+                    pcsir.sir_step(ctx, st, imgs[k], pool[k % NOISE_POOL], u0, stream)
+                else:
+                    pcsir.pcsir_step(ctx, st, imgs[k], h, pool[k % NOISE_POOL], u0, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if k >= 2:
+                    ms.append(a.elapsed_time(b))
+                r = ctx.last_result()
+                errs.append(np.array(r["estimate"][:2]) - seq.gt[k + 1, :2])
+            e = np.array(errs)
+            rows.append({"method": name, "N": N, "ms_per_step": float(np.mean(ms)),
+                         "rmse_px": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1))))})
+        ctx.close()
+    for r in rows:
+        sir = next(x for x in rows if x["N"] == r["N"] and x["method"] == "sir")
+        r["speedup_vs_sir"] = sir["ms_per_step"] / r["ms_per_step"]
+        r["rmse_vs_sir"] = r["rmse_px"] / sir["rmse_px"] - 1.0
+    return {"workload": "large object: 512x512, PSF sigma 13 px, SNR 2, SSE likelihood sigma_xi 30, 65x65 kernel",
+            "frames": n_frames, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,6 +429,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=100_000)
     ap.add_argument("--pseudo-reps", type=int, default=100, help="repetitions of the pseudo-tracking experiment "
                     "(Section 5.4; 0 skips it)")
+    ap.add_argument("--large-frames", type=int, default=50, help="frames of the large-object comparison "
+                    "(Section 5.3; 0 skips it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -532,6 +583,10 @@ def main():
                                for p, t in pseudo["rmse_px"].items()}
         pseudo["seconds"] = time.perf_counter() - t0
 
+    large = None
+    if args.large_frames > 0:
+        large = run_large_object((12800, 1 << 17, 1 << 20), args.large_frames, SEED + 53 + 1000 * rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_s = 1 << 18
@@ -554,6 +609,7 @@ def main():
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
+            "large_object": large,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),

@@ -91,7 +91,7 @@ enum {
 typedef struct pcsir_config {
   int32_t state_dtype;   /* PCSIR_F32 or PCSIR_F64 */
   int32_t lik_kind;      /* PCSIR_LIK_POISSON or PCSIR_LIK_SSE */
-  int32_t patch;         /* odd, 1 .. 63 */
+  int32_t patch;         /* odd, 1 .. 127 */
   int32_t keep;          /* PCSIR_KEEP_* flags */
   double psf_sigma;      /* > 0, pixels */
   double bg;             /* background intensity; > 0 for PCSIR_LIK_POISSON */

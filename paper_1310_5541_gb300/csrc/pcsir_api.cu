@@ -125,7 +125,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   if (!cfg) return PCSIR_EINVAL;
   if (cfg->state_dtype != PCSIR_F32 && cfg->state_dtype != PCSIR_F64) return PCSIR_EINVAL;
   if (cfg->lik_kind != PCSIR_LIK_POISSON && cfg->lik_kind != PCSIR_LIK_SSE) return PCSIR_EINVAL;
-  if (cfg->patch < 1 || cfg->patch > 63 || (cfg->patch & 1) == 0) return PCSIR_EINVAL;
+  if (cfg->patch < 1 || cfg->patch > 127 || (cfg->patch & 1) == 0) return PCSIR_EINVAL;
   if (!(cfg->psf_sigma > 0.0) || !std::isfinite(cfg->psf_sigma)) return PCSIR_EINVAL;
   if (cfg->lik_kind == PCSIR_LIK_POISSON && !(cfg->bg > 0.0)) return PCSIR_EINVAL;
   if (cfg->lik_kind == PCSIR_LIK_SSE && !(cfg->sigma_xi > 0.0)) return PCSIR_EINVAL;

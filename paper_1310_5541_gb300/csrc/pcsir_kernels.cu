@@ -338,7 +338,7 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
 // update of the dummy only).  One warp per occupied bin.
 // ---------------------------------------------------------------------------
 constexpr int BIN_THREADS = 256;
-constexpr int MAXP = 63;
+constexpr int MAXP = 127;  // largest patch side (shared-memory factor tables)
 
 __device__ __forceinline__ void block_max_to_global(double v, Control* ctl) {
   __shared__ double red[32];

@@ -61,11 +61,11 @@ class Sequence:
 
 
 def make_sequence(W: int, H: int, n_frames: int, model: Model, seed: int,
-                  start=None, vmax=None, margin=None) -> Sequence:
+                  start=None, vmax=None, margin=None, vmin=None) -> Sequence:
     """Ground-truth track and its noisy image sequence.
 
     The track starts at ``start`` (default: image centre) with a speed drawn
-    uniformly in [vmax/2, vmax] px/frame in a uniformly random direction and
+    uniformly in [vmin, vmax] px/frame (vmin defaults to vmax/2) in a uniformly random direction and
     then follows the nearly-constant-velocity model with the model's process
     noise on velocity and intensity (positions advance by the velocity only,
     so the spot moves smoothly).  ``vmax`` defaults to the largest speed that
@@ -79,7 +79,7 @@ def make_sequence(W: int, H: int, n_frames: int, model: Model, seed: int,
     if vmax is None:
         vmax = max(0.05, (min(W, H) / 2.0 - margin) / max(n_frames, 1))
     for _attempt in range(1000):
-        speed = rng.uniform(vmax / 2.0, vmax)
+        speed = rng.uniform(vmax / 2.0 if vmin is None else vmin, vmax)
         ang = rng.uniform(0.0, 2.0 * math.pi)
         s = np.array([start[0], start[1], speed * math.cos(ang), speed * math.sin(ang), model.I0])
         gt = [s.copy()]
@@ -258,3 +258,25 @@ def pseudo_case(prior: str, N: int, seed: int, rep: int, W: int = 32, sigma_psf:
         raise ValueError(prior)
     st[4] = i0
     return img.astype(np.float32), (x0, y0), st.astype(dtype), float(rng.random())
+
+
+# Large-object tracking (Section 5.3): PSF sigma 13 px, SNR 2, speed U[2, 7]
+# px/frame, 512 x 512 frames, 65 x 65 likelihood kernel with the paper's
+# Gaussian (SSE) likelihood.
+def large_object_model(sigma_xi: float = 30.0) -> Model:
+    bg = 10.0
+    return Model(sigma_psf=13.0, I0=i0_from_snr(2.0, bg), bg=bg, patch=65, lik="sse", sigma_xi=sigma_xi,
+                 q=(0.5, 0.5, 0.1, 0.1, 0.1))
+
+
+def large_object_sequence(n_frames: int, seed: int, W: int = 512) -> Sequence:
+    """A track starting at a random position, speed U[2, 7] px/frame, kept 40 px inside the frame."""
+    m = large_object_model()
+    rng = np.random.default_rng([seed, 9])
+    margin = 40.0
+    vmax = 7.0
+    # start far enough from the border for the whole straight-line track
+    room = margin + vmax * n_frames
+    lo, hi = min(room, W / 2.0), max(W - 1 - room, W / 2.0)
+    start = (rng.uniform(lo, hi), rng.uniform(lo, hi))
+    return make_sequence(W, W, n_frames, m, seed, start=start, vmax=vmax, vmin=2.0, margin=margin)

@@ -273,6 +273,35 @@ def test_sse_likelihood_pcsir(pc):
 # ---------------------------------------------------------------------------
 # Stand-alone likelihood and resampling entry points
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_sse_large_object_65x65(pc, h):
+    """The paper's large-object regime (Section 5.3): PSF sigma 13 px, SNR 2, the Gaussian (SSE)
+    likelihood over a 65 x 65 kernel, pcSIR-1x1 and pcSIR-2x2."""
+    m = synth.large_object_model()
+    seq = synth.make_sequence(192, 160, 3, m, seed=SEED + 30, margin=40)
+    N = 20_000 + 37
+    st = _warm_state(seq, N, m, np.float32, 2, h=h)
+    ctx = _ctx(pc, N, torch.float32, m)
+    nz = synth.make_noise(N, m.q, SEED + 30, 2, np.float32)
+    r = compare_pcsir(pc, ctx, st, seq.images[2], nz, synth.make_u0(SEED + 30, 2), h, m)
+    print("pcSIR SSE 65x65 h=%g: %s" % (h, r))
+    assert r["mismatches"] <= 0.01 * N
+    ctx.close()
+
+
+def test_sse_large_object_sir_65x65(pc):
+    m = synth.large_object_model()
+    seq = synth.make_sequence(192, 160, 3, m, seed=SEED + 31, margin=40)
+    N = 3000 + 5
+    st = _warm_state(seq, N, m, np.float32, 2, h=1.0)
+    ctx = _ctx(pc, N, torch.float32, m, keep=1 | 2 | 8)
+    nz = synth.make_noise(N, m.q, SEED + 31, 2, np.float32)
+    r = compare_sir(pc, ctx, st, seq.images[2], nz, synth.make_u0(SEED + 31, 2), m)
+    print("SIR SSE 65x65:", r)
+    assert r["mismatches"] <= 0.01 * N
+    ctx.close()
+
+
 def test_loglik_entry_point(pc):
     seq = synth.make_sequence(96, 80, 1, MODEL_BIG, seed=SEED + 6)
     img = seq.images[0]

@@ -71,7 +71,7 @@ def test_invalid_configs_rejected_on_host(binding):
     lib = binding.lib
     base = dict(state_dtype=0, lik_kind=0, patch=9, keep=0, psf_sigma=1.5, bg=10.0, sigma_xi=20.0,
                 max_particles=1000, dummy=0, reserved=0)
-    bad = [dict(patch=8), dict(patch=0), dict(patch=65), dict(state_dtype=2), dict(lik_kind=5),
+    bad = [dict(patch=8), dict(patch=0), dict(patch=129), dict(state_dtype=2), dict(lik_kind=5),
            dict(psf_sigma=0.0), dict(bg=0.0), dict(max_particles=0), dict(max_particles=(1 << 26) + 1),
            dict(keep=64), dict(keep=16), dict(lik_kind=1, sigma_xi=0.0), dict(dummy=2), dict(reserved=1)]
     for upd in bad:
