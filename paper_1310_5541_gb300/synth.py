@@ -280,3 +280,59 @@ def large_object_sequence(n_frames: int, seed: int, W: int = 512) -> Sequence:
     lo, hi = min(room, W / 2.0), max(W - 1 - room, W / 2.0)
     start = (rng.uniform(lo, hi), rng.uniform(lo, hi))
     return make_sequence(W, W, n_frames, m, seed, start=start, vmax=vmax, vmin=2.0, margin=margin)
+
+
+# ----------------------------------------------------------------------------
+# 3D tracking: state (x, y, z, vx, vy, vz, I0), volumes V[z, y, x] with an
+# anisotropic Gaussian PSF and Poisson noise.
+# ----------------------------------------------------------------------------
+D3 = 7
+Q3 = (0.5, 0.5, 0.5, 0.1, 0.1, 0.1, 1.0)
+
+
+def render3(W: int, H: int, D: int, x0: float, y0: float, z0: float, I0: float, bg: float, sigma_xy: float,
+            sigma_z: float) -> np.ndarray:
+    """Noise-free volume of one spot, point-sampled at integer voxel centres (FP64, [D, H, W])."""
+    gx = np.exp(-((np.arange(W) - x0) ** 2) / (2.0 * sigma_xy * sigma_xy))
+    gy = np.exp(-((np.arange(H) - y0) ** 2) / (2.0 * sigma_xy * sigma_xy))
+    gz = np.exp(-((np.arange(D) - z0) ** 2) / (2.0 * sigma_z * sigma_z))
+    return I0 * gz[:, None, None] * gy[None, :, None] * gx[None, None, :] + bg
+
+
+def make_sequence3(W: int, H: int, D: int, n_frames: int, seed: int, I0: float = 100.0, bg: float = 10.0,
+                   sigma_xy: float = 1.5, sigma_z: float = 3.0, q=Q3, margin: float = 8.0, vmax: float = 1.5):
+    """Ground-truth 3D track (NCV, speed U[vmax/2, vmax] voxel/frame, random direction) and its Poisson
+    volumes; the track stays ``margin`` voxels inside the volume (z: margin / 2)."""
+    rng = np.random.default_rng([seed, 0x3D])
+    for _attempt in range(1000):
+        speed = rng.uniform(vmax / 2.0, vmax)
+        v = rng.normal(size=3)
+        v = v / np.linalg.norm(v) * speed
+        s = np.array([(W - 1) / 2.0, (H - 1) / 2.0, (D - 1) / 2.0, v[0], v[1], v[2], I0])
+        gt = [s.copy()]
+        ok = True
+        for _k in range(n_frames):
+            s = s.copy()
+            s[0:3] += s[3:6]
+            s[3:6] += rng.normal(size=3) * np.asarray(q[3:6])
+            s[6] = max(1.0, s[6] + rng.normal() * q[6])
+            if not (margin <= s[0] <= W - 1 - margin and margin <= s[1] <= H - 1 - margin
+                    and margin / 2 <= s[2] <= D - 1 - margin / 2):
+                ok = False
+                break
+            gt.append(s)
+        if ok:
+            break
+    gt = np.array(gt)
+    vols = np.empty((n_frames, D, H, W), dtype=np.float32)
+    for k in range(n_frames):
+        lam = render3(W, H, D, gt[k + 1, 0], gt[k + 1, 1], gt[k + 1, 2], gt[k + 1, 6], bg, sigma_xy, sigma_z)
+        vols[k] = rng.poisson(lam).astype(np.float32)
+    return Sequence(gt=gt, images=vols)
+
+
+def initial_state3(gt0, N: int, dtype=np.float32) -> np.ndarray:
+    st = np.empty((D3, N), dtype=dtype)
+    for d in range(D3):
+        st[d, :] = gt0[d]
+    return st
