@@ -410,6 +410,52 @@ def run_large_object(counts, n_frames, seed):
             "frames": n_frames, "rows": rows}
 
 
+def run_3d(counts, n_frames, seed):
+    """3D tracking: 256 x 256 x 64 Poisson volumes (PSF sigma 1.5 / 3 voxels, I0 100, bg 10), state
+    (x, y, z, vx, vy, vz, I0), 11 x 11 x 7 likelihood patch; SIR and pcSIR with 0.5 x 0.5 x 1 voxel
+    cells filter the same sequence with the same noise: device time per step and tracking RMSE."""
+    import numpy as np
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seq = synth.make_sequence3(256, 256, 64, n_frames, seed)
+    vols = torch.from_numpy(seq.images).to(dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in counts:
+        pool = [torch.from_numpy(synth.make_noise(N, synth.Q3, seed + 3, j, np.float32)).to(dev)
+                for j in range(NOISE_POOL)]
+        ctx = pcsir.Context3(N)
+        for name, h in (("sir", None), ("pcsir", (0.5, 0.5, 1.0))):
+            st = torch.from_numpy(synth.initial_state3(seq.gt[0], N, np.float32)).to(dev)
+            ms, errs = [], []
+            for k in range(n_frames):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                u0 = synth.make_u0(seed + 5, k)
+                a.record(stream)
+                if h is None:
+                    ctx.sir_step(st, vols[k], pool[k % NOISE_POOL], u0, stream)
+                else:
+                    ctx.step(st, vols[k], h, pool[k % NOISE_POOL], u0, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if k >= 2:
+                    ms.append(a.elapsed_time(b))
+                r = ctx.last_result()
+                if r["device_error"]:
+                    raise RuntimeError("device error %d in 3D %s" % (r["device_error"], name))
+                errs.append(np.array(r["estimate"][:3]) - seq.gt[k + 1, :3])
+            e = np.array(errs)
+            rows.append({"method": name, "N": N, "ms_per_step": float(np.mean(ms)),
+                         "particles_per_s": N * 1e3 / float(np.mean(ms)),
+                         "rmse_voxel": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1))))})
+        ctx.close()
+    return {"workload": "3D: 256x256x64 volumes, 11x11x7 patch, cells 0.5x0.5x1 voxel", "frames": n_frames,
+            "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,6 +477,7 @@ def main():
                     "(Section 5.4; 0 skips it)")
     ap.add_argument("--large-frames", type=int, default=50, help="frames of the large-object comparison "
                     "(Section 5.3; 0 skips it)")
+    ap.add_argument("--frames-3d", type=int, default=20, help="frames of the 3D comparison (0 skips it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -587,6 +634,10 @@ def main():
     if args.large_frames > 0:
         large = run_large_object((12800, 1 << 17, 1 << 20), args.large_frames, SEED + 53 + 1000 * rank)
 
+    track3d = None
+    if args.frames_3d > 0:
+        track3d = run_3d((200_000, 1 << 22), args.frames_3d, SEED + 61 + 1000 * rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_s = 1 << 18
@@ -609,7 +660,7 @@ def main():
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
-            "large_object": large,
+            "large_object": large, "tracking_3d": track3d,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),

@@ -1,0 +1,103 @@
+/* pcSIR and SIR for 3D tracking: C ABI.
+ *
+ * The paper states Algorithms 1 and 2 for a general state and evaluates them
+ * in 2D; its outlook names higher-dimensional settings.  This is the 3D form:
+ *
+ *   state (x, y, z, vx, vy, vz, I0), float32, structure-of-arrays [7][N] on the
+ *   device, updated in place (resampled) by each step;
+ *   nearly-constant-velocity dynamics with unit frame time (Section 5.1):
+ *     x += vx + e_x, y += vy + e_y, z += vz + e_z, vx += e_vx, vy += e_vy,
+ *     vz += e_vz, I0 += e_I, evaluated in float32 in this order;
+ *   cells (Algorithm 2, Section 4.1): boxes of edges (hx, hy, hz) over
+ *     position, b = floor((x + 1/2) / hx) per axis in float32, so unit edges
+ *     are voxels centred on integers; |b| < 2^20 per axis (a particle beyond
+ *     raises PCSIR_DERR_RANGE and is placed in cell (0, 0, 0));
+ *   dummy: the centre of mass of the cell's members (all seven components);
+ *   likelihood (Eq. object with an anisotropic Gaussian PSF, Eq. likelihood):
+ *     the Poisson term z log(lambda / z) - (lambda - z) summed over a
+ *     patch_xy x patch_xy x patch_z block of voxels centred on the nearest
+ *     voxel (floor(x + 1/2), floor(y + 1/2), floor(z + 1/2)), with
+ *     lambda = max(I0, 0) exp(-((u - x)^2 + (v - y)^2) / (2 s_xy^2)
+ *                              - (w - z)^2 / (2 s_z^2)) + bg
+ *     at voxel centres (u, v, w); voxels outside the volume contribute
+ *     nothing.  The volume is float32 [D][H][W] on the device.
+ *   resampling: systematic, every step, one uniform u0 (Algorithm 1/2), as
+ *     in pcsir.h.
+ *
+ * Error behaviour, streams, graph capture and the result copy follow pcsir.h.
+ */
+#ifndef PCSIR3_H_
+#define PCSIR3_H_
+
+#include "pcsir.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcsir3_ctx pcsir3_ctx;
+
+typedef struct pcsir3_config {
+  int32_t patch_xy;       /* odd, 1 .. 63 */
+  int32_t patch_z;        /* odd, 1 .. 63 */
+  int32_t keep;           /* PCSIR_KEEP_* flags, as in pcsir.h */
+  int32_t reserved;       /* must be 0 */
+  double psf_sigma_xy;    /* > 0, voxels */
+  double psf_sigma_z;     /* > 0, voxels */
+  double bg;              /* > 0 */
+  int64_t max_particles;  /* 1 .. 2^26 */
+} pcsir3_config;
+
+typedef struct pcsir3_result {
+  double estimate[7];     /* posterior mean before resampling */
+  double ess;
+  double max_loglik;
+  double sum_wtilde;
+  int64_t n_particles;
+  int64_t n_bins;         /* occupied cells (pcSIR), 0 for SIR */
+  int32_t device_error;   /* PCSIR_DERR_* flags */
+  int32_t kind;           /* 1 pcSIR, 0 SIR */
+} pcsir3_result;
+
+typedef struct pcsir3_outputs {
+  int64_t n_particles;
+  int64_t n_bins;
+  int64_t bin_stride;        /* row stride of bin_xyz and dummy */
+  const float* prop_state;   /* [7][N] propagated states */
+  const int32_t* bin_xyz;    /* [3][bin_stride] cell indices */
+  const uint32_t* bin_count; /* [n_bins] members per cell */
+  const double* dummy;       /* [7][bin_stride] dummy states */
+  const double* bin_loglik;  /* [n_bins] dummy log-likelihoods */
+  const double* loglik;      /* [N] per-particle log-likelihoods (SIR, with PCSIR_KEEP_LOGLIK) */
+  const uint32_t* particle_bin; /* [N] cell of each particle (with PCSIR_KEEP_PARTICLE_BIN) */
+  const int32_t* ancestor;   /* [N] (with PCSIR_KEEP_ANCESTORS) */
+  const double* weight;      /* [N] normalised weights (with PCSIR_KEEP_WEIGHTS) */
+} pcsir3_outputs;
+
+pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out);
+pcsir_status pcsir3_destroy(pcsir3_ctx* ctx);
+const char* pcsir3_last_error(pcsir3_ctx* ctx);
+
+/* One pcSIR step (Algorithm 2) in 3D on state [7][N] in place; noise [7][N]
+   (device float32), u0 in [0, 1), cell edges hx, hy, hz in (0, 8].
+   result_host (may be NULL) receives the step's scalars once the stream
+   reaches the end of the step. */
+pcsir_status pcsir3_step(pcsir3_ctx* ctx, float* state, int64_t N, const float* volume, int32_t W, int32_t H,
+                         int32_t D, double hx, double hy, double hz, const float* noise, double u0, void* stream,
+                         pcsir3_result* result_host);
+
+/* One SIR step (Algorithm 1) in 3D: the likelihood of every particle. */
+pcsir_status sir3_step(pcsir3_ctx* ctx, float* state, int64_t N, const float* volume, int32_t W, int32_t H,
+                       int32_t D, const float* noise, double u0, void* stream, pcsir3_result* result_host);
+
+/* Intermediates of the last step (device pointers into the context, valid
+   until its next step; reading n_bins synchronises the device). */
+pcsir_status pcsir3_get_outputs(pcsir3_ctx* ctx, pcsir3_outputs* out);
+/* The page-locked copy of the last step's result (synchronise the stream first). */
+pcsir_status pcsir3_last_result(pcsir3_ctx* ctx, pcsir3_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCSIR3_H_ */

@@ -183,6 +183,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
     delete c;
     return PCSIR_ENOMEM;
   }
+  b.derr_out = &b.dres->device_error;
   e = prepare_kernels(cfg->state_dtype, b.prop_bin_per_sm);
   if (e == cudaSuccess) e = prepare_resample();
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result));

@@ -20,10 +20,10 @@ struct Control {
   long long T_int;            // sum of the integer weights q_i (exact)
   double T_f;                 // sum of exp(ll_i - max)
   double T2_f;                // sum of exp(ll_i - max)^2
-  double est[5];              // sum of exp(ll_i - max) * state_i
+  double est[7];              // sum of exp(ll_i - max) * state_i (5 components in 2D, 7 in 3D)
   unsigned long long delta_hi, delta_lo;  // T_int / N as 64.64 fixed point
   unsigned long long u0_hi, u0_lo;        // u0 * T_int / N as 64.64 fixed point
-  long long anchor[5];        // fixed-point anchors of the non-position components
+  long long anchor[7];        // fixed-point anchors of the non-position components
   unsigned int tiles_done;    // finished tiles of the resampling kernel
   unsigned int tsum_done;     // finished tiles of the tile-sum kernel
   float inv_delta;            // 1 / Delta rounded to FP32 (first guesses of output indices)
@@ -72,6 +72,7 @@ struct StepBuffers {
   int64_t max_tiles;
   Control* ctl;
   pcsir_result* dres;
+  int32_t* derr_out;        // where the last resampling tile publishes the step's device error flags
   int prop_bin_per_sm[2];   // resident blocks per SM of the propagate/bin kernel (small, large cell table)
   int big_table;            // 1: the propagate/bin kernel uses the large cell table
 };
@@ -139,6 +140,9 @@ cudaError_t prepare_resample();
 int weight_scale_bits(int64_t N);
 cudaError_t launch_resample(const StepBuffers& b, int dtype, void* state_out, int64_t N, double u0,
                             int mode, int keep, int num_sms, cudaStream_t s);
+// 3D state (7 components, FP32)
+cudaError_t launch_resample7(const StepBuffers& b, float* state_out, int64_t N, double u0, int mode, int keep,
+                             cudaStream_t s);
 cudaError_t launch_resample_logw(const StepBuffers& b, const double* logw, int32_t* anc_out, int64_t N, double u0,
                                  cudaStream_t s);
 cudaError_t launch_loglik(const ModelParams& m, const double* x, const double* y, const double* i0,

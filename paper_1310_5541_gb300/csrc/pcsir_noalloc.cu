@@ -86,6 +86,7 @@ extern "C" pcsir_status pcsir_resample_noalloc(const double* logw, int64_t N, do
   StepBuffers b{};
   b.ctl = &sc->ctl;
   b.dres = &sc->res;
+  b.derr_out = &sc->res.device_error;
   b.tile_sum = sc->tile_sum;
   b.tile_excl = sc->tile_excl;
   b.max_tiles = NOALLOC_MAX_TILES;

@@ -217,7 +217,7 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
 // memory); then the outputs are written in order, each gathering its
 // ancestor's propagated state.
 // ---------------------------------------------------------------------------
-template <typename T, int WSRC>
+template <typename T, int WSRC, int NS = 5>
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
@@ -320,14 +320,14 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       const unsigned a0 = zero_sum ? i0 : ub + (unsigned)clamp_item(amap[r0], cnt);
       const unsigned a1 = has1 ? (zero_sum ? i1 : ub + (unsigned)clamp_item(amap[r1], cnt)) : a0;
       if (out != nullptr) {
-        T v0[5], v1[5];
+        T v0[NS], v1[NS];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) {
+        for (int d = 0; d < NS; ++d) {
           v0[d] = prop[d * nb + a0];
           v1[d] = prop[d * nb + a1];
         }
 #pragma unroll
-        for (int d = 0; d < 5; ++d) {
+        for (int d = 0; d < NS; ++d) {
           out[d * nb + i0] = v0[d];
           if (has1) out[d * nb + i1] = v1[d];
         }
@@ -362,7 +362,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       b.hkey[g] = EMPTY_KEY;
       b.hcnt[g] = 0u;
 #pragma unroll
-      for (int d = 0; d < 5; ++d) b.hsum[d * hcap + g] = 0;
+      for (int d = 0; d < NS; ++d) b.hsum[d * hcap + g] = 0;
     }
   }
   // 8. the last tile to finish publishes the step's device error flags
@@ -371,7 +371,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     __threadfence();
     if (atomicAdd(&ctl->tiles_done, 1u) == gridDim.x - 1) {
       __threadfence();
-      b.dres->device_error = (int32_t)(*(volatile unsigned*)&ctl->err);
+      *b.derr_out = (int32_t)(*(volatile unsigned*)&ctl->err);
     }
   }
 }
@@ -386,6 +386,8 @@ cudaError_t prepare_resample() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_BINS>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_PARTICLES>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_LOGW>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_BINS, 7>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_PARTICLES, 7>, a, (int)RS_SMEM);
   return e;
 }
 
@@ -419,6 +421,24 @@ cudaError_t launch_resample(const StepBuffers& b, int dtype, void* state_out, in
   (void)num_sms;
   return dtype == PCSIR_F32 ? resample_launch<float>(b, nullptr, state_out, N, u0, mode, keep, s)
                             : resample_launch<double>(b, nullptr, state_out, N, u0, mode, keep, s);
+}
+
+cudaError_t launch_resample7(const StepBuffers& b, float* state_out, int64_t N, double u0, int mode, int keep,
+                             cudaStream_t s) {
+  const unsigned ntiles = (unsigned)((N + SCAN_TILE - 1) / SCAN_TILE);
+  const int sq = weight_scale_bits(N);
+  if (mode == WSRC_BINS) {
+    k_tile_sums<WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<float, WSRC_BINS, 7><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq, keep);
+  } else {
+    k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<float, WSRC_PARTICLES, 7><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq, keep);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resample_logw(const StepBuffers& b, const double* logw, int32_t* anc_out, int64_t N, double u0,

@@ -71,6 +71,25 @@ SUR_NPARAMS = 256 * 445 + 256 + 256 * 256 + 256 + 256 + 1
 SUR_ROW = 448  # stored inputs per dataset row
 
 
+class pcsir3_config(ctypes.Structure):
+    _fields_ = [("patch_xy", ctypes.c_int32), ("patch_z", ctypes.c_int32), ("keep", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("psf_sigma_xy", ctypes.c_double), ("psf_sigma_z", ctypes.c_double),
+                ("bg", ctypes.c_double), ("max_particles", ctypes.c_int64)]
+
+
+class pcsir3_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double * 7), ("ess", ctypes.c_double), ("max_loglik", ctypes.c_double),
+                ("sum_wtilde", ctypes.c_double), ("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64),
+                ("device_error", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+
+class pcsir3_outputs(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("bin_stride", ctypes.c_int64),
+                ("prop_state", ctypes.c_void_p), ("bin_xyz", ctypes.c_void_p), ("bin_count", ctypes.c_void_p),
+                ("dummy", ctypes.c_void_p), ("bin_loglik", ctypes.c_void_p), ("loglik", ctypes.c_void_p),
+                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+
+
 class PcsirError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
@@ -124,6 +143,13 @@ def _load():
         "pcsir_surrogate_predict_rows": ([P, I64, I64, P, P], I32),
         "pcsir_surrogate_predict": ([P, P, I64, I64, P, I32, I32, D, D, P, P], I32),
         "pcsir_attach_surrogate": ([P, P, D, I32, D, D], I32),
+        "pcsir3_create": ([ctypes.POINTER(pcsir3_config), ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir3_destroy": ([P], I32),
+        "pcsir3_last_error": ([P], ctypes.c_char_p),
+        "pcsir3_step": ([P, P, I64, P, I32, I32, I32, D, D, D, P, D, P, P], I32),
+        "sir3_step": ([P, P, I64, P, I32, I32, I32, P, D, P, P], I32),
+        "pcsir3_get_outputs": ([P, ctypes.POINTER(pcsir3_outputs)], I32),
+        "pcsir3_last_result": ([P, ctypes.POINTER(pcsir3_result)], I32),
         "pcsir_surrogate_last_check": ([P, ctypes.POINTER(pcsir_surrogate_check)], I32),
     }
     for name, (args, res) in sig.items():
@@ -523,3 +549,80 @@ def surrogate_last_check(ctx):
     if st != OK:
         ctx._raise(st)
     return {k: getattr(c, k) for k, _ in pcsir_surrogate_check._fields_ if k != "reserved"}
+
+
+class Context3:
+    """Owns one ``pcsir3_ctx``: 3D tracking, state (x, y, z, vx, vy, vz, I0) float32 [7, N]."""
+
+    def __init__(self, max_particles, patch_xy=11, patch_z=7, psf_sigma_xy=1.5, psf_sigma_z=3.0, bg=10.0, keep=0):
+        cfg = pcsir3_config(patch_xy=int(patch_xy), patch_z=int(patch_z), keep=int(keep), reserved=0,
+                            psf_sigma_xy=float(psf_sigma_xy), psf_sigma_z=float(psf_sigma_z), bg=float(bg),
+                            max_particles=int(max_particles))
+        h = ctypes.c_void_p()
+        st = lib.pcsir3_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise PcsirError(st, "pcsir3_create failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pcsir3_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        raise PcsirError(st, lib.pcsir3_last_error(self.handle).decode())
+
+    def step(self, state, volume, h, noise, u0, stream=None):
+        """One 3D pcSIR step on ``state`` [7, N] in place; ``volume`` float32 [D, H, W]; h = (hx, hy, hz)."""
+        _check_cuda(state, "state", torch.float32)
+        _check_cuda(noise, "noise", torch.float32)
+        _check_cuda(volume, "volume", torch.float32)
+        D, H, W = volume.shape
+        st = lib.pcsir3_step(self.handle, _ptr(state), state.shape[1], _ptr(volume), W, H, D, float(h[0]), float(h[1]),
+                             float(h[2]), _ptr(noise), float(u0), _stream_ptr(stream), None)
+        if st != OK:
+            self._raise(st)
+
+    def sir_step(self, state, volume, noise, u0, stream=None):
+        _check_cuda(state, "state", torch.float32)
+        _check_cuda(noise, "noise", torch.float32)
+        _check_cuda(volume, "volume", torch.float32)
+        D, H, W = volume.shape
+        st = lib.sir3_step(self.handle, _ptr(state), state.shape[1], _ptr(volume), W, H, D, _ptr(noise), float(u0),
+                           _stream_ptr(stream), None)
+        if st != OK:
+            self._raise(st)
+
+    def last_result(self):
+        r = pcsir3_result()
+        lib.pcsir3_last_result(self.handle, ctypes.byref(r))
+        return dict(estimate=list(r.estimate), ess=r.ess, max_loglik=r.max_loglik, sum_wtilde=r.sum_wtilde,
+                    n_particles=r.n_particles, n_bins=r.n_bins, device_error=r.device_error, kind=r.kind)
+
+    def outputs(self):
+        o = pcsir3_outputs()
+        st = lib.pcsir3_get_outputs(self.handle, ctypes.byref(o))
+        if st != OK:
+            self._raise(st)
+        N, B, S = o.n_particles, o.n_bins, o.bin_stride
+
+        def view(ptr, shape, dtype):
+            return _from_ptr(ptr, shape, dtype) if ptr else None
+
+        out = dict(n_particles=N, n_bins=B, prop_state=view(o.prop_state, (7, N), torch.float32),
+                   ancestor=view(o.ancestor, (N,), torch.int32), weight=view(o.weight, (N,), torch.float64))
+        if B > 0:
+            out.update(bin_xyz=view(o.bin_xyz, (3, S), torch.int32)[:, :B],
+                       bin_count=view(o.bin_count, (B,), torch.int32),
+                       dummy=view(o.dummy, (7, S), torch.float64)[:, :B],
+                       bin_loglik=view(o.bin_loglik, (B,), torch.float64),
+                       particle_bin=view(o.particle_bin, (N,), torch.int32))
+        if o.loglik:
+            out["loglik"] = view(o.loglik, (N,), torch.float64)
+        return out

@@ -46,8 +46,11 @@ def test_struct_layout_matches_header(binding, tmp_path):
         "pcsir_target": [f[0] for f in binding.pcsir_target._fields_],
         "pcsir_surrogate_config": [f[0] for f in binding.pcsir_surrogate_config._fields_],
         "pcsir_surrogate_check": [f[0] for f in binding.pcsir_surrogate_check._fields_],
+        "pcsir3_config": [f[0] for f in binding.pcsir3_config._fields_],
+        "pcsir3_result": [f[0] for f in binding.pcsir3_result._fields_],
+        "pcsir3_outputs": [f[0] for f in binding.pcsir3_outputs._fields_],
     }
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', '#include "pcsir_surrogate.h"',
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', '#include "pcsir_surrogate.h"', '#include "pcsir3.h"',
              "int main(void){", 'printf("NPARAMS %d\\n", PCSIR_SUR_NPARAMS);']
     for s, fs in fields.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
