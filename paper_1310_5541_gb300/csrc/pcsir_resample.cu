@@ -312,29 +312,36 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const unsigned w0 = (unsigned)wlo;
     const unsigned nb = (unsigned)N;
     const unsigned ub = (unsigned)base;
-    for (unsigned r0 = tid; r0 < wn; r0 += 2 * SCAN_THREADS) {
-      const unsigned r1 = r0 + SCAN_THREADS;
-      const bool has1 = r1 < wn;
-      const unsigned i0 = w0 + r0, i1 = w0 + r1;
-      // all weights zero (Delta = 0): no distribution to sample, keep every particle
-      const unsigned a0 = zero_sum ? i0 : ub + (unsigned)clamp_item(amap[r0], cnt);
-      const unsigned a1 = has1 ? (zero_sum ? i1 : ub + (unsigned)clamp_item(amap[r1], cnt)) : a0;
+    // four outputs per thread and pass: all gathers are issued before the stores
+    constexpr int RO = 4;
+    for (unsigned r0 = tid; r0 < wn; r0 += RO * SCAN_THREADS) {
+      unsigned ii[RO], aa[RO];
+      bool has[RO];
+#pragma unroll
+      for (int j = 0; j < RO; ++j) {
+        const unsigned r = r0 + j * SCAN_THREADS;
+        has[j] = r < wn;
+        ii[j] = w0 + r;
+        // all weights zero (Delta = 0): no distribution to sample, keep every particle
+        aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(amap[r], cnt)) : 0u;
+      }
       if (out != nullptr) {
-        T v0[NS], v1[NS];
+        T v[RO][NS];
 #pragma unroll
-        for (int d = 0; d < NS; ++d) {
-          v0[d] = prop[d * nb + a0];
-          v1[d] = prop[d * nb + a1];
-        }
+        for (int j = 0; j < RO; ++j)
 #pragma unroll
-        for (int d = 0; d < NS; ++d) {
-          out[d * nb + i0] = v0[d];
-          if (has1) out[d * nb + i1] = v1[d];
-        }
+          for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+          if (has[j]) {
+#pragma unroll
+            for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
+          }
       }
       if (keep & PCSIR_KEEP_ANCESTORS) {
-        b.anc[i0] = (int32_t)a0;
-        if (has1) b.anc[i1] = (int32_t)a1;
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+          if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
       }
     }
     __syncthreads();
