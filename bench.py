@@ -234,6 +234,7 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
         b_.record(s)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b_) / steps
+    phases = bt.phase_times()
     res, derr = bt.results()
     est = np.array([r["estimate"][:2] for r in res])
     rmse = float(np.sqrt(np.mean(np.sum((est - batch.gt[frames, :, :2]) ** 2, axis=1))))
@@ -241,7 +242,9 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
     return {"workload": "batched pcSIR, %d targets, 1024x1024, %d particles FP32" % (T, ntot),
             "value": ntot * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "targets": T, "particles": ntot, "launches_per_step": 1, "graph": True, "rmse_px": rmse,
-            "device_error": derr, "autotune": {"c": table.get("c"), "blocks_per_sm": table.get("blocks_per_sm")}}
+            "device_error": derr, "autotune": {"c": table.get("c"), "blocks_per_sm": table.get("blocks_per_sm")},
+            "phase_ms_last_step": dict(zip(("setup", "prop_bin", "bins_lik", "weights", "tile_sums", "target_scan",
+                                            "resample"), phases))}
 
 
 def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_cap=None):

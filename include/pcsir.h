@@ -309,6 +309,13 @@ pcsir_status pcsir_batch_bins(pcsir_batch* batch, const uint64_t** keys, const u
 
 const char* pcsir_batch_last_error(pcsir_batch* batch);
 
+/* Durations in ms of the last batched step's seven phases (set-up, propagate
+   and cells, dummies and likelihood, weights, tile sums, per-target scan,
+   resampling), from global-timer readings of block 0 at each grid barrier;
+   ms holds n >= 7 values.  Synchronises the device.  Diagnostics only: the
+   paper has no counterpart. */
+pcsir_status pcsir_batch_phase_times(pcsir_batch* batch, double* ms, int32_t n);
+
 /* BF16 tensor-core GEMM (tcgen05, FP32 accumulation), the building block of
    the likelihood surrogate (the paper has no counterpart; exposed for tests).
    C[m * ldc + n] (+)= sum_k A[m * sam + k * sak] * B[n * sbn + k * sbk] for

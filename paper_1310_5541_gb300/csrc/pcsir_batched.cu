@@ -31,7 +31,9 @@ struct BatchTarget {
   int sq;            // integer-weight scale bits (n 2^sq <= 2^61)
   int tile0;         // first global tile of the target
   int ntiles;        // tiles of the target
-  int pad;
+  float hf;          // cell edge as float (the per-particle cell index; a double here would cost an
+                     // FP64-pipe conversion per particle)
+  df c2;             // 1 / (2 sigma^2) as double-float
 };
 
 struct BatchStats {  // per target, zeroed every step
@@ -51,7 +53,18 @@ struct BatchCtl {  // zeroed every step
   unsigned int bar_gen;
   unsigned int abort;
   unsigned int pad;
+  unsigned long long phase_ns[8];  // global-timer reading of block 0 at the start and after each phase
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// block 0, thread 0 stamps the moment it passes phase boundary k
+__device__ __forceinline__ void stamp(BatchCtl* c, int k) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->phase_ns[k] = global_ns();
+}
 
 struct BatchBufs {
   const BatchTarget* tg;
@@ -260,9 +273,15 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     tab.fill = 0u;
   }
   __syncthreads();
+  // each block takes a contiguous range of chunks, so it meets the cells of a few neighbouring
+  // targets only (a grid-stride order would show every block every target's cells and overflow
+  // its table into per-particle global atomics)
   const long long nchunks = (N + BT_CHUNK - 1) / BT_CHUNK;
+  const long long per_block = (nchunks + gridDim.x - 1) / gridDim.x;
+  const long long c_begin = (long long)blockIdx.x * per_block;
+  const long long c_end = c_begin + per_block < nchunks ? c_begin + per_block : nchunks;
   int since_flush = 0;
-  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+  for (long long chunk = c_begin; chunk < c_end; ++chunk) {
     const long long base = chunk * BT_CHUNK;
     float v[BT_PER_THREAD][5];
     int tg[BT_PER_THREAD];
@@ -270,6 +289,31 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     int ls[BT_PER_THREAD];
     const long long i0 = base + (long long)BT_PER_THREAD * threadIdx.x;
     int t = i0 < N ? target_of(offs, b.T, i0) : 0;
+    // the four consecutive particles of this thread with 16-byte loads and stores when the rows allow
+    const bool vec = ((N & 3) == 0) && i0 + 3 < N &&
+                     ((reinterpret_cast<uintptr_t>(st) | reinterpret_cast<uintptr_t>(nz) |
+                       reinterpret_cast<uintptr_t>(b.prop)) & 15u) == 0u;
+    if (vec) {
+      float4 sv[5], nv[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        sv[c] = *reinterpret_cast<const float4*>(st + c * N + i0);
+        nv[c] = *reinterpret_cast<const float4*>(nz + c * N + i0);
+      }
+      const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
+      const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k][0] = __fadd_rn(__fadd_rn(sp[0][k], sp[2][k]), np[0][k]);
+        v[k][1] = __fadd_rn(__fadd_rn(sp[1][k], sp[3][k]), np[1][k]);
+        v[k][2] = __fadd_rn(sp[2][k], np[2][k]);
+        v[k][3] = __fadd_rn(sp[3][k], np[3][k]);
+        v[k][4] = __fadd_rn(sp[4][k], np[4][k]);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        *reinterpret_cast<float4*>(b.prop + c * N + i0) = make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
+    }
 #pragma unroll
     for (int k = 0; k < BT_PER_THREAD; ++k) {
       const long long i = i0 + k;
@@ -278,15 +322,17 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       if (i >= N) continue;
       while (t + 1 < b.T && offs[t + 1] <= i) ++t;
       tg[k] = t;
-      const float x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
-      v[k][0] = __fadd_rn(__fadd_rn(x, vx), nz[i]);
-      v[k][1] = __fadd_rn(__fadd_rn(y, vy), nz[N + i]);
-      v[k][2] = __fadd_rn(vx, nz[2 * N + i]);
-      v[k][3] = __fadd_rn(vy, nz[3 * N + i]);
-      v[k][4] = __fadd_rn(a, nz[4 * N + i]);
+      if (!vec) {
+        const float x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
+        v[k][0] = __fadd_rn(__fadd_rn(x, vx), nz[i]);
+        v[k][1] = __fadd_rn(__fadd_rn(y, vy), nz[N + i]);
+        v[k][2] = __fadd_rn(vx, nz[2 * N + i]);
+        v[k][3] = __fadd_rn(vy, nz[3 * N + i]);
+        v[k][4] = __fadd_rn(a, nz[4 * N + i]);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) b.prop[c * N + i] = v[k][c];
-      const float h = (float)b.tg[t].h;
+        for (int c = 0; c < 5; ++c) b.prop[c * N + i] = v[k][c];
+      }
+      const float h = b.tg[t].hf;
       float fx = floorf(__fdiv_rn(__fadd_rn(v[k][0], 0.5f), h));
       float fy = floorf(__fdiv_rn(__fadd_rn(v[k][1], 0.5f), h));
       bool ok = fabsf(fx) < 33554431.0f && fabsf(fy) < 33554431.0f;
@@ -379,8 +425,7 @@ __device__ void phase_bins(const BatchBufs& b, const float* __restrict__ img, in
     lp.P = T_.patch;
     lp.kind = PCSIR_LIK_POISSON;
     lp.bg = T_.bg;
-    const double c2 = 1.0 / (2.0 * T_.sigma * T_.sigma);
-    lp.c2 = df_from_double(c2);
+    lp.c2 = T_.c2;
     lp.inv2sxi2 = 0.0f;
     const LLSum ls = warp_loglik(img, W, H, lik_pos(mx, my, mi), lp, scratch);
     double ll = ll_to_double(ls);
@@ -504,16 +549,27 @@ __device__ void phase_tile_sums(const BatchBufs& b) {
 }
 
 // one thread per target: scan of its tile sums, the resampling map, the results
+// one warp per target: the exclusive scan of the target's tile sums runs 32 tiles at a time
 __device__ void phase_target_scan(const BatchBufs& b, const double* __restrict__ u0s) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < b.T; t += nwarps) {
     const BatchTarget& T_ = b.tg[t];
     BatchStats& S_ = b.st[t];
-    long long e = 0;
-    for (int k = 0; k < T_.ntiles; ++k) {
-      const long long v = *(volatile long long*)&b.tile_sum[T_.tile0 + k];
-      b.tile_excl[T_.tile0 + k] = e;
-      e += v;
+    long long e = 0;  // running total before the current group of 32 tiles
+    for (int k0 = 0; k0 < T_.ntiles; k0 += 32) {
+      const int k = k0 + lane;
+      const long long v = k < T_.ntiles ? *(volatile long long*)&b.tile_sum[T_.tile0 + k] : 0ll;
+      long long inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      if (k < T_.ntiles) b.tile_excl[T_.tile0 + k] = e + inc - v;
+      e += __shfl_sync(0xffffffffu, inc, 31);
     }
+    if (lane != 0) continue;
     const unsigned long long Tq = (unsigned long long)e;
     const unsigned long long n = (unsigned long long)T_.n;
     S_.dhi = Tq / n;
@@ -605,14 +661,31 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
         }
       }
       __syncthreads();
-      for (long long i = wlo + tid; i < whi; i += BT_THREADS) {
-        int a = sm.amap[i - wlo];
-        a = a < 0 ? 0 : (a >= cnt ? cnt - 1 : a);
-        // all weights zero: no distribution to sample, keep every particle
-        const long long src = zero_sum ? T_.off + i : T_.off + lbase + a;
-        const long long dst = T_.off + i;
+      // four outputs per thread and pass: all gathers issued before the stores
+      for (long long i0 = wlo + tid; i0 < whi; i0 += 4 * BT_THREADS) {
+        long long dst[4], src[4];
+        bool has[4];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) out[d * Ntot + dst] = b.prop[d * Ntot + src];
+        for (int j = 0; j < 4; ++j) {
+          const long long i = i0 + (long long)j * BT_THREADS;
+          has[j] = i < whi;
+          int a = has[j] ? sm.amap[i - wlo] : 0;
+          a = a < 0 ? 0 : (a >= cnt ? cnt - 1 : a);
+          // all weights zero: no distribution to sample, keep every particle
+          src[j] = zero_sum ? T_.off + i : T_.off + lbase + a;
+          dst[j] = T_.off + i;
+        }
+        float v[4][5];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int d = 0; d < 5; ++d) v[j][d] = has[j] ? b.prop[d * Ntot + src[j]] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (has[j]) {
+#pragma unroll
+            for (int d = 0; d < 5; ++d) out[d * Ntot + dst[j]] = v[j][d];
+          }
       }
       __syncthreads();
     }
@@ -624,6 +697,7 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
                const float* __restrict__ img, int W, int H, const double* __restrict__ u0s) {
   extern __shared__ __align__(16) unsigned char bt_smem[];
   long long* offs = reinterpret_cast<long long*>(bt_smem + BT_SMEM_UNION);
+  stamp(b.ctl, 0);
   for (int t = threadIdx.x; t <= b.T; t += blockDim.x) offs[t] = b.offs[t];
   // anchors of vx, vy, I0 per target: the target's first particle's input value
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
@@ -632,16 +706,21 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
     for (int c = 0; c < 3; ++c) b.st[t].anchor[c] = to_fixed(st[(2 + c) * b.ntot + i], 4194304.0f);
   }
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 1);
   phase_prop_bin(b, st, nz, *reinterpret_cast<BatchLocal*>(bt_smem), offs);
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 2);
   phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 3);
   phase_weights(b);
   // the cells are not needed any more: return their hash slots to empty
   // after the tile sums, which still read the slots' integer weights
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 4);
   phase_tile_sums(b);
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 5);
   phase_target_scan(b, u0s);
   {
     const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
@@ -655,7 +734,10 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
     }
   }
   if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 6);
   phase_resample(b, out, *reinterpret_cast<BatchResampleSmem*>(bt_smem));
+  if (!grid_barrier(b.ctl)) return;
+  stamp(b.ctl, 7);
 }
 
 }  // namespace pcsir
@@ -714,6 +796,12 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
     tg[t].off = ntot;
     tg[t].n = x.n_particles;
     tg[t].h = (double)(float)x.h;
+    tg[t].hf = (float)x.h;
+    {
+      const double c2 = 1.0 / (2.0 * x.psf_sigma * x.psf_sigma);
+      tg[t].c2.hi = (float)c2;
+      tg[t].c2.lo = (float)(c2 - (double)tg[t].c2.hi);
+    }
     tg[t].hq = llrint(x.h * 2147483648.0);
     tg[t].sigma = x.psf_sigma;
     tg[t].bg = (float)x.bg;
@@ -721,7 +809,7 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
     tg[t].sq = weight_scale_bits(x.n_particles);
     tg[t].tile0 = ntiles;
     tg[t].ntiles = (int)((x.n_particles + BT_TILE - 1) / BT_TILE);
-    tg[t].pad = 0;
+
     ntot += x.n_particles;
     ntiles += tg[t].ntiles;
   }
@@ -871,5 +959,18 @@ pcsir_status pcsir_batch_bins(pcsir_batch* c, const uint64_t** keys, const uint3
 }
 
 const char* pcsir_batch_last_error(pcsir_batch* c) { return c ? c->err.c_str() : "NULL batch"; }
+
+pcsir_status pcsir_batch_phase_times(pcsir_batch* c, double* ms, int32_t n) {
+  if (!c || !ms || n < 7) return PCSIR_EINVAL;
+  BatchCtl h{};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, c->b.ctl, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PCSIR_ECUDA;
+  }
+  for (int k = 0; k < 7; ++k) ms[k] = (double)(h.phase_ns[k + 1] - h.phase_ns[k]) * 1e-6;
+  return PCSIR_OK;
+}
 
 }  // extern "C"

@@ -124,6 +124,7 @@ def _load():
         "pcsir_batch_bins": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
+        "pcsir_batch_phase_times": ([P, ctypes.POINTER(ctypes.c_double), I32], I32),
         "pcsir_gemm_bf16": ([P, I64, I64, P, I64, I64, P, I64, I32, I32, I32, I32, P], I32),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
         "pcsir_surrogate_create": ([ctypes.POINTER(pcsir_surrogate_config), ctypes.POINTER(ctypes.c_void_p)], I32),
@@ -379,6 +380,14 @@ class Batch:
                                     _stream_ptr(stream))
         if st != OK:
             raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def phase_times(self):
+        """Durations (ms) of the last step's seven phases (synchronises)."""
+        buf = (ctypes.c_double * 7)()
+        st = lib.pcsir_batch_phase_times(self.handle, buf, 7)
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_phase_times failed")
+        return list(buf)
 
     def set_grid(self, blocks_per_sm):
         st = lib.pcsir_batch_set_grid(self.handle, int(blocks_per_sm))
