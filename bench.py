@@ -241,7 +241,8 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
     bt.close()
     return {"workload": "batched pcSIR, %d targets, 1024x1024, %d particles FP32" % (T, ntot),
             "value": ntot * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "targets": T, "particles": ntot, "launches_per_step": 1, "graph": True, "rmse_px": rmse,
+            "targets": T, "particles": ntot, "cells_last_step": int(sum(r["n_bins"] for r in res)),
+            "launches_per_step": 1, "graph": True, "rmse_px": rmse,
             "device_error": derr, "autotune": {"c": table.get("c"), "blocks_per_sm": table.get("blocks_per_sm")},
             "phase_ms_last_step": dict(zip(("setup", "prop_bin", "bins_lik", "weights", "tile_sums", "target_scan",
                                             "resample"), phases))}

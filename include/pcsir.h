@@ -295,10 +295,13 @@ pcsir_status pcsir_batched_step(pcsir_batch* batch, float* state, const float* i
    synchronises the device). */
 pcsir_status pcsir_batch_results(pcsir_batch* batch, pcsir_result* out, int32_t T, int32_t* device_error);
 
-/* Device pointers of the last step's propagated states [5][sum n_t] and
-   per-particle cell slots (for inspection), and the total particle count. */
-pcsir_status pcsir_batch_outputs(pcsir_batch* batch, const float** prop_state, const unsigned int** particle_slot,
-                                 int64_t* n_total);
+/* Device pointers of the last step's propagated states (5 rows of sum n_t
+   values, row r at prop_state + r * row_stride; row_stride is sum n_t rounded
+   up to a multiple of 4 so that every row starts on a 16-byte boundary) and
+   per-particle cell slots (for inspection), and the total particle count.
+   Any out-pointer may be NULL. */
+pcsir_status pcsir_batch_outputs(pcsir_batch* batch, const float** prop_state, int64_t* row_stride,
+                                 const unsigned int** particle_slot, int64_t* n_total);
 
 /* Device pointers to the last step's occupied cells of all targets (n_bins of
    them, in an unspecified order): keys (target << 52 | (by + 2^25) << 26 |

@@ -85,7 +85,8 @@ struct BatchBufs {
   unsigned int* bin_cnt;
   unsigned long long* bin_key;
   unsigned int* pslot;
-  float* prop;
+  float* prop;           // [5][pstride] propagated states
+  long long pstride;     // row stride of prop: ntot rounded up to a multiple of 4
   long long* tile_sum;
   long long* tile_excl;
   pcsir_result* res;  // [T]
@@ -245,6 +246,16 @@ __device__ void blocal_flush(BatchLocal& t, const BatchBufs& b, bool clear_keys)
   __syncthreads();
 }
 
+// the four floats starting m (0..3, uniform) elements after the 16-byte aligned quad a
+__device__ __forceinline__ float4 shift_quad(const float4 a, const float4 b, int m) {
+  switch (m) {
+    case 0: return a;
+    case 1: return make_float4(a.y, a.z, a.w, b.x);
+    case 2: return make_float4(a.z, a.w, b.x, b.y);
+    default: return make_float4(a.w, b.x, b.y, b.z);
+  }
+}
+
 // target owning particle i (offsets in shared memory, T + 1 entries)
 __device__ __forceinline__ int target_of(const long long* offs, int T, long long i) {
   int lo = 0, hi = T;  // offs[lo] <= i < offs[hi]
@@ -262,6 +273,7 @@ __device__ __forceinline__ int target_of(const long long* offs, int T, long long
 __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st, const float* __restrict__ nz,
                                BatchLocal& tab, const long long* offs) {
   const long long N = b.ntot;
+  const long long P = b.pstride;
   const size_t hcap = size_t(1) << b.hbits;
   for (int j = threadIdx.x; j < BT_LT; j += blockDim.x) {
     tab.key[j] = EMPTY_KEY;
@@ -284,21 +296,34 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
   for (long long chunk = c_begin; chunk < c_end; ++chunk) {
     const long long base = chunk * BT_CHUNK;
     float v[BT_PER_THREAD][5];
-    int tg[BT_PER_THREAD];
-    unsigned long long key[BT_PER_THREAD];
+    // per particle: -2 none, >= 0 local slot, <= -3 global slot -3 - ls (local table full); the
+    // cell key is read back from the table, and the target found again from t0, so that no
+    // per-particle key or target stays live across the barrier (the kernel runs at 64 registers)
     int ls[BT_PER_THREAD];
     const long long i0 = base + (long long)BT_PER_THREAD * threadIdx.x;
-    int t = i0 < N ? target_of(offs, b.T, i0) : 0;
-    // the four consecutive particles of this thread with 16-byte loads and stores when the rows allow
-    const bool vec = ((N & 3) == 0) && i0 + 3 < N &&
-                     ((reinterpret_cast<uintptr_t>(st) | reinterpret_cast<uintptr_t>(nz) |
-                       reinterpret_cast<uintptr_t>(b.prop)) & 15u) == 0u;
+    const int t0 = i0 < N ? target_of(offs, b.T, i0) : 0;
+    int t = t0;
+    // the four consecutive particles of this thread with 16-byte loads and stores.  Row c of the
+    // state and noise starts (c N) mod 4 floats off a 16-byte boundary: the thread reads the two
+    // aligned quads around its four values (the second is the next thread's first, an L1 hit) and
+    // shifts.  i0 + 8 <= N keeps the second quad of the last row inside the arrays.
+    const bool vec = i0 + 8 <= N &&
+                     ((reinterpret_cast<uintptr_t>(st) | reinterpret_cast<uintptr_t>(nz)) & 15u) == 0u;
     if (vec) {
       float4 sv[5], nv[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        sv[c] = *reinterpret_cast<const float4*>(st + c * N + i0);
-        nv[c] = *reinterpret_cast<const float4*>(nz + c * N + i0);
+        const int m = (int)((c * N) & 3);
+        const long long a = c * N + i0 - m;
+        const float4 s0 = *reinterpret_cast<const float4*>(st + a);
+        const float4 n0 = *reinterpret_cast<const float4*>(nz + a);
+        if (m == 0) {
+          sv[c] = s0;
+          nv[c] = n0;
+        } else {
+          sv[c] = shift_quad(s0, *reinterpret_cast<const float4*>(st + a + 4), m);
+          nv[c] = shift_quad(n0, *reinterpret_cast<const float4*>(nz + a + 4), m);
+        }
       }
       const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
       const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
@@ -312,16 +337,14 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c)
-        *reinterpret_cast<float4*>(b.prop + c * N + i0) = make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
+        *reinterpret_cast<float4*>(b.prop + c * P + i0) = make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
     }
 #pragma unroll
     for (int k = 0; k < BT_PER_THREAD; ++k) {
       const long long i = i0 + k;
       ls[k] = -2;
-      tg[k] = 0;
       if (i >= N) continue;
       while (t + 1 < b.T && offs[t + 1] <= i) ++t;
-      tg[k] = t;
       if (!vec) {
         const float x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
         v[k][0] = __fadd_rn(__fadd_rn(x, vx), nz[i]);
@@ -330,7 +353,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
         v[k][3] = __fadd_rn(vy, nz[3 * N + i]);
         v[k][4] = __fadd_rn(a, nz[4 * N + i]);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) b.prop[c * N + i] = v[k][c];
+        for (int c = 0; c < 5; ++c) b.prop[c * P + i] = v[k][c];
       }
       const float h = b.tg[t].hf;
       float fx = floorf(__fdiv_rn(__fadd_rn(v[k][0], 0.5f), h));
@@ -343,21 +366,33 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
         fx = fy = 0.0f;
         v[k][0] = v[k][1] = 0.0f;
       }
-      key[k] = bkey(t, (int)fx, (int)fy);
+      const unsigned long long key = bkey(t, (int)fx, (int)fy);
       bool created;
-      ls[k] = blocal_insert(tab, key[k], created);
-      if (created) tab.gslot[ls[k]] = bglobal_insert(b, key[k]);
+      ls[k] = blocal_insert(tab, key, created);
+      if (created) tab.gslot[ls[k]] = bglobal_insert(b, key);
+      if (ls[k] == -1) ls[k] = -3 - (int)bglobal_insert(b, key);
     }
     __syncthreads();
+    unsigned gs[BT_PER_THREAD];
+    // a thread's four particles are consecutive, and after resampling neighbours are often
+    // offspring of one ancestor in one cell: a run of equal local slots is summed in registers
+    // (exact integer pieces) and reaches the shared counters with one set of atomics
+    unsigned run[BT_NACC];
+#pragma unroll
+    for (int a = 0; a < BT_NACC; ++a) run[a] = 0u;
+    t = t0;
 #pragma unroll
     for (int k = 0; k < BT_PER_THREAD; ++k) {
+      gs[k] = 0u;
       if (ls[k] == -2) continue;
       const long long i = i0 + k;
-      const BatchTarget& T_ = b.tg[tg[k]];
-      const BatchStats& S_ = b.st[tg[k]];
+      while (t + 1 < b.T && offs[t + 1] <= i) ++t;
+      const unsigned long long key = ls[k] >= 0 ? tab.key[ls[k]] : b.hkey[-3 - ls[k]];
+      const BatchTarget& T_ = b.tg[t];
+      const BatchStats& S_ = b.st[t];
       long long bv[5];
-      bv[0] = to_fixed(v[k][0], 2147483648.0f) - (long long)bkey_bx(key[k]) * T_.hq + BT_POS_BIAS;
-      bv[1] = to_fixed(v[k][1], 2147483648.0f) - (long long)bkey_by(key[k]) * T_.hq + BT_POS_BIAS;
+      bv[0] = to_fixed(v[k][0], 2147483648.0f) - (long long)bkey_bx(key) * T_.hq + BT_POS_BIAS;
+      bv[1] = to_fixed(v[k][1], 2147483648.0f) - (long long)bkey_by(key) * T_.hq + BT_POS_BIAS;
 #pragma unroll
       for (int c = 0; c < 3; ++c) bv[2 + c] = to_fixed(v[k][2 + c], 4194304.0f) - S_.anchor[c] + BT_VAL_BIAS;
       bool bad = false;
@@ -372,14 +407,21 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       if (ls[k] >= 0) {
         const int s = ls[k];
         g = tab.gslot[s];
-        atomicAdd(&tab.acc[0][s], 1u);
+        run[0] += 1u;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & BT_PIECE_MASK));
-          atomicAdd(&tab.acc[2 + 2 * c][s], (unsigned)(bv[c] >> BT_PIECE_BITS));
+          run[1 + 2 * c] += (unsigned)(bv[c] & BT_PIECE_MASK);
+          run[2 + 2 * c] += (unsigned)(bv[c] >> BT_PIECE_BITS);
+        }
+        if (k == BT_PER_THREAD - 1 || ls[k + 1 < BT_PER_THREAD ? k + 1 : k] != s) {
+#pragma unroll
+          for (int a = 0; a < BT_NACC; ++a) {
+            atomicAdd(&tab.acc[a][s], run[a]);
+            run[a] = 0u;
+          }
         }
       } else {
-        g = bglobal_insert(b, key[k]);
+        g = (unsigned)(-3 - ls[k]);
         atomicAdd(&b.hcnt[g], 1u);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -387,8 +429,10 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
           atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias));
         }
       }
-      b.pslot[i] = g;
+      gs[k] = g;
+      if (!vec) b.pslot[i] = g;
     }
+    if (vec) *reinterpret_cast<uint4*>(b.pslot + i0) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
     since_flush += BT_CHUNK;
     __syncthreads();
     const bool full = tab.fill >= BT_LT_CAP;
@@ -679,7 +723,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-          for (int d = 0; d < 5; ++d) v[j][d] = has[j] ? b.prop[d * Ntot + src[j]] : 0.0f;
+          for (int d = 0; d < 5; ++d) v[j][d] = has[j] ? b.prop[d * b.pstride + src[j]] : 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (has[j]) {
@@ -825,6 +869,7 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   BatchBufs& b = c->b;
   b.T = T;
   b.ntot = ntot;
+  b.pstride = (ntot + 3) & ~3ll;
   b.ntiles_total = ntiles;
   b.hbits = hbits;
   BatchTarget* dtg = nullptr;
@@ -834,7 +879,7 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
             balloc(c, &b.hq, hcap) && balloc(c, &b.occ, (size_t)ntot) && balloc(c, &b.bin_ll, (size_t)ntot) &&
             balloc(c, &b.bin_cnt, (size_t)ntot) && balloc(c, &b.bin_key, (size_t)ntot) &&
             balloc(c, &b.pslot, (size_t)ntot) &&
-            balloc(c, &b.prop, 5 * (size_t)ntot) && balloc(c, &b.tile_sum, (size_t)ntiles) &&
+            balloc(c, &b.prop, 5 * (size_t)b.pstride) && balloc(c, &b.tile_sum, (size_t)ntiles) &&
             balloc(c, &b.tile_excl, (size_t)ntiles) && balloc(c, &b.res, (size_t)T);
   if (!ok) {
     bfree(c);
@@ -935,10 +980,11 @@ pcsir_status pcsir_batch_results(pcsir_batch* c, pcsir_result* out, int32_t T, i
   return PCSIR_OK;
 }
 
-pcsir_status pcsir_batch_outputs(pcsir_batch* c, const float** prop_state, const unsigned int** particle_slot,
-                                 int64_t* n_total) {
+pcsir_status pcsir_batch_outputs(pcsir_batch* c, const float** prop_state, int64_t* row_stride,
+                                 const unsigned int** particle_slot, int64_t* n_total) {
   if (!c) return PCSIR_EINVAL;
   if (prop_state) *prop_state = c->b.prop;
+  if (row_stride) *row_stride = c->b.pstride;
   if (particle_slot) *particle_slot = c->b.pslot;
   if (n_total) *n_total = c->ntot;
   return PCSIR_OK;

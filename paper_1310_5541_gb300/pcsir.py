@@ -119,8 +119,8 @@ def _load():
         "pcsir_batch_set_grid": ([P, I32], I32),
         "pcsir_batched_step": ([P, P, P, I32, I32, P, P, P], I32),
         "pcsir_batch_results": ([P, ctypes.POINTER(pcsir_result), I32, ctypes.POINTER(ctypes.c_int32)], I32),
-        "pcsir_batch_outputs": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
-                                 ctypes.POINTER(ctypes.c_int64)], I32),
+        "pcsir_batch_outputs": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
         "pcsir_batch_bins": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
@@ -406,12 +406,13 @@ class Batch:
         return out, err.value
 
     def outputs(self):
-        prop, slot, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
-        lib.pcsir_batch_outputs(self.handle, ctypes.byref(prop), ctypes.byref(slot), ctypes.byref(n))
+        prop, stride, slot, n = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_int64()
+        lib.pcsir_batch_outputs(self.handle, ctypes.byref(prop), ctypes.byref(stride), ctypes.byref(slot),
+                                ctypes.byref(n))
         keys, cnts, ll, nb = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
         lib.pcsir_batch_bins(self.handle, ctypes.byref(keys), ctypes.byref(cnts), ctypes.byref(ll), ctypes.byref(nb))
         B = nb.value
-        return dict(prop_state=_from_ptr(prop.value, (5, n.value), torch.float32),
+        return dict(prop_state=_from_ptr(prop.value, (5, stride.value), torch.float32)[:, :n.value],
                     bin_key=_from_ptr(keys.value, (B,), torch.int64) if B else None,
                     bin_count=_from_ptr(cnts.value, (B,), torch.int32) if B else None,
                     bin_loglik=_from_ptr(ll.value, (B,), torch.float64) if B else None)

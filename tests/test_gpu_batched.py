@@ -118,6 +118,17 @@ def test_batched_many_small_targets(pc):
     assert mism <= 0.01 * batch.n.sum()
 
 
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_batched_rows_at_every_alignment(pc, r):
+    # sum n_t = 8000 + r: state and noise rows start r, 2r, 3r, 4r floats (mod 4) off a
+    # 16-byte boundary, which the vector loads of the propagation phase shift back into place
+    n = [4000, 3990 + r, 10]
+    batch = synth.make_batch(len(n), 160, 160, 1, seed=SEED + 30 + r, n_values=n, min_sep=30.0)
+    st = synth.batch_initial_state(batch, np.float32)
+    mism = _compare(pc, batch, st, 0, SEED + 31 + r)
+    assert mism <= 0.01 * batch.n.sum()
+
+
 def test_batched_step_graph_capture_replays(pc):
     n = [5000, 7000, 123]
     batch = synth.make_batch(len(n), 128, 128, 1, seed=SEED + 20, n_values=n, min_sep=30.0)
