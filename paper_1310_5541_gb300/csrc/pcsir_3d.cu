@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pcsir3.h"
+#include "pcsir3.h"
 #include "pcsir_device.cuh"
 
 namespace pcsir {

@@ -89,6 +89,7 @@ struct BatchBufs {
   long long pstride;     // row stride of prop: ntot rounded up to a multiple of 4
   long long* tile_sum;
   long long* tile_excl;
+  const int* tile_target;  // [ntiles_total] target owning each tile (fixed at creation)
   pcsir_result* res;  // [T]
 };
 
@@ -108,7 +109,6 @@ constexpr int BT_NACC = 11;
 constexpr int BT_MAX_TARGETS = 2047;
 constexpr int BT_TILE = 4096;
 constexpr int BT_ITEMS = BT_TILE / BT_THREADS;  // 8
-constexpr int BT_WINDOW = 4608;
 constexpr int BT_BARRIER_SPINS = 1 << 22;
 
 // cell key: target (11 bits) | by + 2^25 (26 bits) | bx + 2^25 (26 bits)
@@ -130,8 +130,7 @@ struct BatchLocal {
 };
 
 struct BatchResampleSmem {
-  long long Cs[BT_TILE + BT_TILE / 16];
-  int amap[BT_WINDOW];
+  long long Cs[BT_TILE + BT_TILE / 16];  // inclusive cumulative integer weights, padded (j + j / 16)
   long long wtot[BT_THREADS / 32];
   long long s_lo, s_hi;
 };
@@ -521,15 +520,7 @@ __device__ void phase_weights(const BatchBufs& b) {
 // ---------------------------------------------------------------------------
 // Phases D-F: resampling per (target, tile) item
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int item_target(const BatchBufs& b, int item) {
-  int lo = 0, hi = b.T;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (b.tg[mid].tile0 <= item) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
+__device__ __forceinline__ int item_target(const BatchBufs& b, int item) { return b.tile_target[item]; }
 
 __device__ __forceinline__ long long bu_int(unsigned long long dhi, unsigned long long dlo, unsigned long long uhi,
                                             unsigned long long ulo, long long i) {
@@ -540,20 +531,8 @@ __device__ __forceinline__ long long bu_int(unsigned long long dhi, unsigned lon
   return (long long)(ui * dhi + uhi + phi + (s < plo ? 1ull : 0ull));
 }
 
-__device__ long long bfirst_out(const BatchStats& S, long long C, long long N) {
-  if (C <= 0) return 0;
-  const double dd = (double)S.dhi + (double)S.dlo * 5.421010862427522e-20;
-  if (dd <= 0.0) return N;
-  const double ud = (double)S.uhi + (double)S.ulo * 5.421010862427522e-20;
-  const double x = ((double)C - ud) / dd;
-  long long i = x < 0.0 ? 0 : (x > (double)N ? N : (long long)ceil(x));
-  int guard = 0;
-  while (i > 0 && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i - 1) >= C && guard++ < 64) --i;
-  while (i < N && bu_int(S.dhi, S.dlo, S.uhi, S.ulo, i) < C && guard++ < 128) ++i;
-  return i;
-}
-
-// bfirst_out without FP64: a float guess of (C - U0) / Delta, then the exact integer correction
+// first output i with U_i >= C (N if none; U_i = U0 + i Delta in 64.64 fixed point): a float
+// guess of (C - U0) / Delta, then the exact integer correction
 __device__ long long bfirst_out_f(const BatchStats& S, long long C, long long N) {
   if (C <= 0) return 0;
   if (S.dhi == 0ull && S.dlo == 0ull) return N;
@@ -675,64 +654,57 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
       agg += v;
     }
     const long long texcl = woff + inc - run;
+    // entries past the tile's last particle compare above every U_i (the fixed-step search below)
 #pragma unroll
-    for (int k = 0; k < BT_ITEMS; ++k) sm.Cs[(tid * BT_ITEMS + k) + ((tid * BT_ITEMS + k) >> 4)] = excl + texcl + loc[k];
-    if (tid == 0) {
-      sm.s_lo = bfirst_out(S_, excl, N);
-      sm.s_hi = (lbase + cnt >= N) ? N : bfirst_out(S_, excl + agg, N);
+    for (int k = 0; k < BT_ITEMS; ++k) {
+      const int jj = tid * BT_ITEMS + k;
+      sm.Cs[jj + (jj >> 4)] = jj < cnt ? excl + texcl + loc[k] : LLONG_MAX;
     }
+    // outputs [lo, hi) of the tile: U_lo >= C_{-1} = excl, U_{hi-1} < C_{cnt-1} = excl + agg
+    if (tid == 0) sm.s_lo = bfirst_out_f(S_, excl, N);
+    if (tid == 32) sm.s_hi = (lbase + cnt >= N) ? N : bfirst_out_f(S_, excl + agg, N);
     __syncthreads();
     const long long lo = sm.s_lo, hi = sm.s_hi;
     const bool zero_sum = (S_.dhi == 0ull && S_.dlo == 0ull);
-    long long cur = bfirst_out_f(S_, excl + texcl, N);
-    unsigned long long ufrac = (unsigned long long)cur * S_.dlo + S_.ulo;
-    long long uint_cur = bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, cur);
-    int kk = 0;
-    for (long long wlo = lo; wlo < hi; wlo += BT_WINDOW) {
-      const long long whi = (hi - wlo) < BT_WINDOW ? hi : wlo + BT_WINDOW;
-      if (!zero_sum) {
-        while (kk < BT_ITEMS && cur < whi) {
-          const int jj = tid * BT_ITEMS + kk;
-          if (uint_cur < sm.Cs[jj + (jj >> 4)]) {
-            if (cur >= wlo) sm.amap[cur - wlo] = jj;
-            ++cur;
-            const unsigned long long f = ufrac + S_.dlo;
-            uint_cur += (long long)(S_.dhi + (f < ufrac ? 1ull : 0ull));
-            ufrac = f;
-          } else {
-            ++kk;
+    // four outputs per thread and pass.  Output i's ancestor is the tile's particle j with
+    // C_{j-1} <= U_i < C_j, i.e. the number of C_j <= floor(U_i) (the C_j are integers): a
+    // 12-step search over the cumulative weights in shared memory, independent for every
+    // output, so a particle with many offspring does not serialise its thread
+    for (long long i0 = lo + tid; i0 < hi; i0 += 4 * BT_THREADS) {
+      long long src[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long i = i0 + (long long)j * BT_THREADS;
+        int a = 0;
+        if (i < hi && !zero_sum) {
+          const long long u = bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, i);
+#pragma unroll
+          for (int step = BT_TILE / 2; step > 0; step >>= 1) {
+            const int probe = a + step - 1;
+            if (sm.Cs[probe + (probe >> 4)] <= u) a += step;
           }
+          a = a < cnt ? a : cnt - 1;
+        }
+        // all weights zero: no distribution to sample, keep every particle
+        src[j] = zero_sum ? T_.off + i : T_.off + lbase + a;
+      }
+      float v[4][5];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool has = i0 + (long long)j * BT_THREADS < hi;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) v[j][d] = has ? b.prop[d * b.pstride + src[j]] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long i = i0 + (long long)j * BT_THREADS;
+        if (i < hi) {
+#pragma unroll
+          for (int d = 0; d < 5; ++d) out[d * Ntot + T_.off + i] = v[j][d];
         }
       }
-      __syncthreads();
-      // four outputs per thread and pass: all gathers issued before the stores
-      for (long long i0 = wlo + tid; i0 < whi; i0 += 4 * BT_THREADS) {
-        long long dst[4], src[4];
-        bool has[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const long long i = i0 + (long long)j * BT_THREADS;
-          has[j] = i < whi;
-          int a = has[j] ? sm.amap[i - wlo] : 0;
-          a = a < 0 ? 0 : (a >= cnt ? cnt - 1 : a);
-          // all weights zero: no distribution to sample, keep every particle
-          src[j] = zero_sum ? T_.off + i : T_.off + lbase + a;
-          dst[j] = T_.off + i;
-        }
-        float v[4][5];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int d = 0; d < 5; ++d) v[j][d] = has[j] ? b.prop[d * b.pstride + src[j]] : 0.0f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (has[j]) {
-#pragma unroll
-            for (int d = 0; d < 5; ++d) out[d * Ntot + dst[j]] = v[j][d];
-          }
-      }
-      __syncthreads();
     }
+    __syncthreads();
   }
 }
 
@@ -874,13 +846,15 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   b.hbits = hbits;
   BatchTarget* dtg = nullptr;
   long long* doffs = nullptr;
+  int* dtile_target = nullptr;
   bool ok = balloc(c, &dtg, T) && balloc(c, &b.st, T) && balloc(c, &b.ctl, 1) && balloc(c, &doffs, T + 1) &&
             balloc(c, &b.hkey, hcap) && balloc(c, &b.hcnt, hcap) && balloc(c, &b.hsum, 5 * hcap) &&
             balloc(c, &b.hq, hcap) && balloc(c, &b.occ, (size_t)ntot) && balloc(c, &b.bin_ll, (size_t)ntot) &&
             balloc(c, &b.bin_cnt, (size_t)ntot) && balloc(c, &b.bin_key, (size_t)ntot) &&
             balloc(c, &b.pslot, (size_t)ntot) &&
             balloc(c, &b.prop, 5 * (size_t)b.pstride) && balloc(c, &b.tile_sum, (size_t)ntiles) &&
-            balloc(c, &b.tile_excl, (size_t)ntiles) && balloc(c, &b.res, (size_t)T);
+            balloc(c, &b.tile_excl, (size_t)ntiles) && balloc(c, &b.res, (size_t)T) &&
+            balloc(c, &dtile_target, (size_t)ntiles);
   if (!ok) {
     bfree(c);
     delete c;
@@ -888,10 +862,16 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   }
   b.tg = dtg;
   b.offs = doffs;
+  b.tile_target = dtile_target;
   std::vector<long long> offs(T + 1);
   for (int t = 0; t < T; ++t) offs[t] = tg[t].off;
   offs[T] = ntot;
+  std::vector<int> tile_target(ntiles);
+  for (int t = 0; t < T; ++t)
+    for (int k = 0; k < tg[t].ntiles; ++k) tile_target[tg[t].tile0 + k] = t;
   cudaError_t e = cudaMemcpy(dtg, tg.data(), sizeof(BatchTarget) * T, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(dtile_target, tile_target.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(doffs, offs.data(), sizeof(long long) * (T + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b.hcnt, 0, hcap * sizeof(unsigned int));
