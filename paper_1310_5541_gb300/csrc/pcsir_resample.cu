@@ -21,8 +21,6 @@
 
 namespace pcsir {
 
-constexpr int RS_WINDOW = 5120;  // outputs mapped to ancestors per pass (a tile has ~4096)
-
 struct Map64 {
   unsigned long long dhi, dlo, uhi, ulo;
 };
@@ -37,22 +35,8 @@ __device__ __forceinline__ long long u_int(const Map64& mp, long long i) {
   return (long long)(ui * mp.dhi + mp.uhi + phi + carry);
 }
 
-// first output index i in [0, N] with U_i >= C (FP64 first guess: one thread per block)
-__device__ long long first_out(const Map64& mp, long long C, long long N) {
-  if (C <= 0) return 0;
-  const double dd = (double)mp.dhi + (double)mp.dlo * 5.421010862427522e-20;
-  const double ud = (double)mp.uhi + (double)mp.ulo * 5.421010862427522e-20;
-  if (dd <= 0.0) return N;
-  double x = ((double)C - ud) / dd;
-  long long i = x < 0.0 ? 0 : (x > (double)N ? N : (long long)ceil(x));
-  int guard = 0;
-  while (i > 0 && u_int(mp, i - 1) >= C && guard++ < 64) --i;
-  while (i < N && u_int(mp, i) < C && guard++ < 128) ++i;
-  return i;
-}
-
-// first_out without FP64: a float guess of (C - U0) / Delta, then the exact
-// integer correction of first_out
+// first output index i in [0, N] with U_i >= C (N if none): a float guess of
+// (C - U0) / Delta, then the exact integer correction
 __device__ long long first_out_f(const Map64& mp, long long C, long long N, float inv_delta) {
   if (C <= 0) return 0;
   if (mp.dhi == 0ull && mp.dlo == 0ull) return N;
@@ -210,19 +194,16 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
 }
 
 // ---------------------------------------------------------------------------
-// Resampling of one tile: inclusive cumulative weights of the tile, then the
-// tile's outputs in windows of RS_WINDOW.  Each thread walks its consecutive
-// particles k and the outputs i from first_out(C_{k-1}) on, giving output i to
-// the particle k with C_{k-1} <= U_i < C_k (an ancestor map in shared
-// memory); then the outputs are written in order, each gathering its
-// ancestor's propagated state.
+// Resampling of one tile: inclusive cumulative weights of the tile in shared
+// memory, then the tile's outputs i (those with C_{-1} <= U_i < C_{cnt-1}),
+// each finding by binary search the particle k with C_{k-1} <= U_i < C_k and
+// gathering its propagated state.
 // ---------------------------------------------------------------------------
 template <typename T, int WSRC, int NS = 5>
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   long long* Cs = reinterpret_cast<long long*>(rs_smem);                       // SCAN_TILE + SCAN_TILE / 16
-  int* amap = reinterpret_cast<int*>(rs_smem + sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16));  // RS_WINDOW
   __shared__ long long wtot[SCAN_THREADS / 32];
   __shared__ long long s_lo, s_hi;
   Control* ctl = b.ctl;
@@ -273,78 +254,65 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     agg += t;
   }
   const long long texcl = woff + inc - run;
-  if (tid == 0) {
-    s_lo = first_out(mp, excl, N);
-    s_hi = (base + cnt >= N) ? N : first_out(mp, excl + agg, N);
-  }
-  // 4. inclusive cumulative weights C_j of the tile
+  // 4. inclusive cumulative weights C_j of the tile; entries past its last particle compare
+  //    above every U_i (the fixed-step search below)
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) Cs[pad_idx(tid * SCAN_ITEMS + k)] = excl + texcl + loc[k];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int jj = tid * SCAN_ITEMS + k;
+    Cs[pad_idx(jj)] = jj < cnt ? excl + texcl + loc[k] : LLONG_MAX;
+  }
+  // the tile's outputs [lo, hi): U_lo >= C_{-1} = excl and U_{hi-1} < C_{cnt-1} = excl + agg
+  const float inv_delta = ctl->inv_delta;
+  if (tid == 0) s_lo = first_out_f(mp, excl, N, inv_delta);
+  if (tid == 32) s_hi = (base + cnt >= N) ? N : first_out_f(mp, excl + agg, N, inv_delta);
   __syncthreads();
-  // 5. the tile's outputs
+  // 5. the tile's outputs, four per thread and pass (all gathers issued before the stores).
+  //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
+  //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
+  //    weights in shared memory, independent for every output, so a particle with many
+  //    offspring does not serialise one thread.  Row offsets fit 32 bits (N <= 2^26).
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
   const long long lo = s_lo, hi = s_hi;
   const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
-  const float inv_delta = ctl->inv_delta;
-  long long cur = first_out_f(mp, excl + texcl, N, inv_delta);  // first output of this thread's particles
-  // U_cur kept as integer part + 64-bit fraction and advanced by Delta per output
-  unsigned long long ufrac = (unsigned long long)cur * mp.dlo + mp.ulo;
-  long long uint_cur = u_int(mp, cur);
-  int kk = 0;
-  for (long long wlo = lo; wlo < hi; wlo += RS_WINDOW) {
-    const long long whi = (hi - wlo) < RS_WINDOW ? hi : wlo + RS_WINDOW;
-    if (!zero_sum) {
-      while (kk < SCAN_ITEMS && cur < whi) {
-        if (uint_cur < Cs[pad_idx(tid * SCAN_ITEMS + kk)]) {
-          if (cur >= wlo) amap[cur - wlo] = tid * SCAN_ITEMS + kk;
-          ++cur;
-          const unsigned long long f = ufrac + mp.dlo;
-          uint_cur += (long long)(mp.dhi + (f < ufrac ? 1ull : 0ull));
-          ufrac = f;
-        } else {
-          ++kk;
+  const unsigned nb = (unsigned)N;
+  const unsigned ub = (unsigned)base;
+  constexpr int RO = 4;
+  for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS) {
+    unsigned ii[RO], aa[RO];
+    bool has[RO];
+#pragma unroll
+    for (int j = 0; j < RO; ++j) {
+      const long long i = r0 + (long long)j * SCAN_THREADS;
+      has[j] = i < hi;
+      ii[j] = (unsigned)i;
+      int a = 0;
+      if (has[j] && !zero_sum) {
+        const long long u = u_int(mp, i);
+#pragma unroll
+        for (int step = SCAN_TILE / 2; step > 0; step >>= 1)
+          if (Cs[pad_idx(a + step - 1)] <= u) a += step;
+      }
+      // all weights zero (Delta = 0): no distribution to sample, keep every particle
+      aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
+    }
+    if (out != nullptr) {
+      T v[RO][NS];
+#pragma unroll
+      for (int j = 0; j < RO; ++j)
+#pragma unroll
+        for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
+#pragma unroll
+      for (int j = 0; j < RO; ++j)
+        if (has[j]) {
+#pragma unroll
+          for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
         }
-      }
     }
-    __syncthreads();
-    // row offsets fit 32 bits (N <= 2^26)
-    const unsigned wn = (unsigned)(whi - wlo);
-    const unsigned w0 = (unsigned)wlo;
-    const unsigned nb = (unsigned)N;
-    const unsigned ub = (unsigned)base;
-    // four outputs per thread and pass: all gathers are issued before the stores
-    constexpr int RO = 4;
-    for (unsigned r0 = tid; r0 < wn; r0 += RO * SCAN_THREADS) {
-      unsigned ii[RO], aa[RO];
-      bool has[RO];
+    if (keep & PCSIR_KEEP_ANCESTORS) {
 #pragma unroll
-      for (int j = 0; j < RO; ++j) {
-        const unsigned r = r0 + j * SCAN_THREADS;
-        has[j] = r < wn;
-        ii[j] = w0 + r;
-        // all weights zero (Delta = 0): no distribution to sample, keep every particle
-        aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(amap[r], cnt)) : 0u;
-      }
-      if (out != nullptr) {
-        T v[RO][NS];
-#pragma unroll
-        for (int j = 0; j < RO; ++j)
-#pragma unroll
-          for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
-#pragma unroll
-        for (int j = 0; j < RO; ++j)
-          if (has[j]) {
-#pragma unroll
-            for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
-          }
-      }
-      if (keep & PCSIR_KEEP_ANCESTORS) {
-#pragma unroll
-        for (int j = 0; j < RO; ++j)
-          if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
-      }
+      for (int j = 0; j < RO; ++j)
+        if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
     }
-    __syncthreads();
   }
   // 6. optional per-particle outputs of the tile
   if (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN)) {
@@ -383,7 +351,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   }
 }
 
-constexpr size_t RS_SMEM = sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16) + sizeof(int) * RS_WINDOW;
+constexpr size_t RS_SMEM = sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16);
 
 cudaError_t prepare_resample() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
