@@ -546,6 +546,17 @@ __device__ long long bfirst_out_f(const BatchStats& S, long long C, long long N)
   return i;
 }
 
+// number of the tile's cumulative weights C_j <= u, j < BT_TILE, over Cs padded as j + j / 16:
+// while the search adds steps >= 16 the position stays a multiple of 16, so every probe is the
+// running padded position plus a constant (the smaller steps never cross a pad)
+__device__ __forceinline__ int btile_search(const long long* __restrict__ Cs, long long u) {
+  int pa = 0;
+#pragma unroll
+  for (int step = BT_TILE / 2; step > 0; step >>= 1)
+    if (Cs[pa + (step - 1) + ((step - 1) >> 4)] <= u) pa += step + (step >> 4);
+  return pa - pa / 17;  // pa = 17 (a / 16) + a % 16
+}
+
 __device__ void phase_tile_sums(const BatchBufs& b) {
   __shared__ long long red[BT_THREADS / 32];
   for (int item = blockIdx.x; item < b.ntiles_total; item += gridDim.x) {
@@ -677,12 +688,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
         const long long i = i0 + (long long)j * BT_THREADS;
         int a = 0;
         if (i < hi && !zero_sum) {
-          const long long u = bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, i);
-#pragma unroll
-          for (int step = BT_TILE / 2; step > 0; step >>= 1) {
-            const int probe = a + step - 1;
-            if (sm.Cs[probe + (probe >> 4)] <= u) a += step;
-          }
+          a = btile_search(sm.Cs, bu_int(S_.dhi, S_.dlo, S_.uhi, S_.ulo, i));
           a = a < cnt ? a : cnt - 1;
         }
         // all weights zero: no distribution to sample, keep every particle

@@ -61,6 +61,20 @@ __device__ __forceinline__ Map64 load_map(const Control* ctl) {
 
 __device__ __forceinline__ int pad_idx(int j) { return j + (j >> 4); }
 
+// Number of the tile's cumulative weights C_j <= u (j < SCAN_TILE), by a fixed
+// 12-step binary search over Cs in the padded layout (index j at j + j / 16).
+// While the search adds steps >= 16 the position a stays a multiple of 16, so
+// the probe a + step - 1 sits at pa + (step - 1) + (step - 1) / 16 with
+// pa = a + a / 16; the smaller steps never cross a pad.  Every probe is thus
+// the running padded position plus a constant.
+__device__ __forceinline__ int tile_search(const long long* __restrict__ Cs, long long u) {
+  int pa = 0;
+#pragma unroll
+  for (int step = SCAN_TILE / 2; step > 0; step >>= 1)
+    if (Cs[pa + (step - 1) + ((step - 1) >> 4)] <= u) pa += step + (step >> 4);
+  return pa - pa / 17;  // pa = 17 (a / 16) + a % 16
+}
+
 // every map entry is written before it is read; the clamp only keeps a
 // gather inside the tile should that ever fail
 __device__ __forceinline__ int clamp_item(int a, int cnt) { return a < 0 ? 0 : (a >= cnt ? cnt - 1 : a); }
@@ -286,12 +300,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       has[j] = i < hi;
       ii[j] = (unsigned)i;
       int a = 0;
-      if (has[j] && !zero_sum) {
-        const long long u = u_int(mp, i);
-#pragma unroll
-        for (int step = SCAN_TILE / 2; step > 0; step >>= 1)
-          if (Cs[pad_idx(a + step - 1)] <= u) a += step;
-      }
+      if (has[j] && !zero_sum) a = tile_search(Cs, u_int(mp, i));
       // all weights zero (Delta = 0): no distribution to sample, keep every particle
       aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
     }
