@@ -47,9 +47,12 @@ notes):
       pixel, so pixels outside S_x count as predicted; for two evaluations
       with the same patch it differs from the full Poisson log-pmf by a
       constant.
-* Resampling: systematic, every step, with one uniform u0 shared by all
-  outputs, ``U_i = (i + u0) / N`` and ``s(i) = min{l : C_l > U_i}`` where C is
-  the inclusive cumulative sum of the normalised weights in particle order.
+* Resampling: systematic, with one uniform u0 shared by all outputs,
+  ``U_i = (i + u0) / N`` and ``s(i) = min{l : C_l > U_i}`` where C is the
+  inclusive cumulative sum of the normalised weights in particle order; at
+  every step (``sir_step``, ``pcsir_step``), or only when N_eff < N_thr
+  (``sir_step_ess``, ``pcsir_step_ess``: Algorithm 1's test, with the weights
+  carried to the next step when it fails).
 * Estimate: posterior mean before resampling.
 """
 from __future__ import annotations
@@ -272,6 +275,43 @@ def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None, dum
     return dict(prop=prop, bin_keys=keys, bin_counts=counts, member_bin=member,
                 dummies=dum, ll_bins=ll_bins, ll=ll, w=w, max_logw=m, ess=ess(w),
                 estimate=posterior_mean(w, prop), ancestors=anc, new_state=np.ascontiguousarray(prop[:, anc]))
+
+
+def _ess_branch(r, logw_prev, ess_min):
+    """Algorithm 1/2's resampling branch: resample only when N_eff < ess_min.
+
+    Adds 'resampled' and 'logw_out' (the log-weights the next step starts
+    from: zeros after resampling, else this step's log-weights minus their
+    maximum) and replaces 'new_state' by the propagated state when the step
+    does not resample.
+    """
+    logw = r["ll"] if logw_prev is None else np.asarray(logw_prev, np.float64) + r["ll"]
+    r["logw"] = logw
+    r["resampled"] = bool(r["ess"] < ess_min)
+    if r["resampled"]:
+        r["logw_out"] = np.zeros_like(logw)
+    else:
+        r["logw_out"] = logw - np.max(logw)
+        r["ancestors"] = np.arange(logw.shape[0])
+        r["new_state"] = np.ascontiguousarray(r["prop"])
+    return r
+
+
+def sir_step_ess(state, logw_prev, image, noise, u0, ess_min, model, lik=None):
+    """Algorithm 1 with its threshold test: weights carry the previous step's
+    log-weights (``logw_prev``, None for uniform), w_k = w_{k-1} p(z|x_k), and
+    the particles are resampled only when N_eff < ess_min."""
+    r = sir_step(state, image, noise, u0, model, lik=lik, prior_logw=logw_prev)
+    return _ess_branch(r, logw_prev, ess_min)
+
+
+def pcsir_step_ess(state, logw_prev, image, noise, u0, h, ess_min, model, lik=None, dummy="com"):
+    """Algorithm 2 with its threshold test: the dummy of a bin is the mean of
+    its members weighted by w_{k-1} (Section 4), every member's weight is
+    multiplied by the dummy's likelihood, and the particles are resampled only
+    when N_eff < ess_min."""
+    r = pcsir_step(state, image, noise, u0, h, model, lik=lik, prior_logw=logw_prev, dummy=dummy)
+    return _ess_branch(r, logw_prev, ess_min)
 
 
 def run_filter(kind, seq_images, gt0, N, noise_fn, u0_fn, model, h=None, dtype=np.float64,
