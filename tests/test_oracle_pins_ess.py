@@ -154,11 +154,12 @@ def test_one_particle_per_bin_is_sir_with_carried_weights():
         a = O.sir_step_ess(st, lw, seq.images[k], noise, u0, 0.1 * N, m)
         b = O.pcsir_step_ess(st, lw, seq.images[k], noise, u0, 1e-4, 0.1 * N, m)
         assert b["bin_counts"].max() == 1
-        np.testing.assert_array_equal(a["w"], b["w"])
-        np.testing.assert_array_equal(a["estimate"], b["estimate"])
+        # a one-member weighted mean (w x) / w can differ from x in the last bit (FP64)
+        np.testing.assert_allclose(a["w"], b["w"], rtol=1e-9, atol=0)
+        np.testing.assert_allclose(a["estimate"], b["estimate"], rtol=1e-12, atol=0)
         assert a["resampled"] == b["resampled"]
         np.testing.assert_array_equal(a["new_state"], b["new_state"])
-        np.testing.assert_array_equal(a["logw_out"], b["logw_out"])
+        np.testing.assert_allclose(a["logw_out"], b["logw_out"], rtol=0, atol=1e-9)
         decisions.append(a["resampled"])
         st, lw = a["new_state"], a["logw_out"]
     assert True in decisions and False in decisions
