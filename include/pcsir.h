@@ -118,6 +118,8 @@ typedef struct pcsir_result {
   int64_t n_bins;       /* pcSIR: occupied bins B; SIR: 0 */
   int32_t device_error; /* PCSIR_DERR_* flags, 0 if none */
   int32_t kind;         /* 0 = SIR step, 1 = pcSIR step */
+  int32_t resampled;    /* 1 if the step resampled (always, except in the ESS-thresholded steps) */
+  int32_t reserved;
 } pcsir_result;
 
 /* Device pointers to intermediates of the most recent step of a context,
@@ -186,6 +188,40 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
 pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image,
                       int32_t W, int32_t H, const void* noise, double u0,
                       void* stream, pcsir_result* result_host);
+
+/* ESS-thresholded steps: Algorithms 1 and 2 with their test "if N_eff < N_thr:
+ * resample" (Section 3, Algorithm 1), the weights being carried to the next
+ * step when the test fails.  pcsir_step / sir_step are the case that always
+ * resamples.
+ *
+ * logw: device int64 [N], read and written, the particles' carried
+ *   log-weights in fixed point: log w = logw * 2^-32.  On entry, what the
+ *   previous call returned (all zeros for uniform weights, e.g. on the first
+ *   step): values <= 0 whose maximum is 0, or INT64_MIN for a particle of
+ *   zero weight.  On return: all zeros if the step resampled, else the step's
+ *   log-weights log w_{k-1} + log p(z | x_k) minus their maximum.
+ * ess_min: the step resamples when N_eff < ess_min (ess_min > N: every step;
+ *   ess_min <= 0: never).  N_eff = (sum w)^2 / sum w^2 is result->ess.
+ * pcsir_step_ess: each cell's dummy is the mean of its members weighted by
+ *   w_{k-1} (Section 4, centre of mass of the state vectors and weights); the
+ *   members' weights are multiplied by the dummy's likelihood.  The weighted
+ *   sums are formed in FP32 per block and FP64 across blocks (within a few
+ *   FP32 units in the last place of the weighted offsets, and not bit-for-bit
+ *   reproducible); a member whose carried weight is below about e^-87 of the
+ *   largest adds nothing to its cell's centre of mass (FP32 exponential), and
+ *   a cell with no member above that takes the plain mean.
+ * Without resampling the state becomes the propagated state and
+ * PCSIR_KEEP_ANCESTORS gives the identity; result->resampled tells which branch
+ * the step took.  FP32 state only (PCSIR_ENOTSUP for FP64), and not with an
+ * attached surrogate (PCSIR_ENOTSUP).  Other arguments, errors, streams and
+ * graph capture as pcsir_step / sir_step.
+ */
+pcsir_status pcsir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N, const float* image,
+                            int32_t W, int32_t H, double h, const void* noise, double u0, double ess_min,
+                            void* stream, pcsir_result* result_host);
+pcsir_status sir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N, const float* image,
+                          int32_t W, int32_t H, const void* noise, double u0, double ess_min,
+                          void* stream, pcsir_result* result_host);
 
 /* Log-likelihood (Eq. likelihood with the context's model) of n positions:
    x, y, I0 device float64 [n], out device float64 [n].  The same device code

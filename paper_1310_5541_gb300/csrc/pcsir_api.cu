@@ -184,6 +184,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
     return PCSIR_ENOMEM;
   }
   b.derr_out = &b.dres->device_error;
+  b.resampled_out = &b.dres->resampled;
   e = prepare_kernels(cfg->state_dtype, b.prop_bin_per_sm);
   if (e == cudaSuccess) e = prepare_resample();
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result));
@@ -262,6 +263,66 @@ pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image
   e = launch_resample(ctx->b, ctx->cfg.state_dtype, state, N, u0, WSRC_PARTICLES,
                       ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN, ctx->num_sms, s);
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
+  return finish_step(ctx, s, result_host, 0, N);
+}
+
+namespace {
+// arguments shared by the two ESS-thresholded steps
+pcsir_status check_ess_args(pcsir_ctx* ctx, const int64_t* logw, double ess_min) {
+  if (!logw) return fail(ctx, PCSIR_EINVAL, "logw must be a non-NULL device pointer");
+  if (ess_min != ess_min) return fail(ctx, PCSIR_EINVAL, "ess_min must not be NaN");
+  if (ctx->cfg.state_dtype != PCSIR_F32) return fail(ctx, PCSIR_ENOTSUP, "ESS-thresholded steps take FP32 state");
+  if (ctx->sur_on) return fail(ctx, PCSIR_ENOTSUP, "ESS-thresholded steps do not use the likelihood surrogate");
+  return PCSIR_OK;
+}
+}  // namespace
+
+pcsir_status pcsir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N, const float* image, int32_t W,
+                            int32_t H, double h, const void* noise, double u0, double ess_min, void* stream,
+                            pcsir_result* result_host) {
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  if ((st = check_ess_args(ctx, logw, ess_min)) != PCSIR_OK) return st;
+  if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  const int64_t prev_bins = ctx->last_kind == 1 ? ((volatile pcsir_result*)ctx->host_res)->n_bins : -1;
+  ctx->b.big_table = prev_bins >= 0 ? (prev_bins > 1200 ? 1 : 0) : (h < 0.15 ? 1 : 0);
+  StepBuffers b = ctx->b;
+  b.lw_out = reinterpret_cast<long long*>(logw);
+  b.ess_min = ess_min;
+  const long long* lw_in = reinterpret_cast<const long long*>(logw);
+  e = launch_prop_bin(b, PCSIR_F32, state, noise, N, h, ctx->num_sms, s);
+  if (e == cudaSuccess) e = launch_pcsir_ess_front(b, ctx->m, lw_in, image, W, H, N, h, ctx->num_sms, s);
+  if (e == cudaSuccess) e = launch_particle_weights(b, PCSIR_F32, N, ctx->num_sms, 2, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels (ESS)");
+  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_PARTICLES, ctx->cfg.keep, ctx->num_sms, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
+  return finish_step(ctx, s, result_host, 1, N);
+}
+
+pcsir_status sir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N, const float* image, int32_t W,
+                          int32_t H, const void* noise, double u0, double ess_min, void* stream,
+                          pcsir_result* result_host) {
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  if ((st = check_ess_args(ctx, logw, ess_min)) != PCSIR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  StepBuffers b = ctx->b;
+  b.lw_out = reinterpret_cast<long long*>(logw);
+  b.ess_min = ess_min;
+  const StageEvents none{};
+  e = launch_sir_front(b, ctx->m, PCSIR_F32, state, noise, N, image, W, H, ctx->num_sms, s, none, ctx->cfg.keep,
+                       0);
+  if (e == cudaSuccess) e = launch_sir_ess_front(b, reinterpret_cast<const long long*>(logw), N, ctx->num_sms, s);
+  if (e == cudaSuccess) e = launch_particle_weights(b, PCSIR_F32, N, ctx->num_sms, 0, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "SIR front kernels (ESS)");
+  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_PARTICLES, ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN,
+                      ctx->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
   return finish_step(ctx, s, result_host, 0, N);
 }

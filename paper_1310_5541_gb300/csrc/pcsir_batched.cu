@@ -625,6 +625,7 @@ __device__ void phase_target_scan(const BatchBufs& b, const double* __restrict__
     r.n_particles = T_.n;
     r.n_bins = S_.nbins;
     r.kind = 1;
+    r.resampled = 1;
     r.device_error = Tq == 0ull ? PCSIR_DERR_ZEROSUM : 0;
   }
 }

@@ -1,0 +1,242 @@
+// ESS-thresholded SIR and pcSIR steps (Algorithms 1 and 2 with the test
+// "if N_eff < N_thr: resample", Section 3): the particles carry log-weights
+// from step to step until the test resamples them.
+//
+// The carried log-weights are int64 fixed point (units of 2^-32), the form in
+// which SIR's per-particle log-likelihoods already enter the integer weights of
+// the resampling kernel; adding a step's log-likelihood is an exact integer
+// addition.  pcSIR with carried weights needs each cell's centre of mass
+// weighted by w_{k-1} (Section 4: "state vectors and weights"):
+//
+//   k_ess_rank   bin index of every occupied hash slot; zeroes the per-bin sums
+//   k_ess_wsums  per bin: sum of w_i and of w_i (s_i - r_b) for every state
+//                component, w_i = exp(logw_i 2^-32) (logw <= 0, maximum 0),
+//                r_b the cell's lower corner for x, y and the step's anchors
+//                (particle 0's input values) for vx, vy, I0.  FP32 products
+//                summed in shared memory over rounds of ESS_ROUND particles,
+//                then added into FP64 per-bin sums.
+//   k_ess_bins   weighted dummy r_b + S_b / W_b (the plain mean when W_b = 0),
+//                or the cell centre for x, y with pcSIR-CoC, and its
+//                likelihood; the hash slots return to empty
+//   k_ess_lw     logw_i + ll_{bin(i)} in fixed point, and its maximum
+//
+// then the usual per-particle weight reduction (ESS, posterior mean) and the
+// resampling kernel, which decides on the device whether to resample.
+#include <algorithm>
+
+#include "pcsir_device.cuh"
+
+namespace pcsir {
+
+LikParams make_lik(const ModelParams& m);  // pcsir_kernels.cu
+
+constexpr int ESS_THREADS = 256;
+constexpr int ESS_SMEM_BINS = 2048;  // bins whose sums a block keeps in shared memory
+constexpr int ESS_ROUND = 8192;      // particles per shared-memory round of a block
+constexpr int ESS_BIN_WARPS = ESS_THREADS / 32;
+constexpr int ESS_MAXP = 127;        // largest patch side
+
+__device__ __forceinline__ float lw_to_float(long long v) {
+  // v 2^-32 from two 32-bit conversions (the 64-bit conversion runs on the FP64 pipe)
+  return (float)(int)(v >> 32) + (float)(unsigned)(v & 0xffffffffll) * 2.3283064365386963e-10f;
+}
+
+// lower corner of cell b along one axis, the reference of the weighted position offsets
+__device__ __forceinline__ float cell_ref(int b, float h) { return __fsub_rn(__fmul_rn((float)b, h), 0.5f); }
+
+__device__ __forceinline__ float anchor_f(const Control* ctl, int c) {
+  return (float)((double)ctl->anchor[2 + c] * VAL_INV);
+}
+
+__global__ void __launch_bounds__(ESS_THREADS) k_ess_rank(StepBuffers b) {
+  const unsigned B = b.ctl->nocc;
+  const int64_t bs = b.bin_stride;
+  for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < B; bi += gridDim.x * blockDim.x) {
+    b.hrank[b.occ[bi]] = bi;
+    b.bin_ll[bi] = 0.0;  // sum of the members' weights until k_ess_bins
+#pragma unroll
+    for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const long long* __restrict__ lw,
+                                                           int64_t N, float h) {
+  __shared__ float acc[6][ESS_SMEM_BINS];
+  const unsigned B = b.ctl->nocc;
+  const bool local = B <= (unsigned)ESS_SMEM_BINS;
+  const float* __restrict__ prop = static_cast<const float*>(b.prop);
+  const int64_t bs = b.bin_stride;
+  float anc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) anc[c] = anchor_f(b.ctl, c);
+  if (local) {
+    for (unsigned j = threadIdx.x; j < B; j += blockDim.x)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) acc[a][j] = 0.0f;
+  }
+  __syncthreads();
+  // a contiguous range of particles per block, in rounds of ESS_ROUND
+  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per;
+  const int64_t hi = lo + per < N ? lo + per : N;
+  for (int64_t r0 = lo; r0 < hi; r0 += ESS_ROUND) {
+    const int64_t r1 = r0 + ESS_ROUND < hi ? r0 + ESS_ROUND : hi;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const unsigned g = b.pslot[i];
+      const unsigned bi = b.hrank[g];
+      if (bi >= B) continue;  // only after a failed cell insertion (PCSIR_DERR_RANGE is set)
+      const unsigned long long key = b.hkey[g];
+      const long long l = lw[i];
+      const float w = l == LLQ_NONE ? 0.0f : expf(lw_to_float(l));
+      float d[5];
+      d[0] = prop[i] - cell_ref(key_bx(key), h);
+      d[1] = prop[N + i] - cell_ref(key_by(key), h);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[2 + c] = prop[(2 + c) * N + i] - anc[c];
+      if (local) {
+        atomicAdd(&acc[0][bi], w);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) atomicAdd(&acc[1 + c][bi], w * d[c]);
+      } else {
+        atomicAdd(&b.bin_ll[bi], (double)w);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + bi], (double)(w * d[c]));
+      }
+    }
+    if (local) {
+      __syncthreads();
+      for (unsigned j = threadIdx.x; j < B; j += blockDim.x) {
+        if (acc[0][j] != 0.0f) {
+          atomicAdd(&b.bin_ll[j], (double)acc[0][j]);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + j], (double)acc[1 + c][j]);
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) acc[a][j] = 0.0f;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ESS_THREADS) k_ess_bins(StepBuffers b, LikParams lp, const float* __restrict__ img,
+                                                          int W, int H, float h, long long hq, int coc) {
+  __shared__ float scratch[ESS_BIN_WARPS][4 * ESS_MAXP];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const unsigned B = b.ctl->nocc;
+  const size_t hcap = size_t(1) << b.hbits;
+  const int64_t bs = b.bin_stride;
+  double mymax = -INFINITY;
+  for (unsigned bi = blockIdx.x * ESS_BIN_WARPS + wp; bi < B; bi += gridDim.x * ESS_BIN_WARPS) {
+    const unsigned g = b.occ[bi];
+    const unsigned long long key = b.hkey[g];
+    const int bx = key_bx(key), by = key_by(key);
+    const unsigned n = b.hcnt[g];
+    const double wsum = b.bin_ll[bi];
+    double dum[5];
+    if (wsum > 0.0) {
+      dum[0] = (double)cell_ref(bx, h) + b.dummy[bi] / wsum;
+      dum[1] = (double)cell_ref(by, h) + b.dummy[bs + bi] / wsum;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dum[2 + c] = (double)anchor_f(b.ctl, c) + b.dummy[(2 + c) * bs + bi] / wsum;
+    } else {  // no member carries weight: the plain mean from the exact sums
+      const double dn = (double)n;
+      dum[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] / dn) * POS_INV;
+      dum[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
+#pragma unroll
+      for (int c = 2; c < 5; ++c) dum[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    }
+    if (coc) {  // pcSIR-CoC: the cell's geometric centre
+      dum[0] = ((double)bx + 0.5) * (double)h - 0.5;
+      dum[1] = ((double)by + 0.5) * (double)h - 0.5;
+    }
+    __syncwarp();
+    const LLSum ls = warp_loglik(img, W, H, lik_pos(dum[0], dum[1], dum[4]), lp, scratch[wp]);
+    const double ll = ls.bad ? -INFINITY : ll_to_double(ls);
+    __syncwarp();
+    if (lane == 0) {
+      if (ls.bad) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = dum[c];
+      b.bin_ll[bi] = ll;
+      b.bin_cnt[bi] = n;
+      b.bin_xy[bi] = bx;
+      b.bin_xy[bs + bi] = by;
+      b.hq[g] = llq_of(ls);  // the cell's fixed-point log-likelihood, read per particle next
+      b.hkey[g] = EMPTY_KEY;
+      b.hcnt[g] = 0u;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) b.hsum[c * hcap + g] = 0;
+    }
+    mymax = fmax(mymax, ll);
+  }
+  // maximum over the dummies (reported only; the weights use the particles' maximum)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+  if (lane == 0 && mymax > -INFINITY) atomicMax(&b.ctl->max_ll, ord_encode(mymax));
+}
+
+__device__ __forceinline__ void ess_block_max(long long v, Control* ctl) {
+  __shared__ long long red[ESS_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = LLQ_NONE;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) m = red[j] > m ? red[j] : m;
+    if (m != LLQ_NONE) atomicMax(&ctl->max_llq, llq_enc(m));
+  }
+}
+
+// logw_i + ll_i: from the particle's cell (pcSIR, PCSIR = true) or from SIR's per-particle
+// values already in b.llq; INT64_MIN (no weight) on either side stays INT64_MIN
+template <bool PCSIR>
+__global__ void __launch_bounds__(ESS_THREADS) k_ess_lw(StepBuffers b, const long long* __restrict__ lw, int64_t N) {
+  long long m = LLQ_NONE;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const long long l = PCSIR ? b.hq[b.pslot[i]] : b.llq[i];
+    const long long p = lw[i];
+    const long long v = (l == LLQ_NONE || p == LLQ_NONE) ? LLQ_NONE : p + l;
+    b.llq[i] = v;
+    if (PCSIR && b.pbin) b.pbin[i] = b.hrank[b.pslot[i]];
+    m = v > m ? v : m;
+  }
+  ess_block_max(m, b.ctl);
+}
+
+static int ess_grid(int64_t n, int threads, int num_sms, int per_sm) {
+  const int64_t want = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * per_sm));
+}
+
+cudaError_t launch_pcsir_ess_front(const StepBuffers& b, const ModelParams& m, const long long* lw_in,
+                                   const float* img, int W, int H, int64_t N, double h, int num_sms,
+                                   cudaStream_t s) {
+  const int full = num_sms * 8;  // blocks of the per-bin kernels (they stop at the device's bin count)
+  k_ess_rank<<<full, ESS_THREADS, 0, s>>>(b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ess_wsums<<<ess_grid(N, ESS_ROUND, num_sms, 4), ESS_THREADS, 0, s>>>(b, lw_in, N, (float)h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long hq = llrint(h * 2147483648.0);
+  k_ess_bins<<<full, ESS_THREADS, 0, s>>>(b, make_lik(m), img, W, H, (float)h, hq, m.coc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ess_lw<true><<<ess_grid(N, ESS_THREADS, num_sms, 8), ESS_THREADS, 0, s>>>(b, lw_in, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sir_ess_front(const StepBuffers& b, const long long* lw_in, int64_t N, int num_sms,
+                                 cudaStream_t s) {
+  // the maximum so far is that of the log-likelihoods alone: start again for the sums
+  cudaError_t e = cudaMemsetAsync(&b.ctl->max_llq, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_ess_lw<false><<<ess_grid(N, ESS_THREADS, num_sms, 8), ESS_THREADS, 0, s>>>(b, lw_in, N);
+  return cudaGetLastError();
+}
+
+}  // namespace pcsir

@@ -73,6 +73,11 @@ struct StepBuffers {
   Control* ctl;
   pcsir_result* dres;
   int32_t* derr_out;        // where the last resampling tile publishes the step's device error flags
+  int32_t* resampled_out;   // where it publishes whether the step resampled (nullptr: nowhere)
+  // ESS-thresholded steps: with lw_out set the resampling kernel resamples only when
+  // N_eff < ess_min and writes the carried fixed-point log-weights to lw_out
+  long long* lw_out;
+  double ess_min;
   int prop_bin_per_sm[2];   // resident blocks per SM of the propagate/bin kernel (small, large cell table)
   int big_table;            // 1: the propagate/bin kernel uses the large cell table
 };
@@ -129,11 +134,27 @@ int64_t sur_max_pixels(const pcsir_surrogate* s);
 // surrogate predictions of the non-clipped dummies and the held-out check (pcsir_surrogate.cu)
 cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const ModelParams& m, const float* img, int W,
                             int H, cudaStream_t s);
+// with_weights = 0: only the per-particle log-likelihoods and their maximum (the caller
+// reduces the weights itself)
 cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                              const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
-                             cudaStream_t s, StageEvents se, int keep);
+                             cudaStream_t s, StageEvents se, int keep, int with_weights = 1);
 cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t N, int num_sms,
                               cudaStream_t s);
+// propagate + cells + centre-of-mass sums only (the first kernel of launch_pcsir_front)
+cudaError_t launch_prop_bin(const StepBuffers& b, int dtype, const void* state, const void* noise, int64_t N,
+                            double h, int num_sms, cudaStream_t s);
+// weights, ESS and posterior mean from the per-particle fixed-point log-weights b.llq
+// (kind 0: SIR result, 2: pcSIR result with per-particle weights)
+cudaError_t launch_particle_weights(const StepBuffers& b, int dtype, int64_t N, int num_sms, int kind,
+                                    cudaStream_t s);
+// ESS-thresholded steps (pcsir_ess.cu): prior-weighted dummies, their likelihood and the
+// carried log-weights (pcSIR), or the carried log-weights added to SIR's (lw_in: caller's array)
+cudaError_t launch_pcsir_ess_front(const StepBuffers& b, const ModelParams& m, const long long* lw_in,
+                                   const float* img, int W, int H, int64_t N, double h, int num_sms,
+                                   cudaStream_t s);
+cudaError_t launch_sir_ess_front(const StepBuffers& b, const long long* lw_in, int64_t N, int num_sms,
+                                 cudaStream_t s);
 cudaError_t prepare_kernels(int dtype, int prop_bin_per_sm[2]);
 cudaError_t prepare_resample();
 // integer-weight scale: q = rint(exp(ll - max) * 2^sq) with N * 2^sq <= 2^61

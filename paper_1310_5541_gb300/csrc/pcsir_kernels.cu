@@ -551,6 +551,8 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
     pcsir_result* r = b.dres;
     for (int c = 0; c < 5; ++c) r->estimate[c] = with_est ? vc->est[c] / Tf : 0.0;
     r->ess = Tf * Tf / T2;
+    // kind 1: pcSIR (maximum over the dummies), 0: SIR, 2: pcSIR with per-particle
+    // log-weights (both: maximum over the particles' fixed-point log-weights)
     if (kind == 1) {
       r->max_loglik = ord_decode(vc->max_ll);
     } else {
@@ -559,8 +561,8 @@ __device__ void block_reduce_commit(RedAcc a, const StepBuffers& b, int64_t N, i
     }
     r->sum_wtilde = Tf;
     r->n_particles = N;
-    r->n_bins = kind == 1 ? (int64_t)vc->nocc : 0;
-    r->kind = kind;
+    r->n_bins = kind != 0 ? (int64_t)vc->nocc : 0;
+    r->kind = kind != 0 ? 1 : 0;
     if (vc->T_int <= 0) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
   }
 }
@@ -656,7 +658,7 @@ __device__ __forceinline__ long long particle_llq(const double* __restrict__ lw,
 
 template <typename T, typename SRC>
 __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC* __restrict__ lls, int64_t N,
-                                                       int sq, int with_est) {
+                                                       int sq, int with_est, int kind) {
   const unsigned long long me = b.ctl->max_llq;
   const long long mq = llq_dec(me);
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC*
 #pragma unroll
   for (int c = 0; c < 5; ++c) a.est[c] = (double)ke[c].s - (double)ke[c].c;
   a.Tint = tint;
-  block_reduce_commit(a, b, N, 0, with_est != 0, gridDim.x);
+  block_reduce_commit(a, b, N, kind, with_est != 0, gridDim.x);
 }
 
 // max of caller-given log-weights (standalone resampling)
@@ -711,7 +713,7 @@ k_loglik(LikParams lp, const double* __restrict__ x, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-static LikParams make_lik(const ModelParams& m) {
+LikParams make_lik(const ModelParams& m) {
   LikParams lp;
   lp.P = m.P;
   lp.kind = m.kind;
@@ -823,7 +825,7 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
 
 cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                              const void* noise, int64_t N, const float* img, int W, int H, int num_sms,
-                             cudaStream_t s, StageEvents se, int keep) {
+                             cudaStream_t s, StageEvents se, int keep, int with_weights) {
   const LikParams lp = make_lik(m);
   const int64_t nb = (N + SL_THREADS - 1) / SL_THREADS;
   const int sq = weight_scale_bits(N);
@@ -834,14 +836,14 @@ cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dty
                                                              keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1);
+    if (with_weights) k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0);
   } else {
     k_sir_prop_lik<double><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const double*>(state),
                                                               static_cast<const double*>(noise), N, lp, img, W, H,
                                                               keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1);
+    if (with_weights) k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
@@ -853,7 +855,25 @@ cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t 
   k_logw_max<<<rgrid, RED_THREADS, 0, s>>>(b, logw, N);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sir_w<float, double><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0);
+  k_sir_w<float, double><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prop_bin(const StepBuffers& b, int dtype, const void* state, const void* noise, int64_t N,
+                            double h, int num_sms, cudaStream_t s) {
+  const long long hq = llrint(h * 2147483648.0);
+  return dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
+                            : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
+}
+
+cudaError_t launch_particle_weights(const StepBuffers& b, int dtype, int64_t N, int num_sms, int kind,
+                                    cudaStream_t s) {
+  const int rgrid = (int)std::min<int64_t>((N + RED_THREADS - 1) / RED_THREADS, (int64_t)num_sms * 4);
+  const int sq = weight_scale_bits(N);
+  if (dtype == PCSIR_F32)
+    k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind);
+  else
+    k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind);
   return cudaGetLastError();
 }
 

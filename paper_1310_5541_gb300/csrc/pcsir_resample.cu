@@ -231,96 +231,125 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
   const Map64 mp = load_map(ctl);
   const long long excl = b.tile_excl[tile];
 
-  // 1. integer weights, into padded shared memory in particle order
-  {
-    long long q[SCAN_ITEMS];
-    tile_weights<WSRC>(b, lsrc, base, cnt, mq, me != 0ull, sq, q);
+  // ESS-thresholded steps (lw_out set): the particles are resampled only when N_eff < ess_min,
+  // from the weight sums of this step (the same for every block)
+  bool skip = false;
+  if (b.lw_out != nullptr) {
+    const double Tf = *(volatile double*)&ctl->T_f, T2 = *(volatile double*)&ctl->T2_f;
+    skip = !(Tf * Tf / T2 < b.ess_min);
+  }
+  if (skip) {
+    // no resampling: the propagated particles and their log-weights (minus the maximum)
+    // carry over to the next step
+    const T* __restrict__ prop = static_cast<const T*>(b.prop);
+    for (int j = tid; j < cnt; j += SCAN_THREADS) {
+      const int64_t i = base + j;
+      if (out != nullptr) {
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
-      const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) Cs[pad_idx(j0 + e)] = q[4 * k + e];
+        for (int d = 0; d < NS; ++d) out[d * N + i] = prop[d * N + i];
+      }
+      const long long q = b.llq[i];
+      b.lw_out[i] = q == LLQ_NONE ? LLQ_NONE : q - mq;
+      if (keep & PCSIR_KEEP_ANCESTORS) b.anc[i] = (int32_t)i;
     }
-  }
-  __syncthreads();
-  // 2. each thread scans its ITEMS consecutive weights
-  long long run = 0;
-  long long loc[SCAN_ITEMS];
+  } else {
+    // 1. integer weights, into padded shared memory in particle order
+    {
+      long long q[SCAN_ITEMS];
+      tile_weights<WSRC>(b, lsrc, base, cnt, mq, me != 0ull, sq, q);
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    run += Cs[pad_idx(tid * SCAN_ITEMS + k)];
-    loc[k] = run;
-  }
-  // 3. exclusive scan of the thread totals across the block
-  long long inc = run;
+      for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+        const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long v = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += v;
-  }
-  if (lane == 31) wtot[w] = inc;
-  __syncthreads();
-  long long woff = 0, agg = 0;
-#pragma unroll
-  for (int j = 0; j < SCAN_THREADS / 32; ++j) {
-    const long long t = wtot[j];
-    if (j < w) woff += t;
-    agg += t;
-  }
-  const long long texcl = woff + inc - run;
-  // 4. inclusive cumulative weights C_j of the tile; entries past its last particle compare
-  //    above every U_i (the fixed-step search below)
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int jj = tid * SCAN_ITEMS + k;
-    Cs[pad_idx(jj)] = jj < cnt ? excl + texcl + loc[k] : LLONG_MAX;
-  }
-  // the tile's outputs [lo, hi): U_lo >= C_{-1} = excl and U_{hi-1} < C_{cnt-1} = excl + agg
-  const float inv_delta = ctl->inv_delta;
-  if (tid == 0) s_lo = first_out_f(mp, excl, N, inv_delta);
-  if (tid == 32) s_hi = (base + cnt >= N) ? N : first_out_f(mp, excl + agg, N, inv_delta);
-  __syncthreads();
-  // 5. the tile's outputs, four per thread and pass (all gathers issued before the stores).
-  //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
-  //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
-  //    weights in shared memory, independent for every output, so a particle with many
-  //    offspring does not serialise one thread.  Row offsets fit 32 bits (N <= 2^26).
-  const T* __restrict__ prop = static_cast<const T*>(b.prop);
-  const long long lo = s_lo, hi = s_hi;
-  const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
-  const unsigned nb = (unsigned)N;
-  const unsigned ub = (unsigned)base;
-  constexpr int RO = 4;
-  for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS) {
-    unsigned ii[RO], aa[RO];
-    bool has[RO];
-#pragma unroll
-    for (int j = 0; j < RO; ++j) {
-      const long long i = r0 + (long long)j * SCAN_THREADS;
-      has[j] = i < hi;
-      ii[j] = (unsigned)i;
-      int a = 0;
-      if (has[j] && !zero_sum) a = tile_search(Cs, u_int(mp, i));
-      // all weights zero (Delta = 0): no distribution to sample, keep every particle
-      aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
+        for (int e = 0; e < 4; ++e) Cs[pad_idx(j0 + e)] = q[4 * k + e];
+      }
     }
-    if (out != nullptr) {
-      T v[RO][NS];
+    __syncthreads();
+    // 2. each thread scans its ITEMS consecutive weights
+    long long run = 0;
+    long long loc[SCAN_ITEMS];
 #pragma unroll
-      for (int j = 0; j < RO; ++j)
-#pragma unroll
-        for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
-#pragma unroll
-      for (int j = 0; j < RO; ++j)
-        if (has[j]) {
-#pragma unroll
-          for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
-        }
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      run += Cs[pad_idx(tid * SCAN_ITEMS + k)];
+      loc[k] = run;
     }
-    if (keep & PCSIR_KEEP_ANCESTORS) {
+    // 3. exclusive scan of the thread totals across the block
+    long long inc = run;
 #pragma unroll
-      for (int j = 0; j < RO; ++j)
-        if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wtot[w] = inc;
+    __syncthreads();
+    long long woff = 0, agg = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_THREADS / 32; ++j) {
+      const long long t = wtot[j];
+      if (j < w) woff += t;
+      agg += t;
+    }
+    const long long texcl = woff + inc - run;
+    // 4. inclusive cumulative weights C_j of the tile; entries past its last particle compare
+    //    above every U_i (the fixed-step search below)
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      const int jj = tid * SCAN_ITEMS + k;
+      Cs[pad_idx(jj)] = jj < cnt ? excl + texcl + loc[k] : LLONG_MAX;
+    }
+    // the tile's outputs [lo, hi): U_lo >= C_{-1} = excl and U_{hi-1} < C_{cnt-1} = excl + agg
+    const float inv_delta = ctl->inv_delta;
+    if (tid == 0) s_lo = first_out_f(mp, excl, N, inv_delta);
+    if (tid == 32) s_hi = (base + cnt >= N) ? N : first_out_f(mp, excl + agg, N, inv_delta);
+    __syncthreads();
+    // 5. the tile's outputs, four per thread and pass (all gathers issued before the stores).
+    //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
+    //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
+    //    weights in shared memory, independent for every output, so a particle with many
+    //    offspring does not serialise one thread.  Row offsets fit 32 bits (N <= 2^26).
+    const T* __restrict__ prop = static_cast<const T*>(b.prop);
+    const long long lo = s_lo, hi = s_hi;
+    const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
+    const unsigned nb = (unsigned)N;
+    const unsigned ub = (unsigned)base;
+    constexpr int RO = 4;
+    for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS) {
+      unsigned ii[RO], aa[RO];
+      bool has[RO];
+#pragma unroll
+      for (int j = 0; j < RO; ++j) {
+        const long long i = r0 + (long long)j * SCAN_THREADS;
+        has[j] = i < hi;
+        ii[j] = (unsigned)i;
+        int a = 0;
+        if (has[j] && !zero_sum) a = tile_search(Cs, u_int(mp, i));
+        // all weights zero (Delta = 0): no distribution to sample, keep every particle
+        aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
+      }
+      if (out != nullptr) {
+        T v[RO][NS];
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+#pragma unroll
+          for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+          if (has[j]) {
+#pragma unroll
+            for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
+          }
+      }
+      if (keep & PCSIR_KEEP_ANCESTORS) {
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+          if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
+      }
+      // resampled particles restart from uniform weights
+      if (b.lw_out != nullptr) {
+#pragma unroll
+        for (int j = 0; j < RO; ++j)
+          if (has[j]) b.lw_out[ii[j]] = 0;
+      }
     }
   }
   // 6. optional per-particle outputs of the tile
@@ -356,6 +385,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     if (atomicAdd(&ctl->tiles_done, 1u) == gridDim.x - 1) {
       __threadfence();
       *b.derr_out = (int32_t)(*(volatile unsigned*)&ctl->err);
+      if (b.resampled_out != nullptr) *b.resampled_out = skip ? 0 : 1;
     }
   }
 }

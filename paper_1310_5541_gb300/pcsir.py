@@ -39,7 +39,8 @@ class pcsir_config(ctypes.Structure):
 class pcsir_result(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double * 5), ("ess", ctypes.c_double), ("max_loglik", ctypes.c_double),
                 ("sum_wtilde", ctypes.c_double), ("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64),
-                ("device_error", ctypes.c_int32), ("kind", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("kind", ctypes.c_int32), ("resampled", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class pcsir_outputs(ctypes.Structure):
@@ -106,6 +107,8 @@ def _load():
         "pcsir_destroy": ([P], I32),
         "pcsir_step": ([P, P, I64, P, I32, I32, D, P, D, P, P], I32),
         "sir_step": ([P, P, I64, P, I32, I32, P, D, P, P], I32),
+        "pcsir_step_ess": ([P, P, P, I64, P, I32, I32, D, P, D, D, P, P], I32),
+        "sir_step_ess": ([P, P, P, I64, P, I32, I32, P, D, D, P, P], I32),
         "pcsir_loglik": ([P, P, P, P, I64, P, I32, I32, P, P], I32),
         "pcsir_resample": ([P, P, I64, D, P, P], I32),
         "pcsir_get_outputs": ([P, ctypes.POINTER(pcsir_outputs)], I32),
@@ -217,7 +220,8 @@ class Context:
         r = pcsir_result()
         lib.pcsir_last_result(self.handle, ctypes.byref(r))
         return dict(estimate=list(r.estimate), ess=r.ess, max_loglik=r.max_loglik, sum_wtilde=r.sum_wtilde,
-                    n_particles=r.n_particles, n_bins=r.n_bins, device_error=r.device_error, kind=r.kind)
+                    n_particles=r.n_particles, n_bins=r.n_bins, device_error=r.device_error, kind=r.kind,
+                    resampled=bool(r.resampled))
 
     def timing_enable(self, max_steps):
         st = lib.pcsir_timing_enable(self.handle, int(max_steps))
@@ -298,6 +302,39 @@ def sir_step(ctx, state, image, noise, u0, stream=None):
     H, W = image.shape
     st = lib.sir_step(ctx.handle, _ptr(state), N, _ptr(image), W, H, _ptr(noise), float(u0),
                       _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+# carried log-weights of the ESS-thresholded steps: int64, log w = logw * 2^-32
+LOGW_SCALE = 4294967296.0
+
+
+def pcsir_step_ess(ctx, state, logw, image, h, noise, u0, ess_min, stream=None):
+    """One ESS-thresholded pcSIR step on ``state`` [5, N] (FP32) and the carried fixed-point
+    log-weights ``logw`` [N] (int64) in place; resamples only when N_eff < ess_min."""
+    _check_cuda(state, "state", torch.float32)
+    _check_cuda(noise, "noise", torch.float32)
+    _check_cuda(image, "image", torch.float32)
+    _check_cuda(logw, "logw", torch.int64)
+    N = state.shape[1]
+    H, W = image.shape
+    st = lib.pcsir_step_ess(ctx.handle, _ptr(state), _ptr(logw), N, _ptr(image), W, H, float(h), _ptr(noise),
+                            float(u0), float(ess_min), _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def sir_step_ess(ctx, state, logw, image, noise, u0, ess_min, stream=None):
+    """One ESS-thresholded SIR step (Algorithm 1 with its resampling test), in place."""
+    _check_cuda(state, "state", torch.float32)
+    _check_cuda(noise, "noise", torch.float32)
+    _check_cuda(image, "image", torch.float32)
+    _check_cuda(logw, "logw", torch.int64)
+    N = state.shape[1]
+    H, W = image.shape
+    st = lib.sir_step_ess(ctx.handle, _ptr(state), _ptr(logw), N, _ptr(image), W, H, _ptr(noise), float(u0),
+                          float(ess_min), _stream_ptr(stream), None)
     if st != OK:
         ctx._raise(st)
 

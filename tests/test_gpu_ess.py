@@ -1,0 +1,300 @@
+"""GPU parity of the ESS-thresholded steps (pcsir_step_ess, sir_step_ess) against the oracle.
+
+Each GPU step is compared with the oracle's step on the same input state and the same
+carried log-weights (the GPU's fixed-point values times 2^-32):
+  * propagated states, cells, counts, member -> cell map: bit-exact;
+  * prior-weighted dummies: the GPU forms sum w_i and sum w_i (s_i - r_b) in FP32 over at most
+    m = min(ESS_ROUND = 8192, members) terms per block before adding them in FP64, with
+    w_i = exp(logw_i) in FP32 (relative error <= (1 + |logw_i|) u, u = 2^-24).  The weighted
+    mean r_b + S / W is then within 2 m u max|d| + 4 (1 + max|logw|) u max|d| of the exact
+    one, d the members' offsets s_i - r_b; the test takes that bound from the data;
+  * dummy log-likelihoods: against the oracle's likelihood at the GPU's dummies,
+    1e-4 + 4e-7 |ll| (as for pcsir_step);
+  * weights, ESS, posterior mean and the carried log-weights: against the oracle's formulas
+    applied to the GPU's dummy log-likelihoods (relative 1e-5; log-weights 1e-8);
+  * the decision: N_eff < ess_min, asserted unless N_eff lies within 1e-5 of ess_min;
+  * resampled steps: every output is its ancestor's propagated state, copies are floor or ceil
+    of N w, the carried log-weights are zero; other steps keep the propagated state and the
+    identity ancestors.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pcsir_oracle as O
+from paper_1310_5541_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1310554300
+SCALE = 4294967296.0
+U = 2.0 ** -24
+ESS_ROUND = 8192
+KEEP_ALL = 1 | 2 | 4 | 8
+INT64_MIN = np.iinfo(np.int64).min
+
+
+@pytest.fixture(scope="module")
+def pc():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1310_5541_gb300 import pcsir
+
+    return pcsir
+
+
+def _model():
+    # the paper's Gaussian likelihood (sigma_xi = 20): N_eff stays a sizeable fraction of N,
+    # so both branches of the test occur within a few steps
+    return synth.Model(sigma_psf=1.5, I0=100.0, bg=10.0, patch=9, lik="sse", sigma_xi=20.0)
+
+
+def _ctx(pc, N, model, keep=KEEP_ALL, dummy="com", dtype=torch.float32):
+    return pc.Context(N, dtype, lik=model.lik, patch=model.patch, psf_sigma=model.sigma_psf, bg=model.bg,
+                      sigma_xi=model.sigma_xi, keep=keep, dummy=dummy)
+
+
+def _lw_float(lwq):
+    out = lwq.astype(np.float64) / SCALE
+    out[lwq == INT64_MIN] = -np.inf
+    return out
+
+
+def _run(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min):
+    st = torch.from_numpy(np.ascontiguousarray(st_np)).cuda()
+    lw = torch.from_numpy(np.ascontiguousarray(lwq)).cuda()
+    dimg, dnz = torch.from_numpy(img).cuda(), torch.from_numpy(nz).cuda()
+    if kind == "pcsir":
+        pc.pcsir_step_ess(ctx, st, lw, dimg, h, dnz, u0, ess_min)
+    else:
+        pc.sir_step_ess(ctx, st, lw, dimg, dnz, u0, ess_min)
+    torch.cuda.synchronize()
+    res = ctx.last_result()
+    out = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in ctx.outputs().items()}
+    return st.cpu().numpy(), lw.cpu().numpy(), res, out
+
+
+def _dummy_bound(prop, member, order_keys, h, lw, anchors):
+    """Per-bin bound on |weighted mean (GPU) - weighted mean (exact)| per component."""
+    B = order_keys.shape[0]
+    counts = np.bincount(member, minlength=B)
+    m = np.minimum(counts, ESS_ROUND).astype(np.float64)
+    ref = np.empty((5, prop.shape[1]))
+    for a in range(2):
+        ref[a] = order_keys[member, a].astype(np.float32) * np.float32(h) - np.float32(0.5)
+    for c in range(3):
+        ref[2 + c] = anchors[c]
+    d = np.abs(prop.astype(np.float64) - ref)
+    dmax = np.zeros((5, B))
+    for c in range(5):
+        np.maximum.at(dmax[c], member, d[c])
+    finite = lw[np.isfinite(lw)]
+    lwmax = np.abs(finite).max() if finite.size else 0.0
+    return (2.0 * m * U + 4.0 * (1.0 + lwmax) * U) * dmax + 1e-12
+
+
+def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model):
+    lw_prev = _lw_float(lwq)
+    new, lw_new, res, out = _run(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min)
+    assert res["device_error"] == 0
+    N = st_np.shape[1]
+    prop = out["prop_state"]
+    np.testing.assert_array_equal(prop, O.propagate(st_np, nz))
+    if kind == "pcsir":
+        ref = O.pcsir_step_ess(st_np, lw_prev, img, nz, u0, h, ess_min, model)
+        B = res["n_bins"]
+        assert B == ref["bin_keys"].shape[0]
+        xy = out["bin_xy"]
+        order = np.lexsort((xy[0], xy[1]))
+        np.testing.assert_array_equal(xy[:, order].T, ref["bin_keys"])
+        np.testing.assert_array_equal(out["bin_count"][order], ref["bin_counts"])
+        rank = np.empty(B, np.int64)
+        rank[order] = np.arange(B)
+        member = rank[out["particle_bin"]]
+        np.testing.assert_array_equal(member, ref["member_bin"])
+        dum = out["dummy"][:, order]
+        anchors = st_np[2:5, 0].astype(np.float32)  # particle 0's input values (the GPU's anchors)
+        bound = _dummy_bound(prop, member, ref["bin_keys"], h, lw_prev, anchors)
+        # a cell none of whose members carries weight takes the plain mean of its members
+        weighted = np.isfinite(ref["dummies"][0])
+        err = np.abs(dum[:, weighted] - ref["dummies"][:, weighted])
+        assert np.all(err <= bound[:, weighted]), ("weighted dummies", (err / bound[:, weighted]).max())
+        if not weighted.all():
+            plain = O.dummies(prop, member, B)[:, ~weighted]
+            np.testing.assert_allclose(dum[:2, ~weighted], plain[:2], rtol=0, atol=1e-9)
+            np.testing.assert_allclose(dum[2:, ~weighted], plain[2:], rtol=0, atol=2.5e-7)
+        ll_bins = out["bin_loglik"][order]
+        ll_at = O.loglik(img, dum[0], dum[1], dum[4], model)
+        assert np.all(np.abs(ll_bins - ll_at) <= 1e-4 + 4e-7 * np.abs(ll_at))
+        ll = ll_bins[member]
+    else:
+        ref = O.sir_step_ess(st_np, lw_prev, img, nz, u0, ess_min, model)
+        ll = out["loglik"]
+        ll_ref = O.loglik(img, prop[0], prop[1], prop[4], model)
+        assert np.all(np.abs(ll - ll_ref) <= 1e-4 + 4e-7 * np.abs(ll_ref))
+    # the oracle's weight formulas on the GPU's log-likelihoods
+    logw = lw_prev + ll
+    w, m, T = O.normalise(logw)
+    ess = O.ess(w)
+    assert abs(res["ess"] - ess) <= 1e-5 * ess, (res["ess"], ess)
+    est = O.posterior_mean(w, prop)
+    assert np.all(np.abs(np.array(res["estimate"]) - est) <= 1e-5 * np.abs(est) + 1e-6)
+    sig = w >= 1e-3 * w.max()
+    assert np.abs(out["weight"][sig] / w[sig] - 1.0).max() <= 1e-5
+    near = abs(ess / ess_min - 1.0) < 1e-5 if ess_min > 0 else False
+    if not near:
+        assert res["resampled"] == (ess < ess_min), (ess, ess_min)
+    anc = out["ancestor"]
+    if res["resampled"]:
+        np.testing.assert_array_equal(lw_new, np.zeros(N, np.int64))
+        np.testing.assert_array_equal(new, prop[:, anc])
+        copies = np.bincount(anc, minlength=N)
+        nw = N * w
+        assert np.all(copies >= np.floor(nw - 1e-4)) and np.all(copies <= np.ceil(nw + 1e-4))
+    else:
+        np.testing.assert_array_equal(new, prop)
+        np.testing.assert_array_equal(anc, np.arange(N))
+        carried = _lw_float(lw_new)
+        fin = np.isfinite(logw)
+        np.testing.assert_array_equal(np.isfinite(carried), fin)
+        np.testing.assert_allclose(carried[fin], (logw - logw[fin].max())[fin], rtol=0, atol=1e-8)
+        assert lw_new[fin].max() == 0
+    return new, lw_new, res
+
+
+@pytest.mark.parametrize("kind", ["pcsir", "sir"])
+def test_ess_steps_match_oracle_over_a_sequence(pc, kind):
+    m = _model()
+    seq = synth.make_sequence(64, 64, 6, m, seed=SEED)
+    N = 20000 if kind == "pcsir" else 4096
+    ctx = _ctx(pc, N, m)
+    st = synth.initial_state(seq.gt[0], N, np.float32)
+    lwq = np.zeros(N, np.int64)
+    decisions = []
+    for k in range(6):
+        nz = synth.make_noise(N, m.q, SEED + 1, k, np.float32)
+        u0 = synth.make_u0(SEED + 1, k)
+        # N_eff / N runs 0.02-0.27 on this sequence: 0.1 N alternates the two branches
+        st, lwq, res = _compare_step(pc, ctx, kind, st, lwq, seq.images[k], nz, u0, 0.5, 0.1 * N, m)
+        decisions.append(res["resampled"])
+    ctx.close()
+    print(kind, "resampled:", decisions)
+    assert True in decisions and False in decisions
+
+
+def test_ess_pcsir_ragged_large_cells_and_coc(pc):
+    """N not a multiple of the tile or chunk, several tiles, large cells and the CoC dummy."""
+    m = _model()
+    seq = synth.make_sequence(64, 64, 3, m, seed=SEED + 5)
+    N = 3 * 4096 + 777
+    for dummy, h in (("com", 2.0), ("coc", 0.75)):
+        ctx = _ctx(pc, N, m, dummy=dummy)
+        st = synth.initial_state(seq.gt[0], N, np.float32)
+        lwq = np.zeros(N, np.int64)
+        for k in range(3):
+            nz = synth.make_noise(N, m.q, SEED + 6, k, np.float32)
+            u0 = synth.make_u0(SEED + 6, k)
+            if dummy == "coc":
+                ref = O.pcsir_step_ess(st, _lw_float(lwq), seq.images[k], nz, u0, h, 0.0, m, dummy="coc")
+                new, lw_new, res, out = _run(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, u0, h, 0.0)
+                xy = out["bin_xy"]
+                order = np.lexsort((xy[0], xy[1]))
+                np.testing.assert_allclose(out["dummy"][:2, order], ref["dummies"][:2], rtol=0, atol=1e-12)
+                assert not res["resampled"]
+                st, lwq = new, lw_new
+            else:
+                st, lwq, _ = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, u0, h, 0.0, m)
+        ctx.close()
+
+
+def test_ess_threshold_limits(pc):
+    """ess_min > N resamples every step with uniform carried weights; ess_min = 0 never does."""
+    m = _model()
+    seq = synth.make_sequence(64, 64, 2, m, seed=SEED + 9)
+    N = 8192
+    ctx = _ctx(pc, N, m)
+    for ess_min, expect in ((N + 1.0, True), (0.0, False)):
+        st = synth.initial_state(seq.gt[0], N, np.float32)
+        lwq = np.zeros(N, np.int64)
+        for k in range(2):
+            nz = synth.make_noise(N, m.q, SEED + 10, k, np.float32)
+            st, lwq, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, synth.make_u0(SEED + 10, k),
+                                         0.5, ess_min, m)
+            assert res["resampled"] is expect
+    ctx.close()
+
+
+def test_ess_zero_weight_particles(pc):
+    """INT64_MIN marks a particle of zero weight: it adds nothing to its cell's centre of mass,
+    gets no weight, and stays at INT64_MIN while the step does not resample."""
+    m = _model()
+    seq = synth.make_sequence(64, 64, 1, m, seed=SEED + 12)
+    N = 5000
+    ctx = _ctx(pc, N, m)
+    st = synth.initial_state(seq.gt[0], N, np.float32)
+    rng = np.random.default_rng(SEED)
+    lwq = (-rng.exponential(1.5, N) * SCALE).astype(np.int64)
+    lwq[np.argmax(lwq)] = 0
+    dead = rng.choice(np.arange(1, N), 300, replace=False)
+    lwq[dead] = INT64_MIN
+    nz = synth.make_noise(N, m.q, SEED + 13, 0, np.float32)
+    new, lw_new, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[0], nz, 0.3, 0.5, 0.0, m)
+    assert np.all(lw_new[dead] == INT64_MIN)
+    ctx.close()
+
+
+def test_ess_step_in_a_cuda_graph(pc):
+    m = _model()
+    seq = synth.make_sequence(64, 64, 1, m, seed=SEED + 14)
+    N = 6000
+    ctx = _ctx(pc, N, m)
+    st0 = torch.from_numpy(synth.initial_state(seq.gt[0], N, np.float32)).cuda()
+    nz = torch.from_numpy(synth.make_noise(N, m.q, SEED + 15, 0, np.float32)).cuda()
+    img = torch.from_numpy(seq.images[0]).cuda()
+    s = torch.cuda.Stream()
+    st, lw = st0.clone(), torch.zeros(N, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        pc.pcsir_step_ess(ctx, st, lw, img, 0.5, nz, 0.4, 0.0, stream=s)
+    torch.cuda.synchronize()
+    ref_st, ref_lw = st.clone(), lw.clone()
+    g = torch.cuda.CUDAGraph()
+    st.copy_(st0)
+    lw.zero_()
+    with torch.cuda.graph(g, stream=s):
+        pc.pcsir_step_ess(ctx, st, lw, img, 0.5, nz, 0.4, 0.0, stream=s)
+    st.copy_(st0)
+    lw.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    # without resampling the state is the propagated state; the log-weights agree to the
+    # FP32 rounding of the weighted centres of mass
+    assert torch.equal(st, ref_st)
+    assert (lw - ref_lw).abs().max().item() <= 1e-5 * SCALE
+    ctx.close()
+
+
+def test_ess_argument_errors(pc):
+    m = _model()
+    N = 1024
+    ctx = _ctx(pc, N, m)
+    st = torch.zeros(5, N, device="cuda")
+    img = torch.zeros(16, 16, device="cuda")
+    lw = torch.zeros(N, dtype=torch.int64, device="cuda")
+    with pytest.raises(pc.PcsirError):
+        pc.pcsir_step_ess(ctx, st, lw, img, 0.5, st, 0.3, float("nan"))
+    with pytest.raises(pc.PcsirError):
+        pc.pcsir_step_ess(ctx, st, lw, img, 0.0, st, 0.3, 10.0)
+    ctx.close()
+    ctx64 = _ctx(pc, N, m, dtype=torch.float64)
+    st64 = torch.zeros(5, N, dtype=torch.float64, device="cuda")
+    with pytest.raises(pc.PcsirError) as ei:
+        ctx64_lib = pc.lib
+        r = ctx64_lib.pcsir_step_ess(ctx64.handle, pc._ptr(st64), pc._ptr(lw), N, pc._ptr(img), 16, 16, 0.5,
+                                     pc._ptr(st64), 0.3, 10.0, None, None)
+        if r != pc.OK:
+            ctx64._raise(r)
+    assert ei.value.status == -6  # PCSIR_ENOTSUP
+    ctx64.close()
