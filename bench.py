@@ -365,6 +365,58 @@ def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_ca
     return out
 
 
+def run_ess(N, n_frames, frac, seed):
+    """ESS-thresholded pcSIR (Algorithm 2 with Algorithm 1's test: resample only when
+    N_eff < frac N, weights carried otherwise) against pcSIR resampling every step, on the
+    single-target workload (512 x 512, Poisson, 21 x 21 patch, h = 0.5 px) with the same
+    sequence, noise and uniforms; per method the device time per step (CUDA events), the
+    tracking RMSE and the fraction of steps that resampled."""
+    import numpy as np
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    model = synth.Model(sigma_psf=SIGMA, I0=I0, bg=BG, patch=PATCH, q=Q)
+    seq = synth.make_sequence(W_IMG, H_IMG, n_frames, model, seed)
+    imgs = torch.from_numpy(seq.images).to(dev)
+    pool = [torch.from_numpy(synth.make_noise(N, Q, seed + 3, j, np.float32)).to(dev) for j in range(NOISE_POOL)]
+    ctx = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG, keep=0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name in ("pcsir", "pcsir-ess"):
+        st = torch.from_numpy(synth.initial_state(seq.gt[0], N, np.float32)).to(dev)
+        lw = torch.zeros(N, dtype=torch.int64, device=dev)
+        ms, ms_res, ms_keep, errs, ess = [], [], [], [], []
+        for k in range(n_frames):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u0 = synth.make_u0(seed + 5, k)
+            a.record(stream)
+            if name == "pcsir":
+                pcsir.pcsir_step(ctx, st, imgs[k], H_DEFAULT, pool[k % NOISE_POOL], u0, stream)
+            else:
+                pcsir.pcsir_step_ess(ctx, st, lw, imgs[k], H_DEFAULT, pool[k % NOISE_POOL], u0, frac * N, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            r = ctx.last_result()
+            if k >= 2:
+                t = a.elapsed_time(b)
+                ms.append(t)
+                (ms_res if r["resampled"] else ms_keep).append(t)
+            errs.append(np.array(r["estimate"][:2]) - seq.gt[k + 1, :2])
+            ess.append(r["ess"] / N)
+        e = np.array(errs)
+        rows.append({"method": name, "ms_per_step": float(np.mean(ms)), "value": N / (np.mean(ms) / 1e3),
+                     "unit": UNIT, "rmse_px": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1)))),
+                     "resampled_fraction": len(ms_res) / max(1, len(ms)),
+                     "ms_resampled_steps": float(np.mean(ms_res)) if ms_res else None,
+                     "ms_carried_steps": float(np.mean(ms_keep)) if ms_keep else None,
+                     "mean_ess_fraction": float(np.mean(ess))})
+    ctx.close()
+    return {"workload": "ESS-thresholded pcSIR (N_thr = %.2f N) vs every-step pcSIR, N=%d, 512x512, 21x21, h=%.2f"
+                        % (frac, N, H_DEFAULT), "frames": n_frames, "rows": rows}
+
+
 def run_large_object(counts, n_frames, seed):
     """The paper's large-object regime (Section 5.3): 512 x 512 frames, PSF sigma 13 px, SNR 2, speed
     U[2, 7] px/frame, Gaussian (SSE) likelihood over a 65 x 65 kernel.  SIR, pcSIR-1x1 (h = 1) and
@@ -484,6 +536,8 @@ def main():
     ap.add_argument("--large-frames", type=int, default=50, help="frames of the large-object comparison "
                     "(Section 5.3; 0 skips it)")
     ap.add_argument("--frames-3d", type=int, default=20, help="frames of the 3D comparison (0 skips it)")
+    ap.add_argument("--ess-frames", type=int, default=20, help="frames of the ESS-threshold comparison (0 skips it)")
+    ap.add_argument("--ess-frac", type=float, default=0.5, help="N_thr / N of the ESS-threshold comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -523,7 +577,9 @@ def main():
     state = state0.clone()
     ctx = pcsir.Context(N, torch.float32, patch=PATCH, psf_sigma=SIGMA, bg=BG, keep=0)
     stream = torch.cuda.current_stream()
-    res_host = torch.zeros((n_frames, 11), dtype=torch.float64).pin_memory()  # 88-byte pcsir_result each
+    res_bytes = pcsir.ctypes.sizeof(pcsir.pcsir_result)
+    assert res_bytes % 8 == 0
+    res_host = torch.zeros((n_frames, res_bytes // 8), dtype=torch.float64).pin_memory()  # one pcsir_result each
 
     def step(k, st):
         r = pcsir.lib.pcsir_step(ctx.handle, pcsir._ptr(st), N, pcsir._ptr(images[k]), W_IMG, H_IMG, float(h),
@@ -558,7 +614,7 @@ def main():
         pg.barrier()
     res = np.frombuffer(res_host.numpy().tobytes(), dtype=np.dtype([
         ("est", "f8", 5), ("ess", "f8"), ("maxll", "f8"), ("sumw", "f8"), ("n", "i8"), ("nb", "i8"),
-        ("err", "i4"), ("kind", "i4")]))
+        ("err", "i4"), ("kind", "i4"), ("resampled", "i4"), ("reserved", "i4")]))
     timed = res[Wm:Wm + K]
     derr = int(np.bitwise_or.reduce(timed["err"]))
     est = timed["est"][:, :2]
@@ -599,7 +655,7 @@ def main():
         pcsir.lib.pcsir_last_result(ctx.handle, pcsir.ctypes.byref(res1))
     e2e_s = time.perf_counter() - t0
     e2e = {"value": N * K_e2e * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": 88}
+           "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": res_bytes}
 
     # plain SIR on the same workload (the comparison path; likelihood for every particle)
     sir = None
@@ -640,6 +696,10 @@ def main():
     if args.large_frames > 0:
         large = run_large_object((12800, 1 << 17, 1 << 20), args.large_frames, SEED + 53 + 1000 * rank)
 
+    ess_cmp = None
+    if args.ess_frames > 0:
+        ess_cmp = run_ess(N, args.ess_frames, args.ess_frac, SEED + 71 + 1000 * rank)
+
     track3d = None
     if args.frames_3d > 0:
         track3d = run_3d((200_000, 1 << 22), args.frames_3d, SEED + 61 + 1000 * rank)
@@ -666,7 +726,7 @@ def main():
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
-            "large_object": large, "tracking_3d": track3d,
+            "large_object": large, "tracking_3d": track3d, "ess_threshold": ess_cmp,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP * K, "rmse_px": rmse, "mean_bins": float(timed["nb"].mean()),
