@@ -298,7 +298,7 @@ pcsir_status pcsir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t 
   if (e == cudaSuccess) e = launch_pcsir_ess_front(b, ctx->m, lw_in, image, W, H, N, h, ctx->num_sms, s);
   if (e == cudaSuccess) e = launch_particle_weights(b, PCSIR_F32, N, ctx->num_sms, 2, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels (ESS)");
-  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_PARTICLES, ctx->cfg.keep, ctx->num_sms, s);
+  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_Q, ctx->cfg.keep, ctx->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
   return finish_step(ctx, s, result_host, 1, N);
 }
@@ -321,7 +321,7 @@ pcsir_status sir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N,
   if (e == cudaSuccess) e = launch_sir_ess_front(b, reinterpret_cast<const long long*>(logw), N, ctx->num_sms, s);
   if (e == cudaSuccess) e = launch_particle_weights(b, PCSIR_F32, N, ctx->num_sms, 0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "SIR front kernels (ESS)");
-  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_PARTICLES, ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN,
+  e = launch_resample(b, PCSIR_F32, state, N, u0, WSRC_Q, ctx->cfg.keep & ~PCSIR_KEEP_PARTICLE_BIN,
                       ctx->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
   return finish_step(ctx, s, result_host, 0, N);

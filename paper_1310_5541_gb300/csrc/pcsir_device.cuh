@@ -463,9 +463,29 @@ __device__ __forceinline__ df wtilde_q(long long llq, long long mq) {
   if (d > 0) d = 0;
   return df_exp_neg(fix32_to_df(d));
 }
+// float -> int64 rounded to nearest, ties to even (the result of __float2ll_rn for |v| < 2^62),
+// by integer instructions: the 64-bit conversion instruction runs on this GPU's slow FP64 pipe
+__device__ __forceinline__ long long f2ll_rn_int(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;  // zero or subnormal: |v| < 2^-126
+  const unsigned m = (b & 0x7fffffu) | 0x800000u;
+  const int sh = e - 150;  // |v| = m 2^sh
+  unsigned long long r;
+  if (sh >= 0) {
+    r = (unsigned long long)m << (sh < 39 ? sh : 39);
+  } else if (sh < -24) {
+    r = 0ull;  // |v| < 1/2
+  } else {
+    const int k = -sh;
+    const unsigned q = m >> k, rem = m & ((1u << k) - 1u), half = 1u << (k - 1);
+    r = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+  }
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
 __device__ __forceinline__ long long q_of_wtilde(df w, int sq) {
   const float scale = __int_as_float((127 + sq) << 23);  // 2^sq, exact
-  return __float2ll_rn(__fmul_rn(w.hi, scale)) + __float2ll_rn(__fmul_rn(w.lo, scale));
+  return f2ll_rn_int(__fmul_rn(w.hi, scale)) + f2ll_rn_int(__fmul_rn(w.lo, scale));
 }
 
 // Atomic OR of an error flag into the control block.

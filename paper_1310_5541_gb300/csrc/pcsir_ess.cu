@@ -81,26 +81,38 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
   const int64_t hi = lo + per < N ? lo + per : N;
   for (int64_t r0 = lo; r0 < hi; r0 += ESS_ROUND) {
     const int64_t r1 = r0 + ESS_ROUND < hi ? r0 + ESS_ROUND : hi;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      const unsigned g = b.pslot[i];
-      const unsigned bi = b.hrank[g];
-      if (bi >= B) continue;  // only after a failed cell insertion (PCSIR_DERR_RANGE is set)
-      const unsigned long long key = b.hkey[g];
-      const long long l = lw[i];
-      const float w = l == LLQ_NONE ? 0.0f : expf(lw_to_float(l));
-      float d[5];
-      d[0] = prop[i] - cell_ref(key_bx(key), h);
-      d[1] = prop[N + i] - cell_ref(key_by(key), h);
+    // four particles per thread and pass, their loads and gathers issued before the atomics
+    for (int64_t i0 = r0 + threadIdx.x; i0 < r1; i0 += 4 * (int64_t)blockDim.x) {
+      unsigned bi[4];
+      float w[4], d[4][5];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) d[2 + c] = prop[(2 + c) * N + i] - anc[c];
-      if (local) {
-        atomicAdd(&acc[0][bi], w);
+      for (int k = 0; k < 4; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        bi[k] = 0xffffffffu;
+        w[k] = 0.0f;
+        if (i >= r1) continue;
+        const unsigned g = b.pslot[i];
+        bi[k] = b.hrank[g];
+        const unsigned long long key = b.hkey[g];
+        const long long l = lw[i];
+        w[k] = l == LLQ_NONE ? 0.0f : expf(lw_to_float(l));
+        d[k][0] = prop[i] - cell_ref(key_bx(key), h);
+        d[k][1] = prop[N + i] - cell_ref(key_by(key), h);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) atomicAdd(&acc[1 + c][bi], w * d[c]);
-      } else {
-        atomicAdd(&b.bin_ll[bi], (double)w);
+        for (int c = 0; c < 3; ++c) d[k][2 + c] = prop[(2 + c) * N + i] - anc[c];
+      }
 #pragma unroll
-        for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + bi], (double)(w * d[c]));
+      for (int k = 0; k < 4; ++k) {
+        if (bi[k] >= B) continue;  // past the range, or after a failed cell insertion (PCSIR_DERR_RANGE)
+        if (local) {
+          atomicAdd(&acc[0][bi[k]], w[k]);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) atomicAdd(&acc[1 + c][bi[k]], w[k] * d[k][c]);
+        } else {
+          atomicAdd(&b.bin_ll[bi[k]], (double)w[k]);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + bi[k]], (double)(w[k] * d[k][c]));
+        }
       }
     }
     if (local) {

@@ -170,7 +170,9 @@ cudaError_t launch_loglik(const ModelParams& m, const double* x, const double* y
                           int64_t n, const float* img, int W, int H, double* out, int num_sms,
                           cudaStream_t s);
 
-// resampling weight sources
-enum { WSRC_BINS = 0, WSRC_PARTICLES = 1, WSRC_LOGW = 2 };
+// resampling weight sources: per-cell integer weights (pcSIR), per-particle fixed-point
+// log-likelihoods (SIR), caller log-weights, or per-particle integer weights already formed by
+// the weight reduction into b.hq (ESS-thresholded steps; b.llq still holds the log-weights)
+enum { WSRC_BINS = 0, WSRC_PARTICLES = 1, WSRC_LOGW = 2, WSRC_Q = 3 };
 
 }  // namespace pcsir

@@ -658,7 +658,7 @@ __device__ __forceinline__ long long particle_llq(const double* __restrict__ lw,
 
 template <typename T, typename SRC>
 __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC* __restrict__ lls, int64_t N,
-                                                       int sq, int with_est, int kind) {
+                                                       int sq, int with_est, int kind, long long* __restrict__ qout) {
   const unsigned long long me = b.ctl->max_llq;
   const long long mq = llq_dec(me);
   const T* __restrict__ prop = static_cast<const T*>(b.prop);
@@ -668,7 +668,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
     const df wd = me == 0ull ? df{0.0f, 0.0f} : wtilde_q(particle_llq(lls, i), mq);
     const float wt = wd.hi;
-    tint += q_of_wtilde(wd, sq);
+    const long long q = q_of_wtilde(wd, sq);
+    tint += q;
+    if (qout) qout[i] = q;  // the resampling reads the integer weights instead of forming them again
     kt.add(wt);
     k2.add(wt * wt);
     if (with_est) {
@@ -836,14 +838,14 @@ cudaError_t launch_sir_front(const StepBuffers& b, const ModelParams& m, int dty
                                                              keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    if (with_weights) k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0);
+    if (with_weights) k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0, nullptr);
   } else {
     k_sir_prop_lik<double><<<(unsigned)nb, SL_THREADS, 0, s>>>(b, static_cast<const double*>(state),
                                                               static_cast<const double*>(noise), N, lp, img, W, H,
                                                               keep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
-    if (with_weights) k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0);
+    if (with_weights) k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, 0, nullptr);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || (e = mark(se, 2, s)) != cudaSuccess) return e;
@@ -855,7 +857,7 @@ cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t 
   k_logw_max<<<rgrid, RED_THREADS, 0, s>>>(b, logw, N);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sir_w<float, double><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0, 0);
+  k_sir_w<float, double><<<rgrid, RED_THREADS, 0, s>>>(b, logw, N, weight_scale_bits(N), 0, 0, nullptr);
   return cudaGetLastError();
 }
 
@@ -870,10 +872,11 @@ cudaError_t launch_particle_weights(const StepBuffers& b, int dtype, int64_t N, 
                                     cudaStream_t s) {
   const int rgrid = (int)std::min<int64_t>((N + RED_THREADS - 1) / RED_THREADS, (int64_t)num_sms * 4);
   const int sq = weight_scale_bits(N);
+  // the per-particle integer weights go to b.hq (capacity >= 2 N), read by WSRC_Q resampling
   if (dtype == PCSIR_F32)
-    k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind);
+    k_sir_w<float, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind, b.hq);
   else
-    k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind);
+    k_sir_w<double, long long><<<rgrid, RED_THREADS, 0, s>>>(b, b.llq, N, sq, 1, kind, b.hq);
   return cudaGetLastError();
 }
 

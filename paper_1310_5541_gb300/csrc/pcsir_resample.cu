@@ -16,6 +16,7 @@
 // within each tile and writes the tile's outputs.  No block ever waits for
 // another.
 #include <cmath>
+#include <type_traits>
 
 #include "pcsir_device.cuh"
 
@@ -84,7 +85,7 @@ __device__ __forceinline__ int clamp_item(int a, int cnt) { return a < 0 ? 0 : (
 // particle's log-weight.  Particles past the end weigh 0.
 template <int WSRC>
 __device__ __forceinline__ long long src_llq(const StepBuffers& b, const double* __restrict__ lsrc, int64_t i) {
-  return WSRC == WSRC_LOGW ? llq_of(lsrc[i]) : b.llq[i];
+  return WSRC == WSRC_LOGW ? llq_of(lsrc[i]) : b.llq[i];  // WSRC_PARTICLES, WSRC_Q
 }
 
 template <int WSRC>
@@ -110,6 +111,23 @@ __device__ __forceinline__ void tile_weights(const StepBuffers& b, const double*
     }
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) q[k] = g[k] != 0xffffffffu ? b.hq[g[k]] : 0ll;
+  } else if (WSRC == WSRC_Q) {
+    // 16-byte loads of four consecutive integer weights (tile starts are 32-byte aligned)
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+      const int j0 = k * (4 * SCAN_THREADS) + 4 * tid;
+      if (j0 + 4 <= cnt) {
+        const longlong2 a = *reinterpret_cast<const longlong2*>(b.hq + base + j0);
+        const longlong2 c = *reinterpret_cast<const longlong2*>(b.hq + base + j0 + 2);
+        q[4 * k] = a.x;
+        q[4 * k + 1] = a.y;
+        q[4 * k + 2] = c.x;
+        q[4 * k + 3] = c.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q[4 * k + e] = (j0 + e < cnt) ? b.hq[base + j0 + e] : 0ll;
+      }
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
@@ -400,6 +418,7 @@ cudaError_t prepare_resample() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_BINS>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_PARTICLES>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<double, WSRC_LOGW>, a, (int)RS_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_Q>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_BINS, 7>, a, (int)RS_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resample<float, WSRC_PARTICLES, 7>, a, (int)RS_SMEM);
   return e;
@@ -421,6 +440,13 @@ static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, voi
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, o, N, sq, keep);
+  } else if (mode == WSRC_Q) {
+    if (!std::is_same<T, float>::value) return cudaErrorInvalidValue;  // FP32 state only
+    k_tile_sums<WSRC_Q><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resample<float, WSRC_Q><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, reinterpret_cast<float*>(o), N, sq,
+                                                                   keep);
   } else {
     k_tile_sums<WSRC_LOGW><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
     cudaError_t e = cudaGetLastError();
