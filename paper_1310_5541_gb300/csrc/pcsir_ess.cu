@@ -32,6 +32,7 @@ LikParams make_lik(const ModelParams& m);  // pcsir_kernels.cu
 
 constexpr int ESS_THREADS = 256;
 constexpr int ESS_SMEM_BINS = 2048;  // bins whose sums a block keeps in shared memory
+constexpr int ESS_WARP_BINS = 256;   // up to this many bins, each warp keeps its own copy
 constexpr int ESS_ROUND = 8192;      // particles per shared-memory round of a block
 constexpr int ESS_BIN_WARPS = ESS_THREADS / 32;
 constexpr int ESS_MAXP = 127;        // largest patch side
@@ -61,18 +62,23 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_rank(StepBuffers b) {
 
 __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const long long* __restrict__ lw,
                                                            int64_t N, float h) {
-  __shared__ float acc[6][ESS_SMEM_BINS];
+  // sums in shared memory: with few cells (B <= ESS_WARP_BINS) one copy per warp, so that only the
+  // lanes of one warp meet on an address; else one copy per block (B <= ESS_SMEM_BINS); else the
+  // FP64 per-bin sums in global memory directly
+  __shared__ float acc[6 * ESS_SMEM_BINS];
   const unsigned B = b.ctl->nocc;
+  const bool per_warp = B <= (unsigned)ESS_WARP_BINS;
   const bool local = B <= (unsigned)ESS_SMEM_BINS;
+  const unsigned nslots = per_warp ? (unsigned)(ESS_THREADS / 32 * 6 * ESS_WARP_BINS) : 6u * B;
+  const unsigned stride = per_warp ? (unsigned)ESS_WARP_BINS : B;  // between the six sums of a copy
+  float* mine = per_warp ? acc + (threadIdx.x >> 5) * 6 * ESS_WARP_BINS : acc;
   const float* __restrict__ prop = static_cast<const float*>(b.prop);
   const int64_t bs = b.bin_stride;
   float anc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) anc[c] = anchor_f(b.ctl, c);
   if (local) {
-    for (unsigned j = threadIdx.x; j < B; j += blockDim.x)
-#pragma unroll
-      for (int a = 0; a < 6; ++a) acc[a][j] = 0.0f;
+    for (unsigned j = threadIdx.x; j < nslots; j += blockDim.x) acc[j] = 0.0f;
   }
   __syncthreads();
   // a contiguous range of particles per block, in rounds of ESS_ROUND
@@ -105,9 +111,9 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
       for (int k = 0; k < 4; ++k) {
         if (bi[k] >= B) continue;  // past the range, or after a failed cell insertion (PCSIR_DERR_RANGE)
         if (local) {
-          atomicAdd(&acc[0][bi[k]], w[k]);
+          atomicAdd(&mine[bi[k]], w[k]);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(&acc[1 + c][bi[k]], w[k] * d[k][c]);
+          for (int c = 0; c < 5; ++c) atomicAdd(&mine[(1 + c) * stride + bi[k]], w[k] * d[k][c]);
         } else {
           atomicAdd(&b.bin_ll[bi[k]], (double)w[k]);
 #pragma unroll
@@ -117,14 +123,22 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
     }
     if (local) {
       __syncthreads();
+      const unsigned ncopies = per_warp ? (unsigned)(ESS_THREADS / 32) : 1u;
       for (unsigned j = threadIdx.x; j < B; j += blockDim.x) {
-        if (acc[0][j] != 0.0f) {
-          atomicAdd(&b.bin_ll[j], (double)acc[0][j]);
+        float t[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        for (unsigned cp = 0; cp < ncopies; ++cp) {
 #pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + j], (double)acc[1 + c][j]);
+          for (int a = 0; a < 6; ++a) {
+            float* slot = acc + cp * 6 * stride + a * stride + j;
+            t[a] += *slot;
+            *slot = 0.0f;
+          }
         }
+        if (t[0] != 0.0f) {
+          atomicAdd(&b.bin_ll[j], (double)t[0]);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) acc[a][j] = 0.0f;
+          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + j], (double)t[1 + c]);
+        }
       }
       __syncthreads();
     }
