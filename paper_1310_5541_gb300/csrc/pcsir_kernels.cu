@@ -665,17 +665,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_sir_w(StepBuffers b, const SRC*
   kahan kt, k2, ke[5];
   long long tint = 0;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gstride) {
-    const df wd = me == 0ull ? df{0.0f, 0.0f} : wtilde_q(particle_llq(lls, i), mq);
-    const float wt = wd.hi;
-    const long long q = q_of_wtilde(wd, sq);
-    tint += q;
-    if (qout) qout[i] = q;  // the resampling reads the integer weights instead of forming them again
-    kt.add(wt);
-    k2.add(wt * wt);
-    if (with_est) {
+  // four of the thread's particles i, i + G, i + 2G, i + 3G per pass (G the grid's threads): their
+  // loads and weights are formed together, then added in that order, as one at a time would
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * gstride) {
+    df wd[4];
+    float x[4][5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) ke[c].add(wt * (float)prop[c * N + i]);
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * gstride;
+      wd[k] = df{0.0f, 0.0f};
+      if (i >= N) continue;
+      if (me != 0ull) wd[k] = wtilde_q(particle_llq(lls, i), mq);
+      if (with_est) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) x[k][c] = (float)prop[c * N + i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * gstride;
+      if (i >= N) continue;
+      const float wt = wd[k].hi;
+      const long long q = q_of_wtilde(wd[k], sq);
+      tint += q;
+      if (qout) qout[i] = q;  // the resampling reads the integer weights instead of forming them again
+      kt.add(wt);
+      k2.add(wt * wt);
+      if (with_est) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) ke[c].add(wt * x[k][c]);
+      }
     }
   }
   RedAcc a;
