@@ -298,3 +298,49 @@ def test_ess_argument_errors(pc):
             ctx64._raise(r)
     assert ei.value.status == -6  # PCSIR_ENOTSUP
     ctx64.close()
+
+
+def test_sir_ess_always_resampling_is_sir_step_bit_for_bit(pc):
+    """With N_thr > N every step resamples, and the SIR step with carried (uniform) weights forms the
+    same integer weights as sir_step: states, ancestors and scalars agree bit for bit."""
+    m = _model()
+    seq = synth.make_sequence(64, 64, 3, m, seed=SEED + 40)
+    N = 3 * 4096 + 5
+    a = _ctx(pc, N, m)
+    b = _ctx(pc, N, m)
+    sa = torch.from_numpy(synth.initial_state(seq.gt[0], N, np.float32)).cuda()
+    sb = sa.clone()
+    lw = torch.zeros(N, dtype=torch.int64, device="cuda")
+    for k in range(3):
+        nz = torch.from_numpy(synth.make_noise(N, m.q, SEED + 41, k, np.float32)).cuda()
+        img = torch.from_numpy(seq.images[k]).cuda()
+        u0 = synth.make_u0(SEED + 41, k)
+        pc.sir_step(a, sa, img, nz, u0)
+        pc.sir_step_ess(b, sb, lw, img, nz, u0, N + 1.0)
+        torch.cuda.synchronize()
+        ra, rb = a.last_result(), b.last_result()
+        assert torch.equal(sa, sb)
+        assert torch.equal(a.outputs()["ancestor"], b.outputs()["ancestor"])
+        # the blocks' partial sums meet in FP64 atomics, whose order varies from run to run
+        assert abs(ra["ess"] - rb["ess"]) <= 1e-12 * ra["ess"]
+        np.testing.assert_allclose(rb["estimate"], ra["estimate"], rtol=1e-12, atol=0)
+        assert rb["resampled"] and int(lw.abs().max().item()) == 0
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("N", [1, 3, 4095, 4097])
+@pytest.mark.parametrize("kind", ["pcsir", "sir"])
+def test_ess_small_and_ragged_sizes(pc, kind, N):
+    m = _model()
+    seq = synth.make_sequence(48, 48, 2, m, seed=SEED + 50)
+    ctx = _ctx(pc, N, m)
+    st = synth.initial_state(seq.gt[0], N, np.float32)
+    lwq = np.zeros(N, np.int64)
+    for k in range(2):
+        nz = synth.make_noise(N, m.q, SEED + 51, k, np.float32)
+        # k = 0 keeps the particles (threshold 0), k = 1 resamples (threshold above N)
+        st, lwq, res = _compare_step(pc, ctx, kind, st, lwq, seq.images[k], nz, synth.make_u0(SEED + 51, k), 0.5,
+                                     0.0 if k == 0 else N + 1.0, m)
+        assert res["resampled"] == (k == 1)
+    ctx.close()
