@@ -232,7 +232,7 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
 // gathering its propagated state.
 // ---------------------------------------------------------------------------
 template <typename T, int WSRC, int NS = 5>
-__global__ void __launch_bounds__(SCAN_THREADS, 4)
+__global__ void __launch_bounds__(SCAN_THREADS, 5)
 k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   long long* Cs = reinterpret_cast<long long*>(rs_smem);                       // SCAN_TILE + SCAN_TILE / 16
@@ -283,14 +283,11 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       }
     }
     __syncthreads();
-    // 2. each thread scans its ITEMS consecutive weights
+    // 2. each thread's total of its ITEMS consecutive weights (the running sums are formed again in
+    //    step 4 from shared memory rather than held in 2 x ITEMS registers, for residency)
     long long run = 0;
-    long long loc[SCAN_ITEMS];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      run += Cs[pad_idx(tid * SCAN_ITEMS + k)];
-      loc[k] = run;
-    }
+    for (int k = 0; k < SCAN_ITEMS; ++k) run += Cs[pad_idx(tid * SCAN_ITEMS + k)];
     // 3. exclusive scan of the thread totals across the block
     long long inc = run;
 #pragma unroll
@@ -310,10 +307,14 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const long long texcl = woff + inc - run;
     // 4. inclusive cumulative weights C_j of the tile; entries past its last particle compare
     //    above every U_i (the fixed-step search below)
+    {
+      long long c = excl + texcl;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      const int jj = tid * SCAN_ITEMS + k;
-      Cs[pad_idx(jj)] = jj < cnt ? excl + texcl + loc[k] : LLONG_MAX;
+      for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int jj = tid * SCAN_ITEMS + k;
+        c += Cs[pad_idx(jj)];  // this thread's own items: no other thread reads or writes them here
+        Cs[pad_idx(jj)] = jj < cnt ? c : LLONG_MAX;
+      }
     }
     // the tile's outputs [lo, hi): U_lo >= C_{-1} = excl and U_{hi-1} < C_{cnt-1} = excl + agg
     const float inv_delta = ctl->inv_delta;
