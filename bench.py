@@ -131,6 +131,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def gpu_cpu_affinity(gpu_index):
+    """CPUs local to the GPU, from `nvidia-smi topo -m` ("CPU Affinity" column), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=30).stdout
+    except Exception:
+        return None
+    lines = [l for l in out.splitlines() if l.strip()]
+    head = next((l for l in lines if "CPU Affinity" in l), None)
+    row = next((l for l in lines if l.split("\t")[0].strip() == "GPU%d" % gpu_index), None)
+    if head is None or row is None:
+        return None
+    cols = [c.strip() for c in head.split("\t")]
+    vals = [c.strip() for c in row.split("\t")]
+    try:
+        field = vals[cols.index("CPU Affinity")]
+        cpus = set()
+        for part in field.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus & set(range(os.cpu_count() or 1)) or None
+    except (ValueError, IndexError):
+        return None
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -548,6 +572,13 @@ def main():
     import torch
 
     torch.cuda.set_device(local)
+    # host threads (and so the page-locked buffers they first touch) on the CPU attached to the GPU
+    cpus = gpu_cpu_affinity(local)
+    if cpus:
+        try:
+            os.sched_setaffinity(0, cpus)
+        except OSError:
+            cpus = None
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -674,9 +705,17 @@ def main():
         pcsir.lib.pcsir_last_result(ctx.handle, pcsir.ctypes.byref(res1))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    # the host link alone: one page-locked noise array to the device, timed with events
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    nz_dev[0].copy_(noise_host[0], non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = noise_host[0].numel() * 4 / (c0.elapsed_time(c1) * 1e-3) / 1e9
     e2e = {"value": N * K_e2e * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": res_bytes,
-           "steps": K_e2e, "copies": "next step's inputs copied during the current step (second stream, two buffers)"}
+           "steps": K_e2e, "copies": "next step's inputs copied during the current step (second stream, two buffers)",
+           "h2d_copy_gbs": h2d_gbs, "host_cpus": len(cpus) if cpus else None}
 
     # plain SIR on the same workload (the comparison path; likelihood for every particle)
     sir = None

@@ -150,37 +150,12 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 // Per-tile sums of the integer weights; the last block scans them into the
 // tiles' exclusive prefixes and fixes Delta and U0.
 // ---------------------------------------------------------------------------
-template <int WSRC>
-__global__ void __launch_bounds__(SCAN_THREADS)
-k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0, int sq) {
-  __shared__ long long red[SCAN_THREADS / 32];
-  __shared__ long long wtot[SCAN_THREADS / 32];
-  __shared__ bool last;
-  Control* ctl = b.ctl;
+// The last block to finish its tiles: exclusive scan of the nt tile sums into the tiles'
+// prefixes, then Delta = T / N, U0 = u0 Delta (64.64 fixed point) and the FP32 reciprocal.
+__device__ void tile_scan_tail(const StepBuffers& b, Control* ctl, int64_t N, double u0, int nt,
+                               long long* wtot) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-  const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
-  const unsigned long long me = ctl->max_llq;
-  long long q[SCAN_ITEMS];
-  tile_weights<WSRC>(b, lsrc, base, cnt, llq_dec(me), me != 0ull, sq, q);
-  long long t = 0;
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) t += q[k];
-  t = warp_sum_i64(t);
-  if (lane == 0) red[w] = t;
-  __syncthreads();
-  if (tid == 0) {
-    long long s = 0;
-    for (int j = 0; j < SCAN_THREADS / 32; ++j) s += red[j];
-    b.tile_sum[blockIdx.x] = s;
-    __threadfence();
-    last = atomicAdd(&ctl->tsum_done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
   // exclusive scan of the tile sums (each thread a run of consecutive tiles)
-  const int nt = (int)gridDim.x;
   const int per = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
   const int t0 = tid * per;
   long long run = 0;
@@ -223,6 +198,100 @@ k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0
     ctl->inv_delta = dd > 0.0 ? (float)(1.0 / dd) : 0.0f;
     if (T == 0ull) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
   }
+}
+
+template <int WSRC>
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_tile_sums(StepBuffers b, const double* __restrict__ lsrc, int64_t N, double u0, int sq) {
+  __shared__ long long red[SCAN_THREADS / 32];
+  __shared__ long long wtot[SCAN_THREADS / 32];
+  __shared__ bool last;
+  Control* ctl = b.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
+  const unsigned long long me = ctl->max_llq;
+  long long q[SCAN_ITEMS];
+  tile_weights<WSRC>(b, lsrc, base, cnt, llq_dec(me), me != 0ull, sq, q);
+  long long t = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) t += q[k];
+  t = warp_sum_i64(t);
+  if (lane == 0) red[w] = t;
+  __syncthreads();
+  if (tid == 0) {
+    long long s = 0;
+    for (int j = 0; j < SCAN_THREADS / 32; ++j) s += red[j];
+    b.tile_sum[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(&ctl->tsum_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  tile_scan_tail(b, ctl, N, u0, (int)gridDim.x, wtot);
+}
+
+// pcSIR tile sums with a resident grid: each block runs over tiles blockIdx.x, + gridDim.x, ...,
+// the slots of its next tile loaded before the current tile's cell weights are gathered, so that
+// the slot reads stay in flight while blocks reduce
+__device__ __forceinline__ void load_tile_slots(const StepBuffers& b, int64_t N, int tile, uint4 g[SCAN_ITEMS / 4]) {
+  const int64_t base = (int64_t)tile * SCAN_TILE;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+    const int64_t j = base + k * (4 * SCAN_THREADS) + 4 * threadIdx.x;
+    if (j + 4 <= N) {
+      g[k] = *reinterpret_cast<const uint4*>(b.pslot + j);
+    } else {
+      g[k].x = j < N ? b.pslot[j] : 0xffffffffu;
+      g[k].y = j + 1 < N ? b.pslot[j + 1] : 0xffffffffu;
+      g[k].z = j + 2 < N ? b.pslot[j + 2] : 0xffffffffu;
+      g[k].w = j + 3 < N ? b.pslot[j + 3] : 0xffffffffu;
+    }
+  }
+}
+
+constexpr int TS_BLOCKS_PER_SM = 6;  // resident tile-sum blocks per SM (40 registers, 256 threads)
+
+__global__ void __launch_bounds__(SCAN_THREADS, TS_BLOCKS_PER_SM) k_tile_sums_bins(StepBuffers b, int64_t N, double u0, int ntiles) {
+  __shared__ long long red[2][SCAN_THREADS / 32];
+  __shared__ long long wtot[SCAN_THREADS / 32];
+  __shared__ bool last;
+  Control* ctl = b.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint4 cur[SCAN_ITEMS / 4], nxt[SCAN_ITEMS / 4];
+  if ((int)blockIdx.x < ntiles) load_tile_slots(b, N, blockIdx.x, cur);
+  int parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, parity ^= 1) {
+    const int next = tile + (int)gridDim.x;
+    if (next < ntiles) load_tile_slots(b, N, next, nxt);
+    long long t = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
+      const unsigned gs[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) t += gs[e] != 0xffffffffu ? b.hq[gs[e]] : 0ll;
+    }
+    t = warp_sum_i64(t);
+    // two halves of the partials alternate, so one barrier per tile separates writes and reads
+    if (lane == 0) red[parity][w] = t;
+    __syncthreads();
+    if (tid == 0) {
+      long long s = 0;
+      for (int j = 0; j < SCAN_THREADS / 32; ++j) s += red[parity][j];
+      b.tile_sum[tile] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS / 4; ++k) cur[k] = nxt[k];
+  }
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl->tsum_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  tile_scan_tail(b, ctl, N, u0, ntiles, wtot);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,12 +496,17 @@ cudaError_t prepare_resample() {
 
 template <typename T>
 static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, void* out, int64_t N, double u0,
-                                   int mode, int keep, cudaStream_t s) {
+                                   int mode, int keep, cudaStream_t s, int num_sms = 0) {
   const unsigned ntiles = (unsigned)((N + SCAN_TILE - 1) / SCAN_TILE);
   const int sq = weight_scale_bits(N);
   T* o = static_cast<T*>(out);
   if (mode == WSRC_BINS) {
-    k_tile_sums<WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
+    if (num_sms > 0) {
+      const unsigned grid = ntiles < (unsigned)(num_sms * TS_BLOCKS_PER_SM) ? ntiles : (unsigned)(num_sms * TS_BLOCKS_PER_SM);
+      k_tile_sums_bins<<<grid, SCAN_THREADS, 0, s>>>(b, N, u0, (int)ntiles);
+    } else {
+      k_tile_sums<WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_resample<T, WSRC_BINS><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
@@ -459,9 +533,8 @@ static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, voi
 
 cudaError_t launch_resample(const StepBuffers& b, int dtype, void* state_out, int64_t N, double u0, int mode,
                             int keep, int num_sms, cudaStream_t s) {
-  (void)num_sms;
-  return dtype == PCSIR_F32 ? resample_launch<float>(b, nullptr, state_out, N, u0, mode, keep, s)
-                            : resample_launch<double>(b, nullptr, state_out, N, u0, mode, keep, s);
+  return dtype == PCSIR_F32 ? resample_launch<float>(b, nullptr, state_out, N, u0, mode, keep, s, num_sms)
+                            : resample_launch<double>(b, nullptr, state_out, N, u0, mode, keep, s, num_sms);
 }
 
 cudaError_t launch_resample7(const StepBuffers& b, float* state_out, int64_t N, double u0, int mode, int keep,
