@@ -677,14 +677,18 @@ def main():
     consumed = [torch.cuda.Event() for _ in range(2)]
     res1 = pcsir.pcsir_result()
     K_e2e = max(3, K // 2)
+    # each step's copies timed on the copy stream (the host link's rate during the loop)
+    cp_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K_e2e)]
 
     def stage_in(k):
         j = k % 2
         with torch.cuda.stream(copy_stream):
             if k >= 2:
                 copy_stream.wait_event(consumed[j])  # the step that read this buffer pair is done
+            cp_ev[k][0].record(copy_stream)
             img_dev[j].copy_(img_host[k], non_blocking=True)
             nz_dev[j].copy_(noise_host[k % NOISE_POOL], non_blocking=True)
+            cp_ev[k][1].record(copy_stream)
             copied[j].record(copy_stream)
 
     state.copy_(state0)
@@ -715,7 +719,9 @@ def main():
     e2e = {"value": N * K_e2e * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(4 * H_IMG * W_IMG + 5 * 4 * N), "d2h_bytes_per_step": res_bytes,
            "steps": K_e2e, "copies": "next step's inputs copied during the current step (second stream, two buffers)",
-           "h2d_copy_gbs": h2d_gbs, "host_cpus": len(cpus) if cpus else None}
+           "h2d_copy_gbs": h2d_gbs, "host_cpus": len(cpus) if cpus else None,
+           "h2d_copy_gbs_in_loop": int(4 * H_IMG * W_IMG + 5 * 4 * N) * K_e2e
+                                   / (sum(a.elapsed_time(b) for a, b in cp_ev) * 1e-3) / 1e9}
 
     # plain SIR on the same workload (the comparison path; likelihood for every particle)
     sir = None

@@ -390,7 +390,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     if (tid == 0) s_lo = first_out_f(mp, excl, N, inv_delta);
     if (tid == 32) s_hi = (base + cnt >= N) ? N : first_out_f(mp, excl + agg, N, inv_delta);
     __syncthreads();
-    // 5. the tile's outputs, four per thread and pass (all gathers issued before the stores).
+    // 5. the tile's outputs, two per thread and pass (both gathers issued before the stores).
     //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
     //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
     //    weights in shared memory, independent for every output, so a particle with many
@@ -400,7 +400,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
     const unsigned nb = (unsigned)N;
     const unsigned ub = (unsigned)base;
-    constexpr int RO = 4;
+    constexpr int RO = 2;
     for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS) {
       unsigned ii[RO], aa[RO];
       bool has[RO];
