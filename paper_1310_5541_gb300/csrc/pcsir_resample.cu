@@ -11,10 +11,11 @@
 // exactly.  Each tile of particles owns the outputs whose U falls between its
 // exclusive and inclusive prefixes, so every output is written exactly once.
 //
-// Two kernels: k_tile_sums adds up each tile's integer weights and its last
-// block scans the tile sums and fixes the 64.64 map; k_resample then scans
-// within each tile and writes the tile's outputs.  No block ever waits for
-// another.
+// Two kernels: k_tile_sums (k_tile_sums_bins, on a resident grid, for pcSIR
+// steps) adds up each tile's integer weights and its last block scans the
+// tile sums and fixes the 64.64 map; k_resample then scans within each tile
+// and gives every output its ancestor by binary search over the tile's
+// cumulative weights.  No block ever waits for another.
 #include <cmath>
 #include <type_traits>
 
