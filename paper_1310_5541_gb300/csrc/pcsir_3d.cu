@@ -26,7 +26,7 @@ namespace pcsir {
 constexpr int NS3 = 7;
 constexpr int NACC3 = 1 + 2 * NS3;  // count, (lo, hi) per component
 constexpr int P3_THREADS = 512;
-constexpr int P3_PER_THREAD = 4;
+constexpr int P3_PER_THREAD = 2;  // two particles per thread: 64 registers, two blocks per SM
 constexpr int P3_CHUNK = P3_THREADS * P3_PER_THREAD;
 constexpr int L3_BITS = 10;
 constexpr int L3 = 1 << L3_BITS;
@@ -240,7 +240,7 @@ __device__ void local_flush3(Local3& t, const StepBuffers& b, bool clear_keys) {
 // ---------------------------------------------------------------------------
 // Propagate + cell + centre-of-mass sums (Algorithm 2, 3D)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(P3_THREADS, 1)
+__global__ void __launch_bounds__(P3_THREADS, 2)
 k_prop_bin3(StepBuffers b, const float* __restrict__ st, const float* __restrict__ nz, int64_t N, float hx, float hy,
             float hz, long long hqx, long long hqy, long long hqz) {
   extern __shared__ __align__(16) unsigned char smem3[];
