@@ -5,7 +5,7 @@
  * weighted by the likelihood of Eq. likelihood (Gaussian PSF of Eq. object
  * rendered over a P x P patch); the surrogate predicts that log-likelihood
  * with a small network evaluated on the tensor cores, and the exact
- * likelihood stays both its fallback and the judge of its error on a
+ * likelihood stays both its fallback and the measure of its error on a
  * held-out set of dummies at every step.
  *
  * Network (all sizes fixed): 445 inputs -> 256 -> 256 -> 1 with SiLU

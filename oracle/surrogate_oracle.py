@@ -9,7 +9,7 @@ pcSIR step (Algorithm 2) the costly quantity is the log-likelihood of each
 dummy particle against its image patch (Eq. likelihood with the PSF of
 Eq. object); the surrogate predicts that number from the patch and the
 dummy's sub-pixel state with a small fully connected network, and the exact
-likelihood stays the judge of its error.  Definitions written out here:
+likelihood stays the measure of its error.  Definitions written out here:
 
 * Inputs (445 = P*P + 4 with P = 21): the P x P patch centred on the pixel
   nearest the position, ``c = floor(x + 0.5)`` as in the exact likelihood,
