@@ -85,17 +85,21 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
   const int64_t per = (N + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * per;
   const int64_t hi = lo + per < N ? lo + per : N;
+  const int lane = threadIdx.x & 31;
   for (int64_t r0 = lo; r0 < hi; r0 += ESS_ROUND) {
     const int64_t r1 = r0 + ESS_ROUND < hi ? r0 + ESS_ROUND : hi;
-    // four particles per thread and pass, their loads and gathers issued before the atomics
-    for (int64_t i0 = r0 + threadIdx.x; i0 < r1; i0 += 4 * (int64_t)blockDim.x) {
+    // four particles per thread and pass, their loads and gathers issued before the sums; the
+    // loop bound is uniform over the warp (the warp-wide match and shuffles below need every lane)
+    for (int64_t w0 = r0 + (threadIdx.x & ~31); w0 < r1; w0 += 4 * (int64_t)blockDim.x) {
       unsigned bi[4];
       float w[4], d[4][5];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        const int64_t i = w0 + lane + (int64_t)k * blockDim.x;
         bi[k] = 0xffffffffu;
         w[k] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) d[k][c] = 0.0f;
         if (i >= r1) continue;
         const unsigned g = b.pslot[i];
         bi[k] = b.hrank[g];
@@ -109,15 +113,36 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (bi[k] >= B) continue;  // past the range, or after a failed cell insertion (PCSIR_DERR_RANGE)
+        // lanes of one cell first add their terms across the warp (the lowest lane of the cell
+        // gathers the others' in lane order), so that an accumulator sees one atomic per cell
+        // and warp instruction; past the range, or after a failed cell insertion
+        // (PCSIR_DERR_RANGE), bi >= B and the lane adds nothing
+        const unsigned cell = bi[k] < B ? bi[k] : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, cell);
+        const unsigned others = peers & ~(1u << lane);
+        const unsigned steps = __reduce_max_sync(0xffffffffu, (unsigned)__popc(others));
+        float v[6] = {w[k], w[k] * d[k][0], w[k] * d[k][1], w[k] * d[k][2], w[k] * d[k][3], w[k] * d[k][4]};
+        float t[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) t[a] = v[a];
+        unsigned rem = others;
+        for (unsigned st = 0; st < steps; ++st) {
+          const int src = rem ? __ffs(rem) - 1 : lane;
+          rem &= rem - 1u;
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            const float x = __shfl_sync(0xffffffffu, v[a], src);
+            if (src != lane) t[a] += x;
+          }
+        }
+        if (cell == 0xffffffffu || (peers & ((1u << lane) - 1u)) != 0u) continue;
         if (local) {
-          atomicAdd(&mine[bi[k]], w[k]);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(&mine[(1 + c) * stride + bi[k]], w[k] * d[k][c]);
+          for (int a = 0; a < 6; ++a) atomicAdd(&mine[a * stride + cell], t[a]);
         } else {
-          atomicAdd(&b.bin_ll[bi[k]], (double)w[k]);
+          atomicAdd(&b.bin_ll[cell], (double)t[0]);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + bi[k]], (double)(w[k] * d[k][c]));
+          for (int c = 0; c < 5; ++c) atomicAdd(&b.dummy[c * bs + cell], (double)t[1 + c]);
         }
       }
     }
