@@ -9,12 +9,17 @@
 // weighted by w_{k-1} (Section 4: "state vectors and weights"):
 //
 //   k_ess_rank   bin index of every occupied hash slot; zeroes the per-bin sums
+//   k_ess_cellmax per bin: M_b, the largest carried log-weight of its members
+//                rounded down to a whole nat
 //   k_ess_wsums  per bin: sum of w_i and of w_i (s_i - r_b) for every state
-//                component, w_i = exp(logw_i 2^-32) (logw <= 0, maximum 0),
-//                r_b the cell's lower corner for x, y and the step's anchors
-//                (particle 0's input values) for vx, vy, I0.  FP32 products
-//                summed in shared memory over rounds of ESS_ROUND particles,
-//                then added into FP64 per-bin sums.
+//                component, w_i = exp(logw_i 2^-32 - M_b): weights relative to
+//                the cell's own largest (a common factor of the cell's sums,
+//                so the weighted mean is unchanged, and no cell's weights all
+//                underflow in FP32 however far below the global maximum they
+//                lie), r_b the cell's lower corner for x, y and the step's
+//                anchors (particle 0's input values) for vx, vy, I0.  FP32
+//                products summed in shared memory over rounds of ESS_ROUND
+//                particles, then added into FP64 per-bin sums.
 //   k_ess_bins   weighted dummy r_b + S_b / W_b (the plain mean when W_b = 0),
 //                or the cell centre for x, y with pcSIR-CoC, and its
 //                likelihood; the hash slots return to empty
@@ -37,9 +42,13 @@ constexpr int ESS_ROUND = 8192;      // particles per shared-memory round of a b
 constexpr int ESS_BIN_WARPS = ESS_THREADS / 32;
 constexpr int ESS_MAXP = 127;        // largest patch side
 
-__device__ __forceinline__ float lw_to_float(long long v) {
-  // v 2^-32 from two 32-bit conversions (the 64-bit conversion runs on the FP64 pipe)
-  return (float)(int)(v >> 32) + (float)(unsigned)(v & 0xffffffffll) * 2.3283064365386963e-10f;
+// exp(l 2^-32 - m) for a fixed-point log-weight l and a whole-nat reference m >= floor(l 2^-32).
+// The exponent is formed from two 32-bit conversions (the 64-bit conversion runs on the FP64 pipe),
+// the whole nats in 64-bit integers so that no difference overflows
+__device__ __forceinline__ float rel_weight(long long l, int m) {
+  const long long dh = (l >> 32) - (long long)m;  // whole nats below the reference, <= 0
+  if (dh < -200) return 0.0f;                     // below FP32's range
+  return expf((float)dh + (float)(unsigned)(l & 0xffffffffll) * 2.3283064365386963e-10f);
 }
 
 // lower corner of cell b along one axis, the reference of the weighted position offsets
@@ -49,14 +58,75 @@ __device__ __forceinline__ float anchor_f(const Control* ctl, int c) {
   return (float)((double)ctl->anchor[2 + c] * VAL_INV);
 }
 
+// M_b per bin, in whole nats (INT_MIN: no member carries weight); it occupies the per-bin count
+// array, which k_ess_bins fills only afterwards
+__device__ __forceinline__ int* cell_max(const StepBuffers& b) { return reinterpret_cast<int*>(b.bin_cnt); }
+
 __global__ void __launch_bounds__(ESS_THREADS) k_ess_rank(StepBuffers b) {
   const unsigned B = b.ctl->nocc;
   const int64_t bs = b.bin_stride;
   for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < B; bi += gridDim.x * blockDim.x) {
     b.hrank[b.occ[bi]] = bi;
     b.bin_ll[bi] = 0.0;  // sum of the members' weights until k_ess_bins
+    cell_max(b)[bi] = INT_MIN;
 #pragma unroll
     for (int c = 0; c < 5; ++c) b.dummy[c * bs + bi] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(ESS_THREADS) k_ess_cellmax(StepBuffers b, const long long* __restrict__ lw,
+                                                             int64_t N) {
+  // per block in shared memory when the bins fit (then one global atomic per bin and block), else
+  // straight into the global array; either way the lanes of one bin first agree across the warp
+  __shared__ int smax[ESS_SMEM_BINS];
+  const unsigned B = b.ctl->nocc;
+  const bool local = B <= (unsigned)ESS_SMEM_BINS;
+  int* __restrict__ gmax = cell_max(b);
+  if (local) {
+    for (unsigned j = threadIdx.x; j < B; j += blockDim.x) smax[j] = INT_MIN;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+  // four particles per thread and pass, their loads and gathers issued first; the loop bound is
+  // uniform over the warp (the warp-wide match and shuffles need every lane)
+  for (int64_t w0 = 4 * (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < N; w0 += stride) {
+    unsigned cell[4];
+    int v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = w0 + lane + (int64_t)k * blockDim.x;
+      cell[k] = 0xffffffffu;
+      v[k] = INT_MIN;
+      if (i >= N) continue;
+      const unsigned bi = b.hrank[b.pslot[i]];
+      const long long l = lw[i];
+      if (bi < B && l != LLQ_NONE) {
+        cell[k] = bi;
+        v[k] = (int)(l >> 32);  // floor of the log-weight in nats
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned peers = __match_any_sync(0xffffffffu, cell[k]);
+      unsigned rem = peers & ~(1u << lane);
+      const unsigned steps = __reduce_max_sync(0xffffffffu, (unsigned)__popc(rem));
+      int m = v[k];
+      for (unsigned st = 0; st < steps; ++st) {
+        const int src = rem ? __ffs(rem) - 1 : lane;
+        rem &= rem - 1u;
+        m = max(m, __shfl_sync(0xffffffffu, v[k], src));
+      }
+      if (cell[k] != 0xffffffffu && (peers & ((1u << lane) - 1u)) == 0u) {
+        if (local) atomicMax(&smax[cell[k]], m);
+        else atomicMax(&gmax[cell[k]], m);
+      }
+    }
+  }
+  if (local) {
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < B; j += blockDim.x)
+      if (smax[j] != INT_MIN) atomicMax(&gmax[j], smax[j]);
   }
 }
 
@@ -73,6 +143,7 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
   const unsigned stride = per_warp ? (unsigned)ESS_WARP_BINS : B;  // between the six sums of a copy
   float* mine = per_warp ? acc + (threadIdx.x >> 5) * 6 * ESS_WARP_BINS : acc;
   const float* __restrict__ prop = static_cast<const float*>(b.prop);
+  const int* __restrict__ cmax = cell_max(b);
   const int64_t bs = b.bin_stride;
   float anc[3];
 #pragma unroll
@@ -105,7 +176,8 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_wsums(StepBuffers b, const 
         bi[k] = b.hrank[g];
         const unsigned long long key = b.hkey[g];
         const long long l = lw[i];
-        w[k] = l == LLQ_NONE ? 0.0f : expf(lw_to_float(l));
+        // relative to the cell's largest carried log-weight (bi < B whenever l carries weight)
+        w[k] = l == LLQ_NONE || bi[k] >= B ? 0.0f : rel_weight(l, cmax[bi[k]]);
         d[k][0] = prop[i] - cell_ref(key_bx(key), h);
         d[k][1] = prop[N + i] - cell_ref(key_by(key), h);
 #pragma unroll
@@ -272,6 +344,8 @@ cudaError_t launch_pcsir_ess_front(const StepBuffers& b, const ModelParams& m, c
   k_ess_rank<<<full, ESS_THREADS, 0, s>>>(b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  k_ess_cellmax<<<ess_grid(N, 4 * ESS_THREADS, num_sms, 8), ESS_THREADS, 0, s>>>(b, lw_in, N);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_ess_wsums<<<ess_grid(N, ESS_ROUND, num_sms, 4), ESS_THREADS, 0, s>>>(b, lw_in, N, (float)h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long hq = llrint(h * 2147483648.0);

@@ -129,6 +129,61 @@ def test_batched_rows_at_every_alignment(pc, r):
     assert mism <= 0.01 * batch.n.sum()
 
 
+def test_batched_full_size_workload_sampled(pc):
+    """The multi-target workload at its full size, in the launch configuration whose throughput is
+    measured (1000 targets with log-uniform particle counts in [10^3, 10^5], about 2.2e7 particles,
+    1024 x 1024 frames, cell edge = PSF width, two blocks per SM): propagated states of every
+    particle bit-exact, and 40 sampled targets (with the largest and the smallest) against the
+    oracle run on their own slices, one by one."""
+    Q = (0.5, 0.5, 0.1, 0.1, 1.0)
+    batch = synth.make_batch(1000, 1024, 1024, 1, seed=SEED + 60)
+    batch.h[:] = batch.sigma * 1.0
+    T = len(batch.n)
+    offs = np.concatenate([[0], np.cumsum(batch.n)])
+    st = synth.batch_initial_state(batch, np.float32)
+    nz = synth.batch_noise(batch, Q, SEED + 61, 0)
+    u0 = synth.batch_u0(T, SEED + 61, 0)
+    bt = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    bt.set_grid(2)
+    d_st = torch.from_numpy(st).cuda()
+    bt.step(d_st, torch.from_numpy(batch.images[0]).cuda(), torch.from_numpy(nz).cuda(), torch.from_numpy(u0).cuda())
+    torch.cuda.synchronize()
+    res, derr = bt.results()
+    assert derr == 0
+    out = bt.outputs()
+    prop = out["prop_state"].cpu().numpy()
+    new = d_st.cpu().numpy()
+    np.testing.assert_array_equal(prop, O.propagate(st, nz))
+    tk, bx, by = _decode(out["bin_key"].cpu().numpy())
+    cnt = out["bin_count"].cpu().numpy()
+    bt.close()
+    rng = np.random.default_rng(SEED + 62)
+    sample = set(rng.choice(T, 40, replace=False).tolist()) | {int(np.argmax(batch.n)), int(np.argmin(batch.n))}
+    mism = 0
+    for t in sorted(sample):
+        sl = slice(offs[t], offs[t + 1])
+        ref = O.pcsir_step(np.ascontiguousarray(st[:, sl]), batch.images[0], np.ascontiguousarray(nz[:, sl]),
+                           u0[t], batch.h[t], _model(batch, t))
+        sel = tk == t
+        order = np.lexsort((bx[sel], by[sel]))
+        np.testing.assert_array_equal(np.stack([bx[sel][order], by[sel][order]], 1), ref["bin_keys"])
+        np.testing.assert_array_equal(cnt[sel][order], ref["bin_counts"])
+        assert res[t]["n_bins"] == ref["bin_keys"].shape[0]
+        est = np.array(res[t]["estimate"])
+        assert np.all(np.abs(est - ref["estimate"]) <= 1e-5 * np.abs(ref["estimate"]) + 1e-6), (t, est)
+        assert abs(res[t]["ess"] - ref["ess"]) <= 1e-5 * ref["ess"]
+        # every output is one of the target's propagated particles
+        P = prop[:, sl]
+        rows = np.ascontiguousarray(P.T).view(np.dtype((np.void, 20))).ravel()
+        outs = np.ascontiguousarray(new[:, sl].T).view(np.dtype((np.void, 20))).ravel()
+        assert np.all(np.isin(outs, rows))
+        mism += int(np.sum(np.any(new[:, sl] != ref["new_state"], axis=0)))
+    n_sampled = int(sum(batch.n[t] for t in sample))
+    print("batched full size: %d particles, %d sampled targets, outputs differing from the oracle: %d of %d"
+          % (int(batch.n.sum()), len(sample), mism, n_sampled))
+    assert mism <= 0.01 * n_sampled
+
+
 def test_batched_step_graph_capture_replays(pc):
     n = [5000, 7000, 123]
     batch = synth.make_batch(len(n), 128, 128, 1, seed=SEED + 20, n_values=n, min_sep=30.0)

@@ -1,18 +1,26 @@
 """GPU parity of the ESS-thresholded steps (pcsir_step_ess, sir_step_ess) against the oracle.
 
-Each GPU step is compared with the oracle's step on the same input state and the same
-carried log-weights (the GPU's fixed-point values times 2^-32):
+Each GPU step is compared with the oracle's step on the same input state and carried
+log-weights (fixed point, 2^-32 units, on both sides); a sequence continues from the ORACLE's new
+state and log-weights, so that no oracle input comes from the GPU:
   * propagated states, cells, counts, member -> cell map: bit-exact;
   * prior-weighted dummies: the GPU forms sum w_i and sum w_i (s_i - r_b) in FP32 over at most
     m = min(ESS_ROUND = 8192, members) terms per block before adding them in FP64, with
-    w_i = exp(logw_i) in FP32 (relative error <= (1 + |logw_i|) u, u = 2^-24).  The weighted
-    mean r_b + S / W is then within 2 m u max|d| + 4 (1 + max|logw|) u max|d| of the exact
-    one, d the members' offsets s_i - r_b; the test takes that bound from the data;
-  * dummy log-likelihoods: against the oracle's likelihood at the GPU's dummies,
-    1e-4 + 4e-7 |ll| (as for pcsir_step);
-  * weights, ESS, posterior mean and the carried log-weights: against the oracle's formulas
-    applied to the GPU's dummy log-likelihoods (relative 1e-5; log-weights 1e-8);
-  * the decision: N_eff < ess_min, asserted unless N_eff lies within 1e-5 of ess_min;
+    w_i = exp(logw_i - M_b) in FP32, M_b the cell's largest log-weight rounded down (exponent
+    within 2 max|logw| + 1 of zero: relative error <= (2 max|logw| + 4) u, u = 2^-24, with the
+    exponential's own; one more rounding per product).  The weighted mean r_b + S / W is then
+    within (2 m + 4 (2 + max|logw|)) u max|d| of the exact one, d the members' offsets s_i - r_b;
+    the test takes that bound from the data;
+  * dummy log-likelihoods: against the oracle's at the oracle's dummies, within
+    1e-4 + 4e-7 |ll| (as for pcsir_step) plus the dummy bound times twice the likelihood's slope
+    there (central differences of the oracle's likelihood);
+  * weights, ESS, posterior mean and the carried log-weights: against the oracle's own, within
+    what log-likelihood errors of at most delta (the largest of those tolerances) allow: each
+    weight within a factor e^(2 delta), N_eff within e^(4 delta), the mean within
+    (e^(2 delta) - 1) sum w |x - mean|; and, as properties of the GPU's own values, its weights,
+    N_eff and mean formed from its own log-likelihoods (relative 1e-5);
+  * the decision: N_eff < ess_min, asserted unless the oracle's N_eff lies within that
+    tolerance of ess_min;
   * resampled steps: every output is its ancestor's propagated state, copies are floor or ceil
     of N w, the carried log-weights are zero; other steps keep the propagated state and the
     identity ancestors.
@@ -92,18 +100,43 @@ def _dummy_bound(prop, member, order_keys, h, lw, anchors):
         np.maximum.at(dmax[c], member, d[c])
     finite = lw[np.isfinite(lw)]
     lwmax = np.abs(finite).max() if finite.size else 0.0
-    return (2.0 * m * U + 4.0 * (1.0 + lwmax) * U) * dmax + 1e-12
+    return (2.0 * m + 4.0 * (2.0 + lwmax)) * U * dmax + 1e-12
 
 
-def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model):
+def _quantise_lw(logw):
+    """Carried log-weights in the library's fixed point (units of 2^-32; INT64_MIN = no weight)."""
+    out = np.full(logw.shape, INT64_MIN, np.int64)
+    fin = np.isfinite(logw)
+    out[fin] = np.rint(logw[fin] * SCALE).astype(np.int64)
+    return out
+
+
+def _ll_slope(img, dum, model, e=1e-3):
+    """|d ll / d x|, |d ll / d y|, |d ll / d I0| of the oracle's likelihood at the oracle's dummies,
+    by central differences with step e (much larger than any dummy displacement bounded here, so
+    that a patch switching pixels within the displacement shows as a large slope)."""
+    x, y, a = dum[0], dum[1], dum[4]
+    gx = (O.loglik(img, x + e, y, a, model) - O.loglik(img, x - e, y, a, model)) / (2 * e)
+    gy = (O.loglik(img, x, y + e, a, model) - O.loglik(img, x, y - e, a, model)) / (2 * e)
+    ga = (O.loglik(img, x, y, a + e, model) - O.loglik(img, x, y, a - e, model)) / (2 * e)
+    return np.abs(gx), np.abs(gy), np.abs(ga)
+
+
+def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model, dummy="com"):
+    """One GPU step against the oracle's step on the same input; returns the ORACLE's next state and
+    carried log-weights (in the library's fixed point), so that a sequence feeds both sides with
+    oracle values only, and the GPU's result."""
     lw_prev = _lw_float(lwq)
     new, lw_new, res, out = _run(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min)
     assert res["device_error"] == 0
     N = st_np.shape[1]
-    prop = out["prop_state"]
-    np.testing.assert_array_equal(prop, O.propagate(st_np, nz))
     if kind == "pcsir":
-        ref = O.pcsir_step_ess(st_np, lw_prev, img, nz, u0, h, ess_min, model)
+        ref = O.pcsir_step_ess(st_np, lw_prev, img, nz, u0, h, ess_min, model, dummy=dummy)
+    else:
+        ref = O.sir_step_ess(st_np, lw_prev, img, nz, u0, ess_min, model)
+    prop = ref["prop"]
+    np.testing.assert_array_equal(out["prop_state"], prop)
+    if kind == "pcsir":
         B = res["n_bins"]
         assert B == ref["bin_keys"].shape[0]
         xy = out["bin_xy"]
@@ -112,56 +145,82 @@ def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model):
         np.testing.assert_array_equal(out["bin_count"][order], ref["bin_counts"])
         rank = np.empty(B, np.int64)
         rank[order] = np.arange(B)
-        member = rank[out["particle_bin"]]
-        np.testing.assert_array_equal(member, ref["member_bin"])
+        member = ref["member_bin"]
+        np.testing.assert_array_equal(rank[out["particle_bin"]], member)
         dum = out["dummy"][:, order]
         anchors = st_np[2:5, 0].astype(np.float32)  # particle 0's input values (the GPU's anchors)
         bound = _dummy_bound(prop, member, ref["bin_keys"], h, lw_prev, anchors)
         # a cell none of whose members carries weight takes the plain mean of its members
         weighted = np.isfinite(ref["dummies"][0])
-        err = np.abs(dum[:, weighted] - ref["dummies"][:, weighted])
-        assert np.all(err <= bound[:, weighted]), ("weighted dummies", (err / bound[:, weighted]).max())
-        if not weighted.all():
-            plain = O.dummies(prop, member, B)[:, ~weighted]
-            np.testing.assert_allclose(dum[:2, ~weighted], plain[:2], rtol=0, atol=1e-9)
-            np.testing.assert_allclose(dum[2:, ~weighted], plain[2:], rtol=0, atol=2.5e-7)
+        plain = O.dummies(prop, member, B)
+        bound[:2, ~weighted] = 1e-9
+        bound[2:, ~weighted] = 2.5e-7
+        want = np.where(weighted[None, :], ref["dummies"], plain)
+        if dummy == "coc":  # the cells' geometric centres, exact on both sides
+            bound[:2] = 1e-12
+        err = np.abs(dum - want)
+        assert np.all(err <= bound), ("dummies", (err / bound).max())
+        # the dummies' log-likelihoods against the oracle's at the oracle's dummies: the likelihood
+        # tolerance plus the dummies' displacement bound times twice the likelihood's slope there
+        ll_ref = O.loglik(img, want[0], want[1], want[4], model)
+        gx, gy, ga = _ll_slope(img, want, model)
+        tol_bins = 1e-4 + 4e-7 * np.abs(ll_ref) + 2.0 * (gx * bound[0] + gy * bound[1] + ga * bound[4])
         ll_bins = out["bin_loglik"][order]
-        ll_at = O.loglik(img, dum[0], dum[1], dum[4], model)
-        assert np.all(np.abs(ll_bins - ll_at) <= 1e-4 + 4e-7 * np.abs(ll_at))
-        ll = ll_bins[member]
+        assert np.all(np.abs(ll_bins - ll_ref) <= tol_bins), ("dummy loglik", np.abs(ll_bins - ll_ref).max())
+        ll, tol = ll_bins[member], tol_bins[member]
+        ll_want = ll_ref[member]
     else:
-        ref = O.sir_step_ess(st_np, lw_prev, img, nz, u0, ess_min, model)
-        ll = out["loglik"]
-        ll_ref = O.loglik(img, prop[0], prop[1], prop[4], model)
-        assert np.all(np.abs(ll - ll_ref) <= 1e-4 + 4e-7 * np.abs(ll_ref))
-    # the oracle's weight formulas on the GPU's log-likelihoods
+        ll, ll_want = out["loglik"], ref["ll"]
+        tol = 1e-4 + 4e-7 * np.abs(ll_want)
+        assert np.all(np.abs(ll - ll_want) <= tol)
+    fin = np.isfinite(lw_prev)
+    delta = float(tol[fin].max()) if fin.any() else 0.0
+    # independent: the oracle's own weights, N_eff and posterior mean, within what log-likelihood
+    # errors of at most delta allow (each normalised weight within a factor e^(2 delta))
+    w_ref, ess_ref, est_ref = ref["w"], ref["ess"], ref["estimate"]
+    rw = np.expm1(2.0 * delta) + 1e-5
+    wmax = w_ref.max()
+    sig = w_ref >= 1e-3 * wmax
+    assert np.abs(out["weight"][sig] / w_ref[sig] - 1.0).max() <= rw
+    assert np.all(np.abs(out["weight"][~sig] - w_ref[~sig]) <= rw * 1e-3 * wmax)
+    assert abs(res["ess"] / ess_ref - 1.0) <= np.expm1(4.0 * delta) + 1e-5, (res["ess"], ess_ref)
+    # sum_i (w'_i - w_i) x_i = sum_i (w'_i - w_i)(x_i - est): within rw sum_i w_i |x_i - est|
+    spread = (w_ref[None, :] * np.abs(prop.astype(np.float64) - est_ref[:, None])).sum(axis=1)
+    assert np.all(np.abs(np.array(res["estimate"]) - est_ref) <= rw * spread + 1e-5 * np.abs(est_ref) + 1e-6)
+    # properties of the GPU's own values: its weights are the normalised exponentials of its carried
+    # plus new log-weights, and its N_eff and estimate are formed from them
     logw = lw_prev + ll
-    w, m, T = O.normalise(logw)
-    ess = O.ess(w)
-    assert abs(res["ess"] - ess) <= 1e-5 * ess, (res["ess"], ess)
-    est = O.posterior_mean(w, prop)
-    assert np.all(np.abs(np.array(res["estimate"]) - est) <= 1e-5 * np.abs(est) + 1e-6)
-    sig = w >= 1e-3 * w.max()
-    assert np.abs(out["weight"][sig] / w[sig] - 1.0).max() <= 1e-5
-    near = abs(ess / ess_min - 1.0) < 1e-5 if ess_min > 0 else False
+    wg = np.exp(logw - logw[fin].max()) if fin.any() else np.zeros(N)
+    wg /= wg.sum()
+    sig = wg >= 1e-3 * wg.max()
+    assert np.abs(out["weight"][sig] / wg[sig] - 1.0).max() <= 1e-5
+    ess_g = 1.0 / np.sum(wg * wg)
+    assert abs(res["ess"] - ess_g) <= 1e-5 * ess_g
+    est_g = (prop.astype(np.float64) * wg[None, :]).sum(axis=1)
+    assert np.all(np.abs(np.array(res["estimate"]) - est_g) <= 1e-5 * np.abs(est_g) + 1e-6)
+    # the decision: N_eff < ess_min, unless the oracle's N_eff lies within the tolerance of ess_min
+    near = ess_min > 0 and abs(ess_ref / ess_min - 1.0) <= np.expm1(4.0 * delta) + 1e-5
     if not near:
-        assert res["resampled"] == (ess < ess_min), (ess, ess_min)
+        assert res["resampled"] == (ess_ref < ess_min), (ess_ref, ess_min)
+        assert ref["resampled"] == res["resampled"]
     anc = out["ancestor"]
     if res["resampled"]:
         np.testing.assert_array_equal(lw_new, np.zeros(N, np.int64))
         np.testing.assert_array_equal(new, prop[:, anc])
         copies = np.bincount(anc, minlength=N)
-        nw = N * w
+        nw = N * out["weight"]
         assert np.all(copies >= np.floor(nw - 1e-4)) and np.all(copies <= np.ceil(nw + 1e-4))
     else:
         np.testing.assert_array_equal(new, prop)
         np.testing.assert_array_equal(anc, np.arange(N))
         carried = _lw_float(lw_new)
-        fin = np.isfinite(logw)
-        np.testing.assert_array_equal(np.isfinite(carried), fin)
-        np.testing.assert_allclose(carried[fin], (logw - logw[fin].max())[fin], rtol=0, atol=1e-8)
-        assert lw_new[fin].max() == 0
-    return new, lw_new, res
+        ok = np.isfinite(ref["logw_out"])
+        np.testing.assert_array_equal(np.isfinite(carried), ok)
+        # log-weights relative to the maximum: each particle's own error plus that of the maximum
+        assert np.all(np.abs(carried[ok] - ref["logw_out"][ok]) <= tol[ok] + delta + 2.0 ** -31)
+        assert lw_new[ok].max() == 0
+    res["gpu_logw"] = lw_new
+    return ref["new_state"], _quantise_lw(ref["logw_out"]), res
 
 
 @pytest.mark.parametrize("kind", ["pcsir", "sir"])
@@ -196,16 +255,8 @@ def test_ess_pcsir_ragged_large_cells_and_coc(pc):
         for k in range(3):
             nz = synth.make_noise(N, m.q, SEED + 6, k, np.float32)
             u0 = synth.make_u0(SEED + 6, k)
-            if dummy == "coc":
-                ref = O.pcsir_step_ess(st, _lw_float(lwq), seq.images[k], nz, u0, h, 0.0, m, dummy="coc")
-                new, lw_new, res, out = _run(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, u0, h, 0.0)
-                xy = out["bin_xy"]
-                order = np.lexsort((xy[0], xy[1]))
-                np.testing.assert_allclose(out["dummy"][:2, order], ref["dummies"][:2], rtol=0, atol=1e-12)
-                assert not res["resampled"]
-                st, lwq = new, lw_new
-            else:
-                st, lwq, _ = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, u0, h, 0.0, m)
+            st, lwq, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[k], nz, u0, h, 0.0, m, dummy=dummy)
+            assert not res["resampled"]
         ctx.close()
 
 
@@ -240,8 +291,8 @@ def test_ess_zero_weight_particles(pc):
     dead = rng.choice(np.arange(1, N), 300, replace=False)
     lwq[dead] = INT64_MIN
     nz = synth.make_noise(N, m.q, SEED + 13, 0, np.float32)
-    new, lw_new, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[0], nz, 0.3, 0.5, 0.0, m)
-    assert np.all(lw_new[dead] == INT64_MIN)
+    _, _, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[0], nz, 0.3, 0.5, 0.0, m)
+    assert np.all(res["gpu_logw"][dead] == INT64_MIN)
     ctx.close()
 
 

@@ -105,7 +105,7 @@ def run_sir(pc, ctx, st_np, img_np, nz_np, u0):
     return st.cpu().numpy(), res, out
 
 
-def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model, dummy="com"):
+def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model, dummy="com", return_step=False):
     ref = O.pcsir_step(st_np, img, nz, u0, h, model, dummy=dummy)
     new, res, out = run_pcsir(pc, ctx, st_np, img, nz, u0, h)
     assert res["device_error"] == 0 and res["kind"] == 1
@@ -129,7 +129,8 @@ def compare_pcsir(pc, ctx, st_np, img, nz, u0, h, model, dummy="com"):
     werr = check_weights(out["weight"], ref["w"])
     check_scalars(res, ref)
     mism = check_resampling(new, out["prop_state"], out["ancestor"], out["weight"], u0, ref["ancestors"])
-    return dict(B=B, werr=werr, mismatches=mism, N=st_np.shape[1])
+    r = dict(B=B, werr=werr, mismatches=mism, N=st_np.shape[1])
+    return (r, new, res) if return_step else r
 
 
 def compare_sir(pc, ctx, st_np, img, nz, u0, model):
@@ -256,6 +257,80 @@ def test_sir_fp32_big_image(pc, big_case):
     print("SIR fp32:", r)
     assert r["mismatches"] <= 0.05 * N2
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# The single-target workload at its full size: N = 2^24 FP32 particles, 512 x 512 image, 21 x 21
+# patch, h = 0.5 px (the configuration whose throughput is measured)
+# ---------------------------------------------------------------------------
+N_FULL = 1 << 24
+CLOUD = (0.6, 0.6, 0.15, 0.15, 5.0)  # spread of the synthetic particle cloud about the ground truth
+
+
+@pytest.fixture(scope="module")
+def full_case():
+    seq = synth.make_sequence(512, 512, 1, MODEL_BIG, seed=SEED + 50)
+    st = synth.initial_state(seq.gt[0], N_FULL, np.float32)
+    st += synth.make_noise(N_FULL, CLOUD, SEED + 51, 0, np.float32)
+    nz = synth.make_noise(N_FULL, MODEL_BIG.q, SEED + 52, 0, np.float32)
+    return seq.images[0], st, nz, synth.make_u0(SEED + 52, 0)
+
+
+def test_pcsir_full_size_workload(pc, full_case):
+    """One pcSIR step at the full size, first as throughput is measured (no per-particle outputs
+    kept), then with every output kept: both give the same new state bit for bit, and the kept
+    outputs match the oracle's full step element by element (cells, counts and member -> cell map
+    bit-exact; dummies, likelihoods, weights, N_eff and posterior mean within the parity
+    tolerances; resampling properties; ancestors that differ from the oracle's counted)."""
+    img, st, nz, u0 = full_case
+    ctx = _ctx(pc, N_FULL, torch.float32, MODEL_BIG, keep=0)
+    s = torch.from_numpy(st).cuda()
+    pc.pcsir_step(ctx, s, torch.from_numpy(img).cuda(), 0.5, torch.from_numpy(nz).cuda(), u0)
+    torch.cuda.synchronize()
+    res0 = ctx.last_result()
+    new0 = s.cpu().numpy()
+    ctx.close()
+    del s
+    assert res0["device_error"] == 0
+    ctx = _ctx(pc, N_FULL, torch.float32, MODEL_BIG)
+    r, new, res = compare_pcsir(pc, ctx, st, img, nz, u0, 0.5, MODEL_BIG, return_step=True)
+    ctx.close()
+    print("pcSIR full size: %s" % r)
+    np.testing.assert_array_equal(new, new0)
+    # the weight sum meets in FP64 atomics whose order varies from run to run
+    np.testing.assert_allclose(res["estimate"], res0["estimate"], rtol=1e-12, atol=0)
+    assert r["mismatches"] <= 0.01 * N_FULL
+
+
+def test_sir_full_size_workload_sampled(pc, full_case):
+    """SIR, the comparison path, on the same full-size input.  Against the oracle: the propagated
+    state of every particle bit-exact, and the log-likelihoods of 4096 sampled particles one by one.
+    Properties over all particles: the weights are the normalised exponentials of the step's own
+    log-likelihoods, N_eff and the posterior mean are formed from them, and the resampling is
+    systematic (outputs are their ancestors' propagated states, floor or ceil of N w copies,
+    ancestors monotone)."""
+    img, st, nz, u0 = full_case
+    ctx = _ctx(pc, N_FULL, torch.float32, MODEL_BIG, keep=1 | 2 | 8)
+    new, res, out = run_sir(pc, ctx, st, img, nz, u0)
+    ctx.close()
+    assert res["device_error"] == 0 and res["kind"] == 0
+    prop = O.propagate(st, nz)
+    np.testing.assert_array_equal(out["prop_state"], prop)
+    idx = np.sort(np.random.default_rng(SEED + 53).choice(N_FULL, 4096, replace=False))
+    p = prop[:, idx].astype(np.float64)
+    ll_ref = O.loglik(img, p[0], p[1], p[4], MODEL_BIG)
+    ll = out["loglik"]
+    assert np.all(np.abs(ll[idx] - ll_ref) <= 1e-4 + 4e-7 * np.abs(ll_ref))
+    w = np.exp(ll - ll.max())
+    w /= w.sum()
+    check_weights(out["weight"], w)
+    check_scalars(res, {"estimate": (prop.astype(np.float64) * w[None, :]).sum(axis=1), "ess": 1.0 / np.sum(w * w)})
+    anc = out["ancestor"]
+    assert anc.min() >= 0 and anc.max() < N_FULL and np.all(np.diff(anc) >= 0)
+    np.testing.assert_array_equal(new, prop[:, anc])
+    copies = np.bincount(anc, minlength=N_FULL)
+    nw = N_FULL * out["weight"]
+    assert np.all(copies >= np.floor(nw - 1e-4)) and np.all(copies <= np.ceil(nw + 1e-4))
 
 
 def test_sse_likelihood_pcsir(pc):

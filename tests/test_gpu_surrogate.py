@@ -368,9 +368,12 @@ def test_rejected_surrogate_gives_the_plain_step(pc):
 
 
 def test_surrogate_step_uses_predictions_and_checks_like_oracle(pc):
-    """Wiring of the surrogate-assisted step: predictions for unclipped dummies, exact values for
-    clipped ones, the held-out set and check statistics as the oracle selects and computes them,
-    and weights / estimate as the oracle step gives with those log-likelihoods."""
+    """Wiring of the surrogate-assisted step against the oracle on the same input: cells and dummies
+    as the oracle forms them, the oracle's network prediction for unclipped dummies and its exact
+    likelihood for clipped ones (within the inference and likelihood bounds), the held-out set the
+    oracle's hash selects, the check statistics the oracle computes, and the estimate of the oracle's
+    step with those log-likelihoods (within what the bounds allow).  The step's predictions also equal
+    the stand-alone inference entry point's at the step's own dummies, bit for bit."""
     N, h = 60000, 0.1
     W, H = 64, 48
     m = synth.Model(patch=21)
@@ -378,7 +381,8 @@ def test_surrogate_step_uses_predictions_and_checks_like_oracle(pc):
     rng = np.random.default_rng(3)
     sur = pc.Surrogate(capacity=1, batch=128)
     p = rand_params(rng, scale=0.5)
-    sur.set_params(S.pack(p), -60.0, 15.0)
+    mean, scale = -60.0, 15.0
+    sur.set_params(S.pack(p), mean, scale)
     ctx = pc.Context(N, torch.float32, patch=21, psf_sigma=m.sigma_psf, bg=m.bg, keep=pc.KEEP_ANCESTORS | pc.KEEP_WEIGHTS | pc.KEEP_PARTICLE_BIN | pc.KEEP_LOGLIK)
     frac, min_ho, window, max_err = 0.03, 8, 25.0, 1e9
     pc.attach_surrogate(ctx, sur, holdout_frac=frac, min_holdout=min_ho, window=window, max_err=max_err)
@@ -393,36 +397,67 @@ def test_surrogate_step_uses_predictions_and_checks_like_oracle(pc):
     out = ctx.outputs()
     chk = pc.surrogate_last_check(ctx)
     B = out["n_bins"]
-    dummy = out["dummy"].cpu().numpy()
     bll = out["bin_loglik"].cpu().numpy()
     bxy = out["bin_xy"].cpu().numpy()
-    X, clipped = S.features(img, dummy[0], dummy[1], dummy[4], m.sigma_psf, m.bg, 100.0, 1.5)
-    assert clipped.any() and not clipped.all()
-    # clipped dummies: the exact likelihood
-    ex = O.loglik(img, dummy[0, clipped], dummy[1, clipped], dummy[4, clipped], m)
-    np.testing.assert_allclose(bll[clipped], ex, rtol=4e-7, atol=1e-4)
-    # the others: the surrogate, as its stand-alone inference gives
-    pred = sur.predict(out["dummy"].contiguous(), torch.from_numpy(img).cuda(), m.bg, m.sigma_psf).cpu().numpy()
-    np.testing.assert_array_equal(bll[~clipped], pred[~clipped])
-    # held-out selection and statistics
-    fe = max(frac, min_ho / B)
-    held = S.holdout_mask(bxy[0], bxy[1], 0, fe) & ~clipped
-    assert chk["n_holdout"] == int(held.sum()) and chk["n_clipped"] == int(clipped.sum())
-    exact_h = O.loglik(img, dummy[0, held], dummy[1, held], dummy[4, held], m)
-    ref = S.holdout_check(bll[held], exact_h, bll.max(), window, max_err)
-    assert chk["n_significant"] == ref["n_significant"]
-    # the exact values differ from the oracle's by the likelihood kernel's tolerance
-    tol = 1e-4 + 4e-7 * np.abs(exact_h).max()
-    assert abs(chk["max_abs_err"] - ref["max_abs_err"]) <= tol
-    assert abs(chk["rms_err"] - ref["rms_err"]) <= tol
-    assert chk["fallback"] == 0 and chk["n_exact"] == int(held.sum()) + int(clipped.sum())
-    # the step with these log-likelihoods, as the oracle computes it
-    lut = {(int(a), int(b)): v for a, b, v in zip(bxy[0], bxy[1], bll)}
+    order = np.lexsort((bxy[0], bxy[1]))
+    # the oracle's cells and dummies (the plain mean of the members), against the step's
     prop = O.propagate(st0, nz)
-    keys, _, _ = O.segment(*O.bin_coords(prop[0], prop[1], h))
-    vec = np.array([lut[(int(a), int(b))] for a, b in keys])
-    r = O.pcsir_step(st0, img, nz, u0, h, m, lik=lambda x, y, i0: vec)
+    keys, member, _ = O.segment(*O.bin_coords(prop[0], prop[1], h))
+    assert B == keys.shape[0]
+    np.testing.assert_array_equal(bxy[:, order].T, keys)
+    dum = O.dummies(prop, member, B)
+    dg = out["dummy"].cpu().numpy()[:, order]
+    np.testing.assert_allclose(dg[:2], dum[:2], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(dg[2:], dum[2:], rtol=0, atol=2.5e-7)
+    bll = bll[order]
+    X, clipped = S.features(img, dum[0], dum[1], dum[4], m.sigma_psf, m.bg, 100.0, 1.5)
+    assert clipped.any() and not clipped.all()
+    assert chk["n_clipped"] == int(clipped.sum())
+    # the oracle's log-likelihood of every cell: exact where the patch is clipped, else the network's
+    exact = O.loglik(img, dum[0], dum[1], dum[4], m)
+    e = 1e-3  # slope of the exact likelihood, for the dummies' displacement (1e-9 px, 2.5e-7 in I0)
+    gx = np.abs(O.loglik(img, dum[0] + e, dum[1], dum[4], m) - O.loglik(img, dum[0] - e, dum[1], dum[4], m)) / (2 * e)
+    gy = np.abs(O.loglik(img, dum[0], dum[1] + e, dum[4], m) - O.loglik(img, dum[0], dum[1] - e, dum[4], m)) / (2 * e)
+    ga = np.abs(O.loglik(img, dum[0], dum[1], dum[4] + e, m) - O.loglik(img, dum[0], dum[1], dum[4] - e, m)) / (2 * e)
+    tol_exact = 1e-4 + 4e-7 * np.abs(exact) + 2.0 * (1e-9 * (gx + gy) + 2.5e-7 * ga)
+    nc = ~clipped
+    T = S.window_term(img, dum[0, nc], dum[1, nc], m.bg)
+    pred = np.full(B, np.nan)
+    pred[nc] = S.predict_ll(p, mean, scale, X[nc], T)
+    tol_pred = np.zeros(B)
+    tol_pred[nc] = scale * forward_bound(p, X[nc]) + window_bound(img, dum[0, nc], dum[1, nc]) + 1e-6 * scale
+    ll_ref = np.where(clipped, exact, pred)
+    tol = np.where(clipped, tol_exact, tol_pred)
+    assert np.all(np.abs(bll - ll_ref) <= tol), ("cell loglik", (np.abs(bll - ll_ref) / tol).max())
+    # the step's predictions are the stand-alone inference's at the step's own dummies
+    pred_gpu = sur.predict(out["dummy"].contiguous(), torch.from_numpy(img).cuda(), m.bg, m.sigma_psf).cpu().numpy()
+    np.testing.assert_array_equal(bll[nc], pred_gpu[order][nc])
+    # held-out selection and statistics, as the oracle selects and computes them
+    fe = max(frac, min_ho / B)
+    held = S.holdout_mask(keys[:, 0], keys[:, 1], 0, fe) & nc
+    assert chk["n_holdout"] == int(held.sum())
+    ref = S.holdout_check(pred[held], exact[held], ll_ref.max(), window, max_err)
+    # each statistic moves by at most the prediction and exact-likelihood bounds of its cells
+    b = tol_pred[held] + tol_exact[held]
+    tmax = float(tol.max())
+    thr = ll_ref.max() - window
+    if np.all(np.abs(np.maximum(pred[held], exact[held]) - thr) > b + tmax):
+        assert chk["n_significant"] == ref["n_significant"]
+    assert abs(chk["max_abs_err"] - ref["max_abs_err"]) <= b.max()
+    assert abs(chk["rms_err"] - ref["rms_err"]) <= b.max()
+    assert chk["fallback"] == 0 and chk["n_exact"] == int(held.sum()) + int(clipped.sum())
+    # the oracle's step with the oracle's cell log-likelihoods: the estimate within what log-likelihood
+    # differences of at most delta allow (each weight within a factor e^(2 delta))
+    r = O.pcsir_step(st0, img, nz, u0, h, m, lik=lambda x, y, i0: ll_ref)
     est = np.array(ctx.last_result()["estimate"])
-    assert np.all(np.abs(est - r["estimate"]) <= 1e-5 * np.abs(r["estimate"]) + 1e-6)
+    rw = np.expm1(2.0 * tmax) + 1e-5
+    spread = (r["w"][None, :] * np.abs(prop.astype(np.float64) - r["estimate"][:, None])).sum(axis=1)
+    assert np.all(np.abs(est - r["estimate"]) <= rw * spread + 1e-5 * np.abs(r["estimate"]) + 1e-6)
+    # and, a property of the step's own values, the estimate formed from its cells' log-likelihoods
+    lw = bll[member]
+    w = np.exp(lw - lw.max())
+    w /= w.sum()
+    est_g = (prop.astype(np.float64) * w[None, :]).sum(axis=1)
+    assert np.all(np.abs(est - est_g) <= 1e-5 * np.abs(est_g) + 1e-6)
     ctx.close()
     sur.close()
