@@ -192,6 +192,8 @@ def test_dataset_rows_follow_state_order(pc):
 
 
 def _dataset_for_grads(pc, n_rows=512):
+    """The GPU's training rows from synthetic states, and the oracle's own rows from the same
+    states: inputs, residual labels and censoring flags (no oracle input read back from the GPU)."""
     rng = np.random.default_rng(SEED + 2)
     W, H = 64, 64
     img = spot_image(W, H, 32.4, 31.7, SEED + 2)
@@ -203,9 +205,10 @@ def _dataset_for_grads(pc, n_rows=512):
     sur.add(torch.from_numpy(st).cuda(), torch.from_numpy(ll).cuda(), torch.from_numpy(img).cuda(), 10.0, 1.5,
             label_floor=floor)
     assert sur.rows() == n_rows
-    dx, dy, dc = sur.dataset()
-    return (sur, bf16_bits_to_f64(dx)[:, :445], dy.cpu().numpy().astype(np.float64),
-            dc.cpu().numpy().astype(bool))
+    X, clipped = S.features(img, st[0], st[1], st[4], 1.5, 10.0, 128.0, 1.5)
+    assert not clipped.any()
+    y = np.maximum(ll, floor) - S.window_term(img, st[0], st[1], 10.0)
+    return sur, X, y, ll < floor
 
 
 def test_gradients_match_oracle_backprop(pc):
