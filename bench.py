@@ -194,6 +194,23 @@ def cpu_oracle_rate(n_sample, budget_s, seed, h, steps=None, warmup=0):
     return n_sample * len(times) / sum(times), len(times), sum(times)
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of the ranks' values (the slowest rank's time); on one rank the value itself."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(n_particles, steps, world, slowest_ms):
+    """Whole-job particle-steps per second of `world` independent replicas of n_particles each
+    (weak scaling): every rank's particles over the slowest rank's time."""
+    return n_particles * steps * world / (slowest_ms / 1e3)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -639,9 +656,7 @@ def main():
     elapsed_ms = e0.elapsed_time(e1)
     stages = np.array(ctx.timing_read(K))
     if pg:
-        t = torch.tensor([elapsed_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(elapsed_ms, pg, dev)
         pg.barrier()
     res = np.frombuffer(res_host.numpy().tobytes(), dtype=np.dtype([
         ("est", "f8", 5), ("ess", "f8"), ("maxll", "f8"), ("sumw", "f8"), ("n", "i8"), ("nb", "i8"),
@@ -651,7 +666,7 @@ def main():
     est = timed["est"][:, :2]
     gt = seq.gt[1 + Wm:1 + Wm + K, :2]
     rmse = float(np.sqrt(np.mean(np.sum((est - gt) ** 2, axis=1))))
-    value = N * K * world / (elapsed_ms / 1e3)
+    value = replica_rate(N, K, world, elapsed_ms)
 
     # roofline of the dominant kernel (propagate + cells + centre-of-mass sums)
     hbm, peak_kind = peaks()
