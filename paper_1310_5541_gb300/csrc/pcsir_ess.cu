@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_rank(StepBuffers b) {
 __global__ void __launch_bounds__(ESS_THREADS) k_ess_cellmax(StepBuffers b, const long long* __restrict__ lw,
                                                              int64_t N) {
   // per block in shared memory when the bins fit (then one global atomic per bin and block), else
-  // straight into the global array; either way the lanes of one bin first agree across the warp
+  // straight into the global array, where the lanes of one bin first agree across the warp
   __shared__ int smax[ESS_SMEM_BINS];
   const unsigned B = b.ctl->nocc;
   const bool local = B <= (unsigned)ESS_SMEM_BINS;
@@ -106,6 +106,12 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_cellmax(StepBuffers b, cons
         v[k] = (int)(l >> 32);  // floor of the log-weight in nats
       }
     }
+    if (local) {  // 32-bit shared atomics settle equal addresses within the warp themselves
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (cell[k] != 0xffffffffu) atomicMax(&smax[cell[k]], v[k]);
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const unsigned peers = __match_any_sync(0xffffffffu, cell[k]);
@@ -117,10 +123,7 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_cellmax(StepBuffers b, cons
         rem &= rem - 1u;
         m = max(m, __shfl_sync(0xffffffffu, v[k], src));
       }
-      if (cell[k] != 0xffffffffu && (peers & ((1u << lane) - 1u)) == 0u) {
-        if (local) atomicMax(&smax[cell[k]], m);
-        else atomicMax(&gmax[cell[k]], m);
-      }
+      if (cell[k] != 0xffffffffu && (peers & ((1u << lane) - 1u)) == 0u) atomicMax(&gmax[cell[k]], m);
     }
   }
   if (local) {
