@@ -207,9 +207,11 @@ pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image
  *   members' weights are multiplied by the dummy's likelihood.  The weighted
  *   sums are formed in FP32 per block and FP64 across blocks (within a few
  *   FP32 units in the last place of the weighted offsets, and not bit-for-bit
- *   reproducible); a member whose carried weight is below about e^-87 of the
- *   largest adds nothing to its cell's centre of mass (FP32 exponential), and
- *   a cell with no member above that takes the plain mean.
+ *   reproducible).  Each member's weight is taken relative to the largest
+ *   carried weight in its own cell, so a cell keeps its weighted mean however
+ *   far below the other cells it lies; a member below about e^-87 of its
+ *   cell's largest adds nothing (FP32 exponential), and a cell none of whose
+ *   members carries weight (all INT64_MIN) takes the plain mean.
  * Without resampling the state becomes the propagated state and
  * PCSIR_KEEP_ANCESTORS gives the identity; result->resampled tells which branch
  * the step took.  FP32 state only (PCSIR_ENOTSUP for FP64), and not with an
