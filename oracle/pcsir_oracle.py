@@ -112,7 +112,9 @@ def dummies(state: np.ndarray, member_bin: np.ndarray, n_bins: int, prior_w=None
     """Dummy particle of each bin: the (prior-weighted) mean of every state component.
 
     Algorithm 2, "x_dum <- mean{x_k^1..x_k^{N_Ij}}"; Section 4 (centre of mass
-    computed from the state vectors and weights).  FP64.
+    computed from the state vectors and weights).  A bin none of whose members
+    carries weight has no weighted mean; it takes the plain mean (its members'
+    weights stay zero whatever its likelihood).  FP64.
     """
     s = state.astype(np.float64)
     if prior_w is None:
@@ -121,8 +123,14 @@ def dummies(state: np.ndarray, member_bin: np.ndarray, n_bins: int, prior_w=None
         wts = np.asarray(prior_w, dtype=np.float64)
     den = np.bincount(member_bin, weights=wts, minlength=n_bins)
     out = np.empty((s.shape[0], n_bins))
-    for d in range(s.shape[0]):
-        out[d] = np.bincount(member_bin, weights=wts * s[d], minlength=n_bins) / den
+    with np.errstate(invalid="ignore", divide="ignore"):  # 0/0 only where the plain mean replaces it
+        for d in range(s.shape[0]):
+            out[d] = np.bincount(member_bin, weights=wts * s[d], minlength=n_bins) / den
+    empty = den == 0  # no member carries weight: the weighted mean is 0/0, the plain mean is taken
+    if empty.any():
+        cnt = np.bincount(member_bin, minlength=n_bins)
+        for d in range(s.shape[0]):
+            out[d, empty] = (np.bincount(member_bin, weights=s[d], minlength=n_bins) / np.maximum(cnt, 1))[empty]
     return out
 
 
@@ -216,6 +224,12 @@ def posterior_mean(w: np.ndarray, state: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # One full step of each filter
 # ----------------------------------------------------------------------------
+def _add_logw(prior_logw, ll):
+    """log w_k = log w_{k-1} + log p(z | x): a particle of zero prior weight keeps zero weight."""
+    prior = np.asarray(prior_logw, np.float64)
+    return np.where(np.isneginf(prior), -np.inf, prior + ll)
+
+
 def _lik_fn(image, model):
     return lambda x, y, i0: loglik(image, x, y, i0, model)
 
@@ -231,7 +245,7 @@ def sir_step(state, image, noise, u0, model, lik=None, prior_logw=None):
     lik = lik or _lik_fn(image, model)
     prop = propagate(state, noise)
     ll = lik(prop[X].astype(np.float64), prop[Y].astype(np.float64), prop[I0].astype(np.float64))
-    logw = ll if prior_logw is None else prior_logw + ll
+    logw = ll if prior_logw is None else _add_logw(prior_logw, ll)
     w, m, T = normalise(logw)
     anc = systematic_resample(w, u0)
     return dict(prop=prop, ll=ll, w=w, max_logw=m, ess=ess(w),
@@ -269,7 +283,7 @@ def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None, dum
         raise ValueError(dummy)
     ll_bins = lik(dum[X], dum[Y], dum[I0])
     ll = ll_bins[member]
-    logw = ll if prior_logw is None else prior_logw + ll
+    logw = ll if prior_logw is None else _add_logw(prior_logw, ll)
     w, m, T = normalise(logw)
     anc = systematic_resample(w, u0)
     return dict(prop=prop, bin_keys=keys, bin_counts=counts, member_bin=member,
@@ -285,7 +299,7 @@ def _ess_branch(r, logw_prev, ess_min):
     maximum) and replaces 'new_state' by the propagated state when the step
     does not resample.
     """
-    logw = r["ll"] if logw_prev is None else np.asarray(logw_prev, np.float64) + r["ll"]
+    logw = r["ll"] if logw_prev is None else _add_logw(logw_prev, r["ll"])
     r["logw"] = logw
     r["resampled"] = bool(r["ess"] < ess_min)
     if r["resampled"]:

@@ -150,12 +150,12 @@ def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model, dum
         dum = out["dummy"][:, order]
         anchors = st_np[2:5, 0].astype(np.float32)  # particle 0's input values (the GPU's anchors)
         bound = _dummy_bound(prop, member, ref["bin_keys"], h, lw_prev, anchors)
-        # a cell none of whose members carries weight takes the plain mean of its members
-        weighted = np.isfinite(ref["dummies"][0])
-        plain = O.dummies(prop, member, B)
+        # a cell none of whose members carries weight takes the plain mean of its members on both
+        # sides: the GPU's from its exact fixed-point sums
+        weighted = np.bincount(member, weights=np.isfinite(lw_prev).astype(np.float64), minlength=B) > 0
         bound[:2, ~weighted] = 1e-9
         bound[2:, ~weighted] = 2.5e-7
-        want = np.where(weighted[None, :], ref["dummies"], plain)
+        want = ref["dummies"]
         if dummy == "coc":  # the cells' geometric centres, exact on both sides
             bound[:2] = 1e-12
         err = np.abs(dum - want)
@@ -279,7 +279,8 @@ def test_ess_threshold_limits(pc):
 
 def test_ess_zero_weight_particles(pc):
     """INT64_MIN marks a particle of zero weight: it adds nothing to its cell's centre of mass,
-    gets no weight, and stays at INT64_MIN while the step does not resample."""
+    gets no weight, and stays at INT64_MIN while the step does not resample.  Every member of the
+    three smallest cells is among them: those cells take their plain mean."""
     m = _model()
     seq = synth.make_sequence(64, 64, 1, m, seed=SEED + 12)
     N = 5000
@@ -287,10 +288,14 @@ def test_ess_zero_weight_particles(pc):
     st = synth.initial_state(seq.gt[0], N, np.float32)
     rng = np.random.default_rng(SEED)
     lwq = (-rng.exponential(1.5, N) * SCALE).astype(np.int64)
-    lwq[np.argmax(lwq)] = 0
-    dead = rng.choice(np.arange(1, N), 300, replace=False)
-    lwq[dead] = INT64_MIN
     nz = synth.make_noise(N, m.q, SEED + 13, 0, np.float32)
+    prop = O.propagate(st, nz)
+    _, member, counts = O.segment(*O.bin_coords(prop[0], prop[1], 0.5))
+    empty = np.argsort(counts, kind="stable")[:3]
+    dead = np.union1d(rng.choice(np.arange(N), 300, replace=False), np.flatnonzero(np.isin(member, empty)))
+    lwq[dead] = INT64_MIN
+    live = np.setdiff1d(np.arange(N), dead)
+    lwq[live[np.argmax(lwq[live])]] = 0
     _, _, res = _compare_step(pc, ctx, "pcsir", st, lwq, seq.images[0], nz, 0.3, 0.5, 0.0, m)
     assert np.all(res["gpu_logw"][dead] == INT64_MIN)
     ctx.close()

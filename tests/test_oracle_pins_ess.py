@@ -180,3 +180,47 @@ def test_shift_of_carried_log_weights_changes_nothing():
     np.testing.assert_allclose(a["w"], b["w"], rtol=1e-9, atol=1e-15)
     assert a["resampled"] == b["resampled"]
     np.testing.assert_allclose(a["logw_out"], b["logw_out"], rtol=0, atol=1e-9)
+
+
+def _two_cell_case():
+    st = np.zeros((5, 6))
+    st[0] = [0.10, 0.20, 0.30, 1.10, 1.20, 1.20]
+    st[1] = [0.00, 0.10, -0.10, 0.00, 0.20, 0.10]
+    st[2] = [0.05, -0.05, 0.025, 0.1, 0.2, -0.1]
+    st[4] = [90.0, 100.0, 110.0, 80.0, 120.0, 100.0]
+    return st
+
+
+def test_cell_without_weighted_members_takes_the_plain_mean():
+    """A cell whose members all carry zero weight has no weighted centre of mass (0/0): it takes the
+    plain mean, its members keep zero weight whatever its likelihood, and the rest of the step is
+    that of the other cells alone."""
+    st = _two_cell_case()
+    lw = np.array([0.0, np.log(2.0), -1.0, -np.inf, -np.inf, -np.inf])
+    ll_of = lambda x, y, i0: -(x - 0.2) ** 2  # finite everywhere
+    res = O.pcsir_step_ess(st, lw, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=ll_of)
+    member = res["member_bin"]
+    dead = member[3]
+    assert np.all(member[3:] == dead) and np.all(member[:3] != dead)
+    for d in range(5):  # brute force: the plain mean of the three zero-weight members' propagated states
+        mean = sum(st[d, i] + (st[d + 2, i] if d < 2 else 0.0) for i in (3, 4, 5)) / 3.0
+        assert res["dummies"][d, dead] == pytest.approx(mean, rel=1e-14, abs=1e-14)
+    assert np.all(np.isfinite(res["dummies"]))
+    np.testing.assert_array_equal(res["w"][3:], 0.0)
+    assert res["w"][:3].sum() == pytest.approx(1.0, rel=1e-14)
+    assert np.all(np.isneginf(res["logw_out"][3:])) and res["logw_out"][:3].max() == 0.0
+
+
+def test_dummy_depends_on_the_weight_ratios_within_its_cell_only():
+    """Section 4's weighted centre of mass of a cell is unchanged when all its members' carried
+    log-weights move by one constant, even far below the other cells' (here 500 nats, beyond the
+    FP32 exponential's range)."""
+    st = _two_cell_case()
+    lw = np.log(np.array([1.0, 2.0, 5.0, 0.5, 0.25, 4.0]))
+    flat = lambda x, y, i0: np.zeros_like(x)
+    a = O.pcsir_step_ess(st, lw, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
+    moved = lw.copy()
+    moved[a["member_bin"] == a["member_bin"][3]] -= 500.0
+    b = O.pcsir_step_ess(st, moved, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
+    np.testing.assert_array_equal(a["member_bin"], b["member_bin"])
+    np.testing.assert_allclose(a["dummies"], b["dummies"], rtol=1e-13, atol=1e-13)
