@@ -162,7 +162,7 @@ def _compare_step(pc, ctx, kind, st_np, lwq, img, nz, u0, h, ess_min, model, dum
         assert np.all(err <= bound), ("dummies", (err / bound).max())
         # the dummies' log-likelihoods against the oracle's at the oracle's dummies: the likelihood
         # tolerance plus the dummies' displacement bound times twice the likelihood's slope there
-        ll_ref = O.loglik(img, want[0], want[1], want[4], model)
+        ll_ref = ref["ll_bins"]
         gx, gy, ga = _ll_slope(img, want, model)
         tol_bins = 1e-4 + 4e-7 * np.abs(ll_ref) + 2.0 * (gx * bound[0] + gy * bound[1] + ga * bound[4])
         ll_bins = out["bin_loglik"][order]
