@@ -16,8 +16,7 @@ primitives) and no fusion or reordering:
   one dummy particle per bin at the mean state of its members, likelihood of
   the dummy only, copy of the dummy's weight to every member, then as SIR.
 
-Readings of points the paper leaves open (each also listed in the design
-notes):
+Readings of points the paper leaves open:
 
 * Proposal = dynamics (bootstrap), so the ratio p(x|x')/pi(x|x') in
   Algorithm 1/2 equals one.
@@ -32,9 +31,12 @@ notes):
 * Dummy weight (Algorithm 2, weight update): ``w_k^i = w_{k-1}^i L(x_dum)`` for
   every member i, which is the only reading for which one particle per bin
   gives back SIR exactly (Section 4.2).  The dummy state is the mean of all
-  state components, weighted by w_{k-1} (Section 4, "state vectors and
-  weights"); after resampling the weights are uniform and this is the plain
-  mean of Algorithm 2.
+  state components, weighted by w_{k-1} (Section 4 forms the centre of mass
+  from both the states and their weights); after resampling the weights are
+  uniform and this is the plain mean of Algorithm 2.  The weighted mean of a
+  cell is a ratio of two sums over that cell, so each cell's weights are
+  taken relative to the largest carried weight among its own members: a cell
+  lying any distance below the others keeps its weighted mean.
 * Likelihood patch S_x: a fixed odd P x P block of pixels centred on the pixel
   nearest the evaluated position, ``c = floor(x + 0.5)``; pixels outside the
   image contribute nothing.  The PSF is point-sampled at pixel centres
@@ -64,7 +66,7 @@ X, Y, VX, VY, I0 = range(5)
 
 
 # ----------------------------------------------------------------------------
-# Algorithm 1/2, "draw a sample from pi(x_k | x_{k-1})": NCV dynamics (Sec. 5.1)
+# Algorithm 1/2, sampling step: the proposal is the NCV dynamics (Sec. 5.1)
 # ----------------------------------------------------------------------------
 def propagate(state: np.ndarray, noise: np.ndarray) -> np.ndarray:
     """Nearly-constant-velocity transition in the state's own precision.
@@ -82,7 +84,7 @@ def propagate(state: np.ndarray, noise: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
-# Algorithm 2, "create B bins of equal size" / "assign x_k^i to a bin"
+# Algorithm 2, binning: equal cells over position, each particle put in its cell
 # ----------------------------------------------------------------------------
 def bin_coords(x: np.ndarray, y: np.ndarray, h: float):
     """Integer cell coordinates (bx, by) of positions, in the positions' precision."""
@@ -108,13 +110,36 @@ def segment(bx: np.ndarray, by: np.ndarray):
     return keys, inverse.reshape(-1), counts
 
 
+def cell_relative_weights(prior_logw, member_bin: np.ndarray, n_bins: int) -> np.ndarray:
+    """Prior weights of the centre of mass, each relative to its own bin's largest (Section 4).
+
+    w_i = exp(log w_i - M_b) with M_b = max of log w over the members of i's
+    bin b.  The factor exp(-M_b) is common to every term of bin b's weighted
+    sums, so the weighted mean is that of the weights exp(log w_i) themselves;
+    taking it per bin keeps every bin's largest weight at 1, so no bin's
+    weights underflow because another bin lies far above it.  Members of zero
+    weight (log w = -inf) get 0; so do all members of a bin that has only such
+    members.  FP64.
+    """
+    lw = np.asarray(prior_logw, np.float64)
+    M = np.full(n_bins, -np.inf)
+    np.maximum.at(M, member_bin, lw)
+    Mi = M[member_bin]
+    out = np.zeros_like(lw)
+    live = ~np.isneginf(lw)
+    out[live] = np.exp(lw[live] - Mi[live])
+    return out
+
+
 def dummies(state: np.ndarray, member_bin: np.ndarray, n_bins: int, prior_w=None) -> np.ndarray:
     """Dummy particle of each bin: the (prior-weighted) mean of every state component.
 
-    Algorithm 2, "x_dum <- mean{x_k^1..x_k^{N_Ij}}"; Section 4 (centre of mass
-    computed from the state vectors and weights).  A bin none of whose members
-    carries weight has no weighted mean; it takes the plain mean (its members'
-    weights stay zero whatever its likelihood).  FP64.
+    Algorithm 2 (the dummy is the mean state of the bin's members); Section 4
+    (the centre of mass uses the members' weights as well).  ``prior_w`` may
+    carry any positive factor common to one bin's members (it cancels in the
+    bin's ratio).  A bin none of whose members carries weight has no weighted
+    mean; it takes the plain mean (its members' weights stay zero whatever its
+    likelihood).  FP64.
     """
     s = state.astype(np.float64)
     if prior_w is None:
@@ -275,7 +300,7 @@ def pcsir_step(state, image, noise, u0, h, model, lik=None, prior_logw=None, dum
     prop = propagate(state, noise)
     bx, by = bin_coords(prop[X], prop[Y], h)
     keys, member, counts = segment(bx, by)
-    prior_w = None if prior_logw is None else np.exp(prior_logw - np.max(prior_logw))
+    prior_w = None if prior_logw is None else cell_relative_weights(prior_logw, member, keys.shape[0])
     dum = dummies(prop, member, keys.shape[0], prior_w)
     if dummy == "coc":
         dum[[X, Y]] = cell_centres(keys, h)

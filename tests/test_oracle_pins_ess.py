@@ -1,5 +1,5 @@
-"""Pins of the oracle's ESS-thresholded steps (Algorithm 1's test "if N_eff < N_thr:
-resample", with the weights carried to the next step when it fails; no GPU).
+"""Pins of the oracle's ESS-thresholded steps (Algorithm 1's test: resample only when N_eff
+is below N_thr, the weights being carried to the next step otherwise; no GPU).
 
 Each test checks ``sir_step_ess`` / ``pcsir_step_ess`` against something other
 than themselves: the every-step filters in the limit that always resamples,
@@ -213,14 +213,38 @@ def test_cell_without_weighted_members_takes_the_plain_mean():
 
 def test_dummy_depends_on_the_weight_ratios_within_its_cell_only():
     """Section 4's weighted centre of mass of a cell is unchanged when all its members' carried
-    log-weights move by one constant, even far below the other cells' (here 500 nats, beyond the
-    FP32 exponential's range)."""
+    log-weights move by one constant, even far below the other cells' (here 500 and 1000 nats:
+    beyond the FP32 and the FP64 exponential's range, respectively)."""
     st = _two_cell_case()
     lw = np.log(np.array([1.0, 2.0, 5.0, 0.5, 0.25, 4.0]))
     flat = lambda x, y, i0: np.zeros_like(x)
     a = O.pcsir_step_ess(st, lw, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
-    moved = lw.copy()
-    moved[a["member_bin"] == a["member_bin"][3]] -= 500.0
-    b = O.pcsir_step_ess(st, moved, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
-    np.testing.assert_array_equal(a["member_bin"], b["member_bin"])
-    np.testing.assert_allclose(a["dummies"], b["dummies"], rtol=1e-13, atol=1e-13)
+    for drop in (500.0, 1000.0):
+        moved = lw.copy()
+        moved[a["member_bin"] == a["member_bin"][3]] -= drop
+        b = O.pcsir_step_ess(st, moved, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
+        np.testing.assert_array_equal(a["member_bin"], b["member_bin"])
+        np.testing.assert_allclose(a["dummies"], b["dummies"], rtol=1e-13, atol=1e-13)
+
+
+def test_far_cell_keeps_its_weighted_mean_bruteforce():
+    """A cell 1000 nats below the best one (every FP64 weight relative to the global maximum
+    underflows to 0 there): its dummy is still its members' weighted mean, formed here by hand
+    with weights taken relative to the cell's FIRST member (a different normaliser from the
+    oracle's), and it differs from the plain mean."""
+    st = _two_cell_case()
+    lw = np.array([0.0, np.log(2.0), -1.0, -1000.0 + np.log(0.5), -1000.0 + np.log(0.25), -1000.0 + np.log(4.0)])
+    flat = lambda x, y, i0: np.zeros_like(x)
+    res = O.pcsir_step_ess(st, lw, None, np.zeros_like(st), 0.5, 1.0, 0.0, MODEL9, lik=flat)
+    far = res["member_bin"][3]
+    assert np.all(res["member_bin"][3:] == far) and np.all(res["member_bin"][:3] != far)
+    members = (3, 4, 5)
+    w = [math.exp(lw[i] - lw[3]) for i in members]  # 1, 1/2, 8
+    for d in range(5):
+        xs = [st[d, i] + (st[d + 2, i] if d < 2 else 0.0) for i in members]
+        wmean = sum(wi * xi for wi, xi in zip(w, xs)) / sum(w)
+        assert res["dummies"][d, far] == pytest.approx(wmean, rel=1e-14, abs=1e-14)
+        if d == 4:
+            assert abs(wmean - sum(xs) / 3.0) > 1.0  # the weights matter for this component
+    # the far cell's members carry (relative) weight ~e^-1000: zero after normalisation in FP64
+    np.testing.assert_array_equal(res["w"][3:], 0.0)
