@@ -13,10 +13,15 @@
 // library holds it (about 17 KB) until the process exits.  Host code cannot
 // use the array's name as a device address, so the first call on each device
 // (with that device current) looks the address up with cudaGetSymbolAddress
-// and caches it; that first call should come before any stream capture.
-// Every call shares the one array per device, and the array keeps the last
-// call's contents: each call clears the parts that must start at zero, and
-// calls whose work overlaps on the GPU race on it.
+// and caches it; that first call should come before any stream capture.  The
+// cache is keyed by the device's current CUDA context: a new primary context
+// (after cudaDeviceReset, say) reloads the library's module, so the next call
+// looks the address up again instead of using a stale one.  Every call shares
+// the one array per device, and the array keeps the last call's contents:
+// each call clears the parts that must start at zero, and calls whose work
+// overlaps on the GPU race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "pcsir_internal.h"
@@ -41,16 +46,49 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mu;
 void* g_scratch_ptr[MAX_DEVICES] = {};
 int g_num_sms[MAX_DEVICES] = {};
+unsigned long long g_ctx_id[MAX_DEVICES] = {};  // context the cached address belongs to
 
-// Once per device, with that device current: the scratch array's device
-// address, the SM count, and the resampling kernel's shared-memory limit.
+// Driver entry points for the current context's unique id, looked up through
+// the runtime (the library does not link the driver library directly).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+cudaError_t current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorNotSupported;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_get_current(&c) != CUDA_SUCCESS || c == nullptr) return cudaErrorDeviceUninitialized;
+  if (g_ctx_get_id(c, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Once per device and context, with that device current: the scratch array's
+// device address, the SM count, and the resampling kernel's shared-memory limit.
 cudaError_t setup_current_device(NoallocScratch** scratch, int* num_sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  // make the device's primary context current (initialising it on first use)
+  e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  if (g_scratch_ptr[dev] == nullptr || g_ctx_id[dev] != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -61,6 +99,7 @@ cudaError_t setup_current_device(NoallocScratch** scratch, int* num_sms) {
     if (e != cudaSuccess) return e;
     g_num_sms[dev] = sms;
     g_scratch_ptr[dev] = p;
+    g_ctx_id[dev] = id;
   }
   *scratch = static_cast<NoallocScratch*>(g_scratch_ptr[dev]);
   *num_sms = g_num_sms[dev];
