@@ -17,8 +17,11 @@
  *  - Images are float32, row-major: Z[y * W + x].
  *  - Work is enqueued on the given cudaStream_t (passed as void*, NULL = the
  *    legacy default stream) and is asynchronous: results are valid after the
- *    stream is synchronised.  No entry point allocates device memory except
- *    pcsir_create; every step call is capturable in a CUDA graph.
+ *    stream is synchronised.  Device memory is allocated only by the create
+ *    calls (pcsir_create, pcsir3_create, pcsir_batch_create,
+ *    pcsir_surrogate_create), by pcsir_batch_keep, and by the first
+ *    pcsir_gemm_bf16 call of the process (a 4-byte error flag); no step call
+ *    allocates, and every step call is capturable in a CUDA graph.
  *  - Every call returns a pcsir_status.  Argument errors are detected on the
  *    host before anything is enqueued.  Errors the GPU detects while running
  *    (non-finite or out-of-range states, a timed-out wait) are reported as
@@ -44,7 +47,7 @@ typedef enum pcsir_status {
   PCSIR_EINVAL = -1,    /* invalid argument (checked on the host) */
   PCSIR_ENOMEM = -2,    /* device allocation failed in pcsir_create */
   PCSIR_ECUDA = -3,     /* a CUDA call failed; the context becomes sticky-failed */
-  PCSIR_ETIMEDOUT = -4, /* reserved for bounded device waits reported on the host */
+  PCSIR_ETIMEDOUT = -4, /* a bounded device wait gave up (pcsir_batch_results) */
   PCSIR_ESTATE = -5,    /* context already failed, or outputs requested before any step */
   PCSIR_ENOTSUP = -6,   /* combination of options not supported */
   PCSIR_ERANGE = -7     /* size beyond the limits fixed at pcsir_create */
@@ -67,7 +70,8 @@ enum {
   PCSIR_KEEP_ANCESTORS = 1,    /* int32 ancestor index s(i) of every output particle */
   PCSIR_KEEP_WEIGHTS = 2,      /* float64 normalised weight w_k^i of every propagated particle */
   PCSIR_KEEP_PARTICLE_BIN = 4, /* uint32 bin index (into the bin arrays) of every particle */
-  PCSIR_KEEP_LOGLIK = 8        /* SIR: float64 log-likelihood of every propagated particle */
+  PCSIR_KEEP_LOGLIK = 8,       /* SIR: float64 log-likelihood of every propagated particle */
+  PCSIR_KEEP_QWEIGHTS = 16     /* int64 integer weight q_i the resampling used for every particle */
 };
 
 /* bit flags of pcsir_result.device_error */
@@ -140,6 +144,11 @@ typedef struct pcsir_outputs {
   const uint32_t* particle_bin;  /* [N] bin index of each particle (PCSIR_KEEP_PARTICLE_BIN) */
   const int32_t* ancestor;       /* [N] s(i) for each output particle i (PCSIR_KEEP_ANCESTORS) */
   const double* weight;          /* [N] normalised weights (PCSIR_KEEP_WEIGHTS) */
+  /* [N] integer weights (PCSIR_KEEP_QWEIGHTS): q_i = rint(w~_i 2^s), w~_i = exp(log w_i - max),
+     with N 2^s <= 2^61 so every cumulative sum C_j = q_0 + ... + q_j is exact.  The resampling
+     of the step is exactly systematic over them: output i takes the first j with
+     C_j > (i + u0) C_{N-1} / N (up to a 2^-64 relative rounding of that bound). */
+  const int64_t* qweight;
 } pcsir_outputs;
 
 /* Create a context on the current CUDA device: validates cfg and allocates
@@ -189,9 +198,9 @@ pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image
                       int32_t W, int32_t H, const void* noise, double u0,
                       void* stream, pcsir_result* result_host);
 
-/* ESS-thresholded steps: Algorithms 1 and 2 with their test "if N_eff < N_thr:
- * resample" (Section 3, Algorithm 1), the weights being carried to the next
- * step when the test fails.  pcsir_step / sir_step are the case that always
+/* ESS-thresholded steps: Algorithms 1 and 2 with their test on the effective
+ * sample size (Section 3, Algorithm 1: resample when N_eff < N_thr), the
+ * weights being carried to the next step when the test fails.  pcsir_step / sir_step are the case that always
  * resamples.
  *
  * logw: device int64 [N], read and written, the particles' carried
@@ -268,12 +277,19 @@ pcsir_status pcsir_timing_read(pcsir_ctx* ctx, float* ms, int32_t capacity, int3
      u0         systematic offset in [0, 1).
      ancestors  device int32 [N], receives s(i) for every output i; the same
                 values pcsir_resample returns for the same inputs.
-   The first call on each device (with that device current) looks up the
-   scratch array's address and sets a kernel attribute; make that first call
-   before any stream capture.  All calls on a device share the one scratch
-   array: calls whose work may overlap on the GPU (different streams without
-   ordering) race on it and must not be issued.  Errors: PCSIR_EINVAL,
-   PCSIR_ERANGE, PCSIR_ECUDA. */
+   If no weight is positive (every log-weight -inf or NaN) there is no
+   distribution to sample: the call still returns PCSIR_OK, with the identity
+   ancestors s(i) = i, as pcsir_resample does; a caller that may pass such
+   weights checks them itself.
+   The first call on each device (with that device current) makes the
+   device's primary context current, looks up the scratch array's address and
+   sets a kernel attribute; make that first call before any stream capture.
+   The lookup is cached per device and CUDA context: after a device reset the
+   next call repeats it (again outside any capture).  All calls on a device
+   share the one scratch array: calls whose work may overlap on the GPU
+   (different streams without ordering) race on it and must not be issued.
+   logw, ancestors and the stream must belong to the current device.
+   Errors: PCSIR_EINVAL, PCSIR_ERANGE, PCSIR_ECUDA. */
 pcsir_status pcsir_resample_noalloc(const double* logw, int64_t N, double u0, int32_t* ancestors, void* stream);
 
 /* Intermediates of the last step (see pcsir_outputs).  Host call, no sync. */
@@ -282,6 +298,33 @@ pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* out);
 /* Copy of the last step's pcsir_result kept by the context in page-locked
    memory (valid after the stream of that step is synchronised). */
 pcsir_status pcsir_last_result(pcsir_ctx* ctx, pcsir_result* out);
+
+/* Checkpoint and resume (the paper has no counterpart: a property of the
+ * library).  Between steps a context carries, besides workspace, only the
+ * state of an attached likelihood surrogate (pcsir_surrogate.h): its network
+ * parameters and label normalisation, its held-out settings, and the count of
+ * surrogate-assisted steps since the attach, which salts the held-out
+ * selection of the next step.  The filter's own state (particle states,
+ * carried log-weights, frame index, seeds) is the caller's and is saved by
+ * the caller.
+ *
+ * pcsir_save(ctx, path) writes that context state to the file path (through
+ * path.tmp, renamed on success).  pcsir_load(ctx, path) restores it into ctx,
+ * which must have been created with the same model and state dtype (every
+ * pcsir_config field but keep; else PCSIR_EINVAL).  When the checkpoint holds
+ * a surrogate, attach one (created with the same i0_ref and sigma_ref) to ctx
+ * first: pcsir_load writes the saved parameters into it (its Adam moments are
+ * zeroed) and restores the held-out settings and the step count, so that the
+ * steps after a load repeat, bit for bit, those that followed the save.
+ * Without a surrogate record pcsir_load detaches any attached surrogate.
+ * Both calls synchronise the device and may not be captured in a CUDA graph.
+ * File layout: an 8-byte magic "PCSIRCK1", version 1, flags, the pcsir_config,
+ * the held-out state, the surrogate record, and an FNV-1a hash of all of it,
+ * in host byte order.  Errors: PCSIR_EINVAL (NULL arguments, unreadable,
+ * unwritable, corrupt or foreign file, model mismatch), PCSIR_ESTATE (context
+ * failed, or a surrogate record without an attached surrogate), PCSIR_ECUDA. */
+pcsir_status pcsir_save(pcsir_ctx* ctx, const char* path);
+pcsir_status pcsir_load(pcsir_ctx* ctx, const char* path);
 
 /* Human-readable description of the last error on ctx (never NULL). */
 const char* pcsir_last_error(pcsir_ctx* ctx);
@@ -330,7 +373,11 @@ pcsir_status pcsir_batched_step(pcsir_batch* batch, float* state, const float* i
 
 /* Results of the last step, one per target (out: host array of T), and the
    step's PCSIR_DERR_* flags (device_error may be NULL; reading them
-   synchronises the device). */
+   synchronises the device).  Returns PCSIR_ETIMEDOUT (with out and
+   *device_error filled) when the flags hold PCSIR_DERR_TIMEOUT: a grid-barrier
+   wait of the step gave up, every block left the kernel, and the step's
+   results are invalid.  The batch stays usable: the next step first clears
+   the cell table the interrupted step may have left partly filled. */
 pcsir_status pcsir_batch_results(pcsir_batch* batch, pcsir_result* out, int32_t T, int32_t* device_error);
 
 /* Device pointers of the last step's propagated states (5 rows of sum n_t
@@ -350,6 +397,29 @@ pcsir_status pcsir_batch_bins(pcsir_batch* batch, const uint64_t** keys, const u
 
 const char* pcsir_batch_last_error(pcsir_batch* batch);
 
+/* Bounded waits of the persistent kernel (failure detection; the paper has no
+   counterpart).  Each grid-barrier wait polls at most max_polls times (default
+   4,194,304, with a 64 ns sleep per poll) before it gives up with
+   PCSIR_DERR_TIMEOUT.  unreachable_barrier in 0 .. 6 makes that barrier of the
+   step wait for one block more than the grid holds, a release that never
+   comes, so that its wait runs out: a test of the timeout path that needs no
+   fault.  -1 (the default) makes every barrier reachable.  Applies to steps
+   launched (or graphs captured) after the call.  Errors: PCSIR_EINVAL. */
+pcsir_status pcsir_batch_set_wait(pcsir_batch* batch, int32_t max_polls, int32_t unreachable_barrier);
+
+/* Per-particle outputs of later steps, kept for inspection: keep is a
+   combination of PCSIR_KEEP_ANCESTORS (int32 [sum n_t]: for output particle i
+   of target t, at off_t + i, the index within the target of its ancestor) and
+   PCSIR_KEEP_QWEIGHTS (int64 [sum n_t]: the integer weight q of each
+   propagated particle, q = rint(exp(ll - max_t) 2^s_t) with n_t 2^s_t <= 2^61;
+   each target is resampled exactly systematically over its own q).  Allocates
+   the arrays (once); call it before capturing steps in a graph.
+   pcsir_batch_kept returns the device pointers (NULL where not kept), valid
+   for the life of the batch; read them after the step's stream is
+   synchronised.  Errors: PCSIR_EINVAL, PCSIR_ENOMEM, PCSIR_ESTATE. */
+pcsir_status pcsir_batch_keep(pcsir_batch* batch, int32_t keep);
+pcsir_status pcsir_batch_kept(pcsir_batch* batch, const int32_t** ancestor, const int64_t** qweight);
+
 /* Durations in ms of the last batched step's seven phases (set-up, propagate
    and cells, dummies and likelihood, weights, tile sums, per-target scan,
    resampling), from global-timer readings of block 0 at each grid barrier;
@@ -361,7 +431,9 @@ pcsir_status pcsir_batch_phase_times(pcsir_batch* batch, double* ms, int32_t n);
    the likelihood surrogate (the paper has no counterpart; exposed for tests).
    C[m * ldc + n] (+)= sum_k A[m * sam + k * sak] * B[n * sbn + k * sbk] for
    m < M, n < N, k < K; A and B device bf16 (as uint16_t), C device float32.
-   accumulate != 0 adds to C.  Errors: PCSIR_EINVAL, PCSIR_ENOMEM, PCSIR_ECUDA. */
+   accumulate != 0 adds to C.  The first call of the process allocates a
+   4-byte device error flag (kept until exit).  Errors: PCSIR_EINVAL,
+   PCSIR_ENOMEM, PCSIR_ECUDA. */
 pcsir_status pcsir_gemm_bf16(const uint16_t* A, int64_t sam, int64_t sak, const uint16_t* B, int64_t sbn,
                              int64_t sbk, float* C, int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t accumulate,
                              void* stream);

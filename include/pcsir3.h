@@ -72,6 +72,7 @@ typedef struct pcsir3_outputs {
   const uint32_t* particle_bin; /* [N] cell of each particle (with PCSIR_KEEP_PARTICLE_BIN) */
   const int32_t* ancestor;   /* [N] (with PCSIR_KEEP_ANCESTORS) */
   const double* weight;      /* [N] normalised weights (with PCSIR_KEEP_WEIGHTS) */
+  const int64_t* qweight;    /* [N] integer weights of the resampling (with PCSIR_KEEP_QWEIGHTS) */
 } pcsir3_outputs;
 
 pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out);

@@ -666,7 +666,8 @@ pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out) {
       !std::isfinite(cfg->psf_sigma_xy) || !std::isfinite(cfg->psf_sigma_z))
     return PCSIR_EINVAL;
   if (cfg->max_particles < 1 || cfg->max_particles > MAX_PARTICLES) return PCSIR_EINVAL;
-  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK))
+  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK |
+                    PCSIR_KEEP_QWEIGHTS))
     return PCSIR_EINVAL;
   pcsir3_ctx* c = new (std::nothrow) pcsir3_ctx();
   if (!c) return PCSIR_ENOMEM;
@@ -701,6 +702,7 @@ pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out) {
   }
   if (ok && (cfg->keep & PCSIR_KEEP_ANCESTORS)) ok = alloc3(c, &b.anc, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_WEIGHTS)) ok = alloc3(c, &b.wout, (size_t)nmax);
+  if (ok && (cfg->keep & PCSIR_KEEP_QWEIGHTS)) ok = alloc3(c, &b.qout, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_PARTICLE_BIN)) ok = alloc3(c, &b.pbin, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_LOGLIK)) ok = alloc3(c, &b.ll, (size_t)nmax);
   if (!ok) {
@@ -822,6 +824,7 @@ pcsir_status pcsir3_get_outputs(pcsir3_ctx* ctx, pcsir3_outputs* o) {
   }
   o->ancestor = b.anc;
   o->weight = b.wout;
+  o->qweight = reinterpret_cast<const int64_t*>(b.qout);
   return PCSIR_OK;
 }
 

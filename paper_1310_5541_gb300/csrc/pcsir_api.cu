@@ -131,7 +131,8 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   if (cfg->lik_kind == PCSIR_LIK_SSE && !(cfg->sigma_xi > 0.0)) return PCSIR_EINVAL;
   if (!std::isfinite(cfg->bg)) return PCSIR_EINVAL;
   if (cfg->max_particles < 1 || cfg->max_particles > MAX_PARTICLES) return PCSIR_EINVAL;
-  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK))
+  if (cfg->keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_LOGLIK |
+                    PCSIR_KEEP_QWEIGHTS))
     return PCSIR_EINVAL;
   if ((cfg->dummy != PCSIR_DUMMY_COM && cfg->dummy != PCSIR_DUMMY_COC) || cfg->reserved != 0) return PCSIR_EINVAL;
 
@@ -176,6 +177,7 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
   }
   if (ok && (cfg->keep & PCSIR_KEEP_ANCESTORS)) ok = dev_alloc(c, &b.anc, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_WEIGHTS)) ok = dev_alloc(c, &b.wout, (size_t)nmax);
+  if (ok && (cfg->keep & PCSIR_KEEP_QWEIGHTS)) ok = dev_alloc(c, &b.qout, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_PARTICLE_BIN)) ok = dev_alloc(c, &b.pbin, (size_t)nmax);
   if (ok && (cfg->keep & PCSIR_KEEP_LOGLIK)) ok = dev_alloc(c, &b.ll, (size_t)nmax);
   if (!ok) {
@@ -422,6 +424,7 @@ pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* o) {
   }
   o->ancestor = b.anc;
   o->weight = b.wout;
+  o->qweight = reinterpret_cast<const int64_t*>(b.qout);
   return PCSIR_OK;
 }
 
@@ -455,6 +458,146 @@ pcsir_status pcsir_attach_surrogate(pcsir_ctx* ctx, pcsir_surrogate* sur, double
   sp.max_err = max_err;
   ctx->sur_on = true;
   ctx->sur_steps = 0;
+  return PCSIR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume.  File layout (host byte order), each record fixed size:
+//   char magic[8] = "PCSIRCK1"; uint32 version = 1; uint32 flags (bit 0: surrogate record)
+//   pcsir_config cfg
+//   uint64 held-out salt (surrogate-assisted steps since the attach); double holdout_frac,
+//   window, max_err; int32 min_holdout, int32 0
+//   [flags & 1] double i0_ref, sigma_ref, label_mean, label_scale; float params[NPARAMS]
+//   uint64 FNV-1a hash of every byte before it
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char CK_MAGIC[8] = {'P', 'C', 'S', 'I', 'R', 'C', 'K', '1'};
+constexpr uint32_t CK_VERSION = 1;
+
+struct CkHead {
+  char magic[8];
+  uint32_t version;
+  uint32_t flags;
+  pcsir_config cfg;
+  uint64_t salt;
+  double frac, window, max_err;
+  int32_t min_holdout, pad;
+};
+
+struct CkSur {
+  double i0_ref, sigma_ref, label_mean, label_scale;
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+constexpr uint64_t FNV_OFFSET = 14695981039346656037ull;
+
+// configs that give the same steps: every field but the kept outputs
+bool same_model(const pcsir_config& a, const pcsir_config& b) {
+  return a.state_dtype == b.state_dtype && a.lik_kind == b.lik_kind && a.patch == b.patch &&
+         a.psf_sigma == b.psf_sigma && a.bg == b.bg && a.sigma_xi == b.sigma_xi && a.dummy == b.dummy;
+}
+
+}  // namespace
+
+pcsir_status pcsir_save(pcsir_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  CkHead h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, CK_MAGIC, sizeof(CK_MAGIC));
+  h.version = CK_VERSION;
+  h.flags = ctx->sur_on ? 1u : 0u;
+  h.cfg = ctx->cfg;
+  h.salt = ctx->sur_steps;
+  h.frac = ctx->sur.frac;
+  h.window = ctx->sur.window;
+  h.max_err = ctx->sur.max_err;
+  h.min_holdout = ctx->sur.min_holdout;
+  std::vector<float> params;
+  CkSur sr{};
+  if (ctx->sur_on) {
+    params.resize(PCSIR_SUR_NPARAMS);
+    pcsir_surrogate* sur = const_cast<pcsir_surrogate*>(ctx->sur.sur);
+    const pcsir_status st = pcsir_surrogate_get_params(sur, params.data(), &sr.label_mean, &sr.label_scale);
+    if (st != PCSIR_OK) return fail(ctx, st, "reading the attached surrogate's parameters");
+    sur_refs(sur, &sr.i0_ref, &sr.sigma_ref);
+  }
+  uint64_t hash = fnv1a(FNV_OFFSET, &h, sizeof(h));
+  if (ctx->sur_on) {
+    hash = fnv1a(hash, &sr, sizeof(sr));
+    hash = fnv1a(hash, params.data(), params.size() * sizeof(float));
+  }
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return fail(ctx, PCSIR_EINVAL, std::string("cannot open ") + tmp + " for writing");
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+  if (ok && ctx->sur_on)
+    ok = std::fwrite(&sr, sizeof(sr), 1, f) == 1 &&
+         std::fwrite(params.data(), sizeof(float), params.size(), f) == params.size();
+  ok = ok && std::fwrite(&hash, sizeof(hash), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(ctx, PCSIR_EINVAL, std::string("cannot write checkpoint ") + path);
+  }
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_load(pcsir_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, PCSIR_EINVAL, std::string("cannot open checkpoint ") + path);
+  CkHead h;
+  CkSur sr{};
+  std::vector<float> params;
+  uint64_t stored = 0;
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, CK_MAGIC, sizeof(CK_MAGIC)) == 0 &&
+            h.version == CK_VERSION && (h.flags & ~1u) == 0u;
+  if (ok && (h.flags & 1u)) {
+    params.resize(PCSIR_SUR_NPARAMS);
+    ok = std::fread(&sr, sizeof(sr), 1, f) == 1 &&
+         std::fread(params.data(), sizeof(float), params.size(), f) == params.size();
+  }
+  ok = ok && std::fread(&stored, sizeof(stored), 1, f) == 1;
+  char extra;
+  ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing may follow the hash
+  std::fclose(f);
+  if (!ok) return fail(ctx, PCSIR_EINVAL, std::string("not a pcSIR checkpoint of this version: ") + path);
+  uint64_t hash = fnv1a(FNV_OFFSET, &h, sizeof(h));
+  if (h.flags & 1u) {
+    hash = fnv1a(hash, &sr, sizeof(sr));
+    hash = fnv1a(hash, params.data(), params.size() * sizeof(float));
+  }
+  if (hash != stored) return fail(ctx, PCSIR_EINVAL, std::string("checkpoint is corrupt (hash): ") + path);
+  if (!same_model(h.cfg, ctx->cfg))
+    return fail(ctx, PCSIR_EINVAL, "checkpoint was written by a context with another model or state dtype");
+  if (h.flags & 1u) {
+    if (!ctx->sur_on)
+      return fail(ctx, PCSIR_ESTATE, "the checkpoint holds a surrogate: attach one to the context before loading");
+    pcsir_surrogate* sur = const_cast<pcsir_surrogate*>(ctx->sur.sur);
+    double i0r = 0.0, sr_ = 0.0;
+    sur_refs(sur, &i0r, &sr_);
+    if (i0r != sr.i0_ref || sr_ != sr.sigma_ref)
+      return fail(ctx, PCSIR_EINVAL, "the attached surrogate's i0_ref / sigma_ref differ from the checkpoint's");
+    const pcsir_status st = pcsir_surrogate_set_params(sur, params.data(), sr.label_mean, sr.label_scale);
+    if (st != PCSIR_OK) return fail(ctx, st, "setting the surrogate's parameters from the checkpoint");
+    ctx->sur.frac = h.frac;
+    ctx->sur.window = h.window;
+    ctx->sur.max_err = h.max_err;
+    ctx->sur.min_holdout = h.min_holdout;
+  } else {
+    ctx->sur_on = false;
+  }
+  ctx->sur_steps = h.salt;
   return PCSIR_OK;
 }
 

@@ -91,6 +91,15 @@ struct BatchBufs {
   long long* tile_excl;
   const int* tile_target;  // [ntiles_total] target owning each tile (fixed at creation)
   pcsir_result* res;  // [T]
+  // optional per-particle outputs (nullptr unless kept): target-local ancestor of every output
+  // particle and the integer weight of every propagated particle
+  int* anc;
+  long long* qout;
+  // set when a barrier wait ran out: the cell table may hold a partial step, and the next step
+  // clears it before use (persists across steps; zeroed at creation)
+  unsigned int* dirty;
+  int bar_spins;  // polls of each barrier wait before it gives up
+  int bar_fail;   // index of a barrier made unreachable (its wait runs out), -1 = none
 };
 
 constexpr int BT_THREADS = 512;
@@ -110,6 +119,7 @@ constexpr int BT_MAX_TARGETS = 2047;
 constexpr int BT_TILE = 4096;
 constexpr int BT_ITEMS = BT_TILE / BT_THREADS;  // 8
 constexpr int BT_BARRIER_SPINS = 1 << 22;
+constexpr int BT_NBARRIERS = 7;  // barriers 0 .. 6 of k_batched_step
 
 // cell key: target (11 bits) | by + 2^25 (26 bits) | bx + 2^25 (26 bits)
 __device__ __forceinline__ unsigned long long bkey(int t, int bx, int by) {
@@ -140,18 +150,24 @@ constexpr size_t BT_SMEM_UNION = cmax(sizeof(BatchLocal), sizeof(BatchResampleSm
 constexpr size_t BT_SMEM = BT_SMEM_UNION + sizeof(long long) * (BT_MAX_TARGETS + 1);
 
 // ---------------------------------------------------------------------------
-// bounded grid-wide barrier (all blocks are co-resident: cooperative launch)
+// bounded grid-wide barrier (all blocks are co-resident: cooperative launch).  Barrier k
+// releases when all gridDim.x blocks have arrived; the barrier b.bar_fail needs one arrival more
+// than there are blocks, so that its wait runs out (a test of the timeout path).  A wait gives
+// up after b.bar_spins polls: it raises PCSIR_DERR_TIMEOUT, the abort flag (every block then
+// leaves at its next poll or barrier) and the dirty mark of the cell table.
 // ---------------------------------------------------------------------------
-__device__ bool grid_barrier(BatchCtl* c) {
+__device__ bool grid_barrier(const BatchBufs& b, int k) {
   __shared__ unsigned s_ok;
+  BatchCtl* c = b.ctl;
   __syncthreads();
   if (threadIdx.x == 0) {
     s_ok = 1u;
     volatile BatchCtl* vc = c;
     const unsigned gen = vc->bar_gen;
+    const unsigned need = gridDim.x + (k == b.bar_fail ? 1u : 0u);
     __threadfence();
     const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == need - 1) {
       c->bar_count = 0u;
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
@@ -159,8 +175,9 @@ __device__ bool grid_barrier(BatchCtl* c) {
       int spins = 0;
       while (vc->bar_gen == gen) {
         if (vc->abort) break;
-        if (++spins > BT_BARRIER_SPINS) {
+        if (++spins > b.bar_spins) {
           atomicOr(&c->err, (unsigned)PCSIR_DERR_TIMEOUT);
+          atomicExch(b.dirty, 1u);
           atomicExch(&c->abort, 1u);
           break;
         }
@@ -647,6 +664,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
     for (int k = 0; k < BT_ITEMS; ++k) {
       const int j = tid * BT_ITEMS + k;
       const long long q = j < cnt ? b.hq[b.pslot[T_.off + lbase + j]] : 0ll;
+      if (b.qout != nullptr && j < cnt) b.qout[T_.off + lbase + j] = q;
       run += q;
       loc[k] = run;
     }
@@ -694,6 +712,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
         }
         // all weights zero: no distribution to sample, keep every particle
         src[j] = zero_sum ? T_.off + i : T_.off + lbase + a;
+        if (b.anc != nullptr && i < hi) b.anc[T_.off + i] = (int)(src[j] - T_.off);
       }
       float v[4][5];
 #pragma unroll
@@ -721,6 +740,18 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   extern __shared__ __align__(16) unsigned char bt_smem[];
   long long* offs = reinterpret_cast<long long*>(bt_smem + BT_SMEM_UNION);
   stamp(b.ctl, 0);
+  // a step whose barrier wait ran out may have left cells in the table: clear all of it first
+  // (ordered before every table access by the first barrier, after which block 0 lifts the mark)
+  const bool was_dirty = *(volatile unsigned*)b.dirty != 0u;
+  if (was_dirty) {
+    const size_t hcap = size_t(1) << b.hbits;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < hcap; g += (size_t)gridDim.x * blockDim.x) {
+      b.hkey[g] = EMPTY_KEY;
+      b.hcnt[g] = 0u;
+#pragma unroll
+      for (int d = 0; d < 5; ++d) b.hsum[d * hcap + g] = 0;
+    }
+  }
   for (int t = threadIdx.x; t <= b.T; t += blockDim.x) offs[t] = b.offs[t];
   // anchors of vx, vy, I0 per target: the target's first particle's input value
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
@@ -728,21 +759,22 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
 #pragma unroll
     for (int c = 0; c < 3; ++c) b.st[t].anchor[c] = to_fixed(st[(2 + c) * b.ntot + i], 4194304.0f);
   }
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 0)) return;
+  if (was_dirty && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(b.dirty, 0u);
   stamp(b.ctl, 1);
   phase_prop_bin(b, st, nz, *reinterpret_cast<BatchLocal*>(bt_smem), offs);
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 1)) return;
   stamp(b.ctl, 2);
   phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 2)) return;
   stamp(b.ctl, 3);
   phase_weights(b);
   // the cells are not needed any more: return their hash slots to empty
   // after the tile sums, which still read the slots' integer weights
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 3)) return;
   stamp(b.ctl, 4);
   phase_tile_sums(b);
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 4)) return;
   stamp(b.ctl, 5);
   phase_target_scan(b, u0s);
   {
@@ -756,10 +788,10 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
       for (int d = 0; d < 5; ++d) b.hsum[d * hcap + g] = 0;
     }
   }
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 5)) return;
   stamp(b.ctl, 6);
   phase_resample(b, out, *reinterpret_cast<BatchResampleSmem*>(bt_smem));
-  if (!grid_barrier(b.ctl)) return;
+  if (!grid_barrier(b, 6)) return;
   stamp(b.ctl, 7);
 }
 
@@ -861,7 +893,7 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
             balloc(c, &b.pslot, (size_t)ntot) &&
             balloc(c, &b.prop, 5 * (size_t)b.pstride) && balloc(c, &b.tile_sum, (size_t)ntiles) &&
             balloc(c, &b.tile_excl, (size_t)ntiles) && balloc(c, &b.res, (size_t)T) &&
-            balloc(c, &dtile_target, (size_t)ntiles);
+            balloc(c, &dtile_target, (size_t)ntiles) && balloc(c, &b.dirty, 1);
   if (!ok) {
     bfree(c);
     delete c;
@@ -870,6 +902,10 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   b.tg = dtg;
   b.offs = doffs;
   b.tile_target = dtile_target;
+  b.anc = nullptr;
+  b.qout = nullptr;
+  b.bar_spins = BT_BARRIER_SPINS;
+  b.bar_fail = -1;
   std::vector<long long> offs(T + 1);
   for (int t = 0; t < T; ++t) offs[t] = tg[t].off;
   offs[T] = ntot;
@@ -883,6 +919,7 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   if (e == cudaSuccess) e = cudaMemset(b.hkey, 0xff, hcap * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b.hcnt, 0, hcap * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b.hsum, 0, 5 * hcap * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(b.dirty, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result) * T);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_batched_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_SMEM);
@@ -963,7 +1000,31 @@ pcsir_status pcsir_batch_results(pcsir_batch* c, pcsir_result* out, int32_t T, i
     BatchCtl ctl;
     if (cudaMemcpy(&ctl, c->b.ctl, sizeof(ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return PCSIR_ECUDA;
     *device_error = (int32_t)ctl.err;
+    if (ctl.err & PCSIR_DERR_TIMEOUT) return PCSIR_ETIMEDOUT;
   }
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_set_wait(pcsir_batch* c, int32_t max_polls, int32_t unreachable_barrier) {
+  if (!c || max_polls < 1 || unreachable_barrier < -1 || unreachable_barrier >= BT_NBARRIERS) return PCSIR_EINVAL;
+  c->b.bar_spins = max_polls;
+  c->b.bar_fail = unreachable_barrier;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_keep(pcsir_batch* c, int32_t keep) {
+  if (!c || (keep & ~(PCSIR_KEEP_ANCESTORS | PCSIR_KEEP_QWEIGHTS))) return PCSIR_EINVAL;
+  if (c->failed) return PCSIR_ESTATE;
+  bool ok = true;
+  if ((keep & PCSIR_KEEP_ANCESTORS) && !c->b.anc) ok = balloc(c, &c->b.anc, (size_t)c->ntot);
+  if (ok && (keep & PCSIR_KEEP_QWEIGHTS) && !c->b.qout) ok = balloc(c, &c->b.qout, (size_t)c->ntot);
+  return ok ? PCSIR_OK : PCSIR_ENOMEM;
+}
+
+pcsir_status pcsir_batch_kept(pcsir_batch* c, const int32_t** ancestor, const int64_t** qweight) {
+  if (!c) return PCSIR_EINVAL;
+  if (ancestor) *ancestor = c->b.anc;
+  if (qweight) *qweight = reinterpret_cast<const int64_t*>(c->b.qout);
   return PCSIR_OK;
 }
 

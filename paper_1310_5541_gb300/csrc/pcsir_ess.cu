@@ -1,12 +1,13 @@
-// ESS-thresholded SIR and pcSIR steps (Algorithms 1 and 2 with the test
-// "if N_eff < N_thr: resample", Section 3): the particles carry log-weights
-// from step to step until the test resamples them.
+// ESS-thresholded SIR and pcSIR steps (Algorithms 1 and 2 with their test on
+// the effective sample size, Section 3: resampling happens only when N_eff
+// falls below N_thr): the particles carry log-weights from step to step until
+// the test resamples them.
 //
 // The carried log-weights are int64 fixed point (units of 2^-32), the form in
 // which SIR's per-particle log-likelihoods already enter the integer weights of
 // the resampling kernel; adding a step's log-likelihood is an exact integer
 // addition.  pcSIR with carried weights needs each cell's centre of mass
-// weighted by w_{k-1} (Section 4: "state vectors and weights"):
+// weighted by w_{k-1} (Section 4 forms it from the states and their weights):
 //
 //   k_ess_rank   bin index of every occupied hash slot; zeroes the per-bin sums
 //   k_ess_cellmax per bin: M_b, the largest carried log-weight of its members

@@ -64,6 +64,7 @@ struct StepBuffers {
   long long* llq;           // SIR per-particle log-likelihood, fixed point 2^-32
   int32_t* anc;
   double* wout;
+  long long* qout;          // integer weights of the resampling (kept on request)
   uint32_t* pbin;
   int64_t bin_stride;       // row stride of bin_xy / dummy (= max particles)
   // scan: per-tile sums of the integer weights and their exclusive prefixes
@@ -131,6 +132,8 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
                                int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur = nullptr);
 // largest image the surrogate's window-term buffer holds (pcsir_surrogate.cu)
 int64_t sur_max_pixels(const pcsir_surrogate* s);
+// the surrogate's input normalisation constants (its creation config)
+void sur_refs(const pcsir_surrogate* s, double* i0_ref, double* sigma_ref);
 // surrogate predictions of the non-clipped dummies and the held-out check (pcsir_surrogate.cu)
 cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const ModelParams& m, const float* img, int W,
                             int H, cudaStream_t s);

@@ -442,7 +442,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     }
   }
   // 6. optional per-particle outputs of the tile
-  if (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN)) {
+  if (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_QWEIGHTS)) {
     const double Tf = *(volatile double*)&ctl->T_f;
     for (int j = tid; j < cnt; j += SCAN_THREADS) {
       const int64_t i = base + j;
@@ -450,9 +450,12 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
         const unsigned g = b.pslot[i];
         if (keep & PCSIR_KEEP_WEIGHTS) b.wout[i] = b.hw[g] / Tf;
         if (keep & PCSIR_KEEP_PARTICLE_BIN) b.pbin[i] = b.hrank[g];
-      } else if (keep & PCSIR_KEEP_WEIGHTS) {
+        if (keep & PCSIR_KEEP_QWEIGHTS) b.qout[i] = b.hq[g];
+      } else {
         const df wd = me == 0ull ? df{0.0f, 0.0f} : wtilde_q(src_llq<WSRC>(b, lsrc, i), mq);
-        b.wout[i] = ((double)wd.hi + (double)wd.lo) / Tf;
+        if (keep & PCSIR_KEEP_WEIGHTS) b.wout[i] = ((double)wd.hi + (double)wd.lo) / Tf;
+        if (keep & PCSIR_KEEP_QWEIGHTS)
+          b.qout[i] = WSRC == WSRC_Q ? b.hq[i] : (me == 0ull ? 0ll : q_of_wtilde(wd, sq));
       }
     }
   }

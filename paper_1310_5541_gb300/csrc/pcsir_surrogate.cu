@@ -915,6 +915,10 @@ cudaError_t fwd_bwd(pcsir_surrogate* s, int bt, float* loss, cudaStream_t st) {
 namespace pcsir {
 
 int64_t sur_max_pixels(const pcsir_surrogate* s) { return s->cfg.max_pixels; }
+void sur_refs(const pcsir_surrogate* s, double* i0_ref, double* sigma_ref) {
+  *i0_ref = s->cfg.i0_ref;
+  *sigma_ref = s->cfg.sigma_ref;
+}
 
 cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const ModelParams& m, const float* img, int W,
                             int H, cudaStream_t st) {

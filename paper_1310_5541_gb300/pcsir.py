@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libpcsir.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, ENOTSUP, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
 F32, F64 = 0, 1
 LIK_POISSON, LIK_SSE = 0, 1
-KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN, KEEP_LOGLIK = 1, 2, 4, 8
+KEEP_ANCESTORS, KEEP_WEIGHTS, KEEP_PARTICLE_BIN, KEEP_LOGLIK, KEEP_QWEIGHTS = 1, 2, 4, 8, 16
 DUMMY_COM, DUMMY_COC = 0, 1
 DERR_RANGE, DERR_TIMEOUT, DERR_NONFINITE, DERR_ZEROSUM = 1, 2, 4, 8
 
@@ -47,7 +47,8 @@ class pcsir_outputs(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("bin_stride", ctypes.c_int64),
                 ("prop_state", ctypes.c_void_p), ("bin_xy", ctypes.c_void_p), ("bin_count", ctypes.c_void_p),
                 ("dummy", ctypes.c_void_p), ("bin_loglik", ctypes.c_void_p), ("loglik", ctypes.c_void_p),
-                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("qweight", ctypes.c_void_p)]
 
 
 class pcsir_target(ctypes.Structure):
@@ -88,7 +89,8 @@ class pcsir3_outputs(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("bin_stride", ctypes.c_int64),
                 ("prop_state", ctypes.c_void_p), ("bin_xyz", ctypes.c_void_p), ("bin_count", ctypes.c_void_p),
                 ("dummy", ctypes.c_void_p), ("bin_loglik", ctypes.c_void_p), ("loglik", ctypes.c_void_p),
-                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+                ("particle_bin", ctypes.c_void_p), ("ancestor", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("qweight", ctypes.c_void_p)]
 
 
 class PcsirError(RuntimeError):
@@ -117,6 +119,8 @@ def _load():
         "pcsir_version": ([], ctypes.c_char_p),
         "pcsir_resample_noalloc": ([P, I64, D, P, P], I32),
         "pcsir_timing_enable": ([P, I32], I32),
+        "pcsir_save": ([P, ctypes.c_char_p], I32),
+        "pcsir_load": ([P, ctypes.c_char_p], I32),
         "pcsir_batch_create": ([ctypes.POINTER(pcsir_target), I32, ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_batch_destroy": ([P], I32),
         "pcsir_batch_set_grid": ([P, I32], I32),
@@ -128,6 +132,9 @@ def _load():
                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
         "pcsir_batch_phase_times": ([P, ctypes.POINTER(ctypes.c_double), I32], I32),
+        "pcsir_batch_set_wait": ([P, I32, I32], I32),
+        "pcsir_batch_keep": ([P, I32], I32),
+        "pcsir_batch_kept": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_gemm_bf16": ([P, I64, I64, P, I64, I64, P, I64, I32, I32, I32, I32, P], I32),
         "pcsir_timing_read": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(ctypes.c_int32)], I32),
         "pcsir_surrogate_create": ([ctypes.POINTER(pcsir_surrogate_config), ctypes.POINTER(ctypes.c_void_p)], I32),
@@ -223,6 +230,18 @@ class Context:
                     n_particles=r.n_particles, n_bins=r.n_bins, device_error=r.device_error, kind=r.kind,
                     resampled=bool(r.resampled))
 
+    def save(self, path):
+        """Checkpoint of the context's state between steps (see pcsir_save)."""
+        st = lib.pcsir_save(self.handle, os.fsencode(path))
+        if st != OK:
+            self._raise(st)
+
+    def load(self, path):
+        """Restore a checkpoint written by ``save`` (attach the surrogate first if it holds one)."""
+        st = lib.pcsir_load(self.handle, os.fsencode(path))
+        if st != OK:
+            self._raise(st)
+
     def timing_enable(self, max_steps):
         st = lib.pcsir_timing_enable(self.handle, int(max_steps))
         if st != OK:
@@ -254,7 +273,8 @@ class Context:
         out = dict(n_particles=N, n_bins=B,
                    prop_state=view(o.prop_state, (5, N), sd),
                    ancestor=view(o.ancestor, (N,), torch.int32),
-                   weight=view(o.weight, (N,), torch.float64))
+                   weight=view(o.weight, (N,), torch.float64),
+                   qweight=view(o.qweight, (N,), torch.int64))
         if B > 0:
             out.update(bin_xy=view(o.bin_xy, (2, S), torch.int32)[:, :B],
                        bin_count=view(o.bin_count, (B,), torch.int32),
@@ -372,6 +392,12 @@ def pcsir_resample_noalloc(logw, u0, out=None, stream=None):
     if out is None:
         out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
     _check_cuda(out, "ancestors", torch.int32)
+    # the library takes its scratch from the current device: every operand must live there
+    dev = torch.cuda.current_device()
+    if logw.device.index != dev or out.device.index != dev:
+        raise ValueError("logw and out must be on the current CUDA device (cuda:%d)" % dev)
+    if stream is not None and stream.device.index != dev:
+        raise ValueError("the stream must belong to the current CUDA device (cuda:%d)" % dev)
     st = lib.pcsir_resample_noalloc(_ptr(logw), logw.numel(), float(u0), _ptr(out), _stream_ptr(stream))
     if st != OK:
         raise PcsirError(st, "pcsir_resample_noalloc failed")
@@ -431,12 +457,35 @@ class Batch:
         if st != OK:
             raise PcsirError(st, "pcsir_batch_set_grid failed")
 
+    def set_wait(self, max_polls=1 << 22, unreachable_barrier=-1):
+        """Bound of each grid-barrier wait, and a barrier made unreachable (tests of the timeout)."""
+        st = lib.pcsir_batch_set_wait(self.handle, int(max_polls), int(unreachable_barrier))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_set_wait failed")
+
+    def keep(self, flags):
+        """Keep per-particle ancestors (KEEP_ANCESTORS) and integer weights (KEEP_QWEIGHTS) of later steps."""
+        st = lib.pcsir_batch_keep(self.handle, int(flags))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_keep failed")
+
+    def kept(self):
+        """The kept per-particle arrays of the last step (None where not kept)."""
+        anc, q = ctypes.c_void_p(), ctypes.c_void_p()
+        st = lib.pcsir_batch_kept(self.handle, ctypes.byref(anc), ctypes.byref(q))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_kept failed")
+        n = self.n_total
+        return dict(ancestor=_from_ptr(anc.value, (n,), torch.int32) if anc.value else None,
+                    qweight=_from_ptr(q.value, (n,), torch.int64) if q.value else None)
+
     def results(self):
-        """Per-target results of the last step and the step's device error flags (synchronises)."""
+        """Per-target results of the last step and the step's device error flags (synchronises).
+        A step whose barrier wait gave up returns its flags (with DERR_TIMEOUT) rather than raising."""
         arr = (pcsir_result * self.T)()
         err = ctypes.c_int32()
         st = lib.pcsir_batch_results(self.handle, arr, self.T, ctypes.byref(err))
-        if st != OK:
+        if st not in (OK, ETIMEDOUT):
             raise PcsirError(st, "pcsir_batch_results failed")
         out = [dict(estimate=list(r.estimate), ess=r.ess, n_bins=r.n_bins, n_particles=r.n_particles,
                     device_error=r.device_error) for r in arr]
@@ -663,7 +712,8 @@ class Context3:
             return _from_ptr(ptr, shape, dtype) if ptr else None
 
         out = dict(n_particles=N, n_bins=B, prop_state=view(o.prop_state, (7, N), torch.float32),
-                   ancestor=view(o.ancestor, (N,), torch.int32), weight=view(o.weight, (N,), torch.float64))
+                   ancestor=view(o.ancestor, (N,), torch.int32), weight=view(o.weight, (N,), torch.float64),
+                   qweight=view(o.qweight, (N,), torch.int64))
         if B > 0:
             out.update(bin_xyz=view(o.bin_xyz, (3, S), torch.int32)[:, :B],
                        bin_count=view(o.bin_count, (B,), torch.int32),

@@ -76,7 +76,7 @@ def test_invalid_configs_rejected_on_host(binding):
                 max_particles=1000, dummy=0, reserved=0)
     bad = [dict(patch=8), dict(patch=0), dict(patch=129), dict(state_dtype=2), dict(lik_kind=5),
            dict(psf_sigma=0.0), dict(bg=0.0), dict(max_particles=0), dict(max_particles=(1 << 26) + 1),
-           dict(keep=64), dict(keep=16), dict(lik_kind=1, sigma_xi=0.0), dict(dummy=2), dict(reserved=1)]
+           dict(keep=64), dict(keep=32), dict(lik_kind=1, sigma_xi=0.0), dict(dummy=2), dict(reserved=1)]
     for upd in bad:
         cfg = binding.pcsir_config(**{**base, **upd})
         h = ctypes.c_void_p(123)
@@ -87,6 +87,23 @@ def test_invalid_configs_rejected_on_host(binding):
     assert lib.sir_step(None, None, 1, None, 1, 1, None, 0.5, None, None) == binding.EINVAL
     assert lib.pcsir_destroy(None) == binding.OK
     assert b"pcsir" in lib.pcsir_version()
+    assert lib.pcsir_save(None, b"x.ck") == binding.EINVAL
+    assert lib.pcsir_load(None, b"x.ck") == binding.EINVAL
+    assert lib.pcsir_batch_set_wait(None, 100, -1) == binding.EINVAL
+    assert lib.pcsir_batch_keep(None, 1) == binding.EINVAL
+    assert lib.pcsir_batch_kept(None, None, None) == binding.EINVAL
+
+
+def test_noalloc_binding_rejects_operands_it_cannot_use(binding):
+    """The allocation-free resampling takes its scratch from the current device: the binding refuses,
+    on the host, operands that are not CUDA tensors of the current device (here: host tensors)."""
+    import torch
+
+    lw = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        binding.pcsir_resample_noalloc(lw, 0.5)
+    with pytest.raises(ValueError):
+        binding.pcsir_resample_noalloc(lw, 0.5, out=torch.zeros(8, dtype=torch.int32))
 
 
 def test_invalid_surrogate_configs_rejected_on_host(binding):
