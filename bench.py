@@ -50,6 +50,32 @@ RESAMPLE_BYTES = 48
 KERNELS_PER_STEP = 5
 
 
+# SIR's likelihood (Eq. likelihood, Poisson): per pixel term the algorithmic work is
+# lambda = I0 gx gy + bg (2), d = lambda - z (1), u = d / z (1), log(1 + u) (1, on the XU),
+# z (u - log(1 + u)) (2) and the accumulation (1): 8 FP32 lane operations, one of them on the XU
+SIR_OPS_PER_TERM = 8
+FP32_LANES_PER_SM = 128  # FP32 lanes per SM (4 sub-partitions x 32)
+XU_LANES_PER_SM = 16     # transcendental (XU) results per SM and clock
+
+
+def sir_roofline(N, ms, num_sms, clocks):
+    """FP32 roofline of a SIR step on the workload: its N P^2 pixel terms (all patches lie inside
+    the image) at SIR_OPS_PER_TERM lane operations each, over the step's device time, against
+    SMs x 128 lanes x the SM clock (the median sampled while SIR ran, else the maximum 2070 MHz);
+    and its one logarithm per term against SMs x 16 XU results per clock."""
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    terms = N * PATCH * PATCH
+    fp32_peak = num_sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    xu_peak = num_sms * XU_LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = terms * SIR_OPS_PER_TERM / (ms * 1e-3) / 1e12
+    xu = terms / (ms * 1e-3) / 1e12
+    return {"kernel": "k_sir_prop_lik", "bound": "fp32", "achieved": achieved, "peak": fp32_peak,
+            "unit": "Tops/s (FP32 lane operations)", "frac": achieved / fp32_peak,
+            "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz" % (num_sms, FP32_LANES_PER_SM, mhz),
+            "xu": {"achieved": xu, "peak": xu_peak, "unit": "T results/s", "frac": xu / xu_peak},
+            "pixel_terms_per_step": terms, "ops_per_term": SIR_OPS_PER_TERM, "traffic": None}
+
+
 def workload_name(N, h):
     return "single-target pcSIR, 512x512 Poisson images, 21x21 patch, N=%d FP32, h=%g px" % (N, h)
 
@@ -192,6 +218,26 @@ def cpu_oracle_rate(n_sample, budget_s, seed, h, steps=None, warmup=0):
         elif time.perf_counter() - t_start > budget_s and len(times) >= 2:
             break
     return n_sample * len(times) / sum(times), len(times), sum(times)
+
+
+def _oracle_worker(args):
+    n_sample, budget_s, seed, h = args
+    return cpu_oracle_rate(n_sample, budget_s, seed, h)
+
+
+def cpu_oracle_rate_all_cores(n_sample, budget_s, seed, h, procs):
+    """The oracle on every host core at once: ``procs`` spawned processes (one thread each), each
+    timing oracle pcSIR steps on its own sample of the workload for about ``budget_s`` seconds.
+    Returns (particle-steps per second over all processes, total steps, seconds of the busiest)."""
+    import multiprocessing as mp
+
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(n_sample, budget_s, seed + j, h) for j in range(procs)])
+    total = sum(n_sample * steps for _, steps, _ in res)
+    busiest = max(tot for _, _, tot in res)
+    return total / busiest, sum(steps for _, steps, _ in res), busiest
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -404,6 +450,22 @@ def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_ca
     out.update(N=N, sequences=n_seq, frames=n_frames, target_rmse_px=target, runs=results,
                matched={"sir": results[0], "pcsir": best("pcsir"), "surrogate_pcsir": best("surrogate")})
     return out
+
+
+def matched_summary(m):
+    """The metric's comparison in compact form: per method the cell size, tracking RMSE and
+    throughput of every run, and the fastest run of each method within 5% of SIR's RMSE."""
+    if not m:
+        return None
+
+    def row(r):
+        return None if r is None else [r["method"], r["h"], round(r["rmse_px"], 5), round(r["steps_per_s"], 2),
+                                       float("%.4g" % r["particles_per_s"])]
+
+    return {"N": m["N"], "target_rmse_px": round(m["target_rmse_px"], 5),
+            "columns": ["method", "h_px", "rmse_px", "steps_per_s", "particles_per_s"],
+            "at_matched_rmse": {k: row(v) for k, v in m["matched"].items()},
+            "runs": [row(r) for r in m["runs"]]}
 
 
 def run_ess(N, n_frames, frac, seed):
@@ -761,13 +823,19 @@ def main():
             pcsir.sir_step(ctx, state, images[k], noise[k % NOISE_POOL], u0s[k], stream)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sir_sampler = ClockSampler(uuid)
+        time.sleep(0.4)
         a.record(stream)
         for k in range(2, 2 + args.sir_steps):
             pcsir.sir_step(ctx, state, images[k], noise[k % NOISE_POOL], u0s[k], stream)
         b.record(stream)
         torch.cuda.synchronize()
+        sir_clocks = sir_sampler.stop()
         ms = a.elapsed_time(b) / args.sir_steps
-        sir = {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.sir_steps}
+        sir = {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.sir_steps,
+               "roofline": sir_roofline(N, ms, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                        sir_clocks),
+               "clocks": sir_clocks}
 
     batched = None
     if args.batched_steps > 0:
@@ -806,10 +874,16 @@ def main():
         rate, steps, tot = cpu_oracle_rate(n_s, 12.0, SEED + 17, h)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "N=2^18 particles of the same workload, %d oracle pcSIR steps (%.1f s)" % (steps, tot)}
+        procs = len(cpus) if cpus else (os.cpu_count() or 1)
+        rate_all, steps_all, busiest = cpu_oracle_rate_all_cores(n_s, 12.0, SEED + 17, h, procs)
+        cpu["all_cores"] = {"value": rate_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                            "sample": "%d processes, each N=2^18 particles of the same workload, %d oracle pcSIR "
+                                      "steps in all (busiest process %.1f s)" % (procs, steps_all, busiest)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "matched": matched_summary(matched),
             "ms_per_step": elapsed_ms / K, "steps_per_s": 1e3 * K / elapsed_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(N, h), "N": N, "h": h, "image": "512x512", "patch": PATCH,
