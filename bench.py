@@ -617,6 +617,66 @@ def run_3d(counts, n_frames, seed):
             "rows": rows}
 
 
+def run_batched3(n_targets, n_per, steps, warmup, seed, world=1):
+    """3D multi-target workload: n_targets spots in 256 x 256 x 64 Poisson volumes (PSF sigma 1.5 / 3
+    voxels, I0 100, bg 10), n_per particles each, 11 x 11 x 7 patches, 0.5 x 0.5 x 1 voxel cells; one
+    step is the fixed kernel sequence of pcsir3_batched_step over all targets, replayed from CUDA
+    graphs.  Algorithmic bytes per particle and step: propagate/cell 88 (state and noise 28 + 28 read,
+    propagated state 28 + slot 4 written), tile sums 8 (slot, integer weight), resampling 60 (slot 4,
+    gathered state 28, written state 28)."""
+    import numpy as np
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, synth
+
+    frames = warmup + steps
+    batch = synth.make_batch3(n_targets, 256, 256, 64, frames, seed, n_particles=n_per)
+    T = len(batch.n)
+    ntot = int(batch.n.sum())
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vols = torch.from_numpy(batch.images).to(dev)
+    noise = [torch.from_numpy(synth.make_noise(ntot, synth.Q3, seed, j, np.float32)).to(dev) for j in range(2)]
+    u0 = torch.from_numpy(np.stack([synth.batch_u0(T, seed, k) for k in range(frames)])).to(dev)
+    st0 = torch.from_numpy(synth.batch3_initial_state(batch)).to(dev)
+    state = st0.clone()
+    bt = pcsir.Batch3(batch.n, batch.h, batch.sigma_xy, batch.sigma_z, batch.bg, batch.patch_xy, batch.patch_z)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bt.step(state, vols[0], noise[0], u0[0], stream=s)  # load the kernels outside capture
+    torch.cuda.synchronize()
+    state.copy_(st0)
+    graphs = []
+    for k in range(frames):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            bt.step(state, vols[k], noise[k % 2], u0[k], stream=s)
+        graphs.append(g)
+    torch.cuda.synchronize()
+    for k in range(warmup):
+        graphs[k].replay()
+    torch.cuda.synchronize()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        a.record(s)
+        for k in range(warmup, frames):
+            graphs[k].replay()
+        b_.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b_) / steps
+    res, derr = bt.results()
+    est = np.array([r["estimate"][:3] for r in res])
+    rmse = float(np.sqrt(np.mean(np.sum((est - batch.gt[frames, :, :3]) ** 2, axis=1))))
+    bt.close()
+    hbm, kind = peaks()
+    bpp = 88 + 8 + 60
+    gbs = bpp * ntot / (ms * 1e-3) / 1e9
+    return {"workload": "batched 3D pcSIR, %d targets x %d particles, 256x256x64, 11x11x7, cells 0.5x0.5x1"
+                        % (T, n_per), "value": ntot * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "particles": ntot, "cells_last_step": int(sum(r["n_bins"] for r in res)),
+            "kernels_per_step": 8, "graph": True, "rmse_voxel": rmse, "device_error": derr,
+            "step_bytes_per_particle": bpp, "step_gbs": gbs, "step_frac_of_hbm": gbs / hbm, "peak_source": kind}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -639,6 +699,8 @@ def main():
     ap.add_argument("--large-frames", type=int, default=50, help="frames of the large-object comparison "
                     "(Section 5.3; 0 skips it)")
     ap.add_argument("--frames-3d", type=int, default=20, help="frames of the 3D comparison (0 skips it)")
+    ap.add_argument("--batched3-steps", type=int, default=5, help="timed steps of the batched 3D workload (0 skips it)")
+    ap.add_argument("--batched3-targets", type=int, default=200)
     ap.add_argument("--ess-frames", type=int, default=20, help="frames of the ESS-threshold comparison (0 skips it)")
     ap.add_argument("--ess-frac", type=float, default=0.5, help="N_thr / N of the ESS-threshold comparison")
     args = ap.parse_args()
@@ -867,6 +929,10 @@ def main():
     track3d = None
     if args.frames_3d > 0:
         track3d = run_3d((200_000, 1 << 22), args.frames_3d, SEED + 61 + 1000 * rank)
+    if args.batched3_steps > 0:
+        track3d = track3d or {}
+        track3d["batched"] = run_batched3(args.batched3_targets, 200_000, args.batched3_steps, 3,
+                                          SEED + 63 + 1000 * rank, world)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

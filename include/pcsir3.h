@@ -97,6 +97,75 @@ pcsir_status pcsir3_get_outputs(pcsir3_ctx* ctx, pcsir3_outputs* out);
 /* The page-locked copy of the last step's result (synchronise the stream first). */
 pcsir_status pcsir3_last_result(pcsir3_ctx* ctx, pcsir3_result* out);
 
+/*
+ * Batched multi-target 3D filtering: T independent targets, each its own
+ * pcSIR filter (Algorithm 2) over the 3D state above, with its own particle
+ * count, cell edges, PSF and patch, observed in one shared volume and
+ * advanced together by one fixed sequence of kernels over all targets per
+ * step (capturable as one CUDA graph).  The particles of all targets are
+ * concatenated: target t owns particles [off_t, off_t + n_t) of the
+ * [7][sum n_t] state, in target order.  The paper states its method for a
+ * general state and names higher-dimensional settings as the extension; the
+ * batching is a property of the library.
+ */
+typedef struct pcsir3_batch pcsir3_batch;
+
+typedef struct pcsir3_target {
+  int64_t n_particles;        /* >= 1 */
+  double hx, hy, hz;          /* cell edges, (0, 8] voxels */
+  double psf_sigma_xy;        /* > 0 */
+  double psf_sigma_z;         /* > 0 */
+  double bg;                  /* > 0 */
+  int32_t patch_xy, patch_z;  /* odd, 1 .. 63 */
+} pcsir3_target;
+
+/* Device pointers to intermediates of the last batched step (valid until the
+   next step).  Cells of all targets, n_bins of them in an unspecified order:
+   bin_key = target << 54 | (bz + 2^17) << 36 | (by + 2^17) << 18 | (bx + 2^17),
+   members, dummies ([7][bin_stride]) and dummy log-likelihoods. */
+typedef struct pcsir3_batch_outputs {
+  int64_t n_total;
+  int64_t n_bins;
+  int64_t bin_stride;
+  const float* prop_state;      /* [7][n_total] propagated states */
+  const uint64_t* bin_key;
+  const uint32_t* bin_count;
+  const double* dummy;
+  const double* bin_loglik;
+  const uint32_t* particle_slot;  /* [n_total] hash slot of each particle's cell (inspection) */
+  const int32_t* ancestor;      /* [n_total] target-local ancestor of each output (PCSIR_KEEP_ANCESTORS) */
+  const int64_t* qweight;       /* [n_total] integer weight of each particle (PCSIR_KEEP_QWEIGHTS) */
+} pcsir3_batch_outputs;
+
+/* Create the workspace for T targets (1 .. 1023, sum of n_particles <= 2^26);
+   targets is a host array; keep: PCSIR_KEEP_ANCESTORS and/or
+   PCSIR_KEEP_QWEIGHTS (per-particle outputs for inspection).  Cell indices
+   must stay below 2^17 - 1 in magnitude (else PCSIR_DERR_RANGE).  Errors:
+   PCSIR_EINVAL, PCSIR_ERANGE, PCSIR_ENOMEM, PCSIR_ECUDA. */
+pcsir_status pcsir3_batch_create(const pcsir3_target* targets, int32_t T, int32_t keep, pcsir3_batch** out);
+pcsir_status pcsir3_batch_destroy(pcsir3_batch* batch);
+const char* pcsir3_batch_last_error(pcsir3_batch* batch);
+
+/* One step of every target.  state: device float32 [7][sum n_t], read-write
+   (resampled in place per target); volume: device float32 [D][H][W]; noise:
+   device float32 [7][sum n_t]; u0: device float64 [T] systematic offsets in
+   [0, 1).  Per target as pcsir3_step: propagate, cells of that target's
+   edges, dummies, their likelihood (that target's PSF and patch), weights,
+   systematic resampling within the target.  The per-target results are
+   copied to page-locked memory of the batch at the end of the step.
+   Allocates nothing; capturable in a CUDA graph. */
+pcsir_status pcsir3_batched_step(pcsir3_batch* batch, float* state, const float* volume, int32_t W, int32_t H,
+                                 int32_t D, const float* noise, const double* u0, void* stream);
+
+/* Results of the last step, one per target (host array of T; synchronise the
+   step's stream first), and the step's PCSIR_DERR_* flags (device_error may
+   be NULL; reading them synchronises the device). */
+pcsir_status pcsir3_batch_results(pcsir3_batch* batch, pcsir3_result* out, int32_t T, int32_t* device_error);
+
+/* Intermediates of the last step (synchronises the device).  Errors:
+   PCSIR_EINVAL, PCSIR_ESTATE (no step yet), PCSIR_ECUDA. */
+pcsir_status pcsir3_batch_get_outputs(pcsir3_batch* batch, pcsir3_batch_outputs* out);
+
 #ifdef __cplusplus
 }
 #endif

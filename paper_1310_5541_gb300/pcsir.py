@@ -93,6 +93,19 @@ class pcsir3_outputs(ctypes.Structure):
                 ("qweight", ctypes.c_void_p)]
 
 
+class pcsir3_target(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("hx", ctypes.c_double), ("hy", ctypes.c_double),
+                ("hz", ctypes.c_double), ("psf_sigma_xy", ctypes.c_double), ("psf_sigma_z", ctypes.c_double),
+                ("bg", ctypes.c_double), ("patch_xy", ctypes.c_int32), ("patch_z", ctypes.c_int32)]
+
+
+class pcsir3_batch_outputs(ctypes.Structure):
+    _fields_ = [("n_total", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("bin_stride", ctypes.c_int64),
+                ("prop_state", ctypes.c_void_p), ("bin_key", ctypes.c_void_p), ("bin_count", ctypes.c_void_p),
+                ("dummy", ctypes.c_void_p), ("bin_loglik", ctypes.c_void_p), ("particle_slot", ctypes.c_void_p),
+                ("ancestor", ctypes.c_void_p), ("qweight", ctypes.c_void_p)]
+
+
 class PcsirError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
@@ -162,6 +175,12 @@ def _load():
         "pcsir3_get_outputs": ([P, ctypes.POINTER(pcsir3_outputs)], I32),
         "pcsir3_last_result": ([P, ctypes.POINTER(pcsir3_result)], I32),
         "pcsir_surrogate_last_check": ([P, ctypes.POINTER(pcsir_surrogate_check)], I32),
+        "pcsir3_batch_create": ([ctypes.POINTER(pcsir3_target), I32, I32, ctypes.POINTER(ctypes.c_void_p)], I32),
+        "pcsir3_batch_destroy": ([P], I32),
+        "pcsir3_batch_last_error": ([P], ctypes.c_char_p),
+        "pcsir3_batched_step": ([P, P, P, I32, I32, I32, P, P, P], I32),
+        "pcsir3_batch_results": ([P, ctypes.POINTER(pcsir3_result), I32, ctypes.POINTER(ctypes.c_int32)], I32),
+        "pcsir3_batch_get_outputs": ([P, ctypes.POINTER(pcsir3_batch_outputs)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -723,3 +742,72 @@ class Context3:
         if o.loglik:
             out["loglik"] = view(o.loglik, (N,), torch.float64)
         return out
+
+
+class Batch3:
+    """Owns one ``pcsir3_batch``: T targets in one 3D volume (state [7, sum N] float32)."""
+
+    def __init__(self, n, h, psf_sigma_xy, psf_sigma_z, bg, patch_xy, patch_z, keep=0):
+        T = len(n)
+        arr = (pcsir3_target * T)()
+        for t in range(T):
+            hx, hy, hz = (float(v) for v in h[t])
+            arr[t] = pcsir3_target(int(n[t]), hx, hy, hz, float(psf_sigma_xy[t]), float(psf_sigma_z[t]),
+                                   float(bg[t]), int(patch_xy[t]), int(patch_z[t]))
+        hdl = ctypes.c_void_p()
+        st = lib.pcsir3_batch_create(arr, T, int(keep), ctypes.byref(hdl))
+        if st != OK:
+            raise PcsirError(st, "pcsir3_batch_create failed")
+        self.handle = hdl
+        self.T = T
+        self.n_total = int(sum(int(x) for x in n))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pcsir3_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, state, volume, noise, u0, stream=None):
+        """One step of every target (state [7, sum N] float32 in place; u0 float64 [T] on the device)."""
+        _check_cuda(state, "state", torch.float32)
+        _check_cuda(noise, "noise", torch.float32)
+        _check_cuda(volume, "volume", torch.float32)
+        _check_cuda(u0, "u0", torch.float64)
+        D, H, W = volume.shape
+        st = lib.pcsir3_batched_step(self.handle, _ptr(state), _ptr(volume), W, H, D, _ptr(noise), _ptr(u0),
+                                     _stream_ptr(stream))
+        if st != OK:
+            raise PcsirError(st, lib.pcsir3_batch_last_error(self.handle).decode())
+
+    def results(self):
+        """Per-target results of the last step and the step's device error flags (synchronises)."""
+        arr = (pcsir3_result * self.T)()
+        err = ctypes.c_int32()
+        st = lib.pcsir3_batch_results(self.handle, arr, self.T, ctypes.byref(err))
+        if st != OK:
+            raise PcsirError(st, "pcsir3_batch_results failed")
+        return [dict(estimate=list(r.estimate), ess=r.ess, n_bins=r.n_bins, n_particles=r.n_particles,
+                     max_loglik=r.max_loglik, device_error=r.device_error) for r in arr], err.value
+
+    def outputs(self):
+        o = pcsir3_batch_outputs()
+        st = lib.pcsir3_batch_get_outputs(self.handle, ctypes.byref(o))
+        if st != OK:
+            raise PcsirError(st, "pcsir3_batch_get_outputs failed")
+        N, B, S = o.n_total, o.n_bins, o.bin_stride
+
+        def view(ptr, shape, dtype):
+            return _from_ptr(ptr, shape, dtype) if ptr else None
+
+        return dict(prop_state=view(o.prop_state, (7, N), torch.float32), n_bins=B,
+                    bin_key=view(o.bin_key, (B,), torch.int64) if B else None,
+                    bin_count=view(o.bin_count, (B,), torch.int32) if B else None,
+                    dummy=view(o.dummy, (7, S), torch.float64)[:, :B] if B else None,
+                    bin_loglik=view(o.bin_loglik, (B,), torch.float64) if B else None,
+                    ancestor=view(o.ancestor, (N,), torch.int32), qweight=view(o.qweight, (N,), torch.int64))

@@ -336,3 +336,79 @@ def initial_state3(gt0, N: int, dtype=np.float32) -> np.ndarray:
     for d in range(D3):
         st[d, :] = gt0[d]
     return st
+
+
+@dataclasses.dataclass
+class Batch3:
+    """Many independent targets in one 3D volume sequence."""
+
+    n: np.ndarray          # [T] particles per target
+    sigma_xy: np.ndarray   # [T] lateral PSF std per target
+    sigma_z: np.ndarray    # [T] axial PSF std per target
+    i0: np.ndarray         # [T] peak intensity per target
+    bg: np.ndarray         # [T] background per target (one shared background)
+    patch_xy: np.ndarray   # [T] odd lateral patch side
+    patch_z: np.ndarray    # [T] odd axial patch side
+    h: np.ndarray          # [T, 3] cell edges per target
+    gt: np.ndarray         # [K+1, T, 7] ground-truth states
+    images: np.ndarray     # [K, D, H, W] float32 Poisson volumes with every target's spot
+
+
+def make_batch3(T: int, W: int, H: int, D: int, n_frames: int, seed: int, n_values=None, n_particles: int = 200_000,
+                sigma_xy: float = 1.5, sigma_z: float = 3.0, i0: float = 100.0, bg: float = 10.0,
+                patch_xy: int = 11, patch_z: int = 7, h=(0.5, 0.5, 1.0), min_sep: float = 10.0,
+                margin_xy: float = 10.0, margin_z: float = 5.0, q=Q3) -> Batch3:
+    """3D multi-target workload: spot centres by dart throwing with a minimum separation inside the
+    margins, slow nearly-constant-velocity tracks (speed U[0.05, 0.3] voxel/frame), one shared
+    Poisson volume per frame (every spot rendered within 4 PSF stds of its centre, plus the
+    background)."""
+    rng = np.random.default_rng([seed, 0xB3D])
+    lo = np.array([margin_xy, margin_xy, margin_z])
+    hi = np.array([W - 1 - margin_xy, H - 1 - margin_xy, D - 1 - margin_z])
+    pos = []
+    for _ in range(T * 500):
+        if len(pos) == T:
+            break
+        p = rng.uniform(lo, hi)
+        if all(np.sum((p - a) ** 2) >= min_sep ** 2 for a in pos):
+            pos.append(p)
+    if len(pos) < T:
+        raise ValueError("cannot place %d targets with separation %g in %dx%dx%d" % (T, min_sep, W, H, D))
+    n = np.full(T, n_particles, np.int64) if n_values is None else np.asarray(n_values, np.int64)
+    gt = np.zeros((n_frames + 1, T, D3))
+    v = rng.normal(size=(T, 3))
+    v *= (rng.uniform(0.05, 0.3, T) / np.linalg.norm(v, axis=1))[:, None]
+    gt[0, :, 0:3] = np.array(pos)
+    gt[0, :, 3:6] = v
+    gt[0, :, 6] = i0
+    for k in range(n_frames):
+        s = gt[k].copy()
+        s[:, 0:3] += s[:, 3:6]
+        s[:, 3:6] += rng.normal(size=(T, 3)) * np.asarray(q[3:6]) * 0.1
+        gt[k + 1] = s
+    images = np.empty((n_frames, D, H, W), dtype=np.float32)
+    rxy, rz = int(np.ceil(4 * sigma_xy)), int(np.ceil(4 * sigma_z))
+    for k in range(n_frames):
+        lam = np.full((D, H, W), bg)
+        for t in range(T):
+            x0, y0, z0, a = gt[k + 1, t, 0], gt[k + 1, t, 1], gt[k + 1, t, 2], gt[k + 1, t, 6]
+            cx, cy, cz = int(round(x0)), int(round(y0)), int(round(z0))
+            xa, xb = max(0, cx - rxy), min(W, cx + rxy + 1)
+            ya, yb = max(0, cy - rxy), min(H, cy + rxy + 1)
+            za, zb = max(0, cz - rz), min(D, cz + rz + 1)
+            gx = np.exp(-((np.arange(xa, xb) - x0) ** 2) / (2 * sigma_xy ** 2))
+            gy = np.exp(-((np.arange(ya, yb) - y0) ** 2) / (2 * sigma_xy ** 2))
+            gz = np.exp(-((np.arange(za, zb) - z0) ** 2) / (2 * sigma_z ** 2))
+            lam[za:zb, ya:yb, xa:xb] += a * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+        images[k] = rng.poisson(lam).astype(np.float32)
+    full = lambda v_: np.full(T, v_)
+    return Batch3(n=n, sigma_xy=full(float(sigma_xy)), sigma_z=full(float(sigma_z)), i0=full(float(i0)),
+                  bg=full(float(bg)), patch_xy=full(int(patch_xy)).astype(np.int64),
+                  patch_z=full(int(patch_z)).astype(np.int64), h=np.tile(np.asarray(h, np.float64), (T, 1)),
+                  gt=gt, images=images)
+
+
+def batch3_initial_state(batch: Batch3, dtype=np.float32) -> np.ndarray:
+    """Concatenated [7, sum N_t] state with each target's particles at its ground truth."""
+    parts = [initial_state3(batch.gt[0, t], int(batch.n[t]), dtype) for t in range(len(batch.n))]
+    return np.ascontiguousarray(np.concatenate(parts, axis=1))

@@ -49,6 +49,8 @@ def test_struct_layout_matches_header(binding, tmp_path):
         "pcsir3_config": [f[0] for f in binding.pcsir3_config._fields_],
         "pcsir3_result": [f[0] for f in binding.pcsir3_result._fields_],
         "pcsir3_outputs": [f[0] for f in binding.pcsir3_outputs._fields_],
+        "pcsir3_target": [f[0] for f in binding.pcsir3_target._fields_],
+        "pcsir3_batch_outputs": [f[0] for f in binding.pcsir3_batch_outputs._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcsir.h"', '#include "pcsir_surrogate.h"', '#include "pcsir3.h"',
              "int main(void){", 'printf("NPARAMS %d\\n", PCSIR_SUR_NPARAMS);']
@@ -92,6 +94,23 @@ def test_invalid_configs_rejected_on_host(binding):
     assert lib.pcsir_batch_set_wait(None, 100, -1) == binding.EINVAL
     assert lib.pcsir_batch_keep(None, 1) == binding.EINVAL
     assert lib.pcsir_batch_kept(None, None, None) == binding.EINVAL
+
+
+def test_invalid_batched3_targets_rejected_on_host(binding):
+    lib = binding.lib
+    good = dict(n_particles=100, hx=0.5, hy=0.5, hz=1.0, psf_sigma_xy=1.5, psf_sigma_z=3.0, bg=10.0,
+                patch_xy=11, patch_z=7)
+    for upd in [dict(n_particles=0), dict(hx=0.0), dict(hz=9.0), dict(psf_sigma_z=0.0), dict(bg=0.0),
+                dict(patch_xy=10), dict(patch_z=65)]:
+        arr = (binding.pcsir3_target * 1)(binding.pcsir3_target(**{**good, **upd}))
+        h = ctypes.c_void_p(123)
+        assert lib.pcsir3_batch_create(arr, 1, 0, ctypes.byref(h)) == binding.EINVAL, upd
+        assert not h.value
+    arr = (binding.pcsir3_target * 1)(binding.pcsir3_target(**good))
+    h = ctypes.c_void_p()
+    assert lib.pcsir3_batch_create(arr, 0, 0, ctypes.byref(h)) == binding.EINVAL
+    assert lib.pcsir3_batch_create(arr, 1, 2, ctypes.byref(h)) == binding.EINVAL  # weights are not kept
+    assert lib.pcsir3_batch_destroy(None) == binding.OK
 
 
 def test_noalloc_binding_rejects_operands_it_cannot_use(binding):
