@@ -297,6 +297,7 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
     u0 = torch.from_numpy(np.stack([synth.batch_u0(T, seed, k) for k in range(frames)])).to(dev)
     state = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).to(dev)
     bt = pcsir.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    bt.set_table(int(table.get("table_bits", 10)))
     bt.set_grid(int(table.get("blocks_per_sm", 2)))
     s = torch.cuda.Stream()
     graphs = []
@@ -330,7 +331,9 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
             "value": ntot * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "targets": T, "particles": ntot, "cells_last_step": int(sum(r["n_bins"] for r in res)),
             "launches_per_step": 1, "graph": True, "rmse_px": rmse,
-            "device_error": derr, "autotune": {"c": table.get("c"), "blocks_per_sm": table.get("blocks_per_sm")},
+            "device_error": derr,
+            "autotune": {k: table.get(k) for k in ("c", "blocks_per_sm", "table_bits", "rmse", "rmse_limit",
+                                                   "first_c_over_limit", "step_ms")},
             "phase_ms_last_step": dict(zip(("setup", "prop_bin", "bins_lik", "weights", "tile_sums", "target_scan",
                                             "resample"), phases))}
 

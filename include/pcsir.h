@@ -359,6 +359,14 @@ pcsir_status pcsir_batch_destroy(pcsir_batch* batch);
    Errors: PCSIR_EINVAL, PCSIR_ERANGE (more than fit), PCSIR_ECUDA. */
 pcsir_status pcsir_batch_set_grid(pcsir_batch* batch, int32_t blocks_per_sm);
 
+/* Size of the persistent kernel's block-private cell table: 2^table_bits
+   slots, table_bits in 9 .. 11 (default 10), a launch-shape knob for the
+   autotuner (results do not depend on it).  A larger table holds more cells
+   before a block spills to the global table but takes more shared memory
+   (2^11: one block per SM); the grid shrinks to what fits.  Errors:
+   PCSIR_EINVAL, PCSIR_ERANGE, PCSIR_ECUDA. */
+pcsir_status pcsir_batch_set_table(pcsir_batch* batch, int32_t table_bits);
+
 /* One step of every target.  state: device float32 [5][sum n_t], read-write
    (resampled in place per target); image: device float32 [H][W]; noise:
    device float32 [5][sum n_t] process noise (Section 5.1); u0: device float64
@@ -372,8 +380,8 @@ pcsir_status pcsir_batched_step(pcsir_batch* batch, float* state, const float* i
                                 const float* noise, const double* u0, void* stream);
 
 /* Results of the last step, one per target (out: host array of T), and the
-   step's PCSIR_DERR_* flags (device_error may be NULL; reading them
-   synchronises the device).  Returns PCSIR_ETIMEDOUT (with out and
+   step's PCSIR_DERR_* flags (device_error may be NULL).  Synchronises the
+   device first, so the results are those of the last step enqueued.  Returns PCSIR_ETIMEDOUT (with out and
    *device_error filled) when the flags hold PCSIR_DERR_TIMEOUT: a grid-barrier
    wait of the step gave up, every block left the kernel, and the step's
    results are invalid.  The batch stays usable: the next step first clears

@@ -157,9 +157,9 @@ const char* pcsir3_batch_last_error(pcsir3_batch* batch);
 pcsir_status pcsir3_batched_step(pcsir3_batch* batch, float* state, const float* volume, int32_t W, int32_t H,
                                  int32_t D, const float* noise, const double* u0, void* stream);
 
-/* Results of the last step, one per target (host array of T; synchronise the
-   step's stream first), and the step's PCSIR_DERR_* flags (device_error may
-   be NULL; reading them synchronises the device). */
+/* Results of the last step, one per target (host array of T), and the step's
+   PCSIR_DERR_* flags (device_error may be NULL).  Synchronises the device
+   first, so the results are those of the last step enqueued. */
 pcsir_status pcsir3_batch_results(pcsir3_batch* batch, pcsir3_result* out, int32_t T, int32_t* device_error);
 
 /* Intermediates of the last step (synchronises the device).  Errors:

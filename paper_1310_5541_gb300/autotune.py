@@ -3,11 +3,13 @@
 The cell edge h trades accuracy for speed (Section 4.2: the piecewise-constant
 likelihood converges to SIR's as h shrinks; larger cells mean fewer dummies).
 For each PSF width the tuner runs the GPU filter on a short synthetic
-sequence with h = c * sigma for several c and keeps the largest c whose
-tracking RMSE stays within ``tol`` of the finest c's (the "matched RMSE"
-criterion), then times the persistent kernel with each number of blocks per
-SM and keeps the fastest.  Results are cached as JSON; ``cell_edges`` reads
-the cache and falls back to h = sigma / 3.
+sequence with h = c * sigma for c from 1/8 up to 4 (cells of 4 PSF widths,
+where the criterion is sure to bind) and keeps the largest c whose tracking
+RMSE stays within ``tol`` of the finest c's (the "matched RMSE" criterion).
+It then times the persistent kernel on the full multi-target workload for
+every launch shape: blocks per SM (1, 2) and the size of each block's cell
+table (2^9, 2^10, 2^11 slots), and keeps the fastest.  Results are cached as
+JSON; ``cell_edges`` reads the cache and falls back to h = sigma / 3.
 """
 from __future__ import annotations
 
@@ -18,7 +20,9 @@ import time
 import numpy as np
 
 DEFAULT_C = 1.0 / 3.0
-CANDIDATES = (1.0 / 8.0, 1.0 / 6.0, 1.0 / 4.0, 1.0 / 3.0, 1.0 / 2.0, 1.0)
+CANDIDATES = (1.0 / 8.0, 1.0 / 6.0, 1.0 / 4.0, 1.0 / 3.0, 1.0 / 2.0, 2.0 / 3.0, 1.0, 1.5, 2.0, 3.0, 4.0)
+TABLE_BITS = (9, 10, 11)
+BLOCKS_PER_SM = (1, 2)
 
 
 def cache_path():
@@ -44,7 +48,7 @@ def cell_edges(sigma, table=None):
 def _track_rmse(pcsir, synth, c, n_targets, frames, seed, n_particles):
     import torch
 
-    batch = synth.make_batch(n_targets, 256, 256, frames, seed, n_values=[n_particles] * n_targets, min_sep=40.0)
+    batch = synth.make_batch(n_targets, 512, 512, frames, seed, n_values=[n_particles] * n_targets, min_sep=32.0)
     batch.h[:] = np.clip(batch.sigma * c, 0.02, 8.0)
     st = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
     bt = pcsir.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
@@ -60,8 +64,9 @@ def _track_rmse(pcsir, synth, c, n_targets, frames, seed, n_particles):
     return float(np.sqrt(np.mean(err)))
 
 
-def tune(tol=0.05, n_targets=16, frames=12, n_particles=20000, seed=1310554400, write=True, verbose=False):
-    """Pick the cell-edge multiplier and the blocks per SM; returns (and caches) the table."""
+def tune(tol=0.05, n_targets=24, frames=16, n_particles=20000, seed=1310554400, write=True, verbose=False,
+         shape_targets=1000):
+    """Pick the cell-edge multiplier and the launch shape; returns (and caches) the table."""
     import torch
 
     from paper_1310_5541_gb300 import pcsir, synth
@@ -70,32 +75,42 @@ def tune(tol=0.05, n_targets=16, frames=12, n_particles=20000, seed=1310554400, 
     finest = rmse[min(CANDIDATES)]
     ok = [c for c in CANDIDATES if rmse[c] <= (1.0 + tol) * finest]
     c_best = max(ok)
-    # launch shape: time the persistent step with each number of blocks per SM
-    batch = synth.make_batch(64, 1024, 1024, 4, seed + 1)
-    batch.h[:] = np.clip(batch.sigma * c_best, 0.02, 8.0)
-    st = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
+    above = [c for c in CANDIDATES if c > c_best]
+    # launch shape on the full multi-target workload (log-uniform particle counts, 1024 x 1024)
+    batch = synth.make_batch(shape_targets, 1024, 1024, 1, seed + 1)
+    batch.h[:] = cell_edges(batch.sigma, {"c": c_best})
+    T = len(batch.n)
+    st0 = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
     nz = torch.from_numpy(synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), seed, 0)).cuda()
     img = torch.from_numpy(batch.images[0]).cuda()
-    u0 = torch.from_numpy(synth.batch_u0(64, seed, 0)).cuda()
+    u0 = torch.from_numpy(synth.batch_u0(T, seed, 0)).cuda()
     bt = pcsir.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
     times = {}
-    for bps in (1, 2):
-        try:
-            bt.set_grid(bps)
-        except pcsir.PcsirError:
-            continue
-        for _ in range(2):
-            bt.step(st, img, nz, u0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(5):
-            bt.step(st, img, nz, u0)
-        torch.cuda.synchronize()
-        times[bps] = (time.perf_counter() - t0) / 5
+    for bits in TABLE_BITS:
+        for bps in BLOCKS_PER_SM:
+            try:
+                bt.set_table(bits)
+                bt.set_grid(bps)
+            except pcsir.PcsirError:
+                continue
+            st = st0.clone()
+            for _ in range(3):  # resampled clouds, as in a running filter
+                bt.step(st, img, nz, u0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(5):
+                bt.step(st, img, nz, u0)
+            b.record()
+            torch.cuda.synchronize()
+            times["%d/%d" % (bits, bps)] = a.elapsed_time(b) / 5
     bt.close()
-    table = {"c": c_best, "blocks_per_sm": min(times, key=times.get) if times else 2,
-             "rmse": {str(k): v for k, v in rmse.items()}, "step_s": {str(k): v for k, v in times.items()},
-             "tol": tol}
+    best = min(times, key=times.get) if times else "10/2"
+    bits_best, bps_best = (int(x) for x in best.split("/"))
+    table = {"c": c_best, "blocks_per_sm": bps_best, "table_bits": bits_best,
+             "rmse": {str(k): v for k, v in rmse.items()}, "rmse_limit": (1.0 + tol) * finest,
+             "first_c_over_limit": min(above) if above else None,
+             "step_ms": times, "shape_particles": int(batch.n.sum()), "tol": tol}
     if verbose:
         print(json.dumps(table, indent=1))
     if write:

@@ -105,9 +105,10 @@ struct BatchBufs {
 constexpr int BT_THREADS = 512;
 constexpr int BT_PER_THREAD = 4;
 constexpr int BT_CHUNK = BT_THREADS * BT_PER_THREAD;
-constexpr int BT_LT_BITS = 10;
-constexpr int BT_LT = 1 << BT_LT_BITS;
-constexpr unsigned BT_LT_CAP = 768;
+// the block-private cell table has 2^LTB slots (a kernel variant per LTB, chosen at run time by
+// the autotuner) and takes new cells until three quarters of them are used
+constexpr int BT_LTB_DEFAULT = 10;
+constexpr int BT_LTB_MIN = 9, BT_LTB_MAX = 11;
 constexpr int BT_PIECE_BITS = 18;
 constexpr unsigned BT_PIECE_MASK = (1u << BT_PIECE_BITS) - 1u;
 constexpr int BT_FLUSH = 1 << 14;
@@ -130,11 +131,14 @@ __device__ __forceinline__ int bkey_t(unsigned long long k) { return (int)(k >> 
 __device__ __forceinline__ int bkey_by(unsigned long long k) { return (int)((k >> 26) & 0x3ffffffu) - (1 << 25); }
 __device__ __forceinline__ int bkey_bx(unsigned long long k) { return (int)(k & 0x3ffffffu) - (1 << 25); }
 
+template <int LTB>
 struct BatchLocal {
-  unsigned long long key[BT_LT];
-  unsigned int acc[BT_NACC][BT_LT];
-  unsigned int gslot[BT_LT];
-  unsigned short list[BT_LT];
+  static constexpr int LT = 1 << LTB;
+  static constexpr unsigned CAP = 3u << (LTB - 2);
+  unsigned long long key[LT];
+  unsigned int acc[BT_NACC][LT];
+  unsigned int gslot[LT];
+  unsigned short list[LT];
   unsigned int nlist;
   unsigned int fill;
 };
@@ -145,9 +149,15 @@ struct BatchResampleSmem {
   long long s_lo, s_hi;
 };
 
-constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t BT_SMEM_UNION = cmax(sizeof(BatchLocal), sizeof(BatchResampleSmem));
-constexpr size_t BT_SMEM = BT_SMEM_UNION + sizeof(long long) * (BT_MAX_TARGETS + 1);
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+template <int LTB>
+__host__ __device__ constexpr size_t bt_smem_union() {
+  return cmax(sizeof(BatchLocal<LTB>), sizeof(BatchResampleSmem));
+}
+template <int LTB>
+constexpr size_t bt_smem() {
+  return bt_smem_union<LTB>() + sizeof(long long) * (BT_MAX_TARGETS + 1);
+}
 
 // ---------------------------------------------------------------------------
 // bounded grid-wide barrier (all blocks are co-resident: cooperative launch).  Barrier k
@@ -156,7 +166,7 @@ constexpr size_t BT_SMEM = BT_SMEM_UNION + sizeof(long long) * (BT_MAX_TARGETS +
 // up after b.bar_spins polls: it raises PCSIR_DERR_TIMEOUT, the abort flag (every block then
 // leaves at its next poll or barrier) and the dirty mark of the cell table.
 // ---------------------------------------------------------------------------
-__device__ bool grid_barrier(const BatchBufs& b, int k) {
+__device__ __noinline__ bool grid_barrier(const BatchBufs& b, int k) {
   __shared__ unsigned s_ok;
   BatchCtl* c = b.ctl;
   __syncthreads();
@@ -212,14 +222,16 @@ __device__ unsigned bglobal_insert(const BatchBufs& b, unsigned long long key) {
   return 0;
 }
 
-__device__ int blocal_insert(BatchLocal& t, unsigned long long key, bool& created) {
+template <int LTB>
+__device__ int blocal_insert(BatchLocal<LTB>& t, unsigned long long key, bool& created) {
+  constexpr int LT = BatchLocal<LTB>::LT;
   created = false;
-  unsigned h = hash_bits(key, BT_LT_BITS);
-  for (int probe = 0; probe < BT_LT; ++probe) {
+  unsigned h = hash_bits(key, LTB);
+  for (int probe = 0; probe < LT; ++probe) {
     const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
     if (k == key) return (int)h;
     if (k == EMPTY_KEY) {
-      if (atomicAdd(&t.fill, 1u) >= BT_LT_CAP) return -1;
+      if (atomicAdd(&t.fill, 1u) >= BatchLocal<LTB>::CAP) return -1;
       const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
       if (old == EMPTY_KEY) {
         created = true;
@@ -228,12 +240,13 @@ __device__ int blocal_insert(BatchLocal& t, unsigned long long key, bool& create
       }
       if (old == key) return (int)h;
     }
-    h = (h + 1u) & (BT_LT - 1u);
+    h = (h + 1u) & (LT - 1u);
   }
   return -1;
 }
 
-__device__ void blocal_flush(BatchLocal& t, const BatchBufs& b, bool clear_keys) {
+template <int LTB>
+__device__ void blocal_flush(BatchLocal<LTB>& t, const BatchBufs& b, bool clear_keys) {
   const size_t hcap = size_t(1) << b.hbits;
   const unsigned n = t.nlist;
   for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
@@ -286,12 +299,13 @@ __device__ __forceinline__ int target_of(const long long* offs, int T, long long
 // ---------------------------------------------------------------------------
 // Phase A: propagate, cell, centre-of-mass sums (cf. k_prop_bin)
 // ---------------------------------------------------------------------------
+template <int LTB>
 __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st, const float* __restrict__ nz,
-                               BatchLocal& tab, const long long* offs) {
+                               BatchLocal<LTB>& tab, const long long* offs) {
   const long long N = b.ntot;
   const long long P = b.pstride;
   const size_t hcap = size_t(1) << b.hbits;
-  for (int j = threadIdx.x; j < BT_LT; j += blockDim.x) {
+  for (int j = threadIdx.x; j < BatchLocal<LTB>::LT; j += blockDim.x) {
     tab.key[j] = EMPTY_KEY;
 #pragma unroll
     for (int a = 0; a < BT_NACC; ++a) tab.acc[a][j] = 0u;
@@ -451,7 +465,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     if (vec) *reinterpret_cast<uint4*>(b.pslot + i0) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
     since_flush += BT_CHUNK;
     __syncthreads();
-    const bool full = tab.fill >= BT_LT_CAP;
+    const bool full = tab.fill >= BatchLocal<LTB>::CAP;
     if (full || since_flush + BT_CHUNK > BT_FLUSH) {
       blocal_flush(tab, b, full);
       since_flush = 0;
@@ -734,11 +748,12 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
   }
 }
 
+template <int LTB>
 __global__ void __launch_bounds__(BT_THREADS, 2)
 k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restrict__ nz, float* __restrict__ out,
                const float* __restrict__ img, int W, int H, const double* __restrict__ u0s) {
   extern __shared__ __align__(16) unsigned char bt_smem[];
-  long long* offs = reinterpret_cast<long long*>(bt_smem + BT_SMEM_UNION);
+  long long* offs = reinterpret_cast<long long*>(bt_smem + bt_smem_union<LTB>());
   stamp(b.ctl, 0);
   // a step whose barrier wait ran out may have left cells in the table: clear all of it first
   // (ordered before every table access by the first barrier, after which block 0 lifts the mark)
@@ -762,7 +777,7 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   if (!grid_barrier(b, 0)) return;
   if (was_dirty && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(b.dirty, 0u);
   stamp(b.ctl, 1);
-  phase_prop_bin(b, st, nz, *reinterpret_cast<BatchLocal*>(bt_smem), offs);
+  phase_prop_bin<LTB>(b, st, nz, *reinterpret_cast<BatchLocal<LTB>*>(bt_smem), offs);
   if (!grid_barrier(b, 1)) return;
   stamp(b.ctl, 2);
   phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
@@ -795,6 +810,21 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   stamp(b.ctl, 7);
 }
 
+// the kernel variant of a cell-table size and its dynamic shared memory
+const void* bt_kernel(int ltb) {
+  switch (ltb) {
+    case 9: return reinterpret_cast<const void*>(k_batched_step<9>);
+    case 11: return reinterpret_cast<const void*>(k_batched_step<11>);
+    default: return reinterpret_cast<const void*>(k_batched_step<10>);
+  }
+}
+size_t bt_smem_bytes(int ltb) {
+  return ltb == 9 ? bt_smem<9>() : (ltb == 11 ? bt_smem<11>() : bt_smem<10>());
+}
+cudaError_t bt_blocks_per_sm(int ltb, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bt_kernel(ltb), BT_THREADS, bt_smem_bytes(ltb));
+}
+
 }  // namespace pcsir
 
 // ---------------------------------------------------------------------------
@@ -807,6 +837,7 @@ struct pcsir_batch {
   long long ntot = 0;
   int ntiles = 0;
   int grid = 0;
+  int ltb = BT_LTB_DEFAULT;  // cell-table bits of the kernel variant
   BatchBufs b{};
   std::vector<void*> allocs;
   pcsir_result* host_res = nullptr;
@@ -921,14 +952,13 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   if (e == cudaSuccess) e = cudaMemset(b.hsum, 0, 5 * hcap * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(b.dirty, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result) * T);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_batched_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_SMEM);
+  for (int ltb = BT_LTB_MIN; ltb <= BT_LTB_MAX && e == cudaSuccess; ++ltb)
+    e = cudaFuncSetAttribute(bt_kernel(ltb), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem_bytes(ltb));
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, BT_THREADS, BT_SMEM);
+  if (e == cudaSuccess) e = bt_blocks_per_sm(BT_LTB_DEFAULT, &per_sm);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess || !coop || per_sm < 1) {
     cudaGetLastError();
@@ -946,10 +976,23 @@ pcsir_status pcsir_batch_set_grid(pcsir_batch* c, int32_t blocks_per_sm) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, BT_THREADS, BT_SMEM);
+  if (e == cudaSuccess) e = bt_blocks_per_sm(c->ltb, &per_sm);
   if (e != cudaSuccess) return PCSIR_ECUDA;
   if (blocks_per_sm > per_sm) return PCSIR_ERANGE;
   c->grid = sms * blocks_per_sm;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batch_set_table(pcsir_batch* c, int32_t table_bits) {
+  if (!c || table_bits < BT_LTB_MIN || table_bits > BT_LTB_MAX) return PCSIR_EINVAL;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = bt_blocks_per_sm(table_bits, &per_sm);
+  if (e != cudaSuccess) return PCSIR_ECUDA;
+  if (per_sm < 1) return PCSIR_ERANGE;
+  c->ltb = table_bits;
+  if (c->grid > sms * per_sm) c->grid = sms * per_sm;  // the larger table fits fewer blocks per SM
   return PCSIR_OK;
 }
 
@@ -981,7 +1024,8 @@ pcsir_status pcsir_batched_step(pcsir_batch* c, float* state, const float* image
     int w = W, h = H;
     const double* u0s = u0;
     void* args[] = {&b, &st_in, &nz, &out, &img, &w, &h, &u0s};
-    e = cudaLaunchCooperativeKernel((const void*)k_batched_step, dim3(c->grid), dim3(BT_THREADS), args, BT_SMEM, s);
+    e = cudaLaunchCooperativeKernel(bt_kernel(c->ltb), dim3(c->grid), dim3(BT_THREADS), args, bt_smem_bytes(c->ltb),
+                                    s);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->host_res, b.res, sizeof(pcsir_result) * c->T, cudaMemcpyDeviceToHost, s);
@@ -995,6 +1039,11 @@ pcsir_status pcsir_batched_step(pcsir_batch* c, float* state, const float* image
 
 pcsir_status pcsir_batch_results(pcsir_batch* c, pcsir_result* out, int32_t T, int32_t* device_error) {
   if (!c || !out || T != c->T) return PCSIR_EINVAL;
+  // the step's copy of the results to page-locked memory is asynchronous: wait for it
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return PCSIR_ECUDA;
+  }
   std::memcpy(out, c->host_res, sizeof(pcsir_result) * T);
   if (device_error) {
     BatchCtl ctl;

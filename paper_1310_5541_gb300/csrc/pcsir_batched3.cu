@@ -738,6 +738,11 @@ pcsir_status pcsir3_batched_step(pcsir3_batch* c, float* state, const float* vol
 
 pcsir_status pcsir3_batch_results(pcsir3_batch* c, pcsir3_result* out, int32_t T, int32_t* device_error) {
   if (!c || !out || T != c->T) return PCSIR_EINVAL;
+  // the step's copy of the results to page-locked memory is asynchronous: wait for it
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return PCSIR_ECUDA;
+  }
   std::memcpy(out, c->host_res, sizeof(pcsir3_result) * T);
   if (device_error) {
     Control ctl;

@@ -146,6 +146,7 @@ def _load():
         "pcsir_batch_last_error": ([P], ctypes.c_char_p),
         "pcsir_batch_phase_times": ([P, ctypes.POINTER(ctypes.c_double), I32], I32),
         "pcsir_batch_set_wait": ([P, I32, I32], I32),
+        "pcsir_batch_set_table": ([P, I32], I32),
         "pcsir_batch_keep": ([P, I32], I32),
         "pcsir_batch_kept": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_gemm_bf16": ([P, I64, I64, P, I64, I64, P, I64, I32, I32, I32, I32, P], I32),
@@ -475,6 +476,12 @@ class Batch:
         st = lib.pcsir_batch_set_grid(self.handle, int(blocks_per_sm))
         if st != OK:
             raise PcsirError(st, "pcsir_batch_set_grid failed")
+
+    def set_table(self, table_bits):
+        """2^table_bits slots in each block's cell table (9 .. 11; results do not depend on it)."""
+        st = lib.pcsir_batch_set_table(self.handle, int(table_bits))
+        if st != OK:
+            raise PcsirError(st, "pcsir_batch_set_table failed")
 
     def set_wait(self, max_polls=1 << 22, unreachable_barrier=-1):
         """Bound of each grid-barrier wait, and a barrier made unreachable (tests of the timeout)."""

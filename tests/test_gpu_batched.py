@@ -271,3 +271,36 @@ def test_batched_barrier_wait_runs_out_and_the_batch_recovers(pc, barrier):
     mism = _compare(pc, batch, st, 1, SEED + 42, bt=bt)
     print("after a timed-out step at barrier %d: ancestors differing from the oracle's %d" % (barrier, mism))
     bt.close()
+
+
+def test_batched_cell_table_size_does_not_change_the_step(pc):
+    """The autotuner's cell-table sizes (2^9, 2^10, 2^11 slots per block) and grids give the same step:
+    new states and cell counts identical, posterior means equal up to the FP64 atomics' order."""
+    n = [3000, 9000, 4097, 600, 15000]
+    batch = synth.make_batch(len(n), 256, 256, 1, seed=SEED + 50, n_values=n, min_sep=30.0)
+    batch.h[:] = [0.25, 0.5, 1.0, 0.1, 0.2]
+    st = synth.batch_initial_state(batch, np.float32)
+    nz = torch.from_numpy(synth.batch_noise(batch, (0.5, 0.5, 0.1, 0.1, 1.0), SEED + 51, 0)).cuda()
+    u0 = torch.from_numpy(synth.batch_u0(len(n), SEED + 51, 0)).cuda()
+    img = torch.from_numpy(batch.images[0]).cuda()
+    outs = []
+    for bits, bps in ((10, 2), (9, 2), (11, 1), (9, 1)):
+        bt = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+        bt.set_table(bits)
+        bt.set_grid(bps)
+        d = torch.from_numpy(st.copy()).cuda()
+        bt.step(d, img, nz, u0)
+        torch.cuda.synchronize()
+        res, derr = bt.results()
+        assert derr == 0
+        o = bt.outputs()
+        keys = o["bin_key"].cpu().numpy()
+        order = np.argsort(keys)
+        outs.append((d.cpu().numpy(), keys[order], o["bin_count"].cpu().numpy()[order],
+                     np.array([r["estimate"] for r in res])))
+        bt.close()
+    for other in outs[1:]:
+        np.testing.assert_array_equal(outs[0][0], other[0])
+        np.testing.assert_array_equal(outs[0][1], other[1])
+        np.testing.assert_array_equal(outs[0][2], other[2])
+        np.testing.assert_allclose(outs[0][3], other[3], rtol=1e-12)
