@@ -43,7 +43,10 @@ k_prop_bin3(StepBuffers b, const float* __restrict__ st, const float* __restrict
 #pragma unroll
     for (int a = 0; a < NACC3; ++a) tab.acc[a][j] = 0u;
   }
-  if (threadIdx.x == 0) tab.fill = 0u;
+  if (threadIdx.x == 0) {
+    tab.fill = 0u;
+    tab.hot = 0u;
+  }
   long long anc[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) anc[c] = to_fixed(st[(3 + c) * N], 4194304.0f);
@@ -56,7 +59,6 @@ k_prop_bin3(StepBuffers b, const float* __restrict__ st, const float* __restrict
   const float hh[3] = {hx, hy, hz};
   const long long hq[3] = {hqx, hqy, hqz};
   const int64_t nchunks = (N + P3_CHUNK - 1) / P3_CHUNK;
-  int since_flush = 0;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t base = chunk * P3_CHUNK;
     float v[P3_PER_THREAD][NS3];
@@ -119,7 +121,7 @@ k_prop_bin3(StepBuffers b, const float* __restrict__ st, const float* __restrict
       if (ls[k] >= 0) {
         const int s = ls[k];
         g = tab.gslot[s];
-        atomicAdd(&tab.acc[0][s], 1u);
+        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == P3_HOT_AT) tab.hot = 1u;
 #pragma unroll
         for (int c = 0; c < NS3; ++c) {
           atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & P3_PIECE_MASK));
@@ -134,12 +136,12 @@ k_prop_bin3(StepBuffers b, const float* __restrict__ st, const float* __restrict
       }
       b.pslot[i] = g;
     }
-    since_flush += P3_CHUNK;
     __syncthreads();
     const bool full = tab.fill >= L3_CAP;
-    if (full || since_flush + P3_CHUNK > P3_FLUSH) {
+    if (full || tab.hot != 0u) {
       local_flush3(tab, b, full);
-      since_flush = 0;
+      // ordered before any count of the next chunk by that chunk's block barrier
+      if (threadIdx.x == 0) tab.hot = 0u;
     }
   }
   local_flush3(tab, b, false);
@@ -179,12 +181,13 @@ k_bins3(StepBuffers b, int32_t* __restrict__ bin_xyz, Lik3 lp, const float* __re
     const unsigned g = b.occ[bi];
     const unsigned long long key = b.hkey[g];
     const double dn = (double)b.hcnt[g];
+    const double rdn = 1.0 / dn;  // one FP64 division per cell (GB300's FP64 rate is low)
     double mean[NS3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
-      mean[p] = ((double)((long long)key3(key, p) * hq[p]) + (double)b.hsum[p * hcap + g] / dn) * POS_INV;
+      mean[p] = ((double)((long long)key3(key, p) * hq[p]) + (double)b.hsum[p * hcap + g] * rdn) * POS_INV;
 #pragma unroll
-    for (int c = 3; c < NS3; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    for (int c = 3; c < NS3; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] * rdn) * VAL_INV;
     if (lane == 0) {
 #pragma unroll
       for (int p = 0; p < 3; ++p) bin_xyz[p * bs + bi] = key3(key, p);

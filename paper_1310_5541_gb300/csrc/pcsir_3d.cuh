@@ -19,7 +19,9 @@ constexpr int L3 = 1 << L3_BITS;
 constexpr unsigned L3_CAP = 768;
 constexpr int P3_PIECE_BITS = 18;
 constexpr unsigned P3_PIECE_MASK = (1u << P3_PIECE_BITS) - 1u;
-constexpr int P3_FLUSH = 1 << 14;
+// a slot's 32-bit counters hold the pieces (< 2^18) of at most 2^14 particles; the table is
+// flushed after any chunk that leaves some slot at 2^14 - P3_CHUNK particles or more
+constexpr unsigned P3_HOT_AT = (1u << 14) - (unsigned)P3_CHUNK;
 constexpr long long P3_POS_BIAS = 1ll << 33;
 constexpr long long P3_VAL_BIAS = 1ll << 34;
 constexpr long long P3_LIMIT = 1ll << 36;
@@ -169,6 +171,7 @@ struct Local3 {
   unsigned int acc[NACC3][L3];
   unsigned int gslot[L3];
   unsigned int fill;
+  unsigned int hot;  // some slot may reach 2^14 particles within the next chunk: flush
 };
 
 __device__ __forceinline__ int local_insert3(Local3& t, unsigned long long key, bool& created) {

@@ -111,7 +111,9 @@ constexpr int BT_LTB_DEFAULT = 10;
 constexpr int BT_LTB_MIN = 9, BT_LTB_MAX = 11;
 constexpr int BT_PIECE_BITS = 18;
 constexpr unsigned BT_PIECE_MASK = (1u << BT_PIECE_BITS) - 1u;
-constexpr int BT_FLUSH = 1 << 14;
+// a slot's 32-bit counters hold the pieces (< 2^18) of at most 2^14 particles; the table is
+// flushed after any chunk that leaves some slot at 2^14 - BT_CHUNK particles or more
+constexpr unsigned BT_HOT_AT = (1u << 14) - (unsigned)BT_CHUNK;
 constexpr long long BT_POS_BIAS = 1ll << 33;
 constexpr long long BT_VAL_BIAS = 1ll << 34;
 constexpr long long BT_BIASED_LIMIT = 1ll << 36;
@@ -141,6 +143,7 @@ struct BatchLocal {
   unsigned short list[LT];
   unsigned int nlist;
   unsigned int fill;
+  unsigned int hot;  // some slot may reach 2^14 particles within the next chunk: flush
 };
 
 struct BatchResampleSmem {
@@ -313,6 +316,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
   if (threadIdx.x == 0) {
     tab.nlist = 0u;
     tab.fill = 0u;
+    tab.hot = 0u;
   }
   __syncthreads();
   // each block takes a contiguous range of chunks, so it meets the cells of a few neighbouring
@@ -322,7 +326,6 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
   const long long per_block = (nchunks + gridDim.x - 1) / gridDim.x;
   const long long c_begin = (long long)blockIdx.x * per_block;
   const long long c_end = c_begin + per_block < nchunks ? c_begin + per_block : nchunks;
-  int since_flush = 0;
   for (long long chunk = c_begin; chunk < c_end; ++chunk) {
     const long long base = chunk * BT_CHUNK;
     float v[BT_PER_THREAD][5];
@@ -444,8 +447,11 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
           run[2 + 2 * c] += (unsigned)(bv[c] >> BT_PIECE_BITS);
         }
         if (k == BT_PER_THREAD - 1 || ls[k + 1 < BT_PER_THREAD ? k + 1 : k] != s) {
+          const unsigned old = atomicAdd(&tab.acc[0][s], run[0]);
+          if (old < BT_HOT_AT && old + run[0] >= BT_HOT_AT) tab.hot = 1u;
+          run[0] = 0u;
 #pragma unroll
-          for (int a = 0; a < BT_NACC; ++a) {
+          for (int a = 1; a < BT_NACC; ++a) {
             atomicAdd(&tab.acc[a][s], run[a]);
             run[a] = 0u;
           }
@@ -463,12 +469,12 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       if (!vec) b.pslot[i] = g;
     }
     if (vec) *reinterpret_cast<uint4*>(b.pslot + i0) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
-    since_flush += BT_CHUNK;
     __syncthreads();
     const bool full = tab.fill >= BatchLocal<LTB>::CAP;
-    if (full || since_flush + BT_CHUNK > BT_FLUSH) {
+    if (full || tab.hot != 0u) {
       blocal_flush(tab, b, full);
-      since_flush = 0;
+      // ordered before any count of the next chunk by that chunk's block barrier
+      if (threadIdx.x == 0) tab.hot = 0u;
     }
   }
   blocal_flush(tab, b, false);
@@ -491,10 +497,11 @@ __device__ void phase_bins(const BatchBufs& b, const float* __restrict__ img, in
     const BatchStats& S_ = b.st[t];
     const unsigned n = b.hcnt[g];
     const double dn = (double)n;
+    const double rdn = 1.0 / dn;  // one FP64 division per cell (GB300's FP64 rate is low)
     const double inv = 1.0 / 2147483648.0;
-    const double mx = ((double)((long long)bkey_bx(key) * T_.hq) + (double)b.hsum[g] / dn) * inv;
-    const double my = ((double)((long long)bkey_by(key) * T_.hq) + (double)b.hsum[hcap + g] / dn) * inv;
-    const double mi = ((double)S_.anchor[2] + (double)b.hsum[4 * hcap + g] / dn) * (1.0 / 4194304.0);
+    const double mx = ((double)((long long)bkey_bx(key) * T_.hq) + (double)b.hsum[g] * rdn) * inv;
+    const double my = ((double)((long long)bkey_by(key) * T_.hq) + (double)b.hsum[hcap + g] * rdn) * inv;
+    const double mi = ((double)S_.anchor[2] + (double)b.hsum[4 * hcap + g] * rdn) * (1.0 / 4194304.0);
     LikParams lp;
     lp.P = T_.patch;
     lp.kind = PCSIR_LIK_POISSON;

@@ -115,11 +115,18 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
     for (int a = 0; a < NACC3; ++a) tab.acc[a][j] = 0u;
   }
   for (int t = threadIdx.x; t <= B.T; t += blockDim.x) offs[t] = B.offs[t];
-  if (threadIdx.x == 0) tab.fill = 0u;
+  if (threadIdx.x == 0) {
+    tab.fill = 0u;
+    tab.hot = 0u;
+  }
   __syncthreads();
+  // each block takes a contiguous range of chunks: it meets the cells of one or two targets, which
+  // its table holds, where a grid-stride order would show it every target's cells
   const long long nchunks = (N + P3_CHUNK - 1) / P3_CHUNK;
-  int since_flush = 0;
-  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+  const long long per_block = (nchunks + gridDim.x - 1) / gridDim.x;
+  const long long c_begin = (long long)blockIdx.x * per_block;
+  const long long c_end = c_begin + per_block < nchunks ? c_begin + per_block : nchunks;
+  for (long long chunk = c_begin; chunk < c_end; ++chunk) {
     const long long base = chunk * P3_CHUNK;
     float v[P3_PER_THREAD][NS3];
     unsigned long long key[P3_PER_THREAD];
@@ -186,7 +193,7 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
       if (ls[k] >= 0) {
         const int s = ls[k];
         g = tab.gslot[s];
-        atomicAdd(&tab.acc[0][s], 1u);
+        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == P3_HOT_AT) tab.hot = 1u;
 #pragma unroll
         for (int c = 0; c < NS3; ++c) {
           atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & P3_PIECE_MASK));
@@ -201,12 +208,12 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
       }
       b.pslot[i] = g;
     }
-    since_flush += P3_CHUNK;
     __syncthreads();
     const bool full = tab.fill >= L3_CAP;
-    if (full || since_flush + P3_CHUNK > P3_FLUSH) {
+    if (full || tab.hot != 0u) {
       local_flush3(tab, b, full);
-      since_flush = 0;
+      // ordered before any count of the next chunk by that chunk's block barrier
+      if (threadIdx.x == 0) tab.hot = 0u;
     }
   }
   local_flush3(tab, b, false);
@@ -232,12 +239,13 @@ __global__ void __launch_bounds__(B3_WTHREADS) k_b3_bins(B3Bufs B, const float* 
     const Target3& T_ = B.tg[t];
     const TStats3& S_ = B.ts[t];
     const double dn = (double)b.hcnt[g];
+    const double rdn = 1.0 / dn;  // one FP64 division per cell (GB300's FP64 rate is low)
     double mean[NS3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
-      mean[p] = ((double)((long long)b3_axis(key, p) * T_.hq[p]) + (double)b.hsum[p * hcap + g] / dn) * POS_INV;
+      mean[p] = ((double)((long long)b3_axis(key, p) * T_.hq[p]) + (double)b.hsum[p * hcap + g] * rdn) * POS_INV;
 #pragma unroll
-    for (int c = 3; c < NS3; ++c) mean[c] = ((double)S_.anchor[c - 3] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    for (int c = 3; c < NS3; ++c) mean[c] = ((double)S_.anchor[c - 3] + (double)b.hsum[c * hcap + g] * rdn) * VAL_INV;
     double ll =
         ll_to_double(warp_loglik3(vol, W, H, D, pos3(mean[0], mean[1], mean[2], mean[6]), T_.lik, scratch[w]));
     if (!isfinite(ll)) {

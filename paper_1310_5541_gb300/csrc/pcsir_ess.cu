@@ -268,10 +268,11 @@ __global__ void __launch_bounds__(ESS_THREADS) k_ess_bins(StepBuffers b, LikPara
       for (int c = 0; c < 3; ++c) dum[2 + c] = (double)anchor_f(b.ctl, c) + b.dummy[(2 + c) * bs + bi] / wsum;
     } else {  // no member carries weight: the plain mean from the exact sums
       const double dn = (double)n;
-      dum[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] / dn) * POS_INV;
-      dum[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
+      const double rdn = 1.0 / dn;  // one FP64 division per cell (GB300's FP64 rate is low)
+      dum[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] * rdn) * POS_INV;
+      dum[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] * rdn) * POS_INV;
 #pragma unroll
-      for (int c = 2; c < 5; ++c) dum[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+      for (int c = 2; c < 5; ++c) dum[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] * rdn) * VAL_INV;
     }
     if (coc) {  // pcSIR-CoC: the cell's geometric centre
       dum[0] = ((double)bx + 0.5) * (double)h - 0.5;

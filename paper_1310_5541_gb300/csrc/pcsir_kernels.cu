@@ -101,7 +101,11 @@ constexpr int PB_PER_THREAD = 4;
 constexpr int PB_CHUNK = PB_THREADS * PB_PER_THREAD;
 constexpr int PIECE_BITS = 18;
 constexpr unsigned PIECE_MASK = (1u << PIECE_BITS) - 1u;
-constexpr int FLUSH_PARTICLES = 1 << 14;
+// A slot's 32-bit counters hold at most 2^14 particles' pieces (each < 2^18).
+// A chunk adds at most CHUNK particles to one slot, so the table is flushed
+// after any chunk that leaves some slot at 2^14 - CHUNK particles or more
+// (the thread whose count crosses that mark raises the table's "hot" flag).
+constexpr unsigned SLOT_PARTICLES = 1u << 14;
 constexpr long long POS_BIAS = 1ll << 33;
 constexpr long long VAL_BIAS = 1ll << 34;
 constexpr long long BIASED_LIMIT = 1ll << 36;
@@ -120,6 +124,7 @@ struct LocalTable {
   unsigned int acc[NACC][LT];
   unsigned int gslot[LT];
   unsigned int fill;
+  unsigned int hot;  // some slot may reach SLOT_PARTICLES within the next chunk: flush
 };
 
 template <int LTB>
@@ -201,7 +206,10 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
 #pragma unroll
     for (int a = 0; a < NACC; ++a) tab.acc[a][j] = 0u;
   }
-  if (threadIdx.x == 0) tab.fill = 0u;
+  if (threadIdx.x == 0) {
+    tab.fill = 0u;
+    tab.hot = 0u;
+  }
   // anchors of vx, vy, I0: particle 0's input value in fixed point
   long long anc[3];
 #pragma unroll
@@ -214,7 +222,7 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
   const T half = T(0.5);
   const T lim = T(1073741823.0);  // 2^30 - 1
   const int64_t nchunks = (N + CHUNK - 1) / CHUNK;
-  int since_flush = 0;
+  constexpr unsigned HOT_AT = SLOT_PARTICLES - (unsigned)CHUNK;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t base = chunk * CHUNK;
     T v[PB_PER_THREAD][5];
@@ -298,7 +306,7 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       if (ls[k] >= 0) {
         const int s = ls[k];
         gs[k] = tab.gslot[s];
-        atomicAdd(&tab.acc[0][s], 1u);
+        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == HOT_AT) tab.hot = 1u;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & PIECE_MASK));
@@ -322,12 +330,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       for (int k = 0; k < PB_PER_THREAD; ++k)
         if (ls[k] != -2) b.pslot[pb_index<false, THR>(base, k)] = gs[k];
     }
-    since_flush += CHUNK;
     __syncthreads();
     const bool full = tab.fill >= LocalTable<LTB>::CAP;
-    if (full || since_flush + CHUNK > FLUSH_PARTICLES) {
+    if (full || tab.hot != 0u) {
       local_flush(tab, b, full);
-      since_flush = 0;
+      // ordered before any count of the next chunk by that chunk's block barrier
+      if (threadIdx.x == 0) tab.hot = 0u;
     }
   }
   local_flush(tab, b, false);
@@ -408,11 +416,12 @@ k_bins(StepBuffers b, LikParams lp, const float* __restrict__ img, int W, int H,
     const int bx = key_bx(key), by = key_by(key);
     const unsigned n = b.hcnt[g];
     const double dn = (double)n;
+    const double rdn = 1.0 / dn;  // one FP64 division per cell (GB300's FP64 rate is low)
     double mean[5];
-    mean[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] / dn) * POS_INV;
-    mean[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] / dn) * POS_INV;
+    mean[0] = ((double)((long long)bx * hq) + (double)b.hsum[g] * rdn) * POS_INV;
+    mean[1] = ((double)((long long)by * hq) + (double)b.hsum[hcap + g] * rdn) * POS_INV;
 #pragma unroll
-    for (int c = 2; c < 5; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] / dn) * VAL_INV;
+    for (int c = 2; c < 5; ++c) mean[c] = ((double)b.ctl->anchor[c] + (double)b.hsum[c * hcap + g] * rdn) * VAL_INV;
     if (coc) {  // pcSIR-CoC: the cell's geometric centre
       mean[0] = ((double)bx + 0.5) * h - 0.5;
       mean[1] = ((double)by + 0.5) * h - 0.5;
