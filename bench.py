@@ -90,10 +90,16 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the propagate/bin kernel's source: its file, the device helpers, and the structures of
+    pcsir_internal.h that its launches pass (declarations elsewhere in that header do not count)."""
     h = hashlib.sha256()
-    for f in ("pcsir_kernels.cu", "pcsir_device.cuh", "pcsir_internal.h"):
-        with open(os.path.join(ROOT, "paper_1310_5541_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1310_5541_gb300", "csrc")
+    for f in ("pcsir_kernels.cu", "pcsir_device.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "pcsir_internal.h"), "rb") as fh:
+        txt = fh.read()
+    h.update(txt[txt.index(b"struct Control {"):txt.index(b"struct ModelParams")])
     return h.hexdigest()[:16]
 
 
@@ -572,7 +578,7 @@ def run_large_object(counts, n_frames, seed):
             "frames": n_frames, "rows": rows}
 
 
-def run_3d(counts, n_frames, seed):
+def run_3d(counts, n_frames, seed, sur_seqs=0, sur_steps=0):
     """3D tracking: 256 x 256 x 64 Poisson volumes (PSF sigma 1.5 / 3 voxels, I0 100, bg 10), state
     (x, y, z, vx, vy, vz, I0), 11 x 11 x 7 likelihood patch; SIR and pcSIR with 0.5 x 0.5 x 1 and
     0.1 x 0.1 x 0.2 voxel cells filter the same sequence with the same noise: device time per step and
@@ -587,11 +593,23 @@ def run_3d(counts, n_frames, seed):
     vols = torch.from_numpy(seq.images).to(dev)
     stream = torch.cuda.current_stream()
     rows = []
+    sur, training = None, None
+    if sur_steps > 0:
+        sur, training = train_surrogate3(sur_seqs, sur_steps, seed + 11)
     for N in counts:
         pool = [torch.from_numpy(synth.make_noise(N, synth.Q3, seed + 3, j, np.float32)).to(dev)
                 for j in range(NOISE_POOL)]
         ctx = pcsir.Context3(N)
-        for name, h in (("sir", None), ("pcsir", (0.5, 0.5, 1.0)), ("pcsir-fine", (0.1, 0.1, 0.2))):
+        methods = [("sir", None), ("pcsir", (0.5, 0.5, 1.0)), ("pcsir-fine", (0.1, 0.1, 0.2))]
+        if sur is not None:
+            # checked: the held-out test falls back to the exact likelihood; unchecked: never (the
+            # surrogate path's own cost, whatever the network's error)
+            methods += [("surrogate-fine", (0.1, 0.1, 0.2)), ("surrogate-fine-unchecked", (0.1, 0.1, 0.2))]
+        for name, h in methods:
+            use_sur = name.startswith("surrogate")
+            pcsir.attach_surrogate3(ctx, sur if use_sur else None, holdout_frac=0.02, min_holdout=32, window=20.0,
+                                    max_err=1e300 if name.endswith("unchecked") else 3.0)
+            exact, dummies, fallbacks = 0, 0, 0
             st = torch.from_numpy(synth.initial_state3(seq.gt[0], N, np.float32)).to(dev)
             ms, errs = [], []
             for k in range(n_frames):
@@ -610,14 +628,47 @@ def run_3d(counts, n_frames, seed):
                 if r["device_error"]:
                     raise RuntimeError("device error %d in 3D %s" % (r["device_error"], name))
                 errs.append(np.array(r["estimate"][:3]) - seq.gt[k + 1, :3])
+                if use_sur:
+                    c = pcsir.surrogate_last_check3(ctx)
+                    exact += c["n_exact"]
+                    dummies += c["n_dummies"]
+                    fallbacks += c["fallback"]
             e = np.array(errs)
-            rows.append({"method": name, "N": N, "ms_per_step": float(np.mean(ms)),
-                         "particles_per_s": N * 1e3 / float(np.mean(ms)),
-                         "rmse_voxel": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1))))})
+            row = {"method": name, "N": N, "ms_per_step": float(np.mean(ms)),
+                   "particles_per_s": N * 1e3 / float(np.mean(ms)),
+                   "rmse_voxel": float(np.sqrt(np.mean(np.sum(e ** 2, axis=1))))}
+            if use_sur:
+                row.update(exact_fraction=exact / max(1, dummies), fallbacks=fallbacks,
+                           mean_dummies=dummies / max(1, len(errs)))
+            rows.append(row)
         ctx.close()
+    if sur is not None:
+        sur.close()
     return {"workload": "3D: 256x256x64 volumes, 11x11x7 patch, cells 0.5x0.5x1 and 0.1x0.1x0.2 voxel",
-            "frames": n_frames,
+            "frames": n_frames, "surrogate_training": training,
             "rows": rows}
+
+
+def train_surrogate3(n_seq, steps, seed):
+    """The 3D surrogate trained on pairs its own method generates: exact 3D pcSIR steps (N = 2^16) over
+    ``n_seq`` four-frame 64 x 64 x 32 sequences of the same model, at the model's process noise with
+    0.1 x 0.1 x 0.2 voxel cells and at scaled-down noise with finer cells (``surrogate.COLLECT3``); then
+    ``steps`` Adam updates."""
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir, surrogate
+
+    t0 = time.perf_counter()
+    sur = pcsir.Surrogate(capacity=max(1 << 20, 1600 * n_seq), batch=4096, i0_ref=128.0, sigma_ref=1.5,
+                          max_pixels=256 * 256 * 64, geometry=3)
+    surrogate.collect3_sequences(sur, n_seq, 4, 1 << 16, seed + 500)
+    t1 = time.perf_counter()
+    sur.init(seed)
+    fit = surrogate.fit(sur, steps=steps, lr=2e-3, seed=3, val_frac=0.02, chunk=2000)
+    torch.cuda.synchronize()
+    return sur, {"rows": sur.rows(), "sequences": n_seq, "train_steps": steps, "collect_s": t1 - t0,
+                 "train_s": time.perf_counter() - t1, "val_rmse_nats": fit["val_rmse"],
+                 "val_max_nats": fit["val_max"], "val_label_std_nats": fit["val_label_std"]}
 
 
 def run_batched3(n_targets, n_per, steps, warmup, seed, world=1):
@@ -704,6 +755,9 @@ def main():
     ap.add_argument("--frames-3d", type=int, default=20, help="frames of the 3D comparison (0 skips it)")
     ap.add_argument("--batched3-steps", type=int, default=5, help="timed steps of the batched 3D workload (0 skips it)")
     ap.add_argument("--batched3-targets", type=int, default=200)
+    ap.add_argument("--surrogate3-sequences", type=int, default=1200,
+                    help="four-frame training sequences of the 3D surrogate")
+    ap.add_argument("--surrogate3-steps", type=int, default=10_000, help="Adam steps of the 3D surrogate (0: none)")
     ap.add_argument("--ess-frames", type=int, default=20, help="frames of the ESS-threshold comparison (0 skips it)")
     ap.add_argument("--ess-frac", type=float, default=0.5, help="N_thr / N of the ESS-threshold comparison")
     args = ap.parse_args()
@@ -931,7 +985,8 @@ def main():
 
     track3d = None
     if args.frames_3d > 0:
-        track3d = run_3d((200_000, 1 << 22), args.frames_3d, SEED + 61 + 1000 * rank)
+        track3d = run_3d((200_000, 1 << 22), args.frames_3d, SEED + 61 + 1000 * rank, args.surrogate3_sequences,
+                         args.surrogate3_steps)
     if args.batched3_steps > 0:
         track3d = track3d or {}
         track3d["batched"] = run_batched3(args.batched3_targets, 200_000, args.batched3_steps, 3,

@@ -82,7 +82,9 @@ const char* pcsir3_last_error(pcsir3_ctx* ctx);
 /* One pcSIR step (Algorithm 2) in 3D on state [7][N] in place; noise [7][N]
    (device float32), u0 in [0, 1), cell edges hx, hy, hz in (0, 8].
    result_host (may be NULL) receives the step's scalars once the stream
-   reaches the end of the step. */
+   reaches the end of the step.  With a 3D surrogate attached
+   (pcsir3_attach_surrogate), a volume of more voxels than the surrogate's
+   max_pixels returns PCSIR_ERANGE before anything is launched. */
 pcsir_status pcsir3_step(pcsir3_ctx* ctx, float* state, int64_t N, const float* volume, int32_t W, int32_t H,
                          int32_t D, double hx, double hy, double hz, const float* noise, double u0, void* stream,
                          pcsir3_result* result_host);

@@ -39,6 +39,17 @@
  * W1 [256][445] row-major, b1 [256], W2 [256][256] row-major, b2 [256],
  * w3 [256], b3 [1].
  *
+ * 3D surrogate (geometry 3; the 3D step of pcsir3.h, whose likelihood is the
+ * Poisson term over an 11 x 11 x 7 voxel patch): 852 inputs -> 256 -> 256 -> 1,
+ *   0..846   the 11 x 11 x 7 patch centred on the nearest voxel (cx, cy, cz),
+ *            x fastest, then y, then z, from (cx - 5, cy - 5, cz - 3), as
+ *            (z - bg) / i0_ref;
+ *   847..849 2 (x - cx), 2 (y - cy), 2 (z - cz);
+ *   850, 851 I0 / i0_ref, sigma_xy / sigma_ref.
+ * The window term sums the image-only part over the 847 voxels of the window
+ * (separable passes along x, y and z, sums in double-float); the packed
+ * parameters (PCSIR_SUR3_NPARAMS) are W1 [256][852], then as in 2D.
+ *
  * Threading: a surrogate object is used by one host thread at a time; its
  * calls are stream-ordered, and work of two calls on one object must not
  * overlap on the GPU.
@@ -47,6 +58,7 @@
 #define PCSIR_SURROGATE_H_
 
 #include "pcsir.h"
+#include "pcsir3.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -56,17 +68,21 @@ extern "C" {
 #define PCSIR_SUR_INPUTS 445
 #define PCSIR_SUR_HIDDEN 256
 #define PCSIR_SUR_NPARAMS (256 * 445 + 256 + 256 * 256 + 256 + 256 + 1)
+#define PCSIR_SUR3_PATCH_XY 11
+#define PCSIR_SUR3_PATCH_Z 7
+#define PCSIR_SUR3_INPUTS 852
+#define PCSIR_SUR3_NPARAMS (256 * 852 + 256 + 256 * 256 + 256 + 256 + 1)
 
 typedef struct pcsir_surrogate pcsir_surrogate;
 
 typedef struct pcsir_surrogate_config {
   int64_t capacity;    /* training rows the dataset holds (>= 1) */
   int32_t batch;       /* training minibatch rows: a multiple of 128 in [128, 65536] */
-  int32_t reserved;    /* must be 0 */
+  int32_t geometry;    /* 0 or 2: the 2D surrogate (21 x 21 patch); 3: the 3D one (11 x 11 x 7) */
   double i0_ref;       /* input scale of patch values and of I0 (> 0); a power of two keeps
                           integer photon counts up to 256 + bg exact in bf16 */
   double sigma_ref;    /* input scale of the PSF width (> 0) */
-  int64_t max_pixels;  /* largest image (W * H) the surrogate sees (>= 1) */
+  int64_t max_pixels;  /* largest image (W * H) or volume (W * H * D) the surrogate sees (>= 1) */
 } pcsir_surrogate_config;
 
 /* Statistics of the last surrogate-assisted pcSIR step (see
@@ -119,14 +135,27 @@ pcsir_status pcsir_surrogate_add(pcsir_surrogate* sur, const double* dummy, int6
                                  const double* ll, double label_floor, const float* image, int32_t W, int32_t H,
                                  double bg, double psf_sigma, void* stream);
 
+/* The same for a 3D surrogate (geometry 3): states of the 3D step (x =
+   dummy[0 * stride + i], y = dummy[1 * stride + i], z = dummy[2 * stride + i],
+   I0 = dummy[6 * stride + i], the layout of pcsir3_outputs.dummy) against a
+   device volume (D x H x W float32), with the lateral PSF width
+   psf_sigma_xy.  Each call accepts the other geometry's surrogate with
+   PCSIR_EINVAL only. */
+pcsir_status pcsir_surrogate_add3(pcsir_surrogate* sur, const double* dummy, int64_t stride, int64_t n,
+                                  const double* ll, double label_floor, const float* volume, int32_t W, int32_t H,
+                                  int32_t D, double bg, double psf_sigma_xy, void* stream);
+
+/* Number of packed parameters: PCSIR_SUR_NPARAMS (2D) or PCSIR_SUR3_NPARAMS (3D). */
+pcsir_status pcsir_surrogate_nparams(pcsir_surrogate* sur, int64_t* nparams);
+
 /* Rows in the dataset (synchronises the device). */
 pcsir_status pcsir_surrogate_rows(pcsir_surrogate* sur, int64_t* rows);
 /* Empties the dataset (stream-ordered). */
 pcsir_status pcsir_surrogate_clear(pcsir_surrogate* sur, void* stream);
 
 /* Device pointers to the dataset: inputs as bf16 (uint16_t) rows of 448
-   values (445 inputs, then 3 zeros), float32 labels and per-row censoring
-   flags (1: the label is a floor). */
+   values (445 inputs, then 3 zeros; 3D: 896 values, 852 inputs then zeros),
+   float32 labels and per-row censoring flags (1: the label is a floor). */
 pcsir_status pcsir_surrogate_dataset(pcsir_surrogate* sur, const uint16_t** inputs, const float** labels,
                                      const uint8_t** censored);
 
@@ -146,7 +175,7 @@ pcsir_status pcsir_surrogate_train(pcsir_surrogate* sur, int64_t begin, int64_t 
 
 /* Gradient of the mean squared error over rows [begin, begin + n) (n a
    multiple of 128, at most cfg.batch) with respect to the packed parameters,
-   without an update; grads is a host float array of PCSIR_SUR_NPARAMS, loss
+   without an update; grads is a host float array of the packed parameters, loss
    a host double.  Synchronises the device. */
 pcsir_status pcsir_surrogate_grads(pcsir_surrogate* sur, int64_t begin, int32_t n, float* grads, double* loss);
 
@@ -161,6 +190,10 @@ pcsir_status pcsir_surrogate_predict_rows(pcsir_surrogate* sur, int64_t begin, i
 pcsir_status pcsir_surrogate_predict(pcsir_surrogate* sur, const double* dummy, int64_t stride, int64_t n,
                                      const float* image, int32_t W, int32_t H, double bg, double psf_sigma,
                                      double* out, void* stream);
+
+pcsir_status pcsir_surrogate_predict3(pcsir_surrogate* sur, const double* dummy, int64_t stride, int64_t n,
+                                      const float* volume, int32_t W, int32_t H, int32_t D, double bg,
+                                      double psf_sigma_xy, double* out, void* stream);
 
 /* Makes pcsir_step on ctx use the surrogate for the dummies' log-likelihoods
    (sur == NULL detaches).  Every step then evaluates the exact likelihood
@@ -182,6 +215,14 @@ pcsir_status pcsir_attach_surrogate(pcsir_ctx* ctx, pcsir_surrogate* sur, double
 
 /* Statistics of the last surrogate-assisted step of ctx (synchronises). */
 pcsir_status pcsir_surrogate_last_check(pcsir_ctx* ctx, pcsir_surrogate_check* out);
+
+/* The same for the 3D step (pcsir3_step) with a 3D surrogate: a cell (bx, by,
+   bz) is held out by the rule above with key = (bx + 2^20) | (by + 2^20) << 21
+   | (bz + 2^20) << 42; requires a context with an 11 x 11 x 7 patch and
+   volumes of at most max_pixels voxels. */
+pcsir_status pcsir3_attach_surrogate(pcsir3_ctx* ctx, pcsir_surrogate* sur, double holdout_frac,
+                                     int32_t min_holdout, double window, double max_err);
+pcsir_status pcsir3_surrogate_last_check(pcsir3_ctx* ctx, pcsir_surrogate_check* out);
 
 #ifdef __cplusplus
 }

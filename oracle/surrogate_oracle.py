@@ -63,14 +63,24 @@ PARAM_SHAPES = (("W1", (HIDDEN, N_IN)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDE
 N_PARAMS = sum(int(np.prod(s)) for _, s in PARAM_SHAPES)
 
 
-def pack(params: dict) -> np.ndarray:
+# 3D surrogate: an 11 x 11 x 7 voxel patch, then the sub-voxel offsets along x, y, z, I0 and sigma_xy
+P3XY, P3Z = 11, 7
+R3XY, R3Z = P3XY // 2, P3Z // 2
+NPIX3 = P3XY * P3XY * P3Z
+N_IN3 = NPIX3 + 5
+PARAM_SHAPES3 = (("W1", (HIDDEN, N_IN3)),) + PARAM_SHAPES[1:]
+N_PARAMS3 = sum(int(np.prod(s)) for _, s in PARAM_SHAPES3)
+
+
+def pack(params: dict, shapes=PARAM_SHAPES) -> np.ndarray:
     """Flatten parameters in the fixed order W1, b1, W2, b2, w3, b3 (float64)."""
-    return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k, _ in PARAM_SHAPES])
+    return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k, _ in shapes])
 
 
-def unpack(flat: np.ndarray) -> dict:
+def unpack(flat: np.ndarray, shapes=PARAM_SHAPES) -> dict:
+    """Parameters from their packed form (``shapes``: PARAM_SHAPES, or PARAM_SHAPES3 in 3D)."""
     out, o = {}, 0
-    for k, s in PARAM_SHAPES:
+    for k, s in shapes:
         n = int(np.prod(s))
         out[k] = np.asarray(flat[o:o + n], np.float64).reshape(s)
         o += n
@@ -115,6 +125,51 @@ def window_term(image: np.ndarray, x, y, bg: float) -> np.ndarray:
     out = np.empty(cx.shape[0])
     for i in range(cx.shape[0]):
         out[i] = e[cy[i] - R:cy[i] + R + 1, cx[i] - R:cx[i] + R + 1].sum() - P * P * bg
+    return out
+
+
+def features3(volume: np.ndarray, x, y, z, i0, sigma_xy, bg: float, i0_ref: float, sigma_ref: float):
+    """3D network inputs; returns (X [n, 852] float64, clipped [n] bool).
+
+    The 11 x 11 x 7 patch centred on the nearest voxel (cx, cy, cz) = floor(. + 0.5), x fastest,
+    then y, then z, as (v - bg) / i0_ref; then 2 (x - cx), 2 (y - cy), 2 (z - cz), I0 / i0_ref and
+    sigma_xy / sigma_ref.  A patch that leaves the volume is clipped."""
+    x, y, z, i0 = (np.asarray(v, np.float64) for v in (x, y, z, i0))
+    sig = np.broadcast_to(np.asarray(sigma_xy, np.float64), x.shape)
+    Dd, Hh, Ww = volume.shape
+    vol = volume.astype(np.float64)
+    cx, cy, cz = np.floor(x + 0.5), np.floor(y + 0.5), np.floor(z + 0.5)
+    clipped = ((cx - R3XY < 0) | (cx + R3XY > Ww - 1) | (cy - R3XY < 0) | (cy + R3XY > Hh - 1) |
+               (cz - R3Z < 0) | (cz + R3Z > Dd - 1))
+    n = x.shape[0]
+    X = np.empty((n, N_IN3))
+    for i in range(n):
+        if clipped[i]:
+            X[i, :NPIX3] = 0.0
+        else:
+            a, b, c = int(cx[i]), int(cy[i]), int(cz[i])
+            blk = vol[c - R3Z:c + R3Z + 1, b - R3XY:b + R3XY + 1, a - R3XY:a + R3XY + 1]
+            X[i, :NPIX3] = ((blk - bg) / i0_ref).reshape(-1)  # x fastest, then y, then z
+    X[:, NPIX3] = 2.0 * (x - cx)
+    X[:, NPIX3 + 1] = 2.0 * (y - cy)
+    X[:, NPIX3 + 2] = 2.0 * (z - cz)
+    X[:, NPIX3 + 3] = i0 / i0_ref
+    X[:, NPIX3 + 4] = sig / sigma_ref
+    return X, clipped
+
+
+def window_term3(volume: np.ndarray, x, y, z, bg: float) -> np.ndarray:
+    """T(cx, cy, cz): the image-only part of the Poisson term summed over the 11 x 11 x 7 window
+    around the states' nearest voxels (windows inside the volume), minus 847 bg."""
+    v = volume.astype(np.float64)
+    e = np.where(v > 0, v - v * np.log(np.where(v > 0, v, 1.0)), 0.0) + np.log(bg) * v
+    cx = np.floor(np.asarray(x, np.float64) + 0.5).astype(np.int64)
+    cy = np.floor(np.asarray(y, np.float64) + 0.5).astype(np.int64)
+    cz = np.floor(np.asarray(z, np.float64) + 0.5).astype(np.int64)
+    out = np.empty(cx.shape[0])
+    for i in range(cx.shape[0]):
+        out[i] = e[cz[i] - R3Z:cz[i] + R3Z + 1, cy[i] - R3XY:cy[i] + R3XY + 1,
+                   cx[i] - R3XY:cx[i] + R3XY + 1].sum() - NPIX3 * bg
     return out
 
 
@@ -214,6 +269,17 @@ def holdout_mask(bx, by, salt: int, frac: float) -> np.ndarray:
     out = np.zeros(len(bx), bool)
     for i, (a, b) in enumerate(zip(np.asarray(bx).tolist(), np.asarray(by).tolist())):
         key = (a & 0xFFFFFFFF) | ((b & 0xFFFFFFFF) << 32)
+        h = splitmix64((key + salt * 0x9E3779B97F4A7C15) & _M64)
+        out[i] = (h >> 40) < thr
+    return out
+
+
+def holdout_mask3(bx, by, bz, salt: int, frac: float) -> np.ndarray:
+    """Held-out 3D cells: the same rule with the key (bx + 2^20) | (by + 2^20) << 21 | (bz + 2^20) << 42."""
+    thr = int(np.floor(frac * (1 << 24)))
+    out = np.zeros(len(bx), bool)
+    for i, (a, b, c) in enumerate(zip(np.asarray(bx).tolist(), np.asarray(by).tolist(), np.asarray(bz).tolist())):
+        key = (a + (1 << 20)) | ((b + (1 << 20)) << 21) | ((c + (1 << 20)) << 42)
         h = splitmix64((key + salt * 0x9E3779B97F4A7C15) & _M64)
         out[i] = (h >> 40) < thr
     return out

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "pcsir_3d.cuh"
+#include "pcsir_surrogate.h"
 
 namespace pcsir {
 
@@ -166,9 +167,30 @@ __device__ __forceinline__ void block_max3(double v, Control* ctl) {
   }
 }
 
+// 3D cells: the key packs (bx + 2^20, by + 2^20, bz + 2^20) in 21-bit fields
+__device__ __forceinline__ bool sur_held3(int bx, int by, int bz, unsigned long long salt, unsigned thr) {
+  const unsigned long long key = (unsigned long long)(unsigned)(bx + (1 << 20)) |
+                                 ((unsigned long long)(unsigned)(by + (1 << 20)) << 21) |
+                                 ((unsigned long long)(unsigned)(bz + (1 << 20)) << 42);
+  const unsigned long long h = splitmix64(key + salt * 0x9E3779B97F4A7C15ull);
+  return (unsigned)(h >> 40) < thr;
+}
+
+// held-out selection and list of a surrogate-assisted step (SUR)
+struct SurBins3 {
+  unsigned long long salt;
+  double frac;
+  int min_holdout;
+  int ho_cap;
+  int* ho_bin;
+  double* ho_ll;
+  SurStats* stats;
+};
+
+template <bool SUR>
 __global__ void __launch_bounds__(B3_THREADS)
 k_bins3(StepBuffers b, int32_t* __restrict__ bin_xyz, Lik3 lp, const float* __restrict__ vol, int W, int H, int D,
-        long long hqx, long long hqy, long long hqz) {
+        long long hqx, long long hqy, long long hqz, SurBins3 sb) {
   constexpr int NW = B3_THREADS / 32;
   __shared__ float scratch[NW][2 * (3 * MAXP3)];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -176,6 +198,7 @@ k_bins3(StepBuffers b, int32_t* __restrict__ bin_xyz, Lik3 lp, const float* __re
   const size_t hcap = size_t(1) << b.hbits;
   const int64_t bs = b.bin_stride;
   const long long hq[3] = {hqx, hqy, hqz};
+  const unsigned thr = SUR ? sur_holdout_threshold(sb.frac, sb.min_holdout, B) : 0u;
   double mymax = -INFINITY;
   for (unsigned bi = blockIdx.x * NW + w; bi < B; bi += gridDim.x * NW) {
     const unsigned g = b.occ[bi];
@@ -196,7 +219,55 @@ k_bins3(StepBuffers b, int32_t* __restrict__ bin_xyz, Lik3 lp, const float* __re
       for (int c = 0; c < NS3; ++c) b.dummy[c * bs + bi] = mean[c];
       b.hrank[g] = bi;
     }
+    bool held = false;
+    if (SUR) {
+      // the surrogate predicts every dummy whose 11 x 11 x 7 patch lies inside the volume,
+      // except the held-out ones
+      const int rxy = lp.Pxy >> 1, rz = lp.Pz >> 1;
+      const double fx = floor(mean[0] + 0.5), fy = floor(mean[1] + 0.5), fz = floor(mean[2] + 0.5);
+      const bool clipped = !(fx - rxy >= 0.0 && fx + rxy <= (double)(W - 1) && fy - rxy >= 0.0 &&
+                             fy + rxy <= (double)(H - 1) && fz - rz >= 0.0 && fz + rz <= (double)(D - 1));
+      held = !clipped && sur_held3(key3(key, 0), key3(key, 1), key3(key, 2), sb.salt, thr);
+      if (!clipped && !held) continue;  // uniform over the warp
+      if (!held && lane == 0) atomicAdd(&sb.stats->n_clipped, 1u);
+    }
     double ll = ll_to_double(warp_loglik3(vol, W, H, D, pos3(mean[0], mean[1], mean[2], mean[6]), lp, scratch[w]));
+    if (!isfinite(ll)) {
+      if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
+      ll = -INFINITY;
+    }
+    if (SUR && held) {
+      if (lane == 0) {
+        const unsigned slot = atomicAdd(&sb.stats->n_ho, 1u);
+        if (slot < (unsigned)sb.ho_cap) {
+          sb.ho_bin[slot] = (int)bi;
+          sb.ho_ll[slot] = ll;
+        }
+      }
+      continue;
+    }
+    if (lane == 0) b.bin_ll[bi] = ll;
+    mymax = fmax(mymax, ll);
+  }
+  block_max3(mymax, b.ctl);
+}
+
+// Exact likelihood of every dummy when the held-out check rejected the surrogate's
+// predictions (stats->fallback); otherwise returns at once.  The dummies are those
+// k_bins3 stored, so the values equal the plain step's.
+__global__ void __launch_bounds__(B3_THREADS)
+k_bins3_fallback(StepBuffers b, Lik3 lp, const float* __restrict__ vol, int W, int H, int D,
+                 const SurStats* __restrict__ stats) {
+  if (*(volatile const unsigned*)&stats->fallback == 0u) return;
+  constexpr int NW = B3_THREADS / 32;
+  __shared__ float scratch[NW][2 * (3 * MAXP3)];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned B = b.ctl->nocc;
+  const int64_t bs = b.bin_stride;
+  double mymax = -INFINITY;
+  for (unsigned bi = blockIdx.x * NW + w; bi < B; bi += gridDim.x * NW) {
+    const double x = b.dummy[bi], y = b.dummy[bs + bi], z = b.dummy[2 * bs + bi], a = b.dummy[6 * bs + bi];
+    double ll = ll_to_double(warp_loglik3(vol, W, H, D, pos3(x, y, z, a), lp, scratch[w]));
     if (!isfinite(ll)) {
       if (lane == 0) raise_flag(b.ctl, PCSIR_DERR_NONFINITE);
       ll = -INFINITY;
@@ -386,6 +457,12 @@ struct pcsir3_ctx {
   int last_kind = -1;
   int64_t last_N = 0;
   int pb_per_sm = 1;
+  // attached likelihood surrogate (3D geometry): per-step held-out list and statistics
+  SurStep sur{};
+  bool sur_on = false;
+  bool sur_ran = false;
+  unsigned long long sur_steps = 0;
+  double psf_sigma_xy = 0.0;
 };
 
 namespace {
@@ -523,6 +600,7 @@ pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out) {
     return e == cudaErrorMemoryAllocation ? PCSIR_ENOMEM : PCSIR_ECUDA;
   }
   std::memset(c->host_res, 0, sizeof(pcsir3_result));
+  c->psf_sigma_xy = cfg->psf_sigma_xy;
   Lik3& lp = c->lik;
   lp.Pxy = cfg->patch_xy;
   lp.Pz = cfg->patch_z;
@@ -550,6 +628,8 @@ pcsir_status pcsir3_step(pcsir3_ctx* ctx, float* state, int64_t N, const float* 
   if (st != PCSIR_OK) return st;
   if (!(hx > 0.0 && hx <= MAX_H && hy > 0.0 && hy <= MAX_H && hz > 0.0 && hz <= MAX_H))
     return fail3(ctx, PCSIR_EINVAL, "cell edges must lie in (0, 8]");
+  if (ctx->sur_on && (int64_t)W * H * D > sur_max_pixels(ctx->sur.sur))
+    return fail3(ctx, PCSIR_ERANGE, "volume larger than the surrogate's max_pixels");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const StepBuffers& b = ctx->b;
   cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(Control), s);
@@ -561,9 +641,29 @@ pcsir_status pcsir3_step(pcsir3_ctx* ctx, float* state, int64_t N, const float* 
                                                        hqz);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    k_bins3<<<ctx->num_sms * 4, B3_THREADS, 0, s>>>(b, ctx->bin_xyz, ctx->lik, volume, W, H, D, hqx, hqy, hqz);
-    e = cudaGetLastError();
+    if (!ctx->sur_on) {
+      k_bins3<false><<<ctx->num_sms * 4, B3_THREADS, 0, s>>>(b, ctx->bin_xyz, ctx->lik, volume, W, H, D, hqx, hqy,
+                                                             hqz, SurBins3{});
+      e = cudaGetLastError();
+    } else {
+      SurStep sp = ctx->sur;
+      sp.salt = ctx->sur_steps;
+      const SurBins3 sb{sp.salt, sp.frac, sp.min_holdout, sp.ho_cap, sp.ho_bin, sp.ho_ll, sp.stats};
+      e = cudaMemsetAsync(sp.stats, 0, sizeof(SurStats), s);
+      if (e == cudaSuccess) {
+        k_bins3<true><<<ctx->num_sms * 4, B3_THREADS, 0, s>>>(b, ctx->bin_xyz, ctx->lik, volume, W, H, D, hqx, hqy,
+                                                              hqz, sb);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = launch_sur_step3(sp, b, ctx->cfg.bg, ctx->psf_sigma_xy, volume, W, H, D, s);
+      if (e == cudaSuccess) {
+        k_bins3_fallback<<<ctx->num_sms * 4, B3_THREADS, 0, s>>>(b, ctx->lik, volume, W, H, D, sp.stats);
+        e = cudaGetLastError();
+      }
+      ctx->sur_steps++;
+    }
   }
+  ctx->sur_ran = ctx->sur_on;
   if (e == cudaSuccess) {
     k_binred3<<<ctx->num_sms * 2, R3_THREADS, 0, s>>>(b, ctx->dres3, N, weight_scale_bits(N));
     e = cudaGetLastError();
@@ -619,6 +719,61 @@ pcsir_status pcsir3_get_outputs(pcsir3_ctx* ctx, pcsir3_outputs* o) {
   o->ancestor = b.anc;
   o->weight = b.wout;
   o->qweight = reinterpret_cast<const int64_t*>(b.qout);
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir3_attach_surrogate(pcsir3_ctx* ctx, pcsir_surrogate* sur, double holdout_frac, int32_t min_holdout,
+                                     double window, double max_err) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail3(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (!sur) {
+    ctx->sur_on = false;
+    return PCSIR_OK;
+  }
+  if (!(holdout_frac >= 0.0 && holdout_frac <= 1.0) || min_holdout < 0 || !(window >= 0.0) || !(max_err >= 0.0))
+    return fail3(ctx, PCSIR_EINVAL, "invalid held-out fraction, window or error threshold");
+  if (sur_dim(sur) != 3) return fail3(ctx, PCSIR_EINVAL, "a 2D surrogate attaches to a 2D context");
+  if (ctx->cfg.patch_xy != PCSIR_SUR3_PATCH_XY || ctx->cfg.patch_z != PCSIR_SUR3_PATCH_Z)
+    return fail3(ctx, PCSIR_EINVAL, "the 3D surrogate models an 11 x 11 x 7 patch");
+  SurStep& sp = ctx->sur;
+  if (!sp.stats) {
+    constexpr int HO_CAP = 1 << 16;
+    if (!(alloc3(ctx, &sp.ho_bin, HO_CAP) && alloc3(ctx, &sp.ho_ll, HO_CAP) && alloc3(ctx, &sp.stats, 1))) {
+      sp.stats = nullptr;
+      return fail3(ctx, PCSIR_ENOMEM, "held-out list allocation");
+    }
+    sp.ho_cap = HO_CAP;
+    const cudaError_t e = cudaMemset(sp.stats, 0, sizeof(SurStats));
+    if (e != cudaSuccess) return cuda_fail3(ctx, e, "held-out statistics");
+  }
+  sp.sur = sur;
+  sp.frac = holdout_frac;
+  sp.min_holdout = min_holdout;
+  sp.window = window;
+  sp.max_err = max_err;
+  ctx->sur_on = true;
+  ctx->sur_steps = 0;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir3_surrogate_last_check(pcsir3_ctx* ctx, pcsir_surrogate_check* out) {
+  if (!ctx || !out) return PCSIR_EINVAL;
+  if (!ctx->sur_ran || ctx->last_kind != 1) return fail3(ctx, PCSIR_ESTATE, "the last step did not use a surrogate");
+  SurStats st{};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ctx->sur.stats, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail3(ctx, e, "reading surrogate statistics");
+  std::memset(out, 0, sizeof(*out));
+  const int64_t nb = ctx->host_res->n_bins;
+  const int64_t nho = std::min<int64_t>(st.n_ho, ctx->sur.ho_cap);
+  out->n_dummies = nb;
+  out->n_holdout = nho;
+  out->n_significant = st.n_sig;
+  out->n_clipped = st.n_clipped;
+  out->fallback = st.fallback ? 1 : 0;
+  out->n_exact = st.fallback ? nb : (int64_t)st.n_ho + (int64_t)st.n_clipped;
+  out->max_abs_err = st.max_err;
+  out->rms_err = nho > 0 ? std::sqrt(st.sum_sq / (double)nho) : 0.0;
   return PCSIR_OK;
 }
 

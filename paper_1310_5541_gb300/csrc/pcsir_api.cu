@@ -440,6 +440,7 @@ pcsir_status pcsir_attach_surrogate(pcsir_ctx* ctx, pcsir_surrogate* sur, double
     return fail(ctx, PCSIR_EINVAL, "invalid held-out fraction, window or error threshold");
   if (ctx->cfg.patch != PCSIR_SUR_PATCH || ctx->cfg.lik_kind != PCSIR_LIK_POISSON)
     return fail(ctx, PCSIR_EINVAL, "the surrogate models the Poisson likelihood over a 21 x 21 patch");
+  if (sur_dim(sur) != 2) return fail(ctx, PCSIR_EINVAL, "a 3D surrogate attaches to a 3D context");
   SurStep& sp = ctx->sur;
   if (!sp.stats) {
     constexpr int HO_CAP = 1 << 16;

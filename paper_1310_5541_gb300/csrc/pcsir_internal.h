@@ -132,6 +132,11 @@ cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int d
                                int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur = nullptr);
 // largest image the surrogate's window-term buffer holds (pcsir_surrogate.cu)
 int64_t sur_max_pixels(const pcsir_surrogate* s);
+// 2 or 3: the surrogate's input geometry
+int sur_dim(const pcsir_surrogate* s);
+// surrogate predictions of the non-clipped dummies of a 3D step and the held-out check
+cudaError_t launch_sur_step3(const SurStep& sp, const StepBuffers& b, double bg, double sigma_xy, const float* vol,
+                             int W, int H, int D, cudaStream_t s);
 // the surrogate's input normalisation constants (its creation config)
 void sur_refs(const pcsir_surrogate* s, double* i0_ref, double* sigma_ref);
 // surrogate predictions of the non-clipped dummies and the held-out check (pcsir_surrogate.cu)

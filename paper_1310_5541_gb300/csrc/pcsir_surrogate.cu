@@ -23,54 +23,113 @@
 
 namespace pcsir {
 
-constexpr int SUR_IN = PCSIR_SUR_INPUTS;  // 445
-constexpr int SUR_K1 = 448;               // inputs padded to 7 chunks of 64
-constexpr int SUR_HID = PCSIR_SUR_HIDDEN; // 256
-constexpr int SUR_NPIX = PCSIR_SUR_PATCH * PCSIR_SUR_PATCH;  // 441
+constexpr int SUR_HID = PCSIR_SUR_HIDDEN;  // 256
+constexpr int SUR_K1_MAX = 896;            // the largest padded input count (3D)
 
-constexpr long long OFF_W1 = 0;
-constexpr long long OFF_B1 = OFF_W1 + (long long)SUR_HID * SUR_K1;
-constexpr long long OFF_W2 = OFF_B1 + SUR_HID;
-constexpr long long OFF_B2 = OFF_W2 + (long long)SUR_HID * SUR_HID;
-constexpr long long OFF_W3 = OFF_B2 + SUR_HID;
-constexpr long long OFF_B3 = OFF_W3 + SUR_HID;
-constexpr long long NDEV = OFF_B3 + 1;
+// Input geometry of a surrogate: the patch and the state features that follow
+// it, and the packed parameter layout that depends on the input count.
+//   2D: 21 x 21 pixels, then 2 (x - cx), 2 (y - cy), I0 / i0_ref, sigma / sigma_ref: 445 inputs
+//   3D: 11 x 11 x 7 voxels, then 2 (x - cx), 2 (y - cy), 2 (z - cz), I0 / i0_ref,
+//       sigma_xy / sigma_ref: 852 inputs
+// Inputs are padded with zeros to k1, a multiple of 64.
+struct SurGeom {
+  int dim;
+  int px, py, pz;  // patch sides
+  int npix, nfeat, nin, k1;
+  int irow;        // row of I0 in the dummy array (2D: 4, 3D: 6)
+  long long off_w1, off_b1, off_w2, off_b2, off_w3, off_b3, ndev;
+};
 
-// Inputs of one state: patch value f < 441, then the four state features.
+inline SurGeom make_geom(int dim) {
+  SurGeom g{};
+  g.dim = dim;
+  if (dim == 3) {
+    g.px = g.py = PCSIR_SUR3_PATCH_XY;
+    g.pz = PCSIR_SUR3_PATCH_Z;
+    g.nfeat = 5;
+    g.irow = 6;
+  } else {
+    g.px = g.py = PCSIR_SUR_PATCH;
+    g.pz = 1;
+    g.nfeat = 4;
+    g.irow = 4;
+  }
+  g.npix = g.px * g.py * g.pz;
+  g.nin = g.npix + g.nfeat;
+  g.k1 = (g.nin + 63) / 64 * 64;
+  g.off_w1 = 0;
+  g.off_b1 = g.off_w1 + (long long)SUR_HID * g.k1;
+  g.off_w2 = g.off_b1 + SUR_HID;
+  g.off_b2 = g.off_w2 + (long long)SUR_HID * SUR_HID;
+  g.off_w3 = g.off_b2 + SUR_HID;
+  g.off_b3 = g.off_w3 + SUR_HID;
+  g.ndev = g.off_b3 + 1;
+  return g;
+}
+
+// Inputs of one state: patch value f < npix, then the state features.
 struct SurFeat {
   float bg, inv_i0ref, sig_feat;
   double inv_i0ref_d;
 };
 
 struct SurRowInfo {
-  long long base;  // image offset of the patch's top-left pixel
-  float fx, fy, fi;
+  long long base;   // volume offset of the patch's first voxel (smallest x, y, z)
+  float feat[4];    // 2D: dx, dy, I0; 3D: dx, dy, dz, I0 (scaled as above)
   int valid;
 };
 
-__device__ __forceinline__ SurRowInfo sur_row_info(const double* dummy, long long stride, long long d, int W, int H,
-                                                   const SurFeat& sf) {
-  SurRowInfo ri{0, 0.f, 0.f, 0.f, 0};
-  const double x = dummy[d], y = dummy[stride + d], i0 = dummy[4 * stride + d];
-  int cx, cy;
-  if (sur_origin(x, y, W, H, &cx, &cy)) {
-    ri.valid = 1;
-    ri.base = (long long)(cy - SUR_R) * W + (cx - SUR_R);
-    ri.fx = (float)(2.0 * (x - (double)cx));
-    ri.fy = (float)(2.0 * (y - (double)cy));
-    ri.fi = (float)(i0 * sf.inv_i0ref_d);
+// nearest voxel of a state and whether its whole patch lies inside the W x H x D volume
+__device__ __forceinline__ SurRowInfo sur_row_info(const SurGeom& g, const double* dummy, long long stride,
+                                                   long long d, int W, int H, int D, const SurFeat& sf) {
+  SurRowInfo ri{0, {0.f, 0.f, 0.f, 0.f}, 0};
+  const double x = dummy[d], y = dummy[stride + d], i0 = dummy[g.irow * stride + d];
+  const int rx = g.px >> 1, ry = g.py >> 1, rz = g.pz >> 1;
+  if (g.dim == 2) {
+    int cx, cy;
+    if (sur_origin(x, y, W, H, &cx, &cy)) {
+      ri.valid = 1;
+      ri.base = (long long)(cy - ry) * W + (cx - rx);
+      ri.feat[0] = (float)(2.0 * (x - (double)cx));
+      ri.feat[1] = (float)(2.0 * (y - (double)cy));
+      ri.feat[2] = (float)(i0 * sf.inv_i0ref_d);
+    }
+  } else {
+    const double z = dummy[2 * stride + d];
+    const double fx = floor(x + 0.5), fy = floor(y + 0.5), fz = floor(z + 0.5);
+    if (fx - rx >= 0.0 && fx + rx <= (double)(W - 1) && fy - ry >= 0.0 && fy + ry <= (double)(H - 1) &&
+        fz - rz >= 0.0 && fz + rz <= (double)(D - 1)) {
+      const int cx = (int)fx, cy = (int)fy, cz = (int)fz;
+      ri.valid = 1;
+      ri.base = ((long long)(cz - rz) * H + (cy - ry)) * W + (cx - rx);
+      ri.feat[0] = (float)(2.0 * (x - fx));
+      ri.feat[1] = (float)(2.0 * (y - fy));
+      ri.feat[2] = (float)(2.0 * (z - fz));
+      ri.feat[3] = (float)(i0 * sf.inv_i0ref_d);
+    }
   }
   return ri;
 }
 
-__device__ __forceinline__ float sur_input(const float* __restrict__ img, const SurRowInfo& ri, int f, int poff_f,
-                                           const SurFeat& sf) {
-  if (f < SUR_NPIX) return (__ldg(img + ri.base + poff_f) - sf.bg) * sf.inv_i0ref;
-  if (f == SUR_NPIX) return ri.fx;
-  if (f == SUR_NPIX + 1) return ri.fy;
-  if (f == SUR_NPIX + 2) return ri.fi;
-  if (f == SUR_NPIX + 3) return sf.sig_feat;
+// offset of patch value f from the patch's first voxel
+__device__ __forceinline__ int sur_poff(const SurGeom& g, int f, int W, int H) {
+  if (f >= g.npix) return 0;
+  const int pxy = g.px * g.py;
+  return ((f / pxy) * H + (f % pxy) / g.px) * W + (f % g.px);
+}
+
+__device__ __forceinline__ float sur_input(const SurGeom& g, const float* __restrict__ img, const SurRowInfo& ri,
+                                           int f, int poff_f, const SurFeat& sf) {
+  if (f < g.npix) return (__ldg(img + ri.base + poff_f) - sf.bg) * sf.inv_i0ref;
+  const int j = f - g.npix;
+  if (j < g.nfeat - 1) return ri.feat[j];
+  if (j == g.nfeat - 1) return sf.sig_feat;
   return 0.0f;
+}
+
+// index of the window term of the window whose first voxel is at base (its centre voxel)
+__device__ __forceinline__ long long sur_tindex(const SurGeom& g, long long base, int W, int H) {
+  return base + ((long long)(g.pz >> 1) * H + (g.py >> 1)) * W + (g.px >> 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,22 +182,78 @@ k_sur_window(const float* __restrict__ img, int W, int H, float log_bg, df pbg, 
   }
 }
 
-// index of the window term of the window whose top-left pixel is at base
-__device__ __forceinline__ long long sur_tindex(long long base, int W) { return base + (long long)SUR_R * W + SUR_R; }
+
+// 3D window term: T(cx, cy, cz) = sum over the px x py x pz window of
+// (z - z log z + log(bg) z) - npix bg, for every window inside the volume (NaN
+// elsewhere).  Three separable passes (x, y, z), each summing in double-float
+// (pairs of FP32); the per-voxel term is formed in the x pass.
+__global__ void k_sur_win3_x(const float* __restrict__ vol, int W, int H, int D, int rx, float log_bg,
+                             float* __restrict__ ah, float* __restrict__ al) {
+  const long long n = (long long)W * H * D;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W);
+    df acc{0.0f, 0.0f};
+    for (int k = -rx; k <= rx; ++k) {
+      const int xx = x + k;
+      if (xx < 0 || xx >= W) continue;
+      const float z = vol[i + k];
+      acc = df_add_f(acc, (z > 0.0f ? z - z * logf(z) : 0.0f) + log_bg * z);
+    }
+    ah[i] = acc.hi;
+    al[i] = acc.lo;
+  }
+}
+
+// one separable pass along y (stride W, extent H) or z (stride W H, extent D)
+__global__ void k_sur_win3_pass(const float* __restrict__ ih, const float* __restrict__ il, int W, int H, int D,
+                                int axis, int r, float* __restrict__ oh, float* __restrict__ ol) {
+  const long long n = (long long)W * H * D;
+  const long long stride = axis == 1 ? (long long)W : (long long)W * H;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = axis == 1 ? (int)((i / W) % H) : (int)(i / ((long long)W * H));
+    const int ext = axis == 1 ? H : D;
+    df acc{0.0f, 0.0f};
+    for (int k = -r; k <= r; ++k) {
+      const int cc = c + k;
+      if (cc < 0 || cc >= ext) continue;
+      acc = df_add(acc, df{ih[i + k * stride], il[i + k * stride]});
+    }
+    oh[i] = acc.hi;
+    ol[i] = acc.lo;
+  }
+}
+
+__global__ void k_sur_win3_final(const float* __restrict__ ih, const float* __restrict__ il, int W, int H, int D,
+                                 int rx, int ry, int rz, df pbg, float* __restrict__ T) {
+  const long long n = (long long)W * H * D;
+  const long long plane = (long long)W * H;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W), y = (int)((i / W) % H), z = (int)(i / plane);
+    df acc{0.0f, 0.0f};
+    for (int k = -rz; k <= rz; ++k) {
+      const int zz = z + k;
+      if (zz < 0 || zz >= D) continue;
+      acc = df_add(acc, df{ih[i + k * plane], il[i + k * plane]});
+    }
+    acc = df_add(acc, df{-pbg.hi, -pbg.lo});
+    const bool inside = x >= rx && x + rx <= W - 1 && y >= ry && y + ry <= H - 1 && z >= rz && z + rz <= D - 1;
+    T[i] = inside ? acc.hi + acc.lo : __int_as_float(0x7fc00000);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Parameters: random initial values and bf16 copies.
 // ---------------------------------------------------------------------------
-__global__ void k_sur_init(float* __restrict__ P, unsigned long long seed) {
+__global__ void k_sur_init(float* __restrict__ P, unsigned long long seed, SurGeom gm) {
   const unsigned long long s0 = splitmix64(seed);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < NDEV; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gm.ndev; i += (long long)gridDim.x * blockDim.x) {
     const float u = (float)(splitmix64(s0 + (unsigned long long)i) >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
     float v = 0.0f;
-    if (i < OFF_B1) {
-      if ((int)(i % SUR_K1) < SUR_IN) v = u * sqrtf(3.0f / SUR_IN);
-    } else if (i >= OFF_W2 && i < OFF_B2) {
+    if (i < gm.off_b1) {
+      if ((int)(i % gm.k1) < gm.nin) v = u * sqrtf(3.0f / gm.nin);
+    } else if (i >= gm.off_w2 && i < gm.off_b2) {
       v = u * sqrtf(3.0f / SUR_HID);
-    } else if (i >= OFF_W3 && i < OFF_B3) {
+    } else if (i >= gm.off_w3 && i < gm.off_b3) {
       v = u * sqrtf(3.0f / SUR_HID);
     }
     P[i] = v;
@@ -146,13 +261,13 @@ __global__ void k_sur_init(float* __restrict__ P, unsigned long long seed) {
 }
 
 __global__ void k_sur_tobf16(const float* __restrict__ P, __nv_bfloat16* __restrict__ W1b,
-                             __nv_bfloat16* __restrict__ W2b) {
-  const long long n1 = (long long)SUR_HID * SUR_K1, n2 = (long long)SUR_HID * SUR_HID;
+                             __nv_bfloat16* __restrict__ W2b, SurGeom gm) {
+  const long long n1 = (long long)SUR_HID * gm.k1, n2 = (long long)SUR_HID * SUR_HID;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2; i += (long long)gridDim.x * blockDim.x) {
     if (i < n1)
-      W1b[i] = __float2bfloat16_rn(P[OFF_W1 + i]);
+      W1b[i] = __float2bfloat16_rn(P[gm.off_w1 + i]);
     else
-      W2b[i - n1] = __float2bfloat16_rn(P[OFF_W2 + i - n1]);
+      W2b[i - n1] = __float2bfloat16_rn(P[gm.off_w2 + i - n1]);
   }
 }
 
@@ -164,15 +279,12 @@ __global__ void k_sur_tobf16(const float* __restrict__ P, __nv_bfloat16* __restr
 constexpr int ADD_THREADS = 256;
 
 __global__ void __launch_bounds__(ADD_THREADS)
-k_sur_add_count(const double* __restrict__ dummy, long long stride, long long n, int W, int H,
+k_sur_add_count(SurGeom gm, const double* __restrict__ dummy, long long stride, long long n, int W, int H, int D,
                 unsigned* __restrict__ blk_cnt, const unsigned long long* __restrict__ count,
                 unsigned long long* __restrict__ base) {
   const long long d = (long long)blockIdx.x * ADD_THREADS + threadIdx.x;
   int ok = 0;
-  if (d < n) {
-    int cx, cy;
-    ok = sur_origin(dummy[d], dummy[stride + d], W, H, &cx, &cy) ? 1 : 0;
-  }
+  if (d < n) ok = sur_row_info(gm, dummy, stride, d, W, H, D, SurFeat{0.f, 0.f, 0.f, 0.0}).valid;
   const int c = __syncthreads_count(ok);
   if (threadIdx.x == 0) {
     blk_cnt[blockIdx.x] = (unsigned)c;
@@ -181,8 +293,9 @@ k_sur_add_count(const double* __restrict__ dummy, long long stride, long long n,
 }
 
 __global__ void __launch_bounds__(ADD_THREADS)
-k_sur_add_write(const double* __restrict__ dummy, long long stride, long long n, const double* __restrict__ ll,
-                double label_floor, const float* __restrict__ T, const float* __restrict__ img, int W, int H, SurFeat sf, const unsigned* __restrict__ blk_cnt,
+k_sur_add_write(SurGeom gm, const double* __restrict__ dummy, long long stride, long long n,
+                const double* __restrict__ ll, double label_floor, const float* __restrict__ T,
+                const float* __restrict__ img, int W, int H, int D, SurFeat sf, const unsigned* __restrict__ blk_cnt,
                 const unsigned long long* __restrict__ base, unsigned long long* __restrict__ count,
                 unsigned* __restrict__ done, long long capacity, __nv_bfloat16* __restrict__ X,
                 float* __restrict__ y, uint8_t* __restrict__ cens) {
@@ -201,8 +314,8 @@ k_sur_add_write(const double* __restrict__ dummy, long long stride, long long n,
   if (lane == 0) atomicAdd(&s_off, acc);
   // this block's states: validity and the exclusive rank among the valid ones
   const long long d = (long long)blockIdx.x * ADD_THREADS + tid;
-  SurRowInfo ri{0, 0.f, 0.f, 0.f, 0};
-  if (d < n) ri = sur_row_info(dummy, stride, d, W, H, sf);
+  SurRowInfo ri{0, {0.f, 0.f, 0.f, 0.f}, 0};
+  if (d < n) ri = sur_row_info(gm, dummy, stride, d, W, H, D, sf);
   const unsigned bal = __ballot_sync(0xffffffffu, ri.valid != 0);
   if (lane == 0) s_wsum[warp] = __popc(bal);
   __syncthreads();
@@ -217,21 +330,17 @@ k_sur_add_write(const double* __restrict__ dummy, long long stride, long long n,
   for (int w = 0; w < ADD_THREADS / 32; ++w) total += s_wsum[w];
   __syncthreads();
   const unsigned long long off = *base + s_off;
-  // one warp per row: 448 inputs, 14 per lane
+  // one warp per row: k1 inputs, k1 / 32 per lane
   for (int r = warp; r < (int)total; r += ADD_THREADS / 32) {
     const unsigned long long row = off + (unsigned long long)r;
     if (row >= (unsigned long long)capacity) break;
     const SurRowInfo q = s_ri[r];
-#pragma unroll
-    for (int j = 0; j < SUR_K1 / 32; ++j) {
-      const int f = lane + 32 * j;
-      const int po = f < SUR_NPIX ? (f / PCSIR_SUR_PATCH) * W + (f % PCSIR_SUR_PATCH) : 0;
-      X[row * SUR_K1 + f] = __float2bfloat16_rn(sur_input(img, q, f, po, sf));
-    }
+    for (int f = lane; f < gm.k1; f += 32)
+      X[row * gm.k1 + f] = __float2bfloat16_rn(sur_input(gm, img, q, f, sur_poff(gm, f, W, H), sf));
     if (lane == 0) {
       const double v = ll[s_src[r]];
       const bool below = v < label_floor;
-      y[row] = (float)((below ? label_floor : v) - (double)T[sur_tindex(q.base, W)]);
+      y[row] = (float)((below ? label_floor : v) - (double)T[sur_tindex(gm, q.base, W, H)]);
       cens[row] = below ? 1 : 0;
     }
   }
@@ -286,18 +395,18 @@ __device__ __forceinline__ long long sur_batch_row(long long begin, long long ra
   return begin + (long long)(h % (unsigned long long)range);
 }
 
-// one warp per minibatch row: 448 bf16 inputs (56 x 16 bytes) and the normalised label
+// one warp per minibatch row: k1 bf16 inputs (k1 / 8 x 16 bytes) and the normalised label
 __global__ void k_sur_gather(const __nv_bfloat16* __restrict__ X, const float* __restrict__ y,
                              const uint8_t* __restrict__ cens, long long begin, long long range,
                              unsigned long long seed, long long step, int bt, const double* __restrict__ norm,
-                             __nv_bfloat16* __restrict__ Xb, float* __restrict__ yb, uint8_t* __restrict__ cb) {
+                             __nv_bfloat16* __restrict__ Xb, float* __restrict__ yb, uint8_t* __restrict__ cb, int k1) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= bt) return;
   const long long r = sur_batch_row(begin, range, seed, step, i, bt);
-  const uint4* src = reinterpret_cast<const uint4*>(X + r * SUR_K1);
-  uint4* dst = reinterpret_cast<uint4*>(Xb + (long long)i * SUR_K1);
-  for (int j = lane; j < SUR_K1 / 8; j += 32) dst[j] = src[j];
+  const uint4* src = reinterpret_cast<const uint4*>(X + r * k1);
+  uint4* dst = reinterpret_cast<uint4*>(Xb + (long long)i * k1);
+  for (int j = lane; j < k1 / 8; j += 32) dst[j] = src[j];
   if (lane == 0) {
     yb[i] = (float)(((double)y[r] - norm[0]) / norm[1]);
     cb[i] = cens[r];
@@ -314,7 +423,7 @@ constexpr int HEAD_THREADS = 256;
 __global__ void __launch_bounds__(HEAD_THREADS)
 k_sur_head(const float* __restrict__ Z2, const float* __restrict__ yb, const uint8_t* __restrict__ cb, int bt,
            const float* __restrict__ P,
-           float* __restrict__ G, __nv_bfloat16* __restrict__ G2, float* __restrict__ loss) {
+           float* __restrict__ G, __nv_bfloat16* __restrict__ G2, float* __restrict__ loss, SurGeom gm) {
   __shared__ float s_w3[SUR_HID], s_db2[SUR_HID];
   __shared__ float s_misc[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -324,8 +433,8 @@ k_sur_head(const float* __restrict__ Z2, const float* __restrict__ yb, const uin
   }
   if (tid < 2) s_misc[tid] = 0.0f;
   __syncthreads();
-  const float* w3 = P + OFF_W3;
-  const float b3 = P[OFF_B3];
+  const float* w3 = P + gm.off_w3;
+  const float b3 = P[gm.off_b3];
   float wl[8], dw3[8], db2[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -372,11 +481,11 @@ k_sur_head(const float* __restrict__ Z2, const float* __restrict__ yb, const uin
   }
   __syncthreads();
   for (int j = tid; j < SUR_HID; j += HEAD_THREADS) {
-    atomicAdd(G + OFF_W3 + j, s_w3[j]);
-    atomicAdd(G + OFF_B2 + j, s_db2[j]);
+    atomicAdd(G + gm.off_w3 + j, s_w3[j]);
+    atomicAdd(G + gm.off_b2 + j, s_db2[j]);
   }
   if (tid == 0) {
-    atomicAdd(G + OFF_B3, s_misc[0]);
+    atomicAdd(G + gm.off_b3, s_misc[0]);
     if (loss) atomicAdd(loss, s_misc[1]);
   }
 }
@@ -386,9 +495,9 @@ k_sur_head(const float* __restrict__ Z2, const float* __restrict__ yb, const uin
 // bf16 weight copies.
 __global__ void k_sur_adam(float* __restrict__ P, float* __restrict__ G, float* __restrict__ Mo,
                            float* __restrict__ V, float lr, float c1, float c2, __nv_bfloat16* __restrict__ W1b,
-                           __nv_bfloat16* __restrict__ W2b) {
+                           __nv_bfloat16* __restrict__ W2b, SurGeom gm) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < NDEV; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gm.ndev; i += (long long)gridDim.x * blockDim.x) {
     const float g = G[i];
     const float m = b1 * Mo[i] + (1.0f - b1) * g;
     const float v = b2 * V[i] + (1.0f - b2) * g * g;
@@ -397,21 +506,21 @@ __global__ void k_sur_adam(float* __restrict__ P, float* __restrict__ G, float* 
     const float p = P[i] - lr * (m * c1) / (sqrtf(v * c2) + eps);
     P[i] = p;
     G[i] = 0.0f;
-    if (i < OFF_B1)
+    if (i < gm.off_b1)
       W1b[i] = __float2bfloat16_rn(p);
-    else if (i >= OFF_W2 && i < OFF_B2)
-      W2b[i - OFF_W2] = __float2bfloat16_rn(p);
+    else if (i >= gm.off_w2 && i < gm.off_b2)
+      W2b[i - gm.off_w2] = __float2bfloat16_rn(p);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Fused inference.  Per tile of 128 states the inputs are built from the
-// image straight into the shared-memory operand layout; layer 1 (K = 448,
-// seven chunks of 64) and layer 2 (K = 256, four chunks, the bf16
+// image straight into the shared-memory operand layout; layer 1 (K = k1:
+// 448 in 2D, seven chunks of 64; 896 in 3D) and layer 2 (K = 256, four chunks, the bf16
 // activations of layer 1 kept in shared memory) accumulate in the same 256
 // TMEM columns, and the output layer runs in FP32 on the TMEM lanes.
 //
-// The eleven weight chunks (32 KB each) are stored pre-arranged in the
+// The weight chunks (32 KB each, k1 / 64 + 4 of them) are stored pre-arranged in the
 // swizzled shared-memory layout, so one thread fetches a chunk with a single
 // bulk asynchronous copy completing on an mbarrier.  Input and weight
 // buffers are doubled: the copy and the input build of chunk q overlap the
@@ -420,29 +529,30 @@ __global__ void k_sur_adam(float* __restrict__ P, float* __restrict__ G, float* 
 // columns in halves.
 // ---------------------------------------------------------------------------
 constexpr int SI_THREADS = 256;
-constexpr int SI_CHUNKS = SUR_K1 / MM_K + SUR_HID / MM_K;  // 7 + 4
+constexpr int SI_CHUNKS_MAX = SUR_K1_MAX / MM_K + SUR_HID / MM_K;  // 14 + 4 (3D)
 constexpr int SI_X = 128 * MM_K * 2;      // 16 KB: one input chunk
 constexpr int SI_W = SUR_HID * MM_K * 2;  // 32 KB: one weight chunk
 constexpr int SI_A = 128 * SUR_HID * 2;   // 64 KB: layer-1 activations (four chunks)
-constexpr int SI_SMEM = 2 * SI_X + 2 * SI_W + SI_A + SUR_K1 * 4 + 128 * (int)sizeof(SurRowInfo) +
+constexpr int SI_SMEM = 2 * SI_X + 2 * SI_W + SI_A + SUR_K1_MAX * 4 + 128 * (int)sizeof(SurRowInfo) +
                         2 * 128 * 4 + 64;
 enum { SRC_STATES = 0, SRC_ROWS = 1 };
 
 struct SurNet {
-  const uint8_t* Wsw;   // SI_CHUNKS weight chunks in the shared-memory layout
+  const uint8_t* Wsw;   // k1 / 64 + 4 weight chunks in the shared-memory layout
   const float* P;       // FP32 parameters (biases, output layer)
   const double* norm;   // label mean and scale
 };
 
 struct SurInfer {
   SurNet net;
+  SurGeom gm;
   const double* dummy;
   long long stride;
   const __nv_bfloat16* rows;
   long long n;
   const unsigned* n_dev;  // when set, the count is *n_dev
   const float* img;
-  int W, H;
+  int W, H, D;
   SurFeat sf;
   const float* T;                 // window terms of img (states), or null (rows: label units)
   double* out;
@@ -452,16 +562,16 @@ struct SurInfer {
   unsigned* err;
 };
 
-// weight chunk q (W1 for q < 7, W2 after) rearranged into the shared-memory layout
+// weight chunk q (W1 for q < k1 / 64, W2 after) rearranged into the shared-memory layout
 __global__ void k_sur_pack(const __nv_bfloat16* __restrict__ W1b, const __nv_bfloat16* __restrict__ W2b,
-                           uint8_t* __restrict__ Wsw) {
-  const int total = SI_CHUNKS * SUR_HID * 8;
+                           uint8_t* __restrict__ Wsw, int k1) {
+  const int c1 = k1 / MM_K;
+  const int total = (c1 + SUR_HID / MM_K) * SUR_HID * 8;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     const int q = g / (SUR_HID * 8), rem = g % (SUR_HID * 8);
     const int r = rem >> 3, kg = (rem & 7) * 8;
-    const uint4 v = q < SUR_K1 / MM_K
-                        ? *reinterpret_cast<const uint4*>(W1b + (long long)r * SUR_K1 + q * MM_K + kg)
-                        : *reinterpret_cast<const uint4*>(W2b + (long long)r * SUR_HID + (q - SUR_K1 / MM_K) * MM_K + kg);
+    const uint4 v = q < c1 ? *reinterpret_cast<const uint4*>(W1b + (long long)r * k1 + q * MM_K + kg)
+                           : *reinterpret_cast<const uint4*>(W2b + (long long)r * SUR_HID + (q - c1) * MM_K + kg);
     *reinterpret_cast<uint4*>(Wsw + (long long)q * SI_W + mm_off(r, kg)) = v;
   }
 }
@@ -497,7 +607,7 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
   uint8_t* sW = sX + 2 * SI_X;           // two weight chunks
   uint8_t* sA = sW + 2 * SI_W;           // layer-1 activations
   int* poff = reinterpret_cast<int*>(sA + SI_A);
-  SurRowInfo* rowi = reinterpret_cast<SurRowInfo*>(poff + SUR_K1);
+  SurRowInfo* rowi = reinterpret_cast<SurRowInfo*>(poff + SUR_K1_MAX);
   float* part = reinterpret_cast<float*>(rowi + 128);  // [2][128] partial output sums
   uint64_t* bar_w = reinterpret_cast<uint64_t*>(part + 2 * 128);
   uint64_t* bar_m = bar_w + 2;
@@ -509,8 +619,10 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
   const long long n = a.n_dev ? (long long)*a.n_dev : a.n;
   const long long ntiles = (n + 127) / 128;
   if ((long long)blockIdx.x >= ntiles) return;
-  for (int f = tid; f < SUR_K1; f += SI_THREADS)
-    poff[f] = f < SUR_NPIX ? (f / PCSIR_SUR_PATCH) * a.W + (f % PCSIR_SUR_PATCH) : 0;
+  const SurGeom& gm = a.gm;
+  const int c1 = gm.k1 / MM_K;              // input chunks of layer 1
+  const int nchunks = c1 + SUR_HID / MM_K;  // and the four of layer 2
+  for (int f = tid; f < gm.k1; f += SI_THREADS) poff[f] = sur_poff(gm, f, a.W, a.H);
   if (warp == 0) tc_alloc(tslot, SUR_HID);
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -525,10 +637,10 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
   const uint32_t tmem = *tslot;
   const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * 128);
   const uint32_t idesc = mm_idesc(128, SUR_HID);
-  const float* b1 = a.net.P + OFF_B1;
-  const float* b2 = a.net.P + OFF_B2;
-  const float* w3 = a.net.P + OFF_W3;
-  const float b3 = a.net.P[OFF_B3];
+  const float* b1 = a.net.P + gm.off_b1;
+  const float* b2 = a.net.P + gm.off_b2;
+  const float* w3 = a.net.P + gm.off_w3;
+  const float b3 = a.net.P[gm.off_b3];
   const double mean = a.net.norm[0], scale = a.net.norm[1];
   uint32_t ph_w[2] = {0u, 0u}, ph_m[2] = {0u, 0u};
   bool out_w[2] = {false, false}, out_m[2] = {false, false};  // copy / MMA in flight on buffer b
@@ -549,15 +661,15 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
     const long long d = t * 128 + (tid & 127);
     if (tid < 128) {
       if (SRC == SRC_STATES) {
-        SurRowInfo ri{0, 0.f, 0.f, 0.f, 0};
-        if (d < n) ri = sur_row_info(a.dummy, a.stride, d, a.W, a.H, a.sf);
+        SurRowInfo ri{0, {0.f, 0.f, 0.f, 0.f}, 0};
+        if (d < n) ri = sur_row_info(gm, a.dummy, a.stride, d, a.W, a.H, a.D, a.sf);
         rowi[tid] = ri;
       } else {
-        rowi[tid] = SurRowInfo{0, 0.f, 0.f, 0.f, d < n ? 1 : 0};
+        rowi[tid] = SurRowInfo{0, {0.f, 0.f, 0.f, 0.f}, d < n ? 1 : 0};
       }
     }
     __syncthreads();
-    for (int c = 0; c < SI_CHUNKS && ok; ++c, ++q) {
+    for (int c = 0; c < nchunks && ok; ++c, ++q) {
       const int b = q & 1;
       wait_mma(b);  // buffers b free again
       if (!ok) break;
@@ -565,7 +677,7 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
         bulk_load(sW + b * SI_W, a.net.Wsw + (long long)c * SI_W, SI_W, &bar_w[b]);
         out_w[b] = true;
       }
-      if (c < SUR_K1 / MM_K) {
+      if (c < c1) {
         // inputs of chunk c: 128 rows x 8 groups of 8, four groups per thread, loads first
         float v[4][8];
         uint4 u[4];
@@ -575,13 +687,13 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
           const int r = g >> 3, kg = (g & 7) * 8;
           const SurRowInfo ri = rowi[r];
           if (SRC == SRC_ROWS) {
-            u[j] = ri.valid ? __ldg(reinterpret_cast<const uint4*>(a.rows + (t * 128 + r) * SUR_K1 + c * MM_K + kg))
+            u[j] = ri.valid ? __ldg(reinterpret_cast<const uint4*>(a.rows + (t * 128 + r) * gm.k1 + c * MM_K + kg))
                             : make_uint4(0u, 0u, 0u, 0u);
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int f = c * MM_K + kg + i;
-              v[j][i] = ri.valid ? sur_input(a.img, ri, f, poff[f], a.sf) : 0.0f;
+              v[j][i] = ri.valid ? sur_input(gm, a.img, ri, f, poff[f], a.sf) : 0.0f;
             }
           }
         }
@@ -592,7 +704,7 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
           if (SRC == SRC_STATES) u[j] = pack_bf16x8(v[j]);
           *reinterpret_cast<uint4*>(sX + b * SI_X + mm_off(r, kg)) = u[j];
         }
-      } else if (c == SUR_K1 / MM_K) {
+      } else if (c == c1) {
         // layer-1 epilogue: all layer-1 MMAs done (the other buffer's too), then bias, SiLU, bf16
         wait_mma(b ^ 1);
         if (!ok) break;
@@ -621,9 +733,8 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
       if (!ok) break;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t a0 = c < SUR_K1 / MM_K ? smem_u32(sX + b * SI_X)
-                                              : smem_u32(sA + (c - SUR_K1 / MM_K) * SI_X);
-        tc_mma_chunk(tmem, a0, smem_u32(sW + b * SI_W), idesc, c == 0 || c == SUR_K1 / MM_K);
+        const uint32_t a0 = c < c1 ? smem_u32(sX + b * SI_X) : smem_u32(sA + (c - c1) * SI_X);
+        tc_mma_chunk(tmem, a0, smem_u32(sW + b * SI_W), idesc, c == 0 || c == c1);
         tc_commit(&bar_m[b]);
       }
       out_m[b] = true;
@@ -648,7 +759,7 @@ __global__ void __launch_bounds__(SI_THREADS, 1) k_sur_infer(SurInfer a) {
     if (tid < 128) {
       const long long dd = t * 128 + tid;
       double ll = mean + scale * (double)(part[tid] + part[128 + tid] + b3);
-      if (SRC == SRC_STATES && rowi[tid].valid) ll += (double)a.T[sur_tindex(rowi[tid].base, a.W)];
+      if (SRC == SRC_STATES && rowi[tid].valid) ll += (double)a.T[sur_tindex(gm, rowi[tid].base, a.W, a.H)];
       if (rowi[tid].valid) {
         if (!isfinite(ll) && a.bad) atomicOr(a.bad, 1u);
         a.out[dd] = ll;
@@ -765,7 +876,8 @@ struct pcsir_surrogate {
   int num_sms = 0;
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *V = nullptr;
   __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
-  uint8_t* Wsw = nullptr;  // SI_CHUNKS x 32 KB, inference layout
+  SurGeom gm{};            // input geometry (2D or 3D patch)
+  uint8_t* Wsw = nullptr;  // (k1 / 64 + 4) x 32 KB, inference layout
   double* norm = nullptr;  // device: label mean, scale
   double host_mean = 0.0, host_scale = 1.0;
   __nv_bfloat16* X = nullptr;
@@ -773,6 +885,7 @@ struct pcsir_surrogate {
   uint8_t* cens = nullptr;
   uint8_t* cb = nullptr;
   float* T = nullptr;  // window terms of the current image (max_pixels)
+  float* wbuf = nullptr;  // 3D: scratch of the separable window passes (4 x max_pixels)
   unsigned long long* count = nullptr;
   unsigned long long* add_base = nullptr;
   unsigned* add_cnt = nullptr;
@@ -833,16 +946,29 @@ SurNet net_of(const pcsir_surrogate* s) { return SurNet{s->Wsw, s->P, s->norm}; 
 
 // inference copy of the weights in the shared-memory layout (after any change of W1b / W2b)
 cudaError_t pack_weights(const pcsir_surrogate* s, cudaStream_t st) {
-  k_sur_pack<<<2 * s->num_sms, 256, 0, st>>>(s->W1b, s->W2b, s->Wsw);
+  k_sur_pack<<<2 * s->num_sms, 256, 0, st>>>(s->W1b, s->W2b, s->Wsw, s->gm.k1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_window(const pcsir_surrogate* s, const float* img, int W, int H, double bg, cudaStream_t st) {
-  if ((long long)W * H > s->cfg.max_pixels) return cudaErrorInvalidValue;
-  dim3 grid((W + WT_TILE - 1) / WT_TILE, (H + WT_TILE - 1) / WT_TILE);
-  const double pbg = (double)SUR_NPIX * bg;
+cudaError_t launch_window(const pcsir_surrogate* s, const float* img, int W, int H, int D, double bg,
+                          cudaStream_t st) {
+  if ((long long)W * H * D > s->cfg.max_pixels) return cudaErrorInvalidValue;
+  const double pbg = (double)s->gm.npix * bg;
   const df pbg_df{(float)pbg, (float)(pbg - (double)(float)pbg)};
-  k_sur_window<<<grid, 256, 0, st>>>(img, W, H, (float)std::log(bg), pbg_df, s->T);
+  if (s->gm.dim == 2) {
+    dim3 grid((W + WT_TILE - 1) / WT_TILE, (H + WT_TILE - 1) / WT_TILE);
+    k_sur_window<<<grid, 256, 0, st>>>(img, W, H, (float)std::log(bg), pbg_df, s->T);
+    return cudaGetLastError();
+  }
+  const long long n = (long long)W * H * D;
+  const int grid = grid_for(n, 256, s->num_sms);
+  float* ah = s->wbuf;
+  float* al = ah + s->cfg.max_pixels;
+  float* bh = al + s->cfg.max_pixels;
+  float* bl = bh + s->cfg.max_pixels;
+  k_sur_win3_x<<<grid, 256, 0, st>>>(img, W, H, D, s->gm.px >> 1, (float)std::log(bg), ah, al);
+  k_sur_win3_pass<<<grid, 256, 0, st>>>(ah, al, W, H, D, 1, s->gm.py >> 1, bh, bl);
+  k_sur_win3_final<<<grid, 256, 0, st>>>(bh, bl, W, H, D, s->gm.px >> 1, s->gm.py >> 1, s->gm.pz >> 1, pbg_df, s->T);
   return cudaGetLastError();
 }
 
@@ -865,21 +991,22 @@ cudaError_t fwd_bwd(pcsir_surrogate* s, int bt, float* loss, cudaStream_t st) {
   GemmArgs g{};
   g.err = s->err;
   // layer 1: Z1 = Xb W1^T + b1, A1 = silu(Z1)
-  g.A = s->Xb; g.sam = SUR_K1; g.sak = 1;
-  g.B = s->W1b; g.sbn = SUR_K1; g.sbk = 1;
+  g.A = s->Xb; g.sam = s->gm.k1; g.sak = 1;
+  g.B = s->W1b; g.sbn = s->gm.k1; g.sbk = 1;
   g.C = s->Z1; g.ldc = SUR_HID;
-  g.M = bt; g.N = SUR_HID; g.K = SUR_K1;
-  g.epi = EPI_ACT; g.bias = s->P + OFF_B1; g.act = s->A1; g.ld_act = SUR_HID;
+  g.M = bt; g.N = SUR_HID; g.K = s->gm.k1;
+  g.epi = EPI_ACT; g.bias = s->P + s->gm.off_b1; g.act = s->A1; g.ld_act = SUR_HID;
   cudaError_t e = launch_gemm(g, st, nt_act, 1);
   if (e != cudaSuccess) return e;
   // layer 2: Z2 = A1 W2^T + b2
   g.A = s->A1; g.sam = SUR_HID; g.sak = 1;
   g.B = s->W2b; g.sbn = SUR_HID; g.sbk = 1;
   g.C = s->Z2; g.K = SUR_HID;
-  g.bias = s->P + OFF_B2; g.act = nullptr;
+  g.bias = s->P + s->gm.off_b2; g.act = nullptr;
   if ((e = launch_gemm(g, st, nt_act, 1)) != cudaSuccess) return e;
   // output layer, loss, G2 and the gradients of w3, b2, b3
-  k_sur_head<<<std::min(mt * 4, sms * 2), HEAD_THREADS, 0, st>>>(s->Z2, s->yb, s->cb, bt, s->P, s->G, s->G2, loss);
+  k_sur_head<<<std::min(mt * 4, sms * 2), HEAD_THREADS, 0, st>>>(s->Z2, s->yb, s->cb, bt, s->P, s->G, s->G2, loss,
+                                                                   s->gm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int kchunks = (bt + MM_K - 1) / MM_K;
   // dW2 = G2^T A1 (both read with rows contiguous), split K
@@ -887,7 +1014,7 @@ cudaError_t fwd_bwd(pcsir_surrogate* s, int bt, float* loss, cudaStream_t st) {
   w.err = s->err;
   w.A = s->G2; w.sam = 1; w.sak = SUR_HID;
   w.B = s->A1; w.sbn = 1; w.sbk = SUR_HID;
-  w.C = s->G + OFF_W2; w.ldc = SUR_HID;
+  w.C = s->G + s->gm.off_w2; w.ldc = SUR_HID;
   w.M = SUR_HID; w.N = SUR_HID; w.K = bt;
   w.epi = EPI_ATOMIC;
   int splits = std::max(1, std::min(kchunks, sms / 2));
@@ -899,13 +1026,13 @@ cudaError_t fwd_bwd(pcsir_surrogate* s, int bt, float* loss, cudaStream_t st) {
   b.B = s->W2b; b.sbn = 1; b.sbk = SUR_HID;
   b.M = bt; b.N = SUR_HID; b.K = SUR_HID;
   b.epi = EPI_DACT; b.pre = s->Z1; b.ld_pre = SUR_HID; b.act = s->G1; b.ld_act = SUR_HID;
-  b.colsum = s->G + OFF_B1;
+  b.colsum = s->G + s->gm.off_b1;
   if ((e = launch_gemm(b, st, nt_act, 1)) != cudaSuccess) return e;
   // dW1 = G1^T Xb, split K
   w.A = s->G1; w.sam = 1; w.sak = SUR_HID;
-  w.B = s->Xb; w.sbn = 1; w.sbk = SUR_K1;
-  w.C = s->G + OFF_W1; w.ldc = SUR_K1;
-  w.M = SUR_HID; w.N = SUR_K1; w.K = bt;
+  w.B = s->Xb; w.sbn = 1; w.sbk = s->gm.k1;
+  w.C = s->G + s->gm.off_w1; w.ldc = s->gm.k1;
+  w.M = SUR_HID; w.N = s->gm.k1; w.K = bt;
   splits = std::max(1, std::min(kchunks, sms / 4));
   return launch_gemm(w, st, 256, splits);
 }
@@ -915,6 +1042,36 @@ cudaError_t fwd_bwd(pcsir_surrogate* s, int bt, float* loss, cudaStream_t st) {
 namespace pcsir {
 
 int64_t sur_max_pixels(const pcsir_surrogate* s) { return s->cfg.max_pixels; }
+int sur_dim(const pcsir_surrogate* s) { return s->gm.dim; }
+
+cudaError_t launch_sur_step3(const SurStep& sp, const StepBuffers& b, double bg, double sigma_xy, const float* vol,
+                             int W, int H, int D, cudaStream_t st) {
+  const pcsir_surrogate* s = sp.sur;
+  SurInfer a{};
+  a.net = net_of(s);
+  a.gm = s->gm;
+  a.dummy = b.dummy;
+  a.stride = b.bin_stride;
+  a.n_dev = &b.ctl->nocc;
+  a.img = vol;
+  a.W = W;
+  a.H = H;
+  a.D = D;
+  a.sf = make_feat(s, bg, sigma_xy);
+  a.T = s->T;
+  a.out = b.bin_ll;
+  a.nan_clipped = 0;
+  a.max_ll = &b.ctl->max_ll;
+  a.bad = &sp.stats->bad;
+  a.err = &b.ctl->err;
+  cudaError_t e = launch_window(s, vol, W, H, D, bg, st);
+  if (e != cudaSuccess) return e;
+  e = launch_infer(s, a, SRC_STATES, (long long)s->num_sms, st);
+  if (e != cudaSuccess) return e;
+  k_sur_check<<<1, CHK_THREADS, 0, st>>>(b.ctl, b.bin_ll, sp.stats, sp.ho_bin, sp.ho_ll, sp.ho_cap, sp.window,
+                                         sp.max_err);
+  return cudaGetLastError();
+}
 void sur_refs(const pcsir_surrogate* s, double* i0_ref, double* sigma_ref) {
   *i0_ref = s->cfg.i0_ref;
   *sigma_ref = s->cfg.sigma_ref;
@@ -925,6 +1082,8 @@ cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const Model
   const pcsir_surrogate* s = sp.sur;
   SurInfer a{};
   a.net = net_of(s);
+  a.gm = s->gm;
+  a.D = 1;
   a.dummy = b.dummy;
   a.stride = b.bin_stride;
   a.n_dev = &b.ctl->nocc;
@@ -938,7 +1097,7 @@ cudaError_t launch_sur_step(const SurStep& sp, const StepBuffers& b, const Model
   a.max_ll = &b.ctl->max_ll;
   a.bad = &sp.stats->bad;
   a.err = &b.ctl->err;
-  cudaError_t e = launch_window(s, img, W, H, m.bg, st);
+  cudaError_t e = launch_window(s, img, W, H, 1, m.bg, st);
   if (e != cudaSuccess) return e;
   e = launch_infer(s, a, SRC_STATES, (long long)s->num_sms, st);
   if (e != cudaSuccess) return e;
@@ -957,13 +1116,14 @@ pcsir_status pcsir_surrogate_create(const pcsir_surrogate_config* cfg, pcsir_sur
   if (!out) return PCSIR_EINVAL;
   *out = nullptr;
   if (!cfg || cfg->capacity < 1 || cfg->batch < 128 || cfg->batch > 65536 || (cfg->batch % 128) != 0 ||
-      cfg->reserved != 0 || !(cfg->i0_ref > 0.0) || !(cfg->sigma_ref > 0.0) || !std::isfinite(cfg->i0_ref) ||
+      (cfg->geometry != 0 && cfg->geometry != 2 && cfg->geometry != 3) || !(cfg->i0_ref > 0.0) || !(cfg->sigma_ref > 0.0) || !std::isfinite(cfg->i0_ref) ||
       !std::isfinite(cfg->sigma_ref) || cfg->max_pixels < 1)
     return PCSIR_EINVAL;
   if (cfg->capacity > (int64_t(1) << 34)) return PCSIR_ERANGE;
   pcsir_surrogate* s = new (std::nothrow) pcsir_surrogate();
   if (!s) return PCSIR_ENOMEM;
   s->cfg = *cfg;
+  s->gm = make_geom(cfg->geometry == 3 ? 3 : 2);
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   if (e == cudaSuccess) e = prepare_surrogate();
@@ -975,29 +1135,30 @@ pcsir_status pcsir_surrogate_create(const pcsir_surrogate_config* cfg, pcsir_sur
   const size_t bt = (size_t)cfg->batch;
   const size_t cap = (size_t)cfg->capacity;
   s->add_max_blocks = 1 << 12;  // up to 2^20 states per add call
-  bool ok = salloc(s, &s->P, NDEV) && salloc(s, &s->G, NDEV) && salloc(s, &s->Mo, NDEV) && salloc(s, &s->V, NDEV) &&
-            salloc(s, &s->W1b, (size_t)SUR_HID * SUR_K1) && salloc(s, &s->W2b, (size_t)SUR_HID * SUR_HID) &&
-            salloc(s, &s->Wsw, (size_t)SI_CHUNKS * SI_W) &&
-            salloc(s, &s->norm, 2) && salloc(s, &s->X, cap * SUR_K1) && salloc(s, &s->y, cap) && salloc(s, &s->cens, cap) &&
+  bool ok = salloc(s, &s->P, s->gm.ndev) && salloc(s, &s->G, s->gm.ndev) && salloc(s, &s->Mo, s->gm.ndev) && salloc(s, &s->V, s->gm.ndev) &&
+            salloc(s, &s->W1b, (size_t)SUR_HID * s->gm.k1) && salloc(s, &s->W2b, (size_t)SUR_HID * SUR_HID) &&
+            salloc(s, &s->Wsw, (size_t)(s->gm.k1 / MM_K + SUR_HID / MM_K) * SI_W) &&
+            salloc(s, &s->norm, 2) && salloc(s, &s->X, cap * s->gm.k1) && salloc(s, &s->y, cap) && salloc(s, &s->cens, cap) &&
             salloc(s, &s->cb, bt) &&
             salloc(s, &s->count, 1) && salloc(s, &s->add_base, 1) && salloc(s, &s->add_cnt, (size_t)s->add_max_blocks) &&
-            salloc(s, &s->add_done, 1) && salloc(s, &s->Xb, bt * SUR_K1) && salloc(s, &s->A1, bt * SUR_HID) &&
+            salloc(s, &s->add_done, 1) && salloc(s, &s->Xb, bt * s->gm.k1) && salloc(s, &s->A1, bt * SUR_HID) &&
             salloc(s, &s->G2, bt * SUR_HID) && salloc(s, &s->G1, bt * SUR_HID) && salloc(s, &s->yb, bt) &&
             salloc(s, &s->Z1, bt * SUR_HID) && salloc(s, &s->Z2, bt * SUR_HID) && salloc(s, &s->loss_scratch, 1) &&
-            salloc(s, &s->fit_acc, 2) && salloc(s, &s->err, 1) && salloc(s, &s->T, (size_t)cfg->max_pixels);
+            salloc(s, &s->fit_acc, 2) && salloc(s, &s->err, 1) && salloc(s, &s->T, (size_t)cfg->max_pixels) &&
+            (s->gm.dim == 2 || salloc(s, &s->wbuf, 4 * (size_t)cfg->max_pixels));
   if (!ok) {
     sfree(s);
     delete s;
     return PCSIR_ENOMEM;
   }
   const double norm0[2] = {0.0, 1.0};
-  e = cudaMemset(s->P, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->G, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->Mo, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->V, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->W1b, 0, (size_t)SUR_HID * SUR_K1 * sizeof(__nv_bfloat16));
+  e = cudaMemset(s->P, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->G, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->Mo, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->V, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->W1b, 0, (size_t)SUR_HID * s->gm.k1 * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMemset(s->W2b, 0, (size_t)SUR_HID * SUR_HID * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMemset(s->Wsw, 0, (size_t)SI_CHUNKS * SI_W);
+  if (e == cudaSuccess) e = cudaMemset(s->Wsw, 0, (size_t)(s->gm.k1 / MM_K + SUR_HID / MM_K) * SI_W);
   if (e == cudaSuccess) e = cudaMemcpy(s->norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->count, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(s->add_done, 0, sizeof(unsigned));
@@ -1024,18 +1185,18 @@ pcsir_status pcsir_surrogate_destroy(pcsir_surrogate* s) {
 pcsir_status pcsir_surrogate_init(pcsir_surrogate* s, uint64_t seed, void* stream) {
   if (!s) return PCSIR_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_sur_init<<<grid_for(NDEV, 256, s->num_sms), 256, 0, st>>>(s->P, (unsigned long long)seed);
+  k_sur_init<<<grid_for(s->gm.ndev, 256, s->num_sms), 256, 0, st>>>(s->P, (unsigned long long)seed, s->gm);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    k_sur_tobf16<<<grid_for((long long)SUR_HID * (SUR_K1 + SUR_HID), 256, s->num_sms), 256, 0, st>>>(s->P, s->W1b,
-                                                                                                     s->W2b);
+    k_sur_tobf16<<<grid_for((long long)SUR_HID * (s->gm.k1 + SUR_HID), 256, s->num_sms), 256, 0, st>>>(s->P, s->W1b,
+                                                                                                     s->W2b, s->gm);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = pack_weights(s, st);
   const double norm0[2] = {0.0, 1.0};
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->G, 0, NDEV * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->Mo, 0, NDEV * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, NDEV * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->G, 0, s->gm.ndev * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->Mo, 0, s->gm.ndev * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, s->gm.ndev * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemcpy(s->norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return scuda(s, e, "surrogate initialisation");
   s->host_mean = 0.0;
@@ -1048,20 +1209,20 @@ pcsir_status pcsir_surrogate_set_params(pcsir_surrogate* s, const float* params,
                                         double label_scale) {
   if (!s || !params || !std::isfinite(label_mean) || !(label_scale > 0.0) || !std::isfinite(label_scale))
     return PCSIR_EINVAL;
-  std::vector<float> dev((size_t)NDEV, 0.0f);
+  std::vector<float> dev((size_t)s->gm.ndev, 0.0f);
   const float* p = params;
   for (int r = 0; r < SUR_HID; ++r)
-    for (int k = 0; k < SUR_IN; ++k) dev[(size_t)(OFF_W1 + r * SUR_K1 + k)] = *p++;
-  for (long long i = OFF_B1; i < NDEV; ++i) dev[(size_t)i] = *p++;
+    for (int k = 0; k < s->gm.nin; ++k) dev[(size_t)(s->gm.off_w1 + r * s->gm.k1 + k)] = *p++;
+  for (long long i = s->gm.off_b1; i < s->gm.ndev; ++i) dev[(size_t)i] = *p++;
   const double norm[2] = {label_mean, label_scale};
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(s->P, dev.data(), NDEV * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->P, dev.data(), s->gm.ndev * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->norm, norm, sizeof(norm), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(s->G, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->Mo, 0, NDEV * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->V, 0, NDEV * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->G, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->Mo, 0, s->gm.ndev * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->V, 0, s->gm.ndev * sizeof(float));
   if (e == cudaSuccess) {
-    k_sur_tobf16<<<grid_for((long long)SUR_HID * (SUR_K1 + SUR_HID), 256, s->num_sms), 256>>>(s->P, s->W1b, s->W2b);
+    k_sur_tobf16<<<grid_for((long long)SUR_HID * (s->gm.k1 + SUR_HID), 256, s->num_sms), 256>>>(s->P, s->W1b, s->W2b, s->gm);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = pack_weights(s, 0);
@@ -1075,49 +1236,102 @@ pcsir_status pcsir_surrogate_set_params(pcsir_surrogate* s, const float* params,
 
 pcsir_status pcsir_surrogate_get_params(pcsir_surrogate* s, float* params, double* label_mean, double* label_scale) {
   if (!s || !params) return PCSIR_EINVAL;
-  std::vector<float> dev((size_t)NDEV);
+  std::vector<float> dev((size_t)s->gm.ndev);
   double norm[2];
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(dev.data(), s->P, NDEV * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(dev.data(), s->P, s->gm.ndev * sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(norm, s->norm, sizeof(norm), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return scuda(s, e, "reading surrogate parameters");
   float* p = params;
   for (int r = 0; r < SUR_HID; ++r)
-    for (int k = 0; k < SUR_IN; ++k) *p++ = dev[(size_t)(OFF_W1 + r * SUR_K1 + k)];
-  for (long long i = OFF_B1; i < NDEV; ++i) *p++ = dev[(size_t)i];
+    for (int k = 0; k < s->gm.nin; ++k) *p++ = dev[(size_t)(s->gm.off_w1 + r * s->gm.k1 + k)];
+  for (long long i = s->gm.off_b1; i < s->gm.ndev; ++i) *p++ = dev[(size_t)i];
   if (label_mean) *label_mean = norm[0];
   if (label_scale) *label_scale = norm[1];
   return PCSIR_OK;
 }
 
-pcsir_status pcsir_surrogate_add(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n, const double* ll,
-                                 double label_floor, const float* image, int32_t W, int32_t H, double bg,
-                                 double psf_sigma, void* stream) {
+}  // extern "C"
+
+namespace {
+
+pcsir_status sur_add(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n, const double* ll,
+                     double label_floor, const float* image, int32_t W, int32_t H, int32_t D, double bg,
+                     double psf_sigma, void* stream) {
   if (!s) return PCSIR_EINVAL;
-  if (n < 0 || W < 1 || H < 1 || stride < n || !std::isfinite(bg) || !(psf_sigma > 0.0) ||
+  if (n < 0 || W < 1 || H < 1 || D < 1 || stride < n || !std::isfinite(bg) || !(psf_sigma > 0.0) ||
       std::isnan(label_floor) || label_floor == INFINITY)
     return sfail(s, PCSIR_EINVAL, "invalid sizes or model parameters");
   if (n == 0) return PCSIR_OK;
   if (!dummy || !ll || !image) return sfail(s, PCSIR_EINVAL, "NULL device pointer");
   const long long blocks = (n + ADD_THREADS - 1) / ADD_THREADS;
   if (blocks > s->add_max_blocks) return sfail(s, PCSIR_ERANGE, "more than 2^20 states in one call");
-  if ((long long)W * H > s->cfg.max_pixels) return sfail(s, PCSIR_ERANGE, "image larger than max_pixels");
+  if ((long long)W * H * D > s->cfg.max_pixels) return sfail(s, PCSIR_ERANGE, "image larger than max_pixels");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = launch_window(s, image, W, H, bg, st);
+  cudaError_t e = launch_window(s, image, W, H, D, bg, st);
   if (e == cudaSuccess) {
-    k_sur_add_count<<<(unsigned)blocks, ADD_THREADS, 0, st>>>(dummy, stride, n, W, H, s->add_cnt, s->count,
-                                                              s->add_base);
+    k_sur_add_count<<<(unsigned)blocks, ADD_THREADS, 0, st>>>(s->gm, dummy, stride, n, W, H, D, s->add_cnt,
+                                                              s->count, s->add_base);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    k_sur_add_write<<<(unsigned)blocks, ADD_THREADS, 0, st>>>(dummy, stride, n, ll, label_floor, s->T, image, W, H,
-                                                              make_feat(s, bg, psf_sigma), s->add_cnt, s->add_base,
-                                                              s->count, s->add_done, s->cfg.capacity, s->X, s->y,
-                                                              s->cens);
+    k_sur_add_write<<<(unsigned)blocks, ADD_THREADS, 0, st>>>(s->gm, dummy, stride, n, ll, label_floor, s->T, image,
+                                                              W, H, D, make_feat(s, bg, psf_sigma), s->add_cnt,
+                                                              s->add_base, s->count, s->add_done, s->cfg.capacity,
+                                                              s->X, s->y, s->cens);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return scuda(s, e, "dataset append");
   return PCSIR_OK;
+}
+
+pcsir_status sur_predict(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n, const float* image,
+                         int32_t W, int32_t H, int32_t D, double bg, double psf_sigma, double* out, void* stream) {
+  if (!s) return PCSIR_EINVAL;
+  if (n < 0 || W < 1 || H < 1 || D < 1 || stride < n || !std::isfinite(bg) || !(psf_sigma > 0.0))
+    return sfail(s, PCSIR_EINVAL, "invalid sizes or model parameters");
+  if (n == 0) return PCSIR_OK;
+  if (!dummy || !image || !out) return sfail(s, PCSIR_EINVAL, "NULL device pointer");
+  if ((long long)W * H * D > s->cfg.max_pixels) return sfail(s, PCSIR_ERANGE, "image larger than max_pixels");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t ew = launch_window(s, image, W, H, D, bg, st);
+  if (ew != cudaSuccess) return scuda(s, ew, "window terms");
+  SurInfer a{};
+  a.net = net_of(s);
+  a.gm = s->gm;
+  a.dummy = dummy;
+  a.stride = stride;
+  a.n = n;
+  a.img = image;
+  a.W = W;
+  a.H = H;
+  a.D = D;
+  a.sf = make_feat(s, bg, psf_sigma);
+  a.T = s->T;
+  a.out = out;
+  a.nan_clipped = 1;
+  a.err = s->err;
+  const cudaError_t e = launch_infer(s, a, SRC_STATES, (n + 127) / 128, st);
+  if (e != cudaSuccess) return scuda(s, e, "surrogate inference");
+  return PCSIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcsir_status pcsir_surrogate_add(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n, const double* ll,
+                                 double label_floor, const float* image, int32_t W, int32_t H, double bg,
+                                 double psf_sigma, void* stream) {
+  if (s && s->gm.dim != 2) return sfail(s, PCSIR_EINVAL, "a 3D surrogate takes pcsir_surrogate_add3");
+  return sur_add(s, dummy, stride, n, ll, label_floor, image, W, H, 1, bg, psf_sigma, stream);
+}
+
+pcsir_status pcsir_surrogate_add3(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n,
+                                  const double* ll, double label_floor, const float* volume, int32_t W, int32_t H,
+                                  int32_t D, double bg, double psf_sigma_xy, void* stream) {
+  if (s && s->gm.dim != 3) return sfail(s, PCSIR_EINVAL, "a 2D surrogate takes pcsir_surrogate_add");
+  return sur_add(s, dummy, stride, n, ll, label_floor, volume, W, H, D, bg, psf_sigma_xy, stream);
 }
 
 pcsir_status pcsir_surrogate_rows(pcsir_surrogate* s, int64_t* rows) {
@@ -1200,7 +1414,7 @@ pcsir_status pcsir_surrogate_train(pcsir_surrogate* s, int64_t begin, int64_t en
   for (int k = 0; k < steps && e == cudaSuccess; ++k) {
     const long long step = s->adam_t;
     k_sur_gather<<<(bt + 7) / 8, 256, 0, st>>>(s->X, s->y, s->cens, begin, range, (unsigned long long)seed, step,
-                                              bt, s->norm, s->Xb, s->yb, s->cb);
+                                              bt, s->norm, s->Xb, s->yb, s->cb, s->gm.k1);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = fwd_bwd(s, bt, loss ? loss + k : nullptr, st);
     if (e != cudaSuccess) break;
@@ -1208,8 +1422,8 @@ pcsir_status pcsir_surrogate_train(pcsir_surrogate* s, int64_t begin, int64_t en
     const double t = (double)s->adam_t;
     const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, t)));
     const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, t)));
-    k_sur_adam<<<grid_for(NDEV, 256, s->num_sms), 256, 0, st>>>(s->P, s->G, s->Mo, s->V, (float)lr, c1, c2, s->W1b,
-                                                               s->W2b);
+    k_sur_adam<<<grid_for(s->gm.ndev, 256, s->num_sms), 256, 0, st>>>(s->P, s->G, s->Mo, s->V, (float)lr, c1, c2, s->W1b,
+                                                               s->W2b, s->gm);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && steps > 0) e = pack_weights(s, st);
@@ -1222,24 +1436,24 @@ pcsir_status pcsir_surrogate_grads(pcsir_surrogate* s, int64_t begin, int32_t n,
   if (n < 128 || n > s->cfg.batch || (n % 128) != 0) return sfail(s, PCSIR_EINVAL, "n must be a multiple of 128 <= batch");
   pcsir_status ps = check_range(s, begin, begin + n);
   if (ps != PCSIR_OK) return ps;
-  cudaError_t e = cudaMemset(s->G, 0, NDEV * sizeof(float));
+  cudaError_t e = cudaMemset(s->G, 0, s->gm.ndev * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(s->loss_scratch, 0, sizeof(float));
   if (e == cudaSuccess) {
     // rows in order: update index 0 takes rows begin .. begin + n - 1
-    k_sur_gather<<<(n + 7) / 8, 256>>>(s->X, s->y, s->cens, begin, n, 0ull, 0, n, s->norm, s->Xb, s->yb, s->cb);
+    k_sur_gather<<<(n + 7) / 8, 256>>>(s->X, s->y, s->cens, begin, n, 0ull, 0, n, s->norm, s->Xb, s->yb, s->cb, s->gm.k1);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = fwd_bwd(s, n, s->loss_scratch, 0);
-  std::vector<float> dev((size_t)NDEV);
+  std::vector<float> dev((size_t)s->gm.ndev);
   float l = 0.0f;
-  if (e == cudaSuccess) e = cudaMemcpy(dev.data(), s->G, NDEV * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(dev.data(), s->G, s->gm.ndev * sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&l, s->loss_scratch, sizeof(float), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemset(s->G, 0, NDEV * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->G, 0, s->gm.ndev * sizeof(float));
   if (e != cudaSuccess) return scuda(s, e, "gradient pass");
   float* p = grads;
   for (int r = 0; r < SUR_HID; ++r)
-    for (int k = 0; k < SUR_IN; ++k) *p++ = dev[(size_t)(OFF_W1 + r * SUR_K1 + k)];
-  for (long long i = OFF_B1; i < NDEV; ++i) *p++ = dev[(size_t)i];
+    for (int k = 0; k < s->gm.nin; ++k) *p++ = dev[(size_t)(s->gm.off_w1 + r * s->gm.k1 + k)];
+  for (long long i = s->gm.off_b1; i < s->gm.ndev; ++i) *p++ = dev[(size_t)i];
   if (loss) *loss = (double)l;
   return PCSIR_OK;
 }
@@ -1251,7 +1465,9 @@ pcsir_status pcsir_surrogate_predict_rows(pcsir_surrogate* s, int64_t begin, int
   if (ps != PCSIR_OK) return ps;
   SurInfer a{};
   a.net = net_of(s);
-  a.rows = s->X + (size_t)begin * SUR_K1;
+  a.gm = s->gm;
+  a.D = 1;
+  a.rows = s->X + (size_t)begin * s->gm.k1;
   a.n = end - begin;
   a.out = out;
   a.err = s->err;
@@ -1263,30 +1479,20 @@ pcsir_status pcsir_surrogate_predict_rows(pcsir_surrogate* s, int64_t begin, int
 pcsir_status pcsir_surrogate_predict(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n,
                                      const float* image, int32_t W, int32_t H, double bg, double psf_sigma,
                                      double* out, void* stream) {
-  if (!s) return PCSIR_EINVAL;
-  if (n < 0 || W < 1 || H < 1 || stride < n || !std::isfinite(bg) || !(psf_sigma > 0.0))
-    return sfail(s, PCSIR_EINVAL, "invalid sizes or model parameters");
-  if (n == 0) return PCSIR_OK;
-  if (!dummy || !image || !out) return sfail(s, PCSIR_EINVAL, "NULL device pointer");
-  if ((long long)W * H > s->cfg.max_pixels) return sfail(s, PCSIR_ERANGE, "image larger than max_pixels");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t ew = launch_window(s, image, W, H, bg, st);
-  if (ew != cudaSuccess) return scuda(s, ew, "window terms");
-  SurInfer a{};
-  a.net = net_of(s);
-  a.dummy = dummy;
-  a.stride = stride;
-  a.n = n;
-  a.img = image;
-  a.W = W;
-  a.H = H;
-  a.sf = make_feat(s, bg, psf_sigma);
-  a.T = s->T;
-  a.out = out;
-  a.nan_clipped = 1;
-  a.err = s->err;
-  const cudaError_t e = launch_infer(s, a, SRC_STATES, (n + 127) / 128, st);
-  if (e != cudaSuccess) return scuda(s, e, "surrogate inference");
+  if (s && s->gm.dim != 2) return sfail(s, PCSIR_EINVAL, "a 3D surrogate takes pcsir_surrogate_predict3");
+  return sur_predict(s, dummy, stride, n, image, W, H, 1, bg, psf_sigma, out, stream);
+}
+
+pcsir_status pcsir_surrogate_predict3(pcsir_surrogate* s, const double* dummy, int64_t stride, int64_t n,
+                                      const float* volume, int32_t W, int32_t H, int32_t D, double bg,
+                                      double psf_sigma_xy, double* out, void* stream) {
+  if (s && s->gm.dim != 3) return sfail(s, PCSIR_EINVAL, "a 2D surrogate takes pcsir_surrogate_predict");
+  return sur_predict(s, dummy, stride, n, volume, W, H, D, bg, psf_sigma_xy, out, stream);
+}
+
+pcsir_status pcsir_surrogate_nparams(pcsir_surrogate* s, int64_t* nparams) {
+  if (!s || !nparams) return PCSIR_EINVAL;
+  *nparams = (int64_t)SUR_HID * s->gm.nin + (s->gm.ndev - s->gm.off_b1);
   return PCSIR_OK;
 }
 

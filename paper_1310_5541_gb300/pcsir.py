@@ -57,7 +57,7 @@ class pcsir_target(ctypes.Structure):
 
 
 class pcsir_surrogate_config(ctypes.Structure):
-    _fields_ = [("capacity", ctypes.c_int64), ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("capacity", ctypes.c_int64), ("batch", ctypes.c_int32), ("geometry", ctypes.c_int32),
                 ("i0_ref", ctypes.c_double), ("sigma_ref", ctypes.c_double), ("max_pixels", ctypes.c_int64)]
 
 
@@ -71,6 +71,8 @@ class pcsir_surrogate_check(ctypes.Structure):
 SUR_PATCH, SUR_INPUTS, SUR_HIDDEN = 21, 445, 256
 SUR_NPARAMS = 256 * 445 + 256 + 256 * 256 + 256 + 256 + 1
 SUR_ROW = 448  # stored inputs per dataset row
+SUR3_NPARAMS = 256 * 852 + 256 + 256 * 256 + 256 + 256 + 1
+SUR3_ROW = 896
 
 
 class pcsir3_config(ctypes.Structure):
@@ -176,6 +178,11 @@ def _load():
         "pcsir3_get_outputs": ([P, ctypes.POINTER(pcsir3_outputs)], I32),
         "pcsir3_last_result": ([P, ctypes.POINTER(pcsir3_result)], I32),
         "pcsir_surrogate_last_check": ([P, ctypes.POINTER(pcsir_surrogate_check)], I32),
+        "pcsir_surrogate_add3": ([P, P, I64, I64, P, D, P, I32, I32, I32, D, D, P], I32),
+        "pcsir_surrogate_predict3": ([P, P, I64, I64, P, I32, I32, I32, D, D, P, P], I32),
+        "pcsir_surrogate_nparams": ([P, ctypes.POINTER(ctypes.c_int64)], I32),
+        "pcsir3_attach_surrogate": ([P, P, D, I32, D, D], I32),
+        "pcsir3_surrogate_last_check": ([P, ctypes.POINTER(pcsir_surrogate_check)], I32),
         "pcsir3_batch_create": ([ctypes.POINTER(pcsir3_target), I32, I32, ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir3_batch_destroy": ([P], I32),
         "pcsir3_batch_last_error": ([P], ctypes.c_char_p),
@@ -552,8 +559,12 @@ def version():
 class Surrogate:
     """Owns one ``pcsir_surrogate``: the likelihood network, its training state and its dataset."""
 
-    def __init__(self, capacity, batch=4096, i0_ref=128.0, sigma_ref=1.5, max_pixels=1 << 20):
-        cfg = pcsir_surrogate_config(capacity=int(capacity), batch=int(batch), reserved=0, i0_ref=float(i0_ref),
+    def __init__(self, capacity, batch=4096, i0_ref=128.0, sigma_ref=1.5, max_pixels=1 << 20, geometry=2):
+        self.geometry = int(geometry)
+        self.nparams = SUR3_NPARAMS if self.geometry == 3 else SUR_NPARAMS
+        self.row = SUR3_ROW if self.geometry == 3 else SUR_ROW
+        cfg = pcsir_surrogate_config(capacity=int(capacity), batch=int(batch), geometry=self.geometry,
+                                     i0_ref=float(i0_ref),
                                      sigma_ref=float(sigma_ref), max_pixels=int(max_pixels))
         h = ctypes.c_void_p()
         st = lib.pcsir_surrogate_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -582,11 +593,11 @@ class Surrogate:
 
     def set_params(self, flat, label_mean=0.0, label_scale=1.0):
         a = np.ascontiguousarray(np.asarray(flat, np.float32))
-        assert a.size == SUR_NPARAMS
+        assert a.size == self.nparams
         self._check(lib.pcsir_surrogate_set_params(self.handle, a.ctypes.data, float(label_mean), float(label_scale)))
 
     def get_params(self):
-        a = np.empty(SUR_NPARAMS, np.float32)
+        a = np.empty(self.nparams, np.float32)
         m, s = ctypes.c_double(), ctypes.c_double()
         self._check(lib.pcsir_surrogate_get_params(self.handle, a.ctypes.data, ctypes.byref(m), ctypes.byref(s)))
         return a, m.value, s.value
@@ -618,7 +629,7 @@ class Surrogate:
         n = self.rows()
         if n == 0:
             return None, None, None
-        return (_from_ptr(xp.value, (n, SUR_ROW), torch.int16), _from_ptr(yp.value, (n,), torch.float32),
+        return (_from_ptr(xp.value, (n, self.row), torch.int16), _from_ptr(yp.value, (n,), torch.float32),
                 _from_ptr(cp.value, (n,), torch.uint8))
 
     def fit_scale(self, begin, end):
@@ -632,7 +643,7 @@ class Surrogate:
                                               _ptr(loss), _stream_ptr(stream)))
 
     def grads(self, begin, n):
-        g = np.empty(SUR_NPARAMS, np.float32)
+        g = np.empty(self.nparams, np.float32)
         loss = ctypes.c_double()
         self._check(lib.pcsir_surrogate_grads(self.handle, int(begin), int(n), g.ctypes.data, ctypes.byref(loss)))
         return g, loss.value
@@ -654,6 +665,50 @@ class Surrogate:
         self._check(lib.pcsir_surrogate_predict(self.handle, _ptr(dummy), dummy.stride(0), n, _ptr(image), W, H,
                                                 float(bg), float(psf_sigma), _ptr(out), _stream_ptr(stream)))
         return out
+
+
+def _surrogate_add3(self, dummy, ll, volume, bg, psf_sigma_xy, label_floor=-math.inf, stream=None):
+    """Append rows for the 3D states ``dummy`` [7, n] (float64 view with unit column stride)."""
+    assert dummy.dtype == torch.float64 and dummy.is_cuda and dummy.stride(1) == 1
+    _check_cuda(ll, "ll", torch.float64)
+    _check_cuda(volume, "volume", torch.float32)
+    n = dummy.shape[1]
+    D, H, W = volume.shape
+    self._check(lib.pcsir_surrogate_add3(self.handle, _ptr(dummy), dummy.stride(0), n, _ptr(ll), float(label_floor),
+                                         _ptr(volume), W, H, D, float(bg), float(psf_sigma_xy), _stream_ptr(stream)))
+
+
+def _surrogate_predict3(self, dummy, volume, bg, psf_sigma_xy, out=None, stream=None):
+    assert dummy.dtype == torch.float64 and dummy.is_cuda and dummy.stride(1) == 1
+    _check_cuda(volume, "volume", torch.float32)
+    n = dummy.shape[1]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=dummy.device)
+    D, H, W = volume.shape
+    self._check(lib.pcsir_surrogate_predict3(self.handle, _ptr(dummy), dummy.stride(0), n, _ptr(volume), W, H, D,
+                                             float(bg), float(psf_sigma_xy), _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+Surrogate.add3 = _surrogate_add3
+Surrogate.predict3 = _surrogate_predict3
+
+
+def attach_surrogate3(ctx3, sur, holdout_frac=0.02, min_holdout=32, window=20.0, max_err=1.0):
+    """Let the 3D step of ``ctx3`` use the 3D surrogate ``sur`` (``sur=None`` detaches)."""
+    st = lib.pcsir3_attach_surrogate(ctx3.handle, sur.handle if sur is not None else None, float(holdout_frac),
+                                     int(min_holdout), float(window), float(max_err))
+    if st != OK:
+        ctx3._raise(st)
+    ctx3.surrogate = sur
+
+
+def surrogate_last_check3(ctx3):
+    c = pcsir_surrogate_check()
+    st = lib.pcsir3_surrogate_last_check(ctx3.handle, ctypes.byref(c))
+    if st != OK:
+        ctx3._raise(st)
+    return {k: getattr(c, k) for k, _ in pcsir_surrogate_check._fields_ if k != "reserved"}
 
 
 def attach_surrogate(ctx, sur, holdout_frac=0.02, min_holdout=32, window=20.0, max_err=1.0):

@@ -127,8 +127,8 @@ def test_noalloc_binding_rejects_operands_it_cannot_use(binding):
 
 def test_invalid_surrogate_configs_rejected_on_host(binding):
     lib = binding.lib
-    base = dict(capacity=1000, batch=256, reserved=0, i0_ref=128.0, sigma_ref=1.5, max_pixels=4096)
-    for upd in [dict(capacity=0), dict(batch=100), dict(batch=0), dict(batch=65536 + 128), dict(reserved=1),
+    base = dict(capacity=1000, batch=256, geometry=0, i0_ref=128.0, sigma_ref=1.5, max_pixels=4096)
+    for upd in [dict(capacity=0), dict(batch=100), dict(batch=0), dict(batch=65536 + 128), dict(geometry=1),
                 dict(i0_ref=0.0), dict(sigma_ref=-1.0), dict(i0_ref=float("nan")), dict(max_pixels=0)]:
         cfg = binding.pcsir_surrogate_config(**{**base, **upd})
         h = ctypes.c_void_p(123)

@@ -205,3 +205,100 @@ def test_pack_roundtrip():
     q = S.unpack(flat)
     for k, _ in S.PARAM_SHAPES:
         assert np.array_equal(p[k], q[k])
+
+
+# ----------------------------------------------------------------------------
+# The 3D surrogate (11 x 11 x 7 voxel patch)
+# ----------------------------------------------------------------------------
+def _spot_volume(rng, W=30, H=26, D=18, x0=14.3, y0=12.6, z0=8.8):
+    from paper_1310_5541_gb300 import synth
+
+    return rng.poisson(synth.render3(W, H, D, x0, y0, z0, 100.0, 10.0, 1.5, 3.0)).astype(np.float32)
+
+
+def test_features3_match_voxel_loop():
+    """Inputs 0..846 are the window's voxels with x fastest, then y, then z; then the sub-voxel
+    offsets, I0 and sigma; a window leaving the volume is clipped."""
+    rng = np.random.default_rng(31)
+    vol = _spot_volume(rng)
+    xs, ys, zs = np.array([14.3, 13.51, 4.2]), np.array([12.6, 11.49, 12.0]), np.array([8.8, 9.5, 9.0])
+    i0 = np.array([100.0, 80.0, 90.0])
+    X, clipped = S.features3(vol, xs, ys, zs, i0, 1.5, 10.0, 128.0, 1.5)
+    assert list(clipped) == [False, False, True]  # x = 4.2: cx - 5 < 0
+    for n in range(2):
+        cx, cy, cz = (math.floor(v + 0.5) for v in (xs[n], ys[n], zs[n]))
+        f = 0
+        for dz in range(-3, 4):
+            for dy in range(-5, 6):
+                for dx in range(-5, 6):
+                    assert X[n, f] == (float(vol[cz + dz, cy + dy, cx + dx]) - 10.0) / 128.0
+                    f += 1
+        assert f == S.NPIX3 == 847
+        assert X[n, 847:].tolist() == [2 * (xs[n] - cx), 2 * (ys[n] - cy), 2 * (zs[n] - cz), i0[n] / 128.0, 1.0]
+
+
+def test_window_term3_splits_the_3d_poisson_likelihood():
+    """ll - T equals the spot-only sum over the 11 x 11 x 7 window, by a voxel loop against the 3D
+    oracle's likelihood (an independent code path); with I0 = 0, ll is the window term itself."""
+    from oracle import pcsir3_oracle as O3
+
+    rng = np.random.default_rng(32)
+    vol = _spot_volume(rng)
+    vol[6, 10, 12] = 0.0  # a zero count inside the windows
+    xs, ys, zs = np.array([14.3, 13.6, 15.4]), np.array([12.6, 13.4, 11.8]), np.array([8.8, 8.2, 9.4])
+    i0 = np.array([100.0, 70.0, 0.0])
+    m = O3.Model3()
+    ll = O3.loglik(vol, xs, ys, zs, i0, m)
+    T = S.window_term3(vol, xs, ys, zs, 10.0)
+    for n in range(len(xs)):
+        cx, cy, cz = (math.floor(v + 0.5) for v in (xs[n], ys[n], zs[n]))
+        r = 0.0
+        for vz in range(cz - 3, cz + 4):
+            for vy in range(cy - 5, cy + 6):
+                for vx in range(cx - 5, cx + 6):
+                    g = math.exp(-((vx - xs[n]) ** 2 + (vy - ys[n]) ** 2) / (2 * 1.5 ** 2)
+                                 - (vz - zs[n]) ** 2 / (2 * 3.0 ** 2))
+                    r += float(vol[vz, vy, vx]) * math.log1p(i0[n] * g / 10.0) - i0[n] * g
+        assert ll[n] - T[n] == pytest.approx(r, rel=1e-9, abs=1e-8)
+    assert ll[2] == pytest.approx(T[2], rel=1e-12)
+
+
+def test_holdout_mask3_key_and_fraction():
+    # the key packs (bx + 2^20, by + 2^20, bz + 2^20) in 21-bit fields; compare with a direct call
+    bx, by, bz = np.array([3, -7, 0]), np.array([-2, 5, 0]), np.array([1, 0, -4])
+    got = S.holdout_mask3(bx, by, bz, 11, 0.5)
+    for i in range(3):
+        key = (int(bx[i]) + 2 ** 20) + ((int(by[i]) + 2 ** 20) << 21) + ((int(bz[i]) + 2 ** 20) << 42)
+        h = S.splitmix64((key + 11 * 0x9E3779B97F4A7C15) % 2 ** 64)
+        assert got[i] == ((h >> 40) < (1 << 23))
+    rng = np.random.default_rng(3)
+    cells = rng.integers(-1000, 1000, size=(3, 20000))
+    frac = S.holdout_mask3(cells[0], cells[1], cells[2], 5, 0.1).mean()
+    assert 0.09 < frac < 0.11
+    assert S.holdout_mask3(cells[0], cells[1], cells[2], 5, 1.0).all()
+
+
+def test_backprop3_shapes_match_central_differences():
+    """The forward and backward passes are shape-generic: a spot check with the 3D input width."""
+    rng = np.random.default_rng(33)
+    p = {k: rng.standard_normal(s) * (0.05 if k == "W1" else 0.1) for k, s in S.PARAM_SHAPES3}
+    X = rng.standard_normal((8, S.N_IN3)) * 0.5
+    t = rng.standard_normal(8)
+    loss, g = S.loss_and_grads(p, X, t)
+    assert g["W1"].shape == (256, 852)
+    eps = 1e-6
+    for k in ("W1", "b1", "w3"):
+        flat = p[k].reshape(-1)
+        for j in rng.choice(flat.size, size=6, replace=False):
+            old = flat[j]
+            flat[j] = old + eps
+            lp = S.loss_and_grads(p, X, t)[0]
+            flat[j] = old - eps
+            lm = S.loss_and_grads(p, X, t)[0]
+            flat[j] = old
+            an = g[k].reshape(-1)[j]
+            assert abs((lp - lm) / (2 * eps) - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9
+    flat = S.pack(p, S.PARAM_SHAPES3)
+    assert flat.size == S.N_PARAMS3
+    back = S.unpack(flat, S.PARAM_SHAPES3)
+    np.testing.assert_array_equal(back["W1"], p["W1"])
