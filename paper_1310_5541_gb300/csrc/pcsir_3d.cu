@@ -565,6 +565,7 @@ pcsir_status pcsir3_create(const pcsir3_config* cfg, pcsir3_ctx** out) {
             alloc3(c, &b.bin_cnt, (size_t)nmax) && alloc3(c, &b.dummy, (size_t)NS3 * nmax) &&
             alloc3(c, &b.bin_ll, (size_t)nmax) && alloc3(c, &b.pslot, (size_t)nmax) && alloc3(c, &b.llq, (size_t)nmax) &&
             alloc3(c, &b.tile_sum, (size_t)b.max_tiles) && alloc3(c, &b.tile_excl, (size_t)b.max_tiles) &&
+            alloc3(c, &b.tile_lo, (size_t)b.max_tiles + 1) && alloc3(c, &b.tile_ovx, (size_t)b.max_tiles + 1) &&
             alloc3(c, &b.ctl, 1) && alloc3(c, &b.dres, 1) && alloc3(c, &c->dres3, 1);
   if (ok) {
     float* p = nullptr;

@@ -168,7 +168,8 @@ pcsir_status pcsir_create(const pcsir_config* cfg, pcsir_ctx** out) {
             dev_alloc(c, &b.bin_cnt, (size_t)nmax) && dev_alloc(c, &b.dummy, 5 * (size_t)nmax) &&
             dev_alloc(c, &b.bin_ll, (size_t)nmax) && dev_alloc(c, &b.pslot, (size_t)nmax) &&
             dev_alloc(c, &b.llq, (size_t)nmax) && dev_alloc(c, &b.tile_sum, (size_t)b.max_tiles) &&
-            dev_alloc(c, &b.tile_excl, (size_t)b.max_tiles) &&
+            dev_alloc(c, &b.tile_excl, (size_t)b.max_tiles) && dev_alloc(c, &b.tile_lo, (size_t)b.max_tiles + 1) &&
+            dev_alloc(c, &b.tile_ovx, (size_t)b.max_tiles + 1) &&
             dev_alloc(c, &b.ctl, 1) && dev_alloc(c, &b.dres, 1);
   if (ok) {
     unsigned char* p = nullptr;

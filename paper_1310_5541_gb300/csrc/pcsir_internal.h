@@ -70,6 +70,10 @@ struct StepBuffers {
   // scan: per-tile sums of the integer weights and their exclusive prefixes
   long long* tile_sum;
   long long* tile_excl;
+  // the tiles' outputs: tile t owns outputs [tile_lo[t], tile_lo[t + 1]); tile_ovx is the
+  // exclusive prefix of the tiles' further output chunks past the first (max_tiles + 1 entries each)
+  long long* tile_lo;
+  int* tile_ovx;
   int64_t max_tiles;
   Control* ctl;
   pcsir_result* dres;

@@ -36,6 +36,8 @@ struct NoallocScratch {
   pcsir_result res;
   long long tile_sum[NOALLOC_MAX_TILES];
   long long tile_excl[NOALLOC_MAX_TILES];
+  long long tile_lo[NOALLOC_MAX_TILES + 1];
+  int tile_ovx[NOALLOC_MAX_TILES + 1];
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
@@ -128,6 +130,8 @@ extern "C" pcsir_status pcsir_resample_noalloc(const double* logw, int64_t N, do
   b.derr_out = &sc->res.device_error;
   b.tile_sum = sc->tile_sum;
   b.tile_excl = sc->tile_excl;
+  b.tile_lo = sc->tile_lo;
+  b.tile_ovx = sc->tile_ovx;
   b.max_tiles = NOALLOC_MAX_TILES;
   b.hbits = 10;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

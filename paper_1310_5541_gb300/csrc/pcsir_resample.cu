@@ -13,9 +13,13 @@
 //
 // Two kernels: k_tile_sums (k_tile_sums_bins, on a resident grid, for pcSIR
 // steps) adds up each tile's integer weights and its last block scans the
-// tile sums and fixes the 64.64 map; k_resample then scans within each tile
-// and gives every output its ancestor by binary search over the tile's
-// cumulative weights.  No block ever waits for another.
+// tile sums, fixes the 64.64 map and each tile's output range; k_resample
+// then scans within each tile and gives every output its ancestor by binary
+// search over the tile's cumulative weights.  A tile whose particles carry a
+// large share of the weight (all of it, when one particle dominates) owns
+// many outputs: they are split into chunks of RS_CHUNK over extra blocks, so
+// the time of the step does not depend on how the weight is spread.  No block
+// ever waits for another.
 #include <cmath>
 #include <type_traits>
 
@@ -62,6 +66,15 @@ __device__ __forceinline__ Map64 load_map(const Control* ctl) {
 }
 
 __device__ __forceinline__ int pad_idx(int j) { return j + (j >> 4); }
+
+// A resampling block writes at most RS_CHUNK outputs: a tile that owns more (its particles carry
+// more than RS_CHUNK / N of the total weight, up to all of it) has its further outputs written
+// by extra blocks, one per chunk, so that no block serialises a large share of the N outputs.
+// The extra blocks launched, ceil(N / RS_CHUNK), cover every case: the further chunks of all
+// tiles number at most N / RS_CHUNK.
+constexpr long long RS_CHUNK = 4LL * SCAN_TILE;
+
+__device__ __forceinline__ int rs_extra_chunks(long long n) { return n > RS_CHUNK ? (int)((n - 1) / RS_CHUNK) : 0; }
 
 // Number of the tile's cumulative weights C_j <= u (j < SCAN_TILE), by a fixed
 // 12-step binary search over Cs in the padded layout (index j at j + j / 16).
@@ -152,9 +165,14 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 // tiles' exclusive prefixes and fixes Delta and U0.
 // ---------------------------------------------------------------------------
 // The last block to finish its tiles: exclusive scan of the nt tile sums into the tiles'
-// prefixes, then Delta = T / N, U0 = u0 Delta (64.64 fixed point) and the FP32 reciprocal.
+// prefixes, then Delta = T / N, U0 = u0 Delta (64.64 fixed point) and the FP32 reciprocal, and
+// the tiles' output ranges: tile t owns the outputs i with excl_t <= U_i < excl_{t+1}, i.e.
+// [tile_lo[t], tile_lo[t + 1]), and the outputs past its first RS_CHUNK form further chunks,
+// whose exclusive prefix over the tiles goes to tile_ovx.
 __device__ void tile_scan_tail(const StepBuffers& b, Control* ctl, int64_t N, double u0, int nt,
                                long long* wtot) {
+  __shared__ Map64 s_mp;
+  __shared__ float s_inv;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // exclusive scan of the tile sums (each thread a run of consecutive tiles)
   const int per = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
@@ -197,8 +215,42 @@ __device__ void tile_scan_tail(const StepBuffers& b, Control* ctl, int64_t N, do
     ctl->u0_lo = (unsigned long long)tot;
     const double dd = (double)dhi + (double)dlo * 5.421010862427522e-20;
     ctl->inv_delta = dd > 0.0 ? (float)(1.0 / dd) : 0.0f;
+    s_mp.dhi = dhi;
+    s_mp.dlo = dlo;
+    s_mp.uhi = (unsigned long long)(tot >> 64);
+    s_mp.ulo = (unsigned long long)tot;
+    s_inv = ctl->inv_delta;
     if (T == 0ull) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
   }
+  __syncthreads();
+  // first output of each tile (the last entry: N)
+  const Map64 mp = s_mp;
+  const float inv = s_inv;
+  for (int k = 0; k < per && t0 + k < nt; ++k) b.tile_lo[t0 + k] = first_out_f(mp, b.tile_excl[t0 + k], N, inv);
+  if (tid == 0) b.tile_lo[nt] = N;
+  __syncthreads();  // also orders this block's global writes above before the reads below
+  // chunks past the first of each tile, and their exclusive prefix
+  int cnt = 0;
+  for (int k = 0; k < per && t0 + k < nt; ++k) cnt += rs_extra_chunks(b.tile_lo[t0 + k + 1] - b.tile_lo[t0 + k]);
+  int ci = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, ci, o);
+    if (lane >= o) ci += v;
+  }
+  if (lane == 31) wtot[w] = ci;  // every thread read wtot before the barriers above
+  __syncthreads();
+  int coff = 0, ctot = 0;
+  for (int j = 0; j < SCAN_THREADS / 32; ++j) {
+    if (j < w) coff += (int)wtot[j];
+    ctot += (int)wtot[j];
+  }
+  int ce = coff + ci - cnt;
+  for (int k = 0; k < per && t0 + k < nt; ++k) {
+    b.tile_ovx[t0 + k] = ce;
+    ce += rs_extra_chunks(b.tile_lo[t0 + k + 1] - b.tile_lo[t0 + k]);
+  }
+  if (tid == 0) b.tile_ovx[nt] = ctot;
 }
 
 template <int WSRC>
@@ -299,18 +351,51 @@ __global__ void __launch_bounds__(SCAN_THREADS, TS_BLOCKS_PER_SM) k_tile_sums_bi
 // Resampling of one tile: inclusive cumulative weights of the tile in shared
 // memory, then the tile's outputs i (those with C_{-1} <= U_i < C_{cnt-1}),
 // each finding by binary search the particle k with C_{k-1} <= U_i < C_k and
-// gathering its propagated state.
+// gathering its propagated state.  Blocks [0, ntiles) take tile blockIdx.x and
+// its first RS_CHUNK outputs; the blocks past them take the further chunks of
+// the tiles that own more outputs, in tile order (tile_ovx), and exit when
+// there are fewer such chunks than blocks.
 // ---------------------------------------------------------------------------
 template <typename T, int WSRC, int NS = 5>
 __global__ void __launch_bounds__(SCAN_THREADS, 5)
-k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep) {
+k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, int64_t N, int sq, int keep,
+           int ntiles) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   long long* Cs = reinterpret_cast<long long*>(rs_smem);                       // SCAN_TILE + SCAN_TILE / 16
   __shared__ long long wtot[SCAN_THREADS / 32];
   __shared__ long long s_lo, s_hi;
+  __shared__ int s_tile;
   Control* ctl = b.ctl;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const unsigned tile = blockIdx.x;
+  if (tid == 0) {
+    // this block's tile and outputs [s_lo, s_hi): the first RS_CHUNK outputs of tile blockIdx.x, or
+    // extra chunk e = blockIdx.x - ntiles: chunk e - tile_ovx[t] + 1 of the tile t with
+    // tile_ovx[t] <= e < tile_ovx[t + 1] (the largest such t); none when e is past them all
+    int t = (int)blockIdx.x;
+    long long chunk = 0;
+    bool idle = false;
+    if (t >= ntiles) {
+      const int e = t - ntiles;
+      idle = e >= b.tile_ovx[ntiles];
+      int lo = 0, hi = ntiles - 1;
+      while (!idle && lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.tile_ovx[mid] <= e) lo = mid;
+        else hi = mid - 1;
+      }
+      t = idle ? 0 : lo;
+      chunk = idle ? 0 : (long long)(e - b.tile_ovx[lo]) + 1;
+    }
+    const long long t_lo = b.tile_lo[t], t_hi = b.tile_lo[t + 1];
+    const long long lo = t_lo + chunk * RS_CHUNK;
+    s_tile = idle ? -1 : t;
+    s_lo = lo;
+    s_hi = idle ? lo : (t_hi < lo + RS_CHUNK ? t_hi : lo + RS_CHUNK);
+  }
+  __syncthreads();
+  const bool idle = s_tile < 0;
+  const bool primary = (int)blockIdx.x < ntiles;
+  const int tile = idle ? 0 : s_tile;
   const int64_t base = (int64_t)tile * SCAN_TILE;
   const int cnt = (int)((N - base) < SCAN_TILE ? (N - base) : SCAN_TILE);
   const unsigned long long me = ctl->max_llq;
@@ -326,11 +411,13 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const double Tf = *(volatile double*)&ctl->T_f, T2 = *(volatile double*)&ctl->T2_f;
     skip = !(Tf * Tf / T2 < b.ess_min);
   }
-  if (skip) {
+  if (idle) {
+    // no outputs left for this block
+  } else if (skip) {
     // no resampling: the propagated particles and their log-weights (minus the maximum)
-    // carry over to the next step
+    // carry over to the next step (the tile's own block only)
     const T* __restrict__ prop = static_cast<const T*>(b.prop);
-    for (int j = tid; j < cnt; j += SCAN_THREADS) {
+    for (int j = tid; primary && j < cnt; j += SCAN_THREADS) {
       const int64_t i = base + j;
       if (out != nullptr) {
 #pragma unroll
@@ -367,13 +454,10 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     }
     if (lane == 31) wtot[w] = inc;
     __syncthreads();
-    long long woff = 0, agg = 0;
+    long long woff = 0;
 #pragma unroll
-    for (int j = 0; j < SCAN_THREADS / 32; ++j) {
-      const long long t = wtot[j];
-      if (j < w) woff += t;
-      agg += t;
-    }
+    for (int j = 0; j < SCAN_THREADS / 32; ++j)
+      if (j < w) woff += wtot[j];
     const long long texcl = woff + inc - run;
     // 4. inclusive cumulative weights C_j of the tile; entries past its last particle compare
     //    above every U_i (the fixed-step search below)
@@ -386,16 +470,14 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
         Cs[pad_idx(jj)] = jj < cnt ? c : LLONG_MAX;
       }
     }
-    // the tile's outputs [lo, hi): U_lo >= C_{-1} = excl and U_{hi-1} < C_{cnt-1} = excl + agg
-    const float inv_delta = ctl->inv_delta;
-    if (tid == 0) s_lo = first_out_f(mp, excl, N, inv_delta);
-    if (tid == 32) s_hi = (base + cnt >= N) ? N : first_out_f(mp, excl + agg, N, inv_delta);
     __syncthreads();
     // 5. the tile's outputs, two per thread and pass (both gathers issued before the stores).
     //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
     //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
     //    weights in shared memory, independent for every output, so a particle with many
     //    offspring does not serialise one thread.  Row offsets fit 32 bits (N <= 2^26).
+    // the tile's outputs are [tile_lo[t], tile_lo[t + 1]) (U >= C_{-1} = excl and U < C_{cnt-1}, the
+    // next tile's excl); this block writes its chunk [s_lo, s_hi) of them
     const T* __restrict__ prop = static_cast<const T*>(b.prop);
     const long long lo = s_lo, hi = s_hi;
     const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
@@ -441,8 +523,8 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       }
     }
   }
-  // 6. optional per-particle outputs of the tile
-  if (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_QWEIGHTS)) {
+  // 6. optional per-particle outputs of the tile (its own block)
+  if (primary && (keep & (PCSIR_KEEP_WEIGHTS | PCSIR_KEEP_PARTICLE_BIN | PCSIR_KEEP_QWEIGHTS))) {
     const double Tf = *(volatile double*)&ctl->T_f;
     for (int j = tid; j < cnt; j += SCAN_THREADS) {
       const int64_t i = base + j;
@@ -460,9 +542,9 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     }
   }
   // 7. pcSIR: return the occupied hash slots to empty for the next step
-  if (WSRC == WSRC_BINS) {
+  if (WSRC == WSRC_BINS && primary) {
     const unsigned B = ctl->nocc;
-    for (unsigned bi = tile * SCAN_THREADS + tid; bi < B; bi += gridDim.x * SCAN_THREADS) {
+    for (unsigned bi = tile * SCAN_THREADS + tid; bi < B; bi += (unsigned)ntiles * SCAN_THREADS) {
       const unsigned g = b.occ[bi];
       b.hkey[g] = EMPTY_KEY;
       b.hcnt[g] = 0u;
@@ -483,6 +565,11 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
 }
 
 constexpr size_t RS_SMEM = sizeof(long long) * (SCAN_TILE + SCAN_TILE / 16);
+
+// resampling grid: one block per tile, then ceil(N / RS_CHUNK) blocks for further output chunks
+static unsigned rs_grid(int64_t N) {
+  return (unsigned)((N + SCAN_TILE - 1) / SCAN_TILE + (N + RS_CHUNK - 1) / RS_CHUNK);
+}
 
 cudaError_t prepare_resample() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -513,24 +600,24 @@ static cudaError_t resample_launch(const StepBuffers& b, const double* lsrc, voi
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<T, WSRC_BINS><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
+    k_resample<T, WSRC_BINS><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep, (int)ntiles);
   } else if (mode == WSRC_PARTICLES) {
     k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<T, WSRC_PARTICLES><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, o, N, sq, keep);
+    k_resample<T, WSRC_PARTICLES><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, o, N, sq, keep, (int)ntiles);
   } else if (mode == WSRC_Q) {
     if (!std::is_same<T, float>::value) return cudaErrorInvalidValue;  // FP32 state only
     k_tile_sums<WSRC_Q><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<float, WSRC_Q><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, reinterpret_cast<float*>(o), N, sq,
-                                                                   keep);
+    k_resample<float, WSRC_Q><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, reinterpret_cast<float*>(o), N,
+                                                                       sq, keep, (int)ntiles);
   } else {
     k_tile_sums<WSRC_LOGW><<<ntiles, SCAN_THREADS, 0, s>>>(b, lsrc, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<T, WSRC_LOGW><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep);
+    k_resample<T, WSRC_LOGW><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, lsrc, o, N, sq, keep, (int)ntiles);
   }
   return cudaGetLastError();
 }
@@ -549,12 +636,14 @@ cudaError_t launch_resample7(const StepBuffers& b, float* state_out, int64_t N, 
     k_tile_sums<WSRC_BINS><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<float, WSRC_BINS, 7><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq, keep);
+    k_resample<float, WSRC_BINS, 7><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq, keep,
+                                                                             (int)ntiles);
   } else {
     k_tile_sums<WSRC_PARTICLES><<<ntiles, SCAN_THREADS, 0, s>>>(b, nullptr, N, u0, sq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample<float, WSRC_PARTICLES, 7><<<ntiles, SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq, keep);
+    k_resample<float, WSRC_PARTICLES, 7><<<rs_grid(N), SCAN_THREADS, RS_SMEM, s>>>(b, nullptr, state_out, N, sq,
+                                                                                  keep, (int)ntiles);
   }
   return cudaGetLastError();
 }
