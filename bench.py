@@ -48,6 +48,11 @@ PROP_BIN_BYTES = 64
 # per output
 RESAMPLE_BYTES = 48
 KERNELS_PER_STEP = 5
+# deferred resampling: the propagate kernel reads the last step's ancestor 4 and gathers that state 20,
+# reads noise 20, writes the propagated state 20 and the slot 4; tile sums + resample read the slot 4
+# (twice) and write the ancestor 4
+DEFERRED_PROP_BIN_BYTES = 68
+DEFERRED_RESAMPLE_BYTES = 12
 
 
 # SIR's likelihood (Eq. likelihood, Poisson): per pixel term the algorithmic work is
@@ -103,16 +108,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(N):
-    """dram bytes per launch of the propagate/bin kernel from the committed ncu summary,
-    scaled to N particles; None if absent or taken on a different kernel source."""
+def profiled_traffic(N, label="dram bytes per particle"):
+    """dram bytes per launch of the propagate/bin kernel from the committed ncu summary (``label``:
+    the plain or the gathering variant's line), scaled to N particles; None if absent or taken on a
+    different kernel source."""
     path = os.path.join(ROOT, "profiles", "k_prop_bin_512x512_h0.5.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
-    m_bpp = re.search(r"dram bytes per particle:\s*([0-9.]+)", txt)
+    m_bpp = re.search(r"^" + re.escape(label) + r":\s*([0-9.]+)", txt, re.M)
     if not (m_hash and m_bpp) or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_bpp.group(1)) * N
@@ -731,6 +737,48 @@ def run_batched3(n_targets, n_per, steps, warmup, seed, world=1):
             "step_bytes_per_particle": bpp, "step_gbs": gbs, "step_frac_of_hbm": gbs / hbm, "peak_source": kind}
 
 
+def run_deferred(ctx, pcsir, state0, images, noise, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm, peak_kind):
+    """The same steps as a deferred-resampling run (pcsir_deferred_*): each resampling recorded as
+    ancestors, gathered by the next step's propagation.  Timed: K steps and, once at the end, the
+    resampled states written out to a caller buffer (pcsir_deferred_state)."""
+    import numpy as np
+    import torch
+
+    out = torch.empty_like(state0)
+    pcsir.pcsir_deferred_begin(ctx, state0, stream=stream)
+    for k in range(Wm):
+        pcsir.pcsir_deferred_step(ctx, images[k], h, noise[k % NOISE_POOL], u0s[k], stream=stream)
+    torch.cuda.synchronize()
+    ctx.timing_enable(K)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(Wm, Wm + K):
+        pcsir.pcsir_deferred_step(ctx, images[k], h, noise[k % NOISE_POOL], u0s[k], stream=stream)
+    pcsir.pcsir_deferred_state(ctx, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1)
+    r = ctx.last_result()
+    stages = np.array(ctx.timing_read(K)).mean(axis=0)
+    if pg:
+        elapsed = max_over_ranks(elapsed, pg, dev)
+    achieved = DEFERRED_PROP_BIN_BYTES * N / (stages[0] * 1e-3) / 1e9
+    return {"value": N * K * 1e3 / elapsed, "unit": "particles/s", "ms_per_step": elapsed / K,
+            "steps": K, "api": "pcsir_deferred_begin / pcsir_deferred_step x K / pcsir_deferred_state (timed)",
+            "stages_ms": {"prop_bin": float(stages[0]), "dummies_lik": float(stages[1]), "weights": float(stages[2]),
+                          "scan_resample": float(stages[3])},
+            "roofline": {"kernel": "k_prop_bin (gathering)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": profiled_traffic(N, "gathering dram bytes per particle"), "peak_source": peak_kind,
+                         "algorithmic_bytes": DEFERRED_PROP_BIN_BYTES * N},
+            "scan_resample_gbs": DEFERRED_RESAMPLE_BYTES * N / (stages[3] * 1e-3) / 1e9,
+            "last_estimate_err_px": float(np.hypot(*(np.array(r["estimate"][:2]) - seq.gt[Wm + K, :2]))),
+            "device_error": int(r["device_error"])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -861,6 +909,8 @@ def main():
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes": bytes_pb}
     resample_gbs = RESAMPLE_BYTES * N / (st_mean[3] * 1e-3) / 1e9
+    deferred = run_deferred(ctx, pcsir, state0, images, noise, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm,
+                            peak_kind)
 
     # end to end through the C ABI: every step's image and noise copied in from page-locked host
     # memory and its result read back; the next step's inputs travel on a second stream into a
@@ -1019,6 +1069,7 @@ def main():
                           "scan_resample": st_mean[3], "share": [float(s) for s in share],
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
+            "deferred": deferred,
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
             "large_object": large, "tracking_3d": track3d, "ess_threshold": ess_cmp,
             "cpu_baseline": cpu,

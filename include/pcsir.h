@@ -192,6 +192,37 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
                         int32_t W, int32_t H, double h, const void* noise, double u0,
                         void* stream, pcsir_result* result_host);
 
+/*
+ * Deferred resampling: a run of pcSIR steps (Algorithm 2, resampling every
+ * step) whose particle set lives in the context between steps.  pcsir_step
+ * gathers the resampled states x_k^i = x~_k^{a(i)} into the caller's buffer
+ * (read and write 5 states per particle) only for the next step to read them
+ * back; here the resampling records the ancestors a(i) and the next step's
+ * propagation reads x~_k^{a(i)} itself.  Same filter, same numbers: each
+ * step's propagated states, cells, dummies, likelihoods, weights, results and
+ * ancestors equal pcsir_step's bit for bit on the same inputs; the saving is
+ * the gather (40 B per FP32 particle and step).
+ *
+ * pcsir_deferred_begin copies `state` ([5][N], the states x_0, all weights
+ *   equal) into the context on `stream` and starts a run of N particles.  On
+ *   its first call it allocates the run's second state buffer and ancestor
+ *   array (24 B per FP32 particle, 44 B FP64); PCSIR_ENOMEM if that fails.
+ * pcsir_deferred_step: one step of the run, arguments as pcsir_step.  The
+ *   outputs (pcsir_get_outputs) are those of pcsir_step; `ancestor` is always
+ *   filled (it is the run's ancestor array).
+ * pcsir_deferred_state writes the run's current resampled states x_k into
+ *   `state` ([5][N], caller-owned, device) on `stream`; the run continues.
+ * Any other step on the context (pcsir_step, sir_step, the ESS steps) ends
+ * the run; pcsir_deferred_step then returns PCSIR_ESTATE until the next
+ * begin.  Not with an attached surrogate (PCSIR_ENOTSUP).  Checkpoints
+ * (pcsir_save) do not hold the run's states: write them out with
+ * pcsir_deferred_state.  Errors otherwise as pcsir_step.
+ */
+pcsir_status pcsir_deferred_begin(pcsir_ctx* ctx, const void* state, int64_t N, void* stream);
+pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
+                                 const void* noise, double u0, void* stream, pcsir_result* result_host);
+pcsir_status pcsir_deferred_state(pcsir_ctx* ctx, void* state, void* stream);
+
 /* One SIR step (Algorithm 1, bootstrap proposal, resampling every step): as
    pcsir_step without the bins; the likelihood is evaluated for every particle. */
 pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image,

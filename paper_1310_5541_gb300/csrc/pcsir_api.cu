@@ -29,6 +29,13 @@ struct pcsir_ctx {
   bool sur_on = false;
   bool sur_ran = false;          // the last pcSIR step used the surrogate
   unsigned long long sur_steps = 0;
+  // deferred resampling run: the particle set is b.prop[., def_anc[i]] (def_has_anc) or b.prop
+  void* def_other = nullptr;  // the run's second state buffer
+  int32_t* def_anc = nullptr;
+  bool def_active = false;
+  bool def_has_anc = false;
+  bool last_deferred = false;  // the last step was a deferred one (its ancestors are def_anc)
+  int64_t def_N = 0;
   // stage timing: 5 events per step slot
   std::vector<cudaEvent_t> events;
   int timing_slots = 0;
@@ -97,6 +104,12 @@ pcsir_status check_step_args(pcsir_ctx* c, const void* state, int64_t N, const f
   if (W < 1 || H < 1) return fail(c, PCSIR_EINVAL, "image width and height must be >= 1");
   if (!(u0 >= 0.0 && u0 < 1.0)) return fail(c, PCSIR_EINVAL, "u0 must lie in [0, 1)");
   return PCSIR_OK;
+}
+
+// a plain step overwrites the propagated-state buffer a deferred run keeps its particles in
+void end_deferred(pcsir_ctx* c) {
+  c->def_active = false;
+  c->last_deferred = false;
 }
 
 pcsir_status finish_step(pcsir_ctx* c, cudaStream_t s, pcsir_result* result_host, int kind, int64_t N) {
@@ -219,6 +232,7 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
                         const void* noise, double u0, void* stream, pcsir_result* result_host) {
   pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
   if (st != PCSIR_OK) return st;
+  end_deferred(ctx);
   if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const StageEvents se = step_events(ctx);
@@ -251,10 +265,89 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
   return finish_step(ctx, s, result_host, 1, N);
 }
 
+pcsir_status pcsir_deferred_begin(pcsir_ctx* ctx, const void* state, int64_t N, void* stream) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (!state) return fail(ctx, PCSIR_EINVAL, "state must be a non-NULL device pointer");
+  if (N < 1) return fail(ctx, PCSIR_EINVAL, "N must be >= 1");
+  if (N > ctx->cfg.max_particles) return fail(ctx, PCSIR_ERANGE, "N exceeds max_particles of the context");
+  if (ctx->sur_on) return fail(ctx, PCSIR_ENOTSUP, "deferred resampling does not use the likelihood surrogate");
+  end_deferred(ctx);
+  const int64_t nmax = ctx->cfg.max_particles;
+  if (!ctx->def_other) {
+    unsigned char* p = nullptr;
+    if (!dev_alloc(ctx, &p, 5 * (size_t)nmax * state_size(ctx)))
+      return fail(ctx, PCSIR_ENOMEM, "state buffer of the deferred run");
+    ctx->def_other = p;
+  }
+  if (!ctx->def_anc && !dev_alloc(ctx, &ctx->def_anc, (size_t)nmax))
+    return fail(ctx, PCSIR_ENOMEM, "ancestor array of the deferred run");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e =
+      cudaMemcpyAsync(ctx->b.prop, state, 5 * (size_t)N * state_size(ctx), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of the run's initial states");
+  ctx->def_active = true;
+  ctx->def_has_anc = false;
+  ctx->def_N = N;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
+                                 const void* noise, double u0, void* stream, pcsir_result* result_host) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (!ctx->def_active && !ctx->failed) return fail(ctx, PCSIR_ESTATE, "no deferred run: call pcsir_deferred_begin");
+  const int64_t N = ctx->def_N;
+  pcsir_status st = check_step_args(ctx, ctx->b.prop, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
+  if (ctx->sur_on) return fail(ctx, PCSIR_ENOTSUP, "deferred resampling does not use the likelihood surrogate");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StageEvents se = step_events(ctx);
+  cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[0], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of step control block");
+  const int64_t prev_bins = ctx->last_kind == 1 ? ((volatile pcsir_result*)ctx->host_res)->n_bins : -1;
+  ctx->b.big_table = prev_bins >= 0 ? (prev_bins > 1200 ? 1 : 0) : (h < 0.15 ? 1 : 0);
+  // this step reads the run's particles from src (through the last step's ancestors) and
+  // propagates them into dst; its resampling records the ancestors only
+  void* src = ctx->b.prop;
+  void* dst = ctx->def_other;
+  StepBuffers b = ctx->b;
+  b.prop = dst;
+  b.anc = ctx->def_anc;
+  e = launch_pcsir_front(b, ctx->m, ctx->cfg.state_dtype, src, noise, N, h, image, W, H, ctx->num_sms, s, se,
+                         nullptr, ctx->def_has_anc ? ctx->def_anc : nullptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels (deferred)");
+  e = launch_resample(b, ctx->cfg.state_dtype, nullptr, N, u0, WSRC_BINS, ctx->cfg.keep | PCSIR_KEEP_ANCESTORS,
+                      ctx->num_sms, s);
+  if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel (deferred)");
+  ctx->b.prop = dst;
+  ctx->def_other = src;
+  ctx->def_has_anc = true;
+  ctx->sur_ran = false;
+  st = finish_step(ctx, s, result_host, 1, N);
+  ctx->last_deferred = true;
+  return st;
+}
+
+pcsir_status pcsir_deferred_state(pcsir_ctx* ctx, void* state, void* stream) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (ctx->failed) return fail(ctx, PCSIR_ESTATE, "context failed earlier: " + ctx->err);
+  if (!ctx->def_active) return fail(ctx, PCSIR_ESTATE, "no deferred run: call pcsir_deferred_begin");
+  if (!state) return fail(ctx, PCSIR_EINVAL, "state must be a non-NULL device pointer");
+  const cudaError_t e = launch_gather_state(ctx->cfg.state_dtype, ctx->b.prop,
+                                            ctx->def_has_anc ? ctx->def_anc : nullptr, state, ctx->def_N,
+                                            static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gather of the run's states");
+  return PCSIR_OK;
+}
+
 pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H,
                       const void* noise, double u0, void* stream, pcsir_result* result_host) {
   pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
   if (st != PCSIR_OK) return st;
+  end_deferred(ctx);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const StageEvents se = step_events(ctx);
   cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
@@ -286,6 +379,7 @@ pcsir_status pcsir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t 
                             pcsir_result* result_host) {
   pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
   if (st != PCSIR_OK) return st;
+  end_deferred(ctx);
   if ((st = check_ess_args(ctx, logw, ess_min)) != PCSIR_OK) return st;
   if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -311,6 +405,7 @@ pcsir_status sir_step_ess(pcsir_ctx* ctx, void* state, int64_t* logw, int64_t N,
                           pcsir_result* result_host) {
   pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
   if (st != PCSIR_OK) return st;
+  end_deferred(ctx);
   if ((st = check_ess_args(ctx, logw, ess_min)) != PCSIR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(ctx->b.ctl, 0, sizeof(Control), s);
@@ -423,7 +518,7 @@ pcsir_status pcsir_get_outputs(pcsir_ctx* ctx, pcsir_outputs* o) {
   } else {
     o->loglik = b.ll;
   }
-  o->ancestor = b.anc;
+  o->ancestor = ctx->last_deferred ? ctx->def_anc : b.anc;
   o->weight = b.wout;
   o->qweight = reinterpret_cast<const int64_t*>(b.qout);
   return PCSIR_OK;

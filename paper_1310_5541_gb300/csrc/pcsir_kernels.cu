@@ -31,10 +31,13 @@ template <> struct Scales<double> {
 };
 
 // Nearly-constant-velocity transition of one particle (Section 5.1).
+// With a resampling of the previous step left unapplied (src_idx), particle i
+// of the resampled set is the propagated particle src_idx[i] of that step.
 template <typename T>
 __device__ __forceinline__ void propagate1(const T* __restrict__ st, const T* __restrict__ nz, int64_t N,
-                                           int64_t i, T v[5]) {
-  const T x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
+                                           int64_t i, T v[5], const int32_t* __restrict__ src_idx = nullptr) {
+  const int64_t j = src_idx ? (int64_t)src_idx[i] : i;
+  const T x = st[j], y = st[N + j], vx = st[2 * N + j], vy = st[3 * N + j], a = st[4 * N + j];
   const T ex = nz[i], ey = nz[N + i], evx = nz[2 * N + i], evy = nz[3 * N + i], ea = nz[4 * N + i];
   v[0] = add_rn(add_rn(x, vx), ex);
   v[1] = add_rn(add_rn(y, vy), ey);
@@ -192,9 +195,12 @@ __device__ __forceinline__ int64_t pb_index(int64_t base, int k) {
   return VEC ? base + 4 * threadIdx.x + k : base + (int64_t)k * THREADS + threadIdx.x;
 }
 
-template <typename T, bool VEC, int LTB>
+// GATHER: the input particle set is st[., src_idx[i]] (deferred resampling: the
+// previous step recorded its ancestors and left the gather to this read).
+template <typename T, bool VEC, int LTB, bool GATHER = false>
 __global__ void __launch_bounds__(PbShape<LTB>::THREADS, LTB == 10 ? 2 : 1)
-k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq) {
+k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq,
+           const int32_t* __restrict__ src_idx = nullptr) {
   constexpr int THR = PbShape<LTB>::THREADS;
   constexpr int CHUNK = PbShape<LTB>::CHUNK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,8 +218,9 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
   }
   // anchors of vx, vy, I0: particle 0's input value in fixed point
   long long anc[3];
+  const int64_t src0 = GATHER ? (int64_t)src_idx[0] : 0;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) anc[c] = to_fixed(st[(2 + c) * N], Scales<T>::VAL);
+  for (int c = 0; c < 3; ++c) anc[c] = to_fixed(st[(2 + c) * N + src0], Scales<T>::VAL);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) b.ctl->anchor[2 + c] = anc[c];
@@ -230,10 +237,22 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       // 16-byte loads and stores of four consecutive particles per component
       const int64_t i0 = base + 4 * threadIdx.x;
       float4 sv[5], nv[5];
+      if (GATHER) {
+        // the four particles' sources: nondecreasing indices (systematic resampling), so a warp's
+        // reads stay within a few cache lines per component
+        const int4 a4 = *reinterpret_cast<const int4*>(src_idx + i0);
+        const float* sf = reinterpret_cast<const float*>(st);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        sv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0);
-        nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
+        for (int c = 0; c < 5; ++c) {
+          sv[c] = make_float4(sf[c * N + a4.x], sf[c * N + a4.y], sf[c * N + a4.z], sf[c * N + a4.w]);
+          nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          sv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0);
+          nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
+        }
       }
       const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
       const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
@@ -255,7 +274,7 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       for (int k = 0; k < PB_PER_THREAD; ++k) {
         const int64_t i = pb_index<false, THR>(base, k);
         if (i < N) {
-          propagate1(st, nz, N, i, v[k]);
+          propagate1(st, nz, N, i, v[k], GATHER ? src_idx : nullptr);
 #pragma unroll
           for (int c = 0; c < 5; ++c) prop[c * N + i] = v[k][c];
         }
@@ -768,8 +787,16 @@ static cudaError_t prop_bin_prepare1(int* per_sm) {
   const size_t smem = sizeof(LocalTable<LTB>);
   cudaError_t e =
       cudaFuncSetAttribute(k_prop_bin<T, VEC, LTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_prop_bin<T, VEC, LTB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // the grid is sized from the plain variant; the gathering one must fit the same number of blocks
+  int g = 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T, VEC, LTB>, PbShape<LTB>::THREADS, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_prop_bin<T, VEC, LTB, true>, PbShape<LTB>::THREADS,
+                                                      smem);
+  if (g < *per_sm) *per_sm = g;
   if (*per_sm < 1) *per_sm = 1;
   return e;
 }
@@ -797,29 +824,36 @@ cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
 
 template <typename T, int LTB>
 static cudaError_t prop_bin_launch_t(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
-                                     int num_sms, int per_sm, cudaStream_t s, long long hq) {
+                                     int num_sms, int per_sm, cudaStream_t s, long long hq, const int32_t* src_idx) {
   const size_t smem = sizeof(LocalTable<LTB>);
   constexpr int THR = PbShape<LTB>::THREADS;
   const int64_t nchunks = (N + PbShape<LTB>::CHUNK - 1) / PbShape<LTB>::CHUNK;
   const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * per_sm);
   const bool vec = std::is_same<T, float>::value && (N % 4 == 0) &&
                    ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(noise) |
-                     reinterpret_cast<uintptr_t>(b.prop) | reinterpret_cast<uintptr_t>(b.pslot)) % 16 == 0);
-  if (vec)
-    k_prop_bin<T, true, LTB><<<grid, THR, smem, s>>>(b, static_cast<const T*>(state),
-                                                      static_cast<const T*>(noise), N, (T)h, hq);
-  else
-    k_prop_bin<T, false, LTB><<<grid, THR, smem, s>>>(b, static_cast<const T*>(state),
-                                                       static_cast<const T*>(noise), N, (T)h, hq);
+                     reinterpret_cast<uintptr_t>(b.prop) | reinterpret_cast<uintptr_t>(b.pslot) |
+                     reinterpret_cast<uintptr_t>(src_idx)) % 16 == 0);
+  const T* st = static_cast<const T*>(state);
+  const T* nz = static_cast<const T*>(noise);
+  if (src_idx != nullptr) {
+    if (vec)
+      k_prop_bin<T, true, LTB, true><<<grid, THR, smem, s>>>(b, st, nz, N, (T)h, hq, src_idx);
+    else
+      k_prop_bin<T, false, LTB, true><<<grid, THR, smem, s>>>(b, st, nz, N, (T)h, hq, src_idx);
+  } else if (vec) {
+    k_prop_bin<T, true, LTB><<<grid, THR, smem, s>>>(b, st, nz, N, (T)h, hq);
+  } else {
+    k_prop_bin<T, false, LTB><<<grid, THR, smem, s>>>(b, st, nz, N, (T)h, hq);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t prop_bin_launch(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
-                                   int num_sms, cudaStream_t s, long long hq) {
+                                   int num_sms, cudaStream_t s, long long hq, const int32_t* src_idx) {
   if (b.big_table)
-    return prop_bin_launch_t<T, 12>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[1], s, hq);
-  return prop_bin_launch_t<T, 10>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[0], s, hq);
+    return prop_bin_launch_t<T, 12>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[1], s, hq, src_idx);
+  return prop_bin_launch_t<T, 10>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[0], s, hq, src_idx);
 }
 
 static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
@@ -828,10 +862,11 @@ static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
 
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
-                               int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur) {
+                               int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur,
+                               const int32_t* src_idx) {
   const long long hq = llrint(h * 2147483648.0);
-  cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
-                                     : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
+  cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq, src_idx)
+                                     : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq, src_idx);
   if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
   const LikParams lp = make_lik(m);
   if (sur == nullptr) {
@@ -892,8 +927,30 @@ cudaError_t launch_logw_front(const StepBuffers& b, const double* logw, int64_t 
 cudaError_t launch_prop_bin(const StepBuffers& b, int dtype, const void* state, const void* noise, int64_t N,
                             double h, int num_sms, cudaStream_t s) {
   const long long hq = llrint(h * 2147483648.0);
-  return dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq)
-                            : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq);
+  return dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq, nullptr)
+                            : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq, nullptr);
+}
+
+// The resampled particle set written out: out[., i] = src[., idx[i]] (idx == nullptr: a copy).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_state(const T* __restrict__ src, const int32_t* __restrict__ idx,
+                                                      T* __restrict__ out, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx ? (int64_t)idx[i] : i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c * N + i] = src[c * N + j];
+  }
+}
+
+cudaError_t launch_gather_state(int dtype, const void* src, const int32_t* idx, void* out, int64_t N,
+                                cudaStream_t s) {
+  const int64_t want = (N + 255) / 256;
+  const unsigned grid = (unsigned)(want < (1 << 20) ? want : (1 << 20));
+  if (dtype == PCSIR_F32)
+    k_gather_state<float><<<grid, 256, 0, s>>>(static_cast<const float*>(src), idx, static_cast<float*>(out), N);
+  else
+    k_gather_state<double><<<grid, 256, 0, s>>>(static_cast<const double*>(src), idx, static_cast<double*>(out), N);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_particle_weights(const StepBuffers& b, int dtype, int64_t N, int num_sms, int kind,

@@ -123,6 +123,9 @@ def _load():
         "pcsir_create": ([ctypes.POINTER(pcsir_config), ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_destroy": ([P], I32),
         "pcsir_step": ([P, P, I64, P, I32, I32, D, P, D, P, P], I32),
+        "pcsir_deferred_begin": ([P, P, I64, P], I32),
+        "pcsir_deferred_step": ([P, P, I32, I32, D, P, D, P, P], I32),
+        "pcsir_deferred_state": ([P, P, P], I32),
         "sir_step": ([P, P, I64, P, I32, I32, P, D, P, P], I32),
         "pcsir_step_ess": ([P, P, P, I64, P, I32, I32, D, P, D, D, P, P], I32),
         "sir_step_ess": ([P, P, P, I64, P, I32, I32, P, D, D, P, P], I32),
@@ -336,6 +339,33 @@ def pcsir_step(ctx, state, image, h, noise, u0, stream=None):
     H, W = image.shape
     st = lib.pcsir_step(ctx.handle, _ptr(state), N, _ptr(image), W, H, float(h), _ptr(noise), float(u0),
                         _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def pcsir_deferred_begin(ctx, state, stream=None):
+    """Start a deferred-resampling run from the states ``state`` [5, N] (copied into the context)."""
+    _check_cuda(state, "state", ctx.torch_dtype)
+    st = lib.pcsir_deferred_begin(ctx.handle, _ptr(state), state.shape[1], _stream_ptr(stream))
+    if st != OK:
+        ctx._raise(st)
+
+
+def pcsir_deferred_step(ctx, image, h, noise, u0, stream=None):
+    """One pcSIR step of the context's deferred run (Algorithm 2; resampling recorded as ancestors)."""
+    _check_cuda(noise, "noise", ctx.torch_dtype)
+    _check_cuda(image, "image", torch.float32)
+    H, W = image.shape
+    st = lib.pcsir_deferred_step(ctx.handle, _ptr(image), W, H, float(h), _ptr(noise), float(u0),
+                                 _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def pcsir_deferred_state(ctx, state, stream=None):
+    """Write the deferred run's current resampled states into ``state`` [5, N]."""
+    _check_cuda(state, "state", ctx.torch_dtype)
+    st = lib.pcsir_deferred_state(ctx.handle, _ptr(state), _stream_ptr(stream))
     if st != OK:
         ctx._raise(st)
 
