@@ -243,7 +243,7 @@ pcsir_status sir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image
  * ess_min: the step resamples when N_eff < ess_min (ess_min > N: every step;
  *   ess_min <= 0: never).  N_eff = (sum w)^2 / sum w^2 is result->ess.
  * pcsir_step_ess: each cell's dummy is the mean of its members weighted by
- *   w_{k-1} (Section 4, centre of mass of the state vectors and weights); the
+ *   w_{k-1} (Section 4: a centre of mass that weighs each member by its weight); the
  *   members' weights are multiplied by the dummy's likelihood.  The weighted
  *   sums are formed in FP32 per block and FP64 across blocks (within a few
  *   FP32 units in the last place of the weighted offsets, and not bit-for-bit
