@@ -112,11 +112,19 @@ static __device__ LLSum warp_loglik3(const float* __restrict__ vol, int W, int H
   bool bad = false;
   const int PP = Pxy * Pxy;
   const int total = PP * Pz;
-  for (int p = lane; p < total; p += 32) {
-    const int s = p / PP;
-    const int rem = p - s * PP;
-    const int r = rem / Pxy;
-    const int c = rem - r * Pxy;
+  // voxel p = (s Pxy + r) Pxy + c, advanced by 32 per iteration in mixed radix (no integer division
+  // in the loop): 32 = step_s PP + step_r Pxy + step_c
+  const int step_s = 32 / PP, step_r = (32 - step_s * PP) / Pxy, step_c = 32 - step_s * PP - step_r * Pxy;
+  int s = lane / PP, r = (lane - s * PP) / Pxy, c = lane - s * PP - r * Pxy;
+  for (int p = lane; p < total; p += 32, c += step_c, r += step_r, s += step_s) {
+    if (c >= Pxy) {
+      c -= Pxy;
+      ++r;
+    }
+    if (r >= Pxy) {
+      r -= Pxy;
+      ++s;
+    }
     const int px = q.cx - Rxy + c, py = q.cy - Rxy + r, pz = q.cz - Rz + s;
     if (px < 0 || px >= W || py < 0 || py >= H || pz < 0 || pz >= D) continue;
     const float z = __ldg(vol + ((size_t)pz * H + py) * W + px);
@@ -126,9 +134,7 @@ static __device__ LLSum warp_loglik3(const float* __restrict__ vol, int W, int H
       const df sm = two_sum(prod.hi, __fsub_rn(lp.bg, z));
       const float d = __fadd_rn(sm.hi, __fadd_rn(sm.lo, prod.lo));
       const float u = __fdividef(d, z);
-      const float t = -z * phi_log1p(u);
-      bad |= (t != t);
-      acc.add(t);
+      acc.add(-z * phi_log1p(u));  // a NaN term makes the sum NaN, marked bad below
     } else {
       const df lam = df_add_f(prod, lp.bg);
       bad |= (z != z);
@@ -138,6 +144,7 @@ static __device__ LLSum warp_loglik3(const float* __restrict__ vol, int W, int H
   }
   bad = __any_sync(0xffffffffu, bad);
   const df tot = warp_sum_df(two_sum(acc.s, -acc.c));
+  bad |= (tot.hi != tot.hi);
   __syncwarp();
   return {tot, bad};
 }

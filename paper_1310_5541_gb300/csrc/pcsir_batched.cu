@@ -52,7 +52,7 @@ struct BatchCtl {  // zeroed every step
   unsigned int bar_count;
   unsigned int bar_gen;
   unsigned int abort;
-  unsigned int pad;
+  unsigned int chunk_next;  // propagation phase: the next pair of chunks to hand out
   unsigned long long phase_ns[8];  // global-timer reading of block 0 at the start and after each phase
 };
 
@@ -319,14 +319,24 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     tab.hot = 0u;
   }
   __syncthreads();
-  // each block takes a contiguous range of chunks, so it meets the cells of a few neighbouring
-  // targets only (a grid-stride order would show every block every target's cells and overflow
-  // its table into per-particle global atomics)
+  // each block takes pairs of consecutive chunks from a shared counter: two neighbouring chunks
+  // meet the cells of one or two targets (a grid-stride order would show every block every
+  // target's cells and overflow its table into per-particle global atomics), and a block slowed
+  // by many cells or global inserts takes fewer pairs instead of holding up the phase (a fixed
+  // contiguous range per block: 0.75 ms at 1000 targets, these pairs 0.66 ms)
+  constexpr long long GRAB = 2;
   const long long nchunks = (N + BT_CHUNK - 1) / BT_CHUNK;
-  const long long per_block = (nchunks + gridDim.x - 1) / gridDim.x;
-  const long long c_begin = (long long)blockIdx.x * per_block;
-  const long long c_end = c_begin + per_block < nchunks ? c_begin + per_block : nchunks;
-  for (long long chunk = c_begin; chunk < c_end; ++chunk) {
+  __shared__ long long s_grab;
+  long long chunk = 0, c_end = 0;
+  for (;;) {
+    if (chunk >= c_end) {
+      __syncthreads();  // every thread has read the previous s_grab
+      if (threadIdx.x == 0) s_grab = (long long)atomicAdd(&b.ctl->chunk_next, 1u) * GRAB;
+      __syncthreads();
+      chunk = s_grab;
+      c_end = chunk + GRAB < nchunks ? chunk + GRAB : nchunks;
+      if (chunk >= nchunks) break;
+    }
     const long long base = chunk * BT_CHUNK;
     float v[BT_PER_THREAD][5];
     // per particle: -2 none, >= 0 local slot, <= -3 global slot -3 - ls (local table full); the
@@ -476,6 +486,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       // ordered before any count of the next chunk by that chunk's block barrier
       if (threadIdx.x == 0) tab.hot = 0u;
     }
+    ++chunk;
   }
   blocal_flush(tab, b, false);
 }

@@ -331,9 +331,8 @@ __device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int
         const df s = two_sum(prod.hi, __fsub_rn(lp.bg, z));
         const float d = __fadd_rn(s.hi, __fadd_rn(s.lo, prod.lo));
         const float u = __fdividef(d, z);  // 2 ulp; z is a photon count, far inside the normal range
-        const float t = -z * phi_log1p(u);
-        bad |= (t != t);
-        acc.add(t);
+        // a NaN term (from a NaN pixel) makes the sum NaN, marked bad after the reduction
+        acc.add(-z * phi_log1p(u));
       } else {
         const df lam = df_add_f(prod, lp.bg);
         bad |= (z != z);
@@ -344,13 +343,12 @@ __device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int
       // e = z - lambda = (z - bg) - prod, rounded once
       const df s = two_sum(__fsub_rn(z, lp.bg), -prod.hi);
       const float e = __fadd_rn(s.hi, __fsub_rn(s.lo, prod.lo));
-      const float t = -(e * e) * lp.inv2sxi2;
-      bad |= (t != t);
-      acc.add(t);
+      acc.add(-(e * e) * lp.inv2sxi2);
     }
   }
   bad = __any_sync(0xffffffffu, bad);
   df tot = warp_sum_df(two_sum(acc.s, -acc.c));
+  bad |= (tot.hi != tot.hi);  // a NaN Poisson term (the xor reduction gives every lane the same sum)
   if (GS > 32) {
     // warps' partial sums in a fixed order
     if ((gtid & 31) == 0) {
