@@ -90,6 +90,7 @@ struct BatchBufs {
   long long* tile_sum;
   long long* tile_excl;
   const int* tile_target;  // [ntiles_total] target owning each tile (fixed at creation)
+  int lik_group;           // lanes per cell in the likelihood phase: 8 (patches <= 15), 16 (<= 31) or 32
   pcsir_result* res;  // [T]
   // optional per-particle outputs (nullptr unless kept): target-local ancestor of every output
   // particle and the integer weight of every propagated particle
@@ -494,6 +495,56 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
 // ---------------------------------------------------------------------------
 // Phase B: dummies and their likelihood, one warp per occupied cell
 // ---------------------------------------------------------------------------
+// The same with 32 / GS cells per warp (GS = 8 or 16 lanes each), for batches whose patches are
+// all small (b.lik_group): the per-cell work (means, one-dimensional PSF factors, the group's sum)
+// then runs for several cells at once instead of leaving most of a warp's lanes idle.
+template <int GS>
+__device__ void phase_bins_sub(const BatchBufs& b, const float* __restrict__ img, int W, int H, float* scratch_all) {
+  constexpr int CPW = 32 / GS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, grp = lane / GS, gtid = lane & (GS - 1);
+  const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
+  const size_t hcap = size_t(1) << b.hbits;
+  float* scratch = scratch_all + w * 4 * 64 + grp * (4 * 64 / CPW);
+  const unsigned nw = gridDim.x * (blockDim.x >> 5);
+  for (unsigned b0 = (blockIdx.x * (blockDim.x >> 5) + w) * CPW; b0 < B; b0 += nw * CPW) {
+    const unsigned bi = b0 + grp;
+    const bool active = bi < B;
+    unsigned long long key = 0ull;
+    int t = 0;
+    unsigned n = 0u;
+    LikParams lp{};
+    LikPos pos{};
+    if (active) {
+      const unsigned g = b.occ[bi];
+      key = b.hkey[g];
+      t = bkey_t(key);
+      const BatchTarget& T_ = b.tg[t];
+      const BatchStats& S_ = b.st[t];
+      n = b.hcnt[g];
+      const double rdn = 1.0 / (double)n;  // one FP64 division per cell (GB300's FP64 rate is low)
+      const double inv = 1.0 / 2147483648.0;
+      const double mx = ((double)((long long)bkey_bx(key) * T_.hq) + (double)b.hsum[g] * rdn) * inv;
+      const double my = ((double)((long long)bkey_by(key) * T_.hq) + (double)b.hsum[hcap + g] * rdn) * inv;
+      const double mi = ((double)S_.anchor[2] + (double)b.hsum[4 * hcap + g] * rdn) * (1.0 / 4194304.0);
+      lp.P = T_.patch;
+      lp.kind = PCSIR_LIK_POISSON;
+      lp.bg = T_.bg;
+      lp.c2 = T_.c2;
+      pos = lik_pos(mx, my, mi);
+    }
+    const LLSum ls = subgroup_loglik<GS>(img, W, H, pos, lp, scratch, active);
+    const double ll = ll_to_double(ls);
+    if (active && gtid == 0) {
+      if (ls.bad) atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_NONFINITE);
+      b.bin_ll[bi] = ll;
+      b.bin_cnt[bi] = n;
+      b.bin_key[bi] = key;
+      if (!ls.bad) atomicMax(&b.st[t].max_ll, ord_encode(ll));
+      atomicAdd(&b.st[t].nbins, 1u);
+    }
+  }
+}
+
 __device__ void phase_bins(const BatchBufs& b, const float* __restrict__ img, int W, int H, float* scratch_all) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned B = *(volatile unsigned*)&b.ctl->nocc;
@@ -798,7 +849,12 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   phase_prop_bin<LTB>(b, st, nz, *reinterpret_cast<BatchLocal<LTB>*>(bt_smem), offs);
   if (!grid_barrier(b, 1)) return;
   stamp(b.ctl, 2);
-  phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
+  if (b.lik_group == 8)
+    phase_bins_sub<8>(b, img, W, H, reinterpret_cast<float*>(bt_smem));
+  else if (b.lik_group == 16)
+    phase_bins_sub<16>(b, img, W, H, reinterpret_cast<float*>(bt_smem));
+  else
+    phase_bins(b, img, W, H, reinterpret_cast<float*>(bt_smem));
   if (!grid_barrier(b, 2)) return;
   stamp(b.ctl, 3);
   phase_weights(b);
@@ -932,6 +988,11 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   b.pstride = (ntot + 3) & ~3ll;
   b.ntiles_total = ntiles;
   b.hbits = hbits;
+  {
+    int pmax = 0;
+    for (int t = 0; t < T; ++t) pmax = std::max(pmax, tg[t].patch);
+    b.lik_group = pmax <= 15 ? 8 : (pmax <= 31 ? 16 : 32);
+  }
   BatchTarget* dtg = nullptr;
   long long* doffs = nullptr;
   int* dtile_target = nullptr;

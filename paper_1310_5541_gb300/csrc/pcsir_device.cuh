@@ -368,6 +368,83 @@ __device__ __forceinline__ LLSum group_loglik(const float* __restrict__ img, int
   return {tot, bad};
 }
 
+// The Poisson likelihood at one position by an aligned group of GS lanes (GS = 8 or 16), every
+// group of the warp at its own position: for small patches, where a whole warp per position
+// leaves most lanes idle in the pixel loop and spends more on the per-position work.  All lanes of
+// the warp call it together; a group with active == false takes no position (and returns zero).
+// The same terms as group_loglik, summed over fewer lanes.  scratch: 4 P floats for this group.
+template <int GS>
+__device__ __forceinline__ LLSum subgroup_loglik(const float* __restrict__ img, int W, int H, const LikPos& q,
+                                                 const LikParams& lp, float* __restrict__ scratch, bool active) {
+  static_assert(GS == 8 || GS == 16, "sub-warp groups of 8 or 16 lanes");
+  const int gtid = threadIdx.x & (GS - 1);
+  const int P = active ? lp.P : 0;
+  const int R = P >> 1;
+  const int cx = q.cx, cy = q.cy;
+  float* gxh = scratch;
+  float* gxl = scratch + P;
+  float* gyh = scratch + 2 * P;
+  float* gyl = scratch + 3 * P;
+  for (int j = gtid; j < 2 * P; j += GS) {
+    const bool col = j < P;
+    const int jj = col ? j : j - P;
+    const df d = col ? pixel_offset(cx - R + jj, q.x) : pixel_offset(cy - R + jj, q.y);
+    df e = df_mul(df_mul(d, d), lp.c2);
+    e.hi = -e.hi;
+    e.lo = -e.lo;
+    df g = df_exp_neg(e);
+    if (col) {
+      g = df_mul(g, q.i0);
+      gxh[jj] = g.hi;
+      gxl[jj] = g.lo;
+    } else {
+      gyh[jj] = g.hi;
+      gyl[jj] = g.lo;
+    }
+  }
+  __syncwarp();
+  kahan acc;
+  bool bad = false;
+  // pixel p = r P + c advanced by GS per iteration: GS = step_r P + step_c (step_c < P)
+  const int step_r = P > 0 ? GS / P : 0, step_c = GS - step_r * P;
+  int r = P > 0 ? gtid / P : 0, c = gtid - r * P;
+  for (int p = gtid; p < P * P; p += GS, r += step_r, c += step_c) {
+    if (c >= P) {
+      c -= P;
+      ++r;
+    }
+    const int px = cx - R + c;
+    const int py = cy - R + r;
+    if (px < 0 || px >= W || py < 0 || py >= H) continue;
+    const float z = __ldg(img + (size_t)py * W + px);
+    const df prod = df_mul({gxh[c], gxl[c]}, {gyh[r], gyl[r]});  // I0 gx gy
+    if (z > 0.0f) {
+      const df s2 = two_sum(prod.hi, __fsub_rn(lp.bg, z));
+      const float d = __fadd_rn(s2.hi, __fadd_rn(s2.lo, prod.lo));
+      acc.add(-z * phi_log1p(__fdividef(d, z)));  // a NaN term makes the sum NaN, marked bad below
+    } else {
+      const df lam = df_add_f(prod, lp.bg);
+      bad |= (z != z);
+      acc.add(-lam.hi);
+      acc.add(-lam.lo);
+    }
+  }
+  // the group's sum: xor shuffles over offsets below GS stay within the aligned group
+  df tot = two_sum(acc.s, -acc.c);
+#pragma unroll
+  for (int o = GS / 2; o > 0; o >>= 1) {
+    df w;
+    w.hi = __shfl_xor_sync(0xffffffffu, tot.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, tot.lo, o);
+    tot = df_add(tot, w);
+  }
+  const unsigned gmask = ((1u << GS) - 1u) << (threadIdx.x & 31 & ~(GS - 1));
+  bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0u;
+  bad |= (tot.hi != tot.hi);
+  __syncwarp();  // scratch may be reused after this
+  return {tot, bad};
+}
+
 // the warp version used per particle (SIR) and for stand-alone evaluations
 __device__ __forceinline__ LLSum warp_loglik(const float* __restrict__ img, int W, int H, const LikPos& q,
                                              const LikParams& lp, float* __restrict__ scratch) {

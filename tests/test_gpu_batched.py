@@ -135,6 +135,18 @@ def test_batched_step_matches_per_target_oracle(pc):
     print("batched: ancestors differing from the oracle's:", mism, "of", int(batch.n.sum()))
 
 
+@pytest.mark.parametrize("patches", [[21, 9, 17, 25, 11, 13, 19], [41, 9, 21, 15, 33, 11, 13]])
+def test_batched_likelihood_lane_groups(pc, patches):
+    """Patches up to 15 pixels take 8 lanes per cell in the likelihood phase, up to 31 take 16, larger
+    ones a warp: the same per-target parity with 16 lanes (largest 25) and with a warp (largest 41)."""
+    n = [3000, 4096, 777, 9000, 2500, 20000, 1]
+    batch = synth.make_batch(len(n), 224, 192, 3, seed=SEED + 40, n_values=n, min_sep=44.0, h_of_sigma=None)
+    batch.patch[:] = patches
+    batch.h[:] = [0.5, 0.25, 1.0, 0.5, 0.5, 0.25, 1.0]
+    st = _warm(batch, 2)
+    _compare(pc, batch, st, 2, SEED + 42)
+
+
 def test_batched_many_small_targets(pc):
     rng = np.random.default_rng(4)
     n = list(rng.integers(50, 3000, 40))
