@@ -53,6 +53,10 @@ KERNELS_PER_STEP = 5
 # (twice) and write the ancestor 4
 DEFERRED_PROP_BIN_BYTES = 68
 DEFERRED_RESAMPLE_BYTES = 12
+# noise drawn in the kernel: no noise array is read (plain: 64 - 20; deferred: 68 - 20)
+DRAWN_PROP_BIN_BYTES = 44
+DRAWN_DEFERRED_PROP_BIN_BYTES = 48
+DRAWN_SEED = 0x5EED_1310_5541
 
 
 # SIR's likelihood (Eq. likelihood, Poisson): per pixel term the algorithmic work is
@@ -99,7 +103,7 @@ def kernel_source_hash():
     pcsir_internal.h that its launches pass (declarations elsewhere in that header do not count)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1310_5541_gb300", "csrc")
-    for f in ("pcsir_kernels.cu", "pcsir_device.cuh"):
+    for f in ("pcsir_kernels.cu", "pcsir_device.cuh", "pcsir_philox.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "pcsir_internal.h"), "rb") as fh:
@@ -737,6 +741,91 @@ def run_batched3(n_targets, n_per, steps, warmup, seed, world=1):
             "step_bytes_per_particle": bpp, "step_gbs": gbs, "step_frac_of_hbm": gbs / hbm, "peak_source": kind}
 
 
+def run_drawn(ctx, pcsir, state0, images, img_host, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm, peak_kind,
+              deferred):
+    """The headline's steps with the process noise drawn in the kernel (pcsir_step_philox, or a
+    deferred run of pcsir_deferred_step_philox): device-resident timing of K steps, and an end-to-end
+    run through the same C ABI in which every step copies its image from page-locked host memory and
+    reads its result back (the noise no longer crosses the host link).  The deferred run writes its
+    resampled states out once at the end of each timed region."""
+    import numpy as np
+    import torch
+
+    q = Q
+    state = state0.clone()
+    out = torch.empty_like(state0)
+    res1 = pcsir.pcsir_result()
+
+    def step(k, img):
+        if deferred:
+            r = pcsir.lib.pcsir_deferred_step_philox(ctx.handle, pcsir._ptr(img), W_IMG, H_IMG, float(h),
+                                                     pcsir._q5(q), DRAWN_SEED, k, float(u0s[k]),
+                                                     pcsir._stream_ptr(stream), None)
+        else:
+            r = pcsir.lib.pcsir_step_philox(ctx.handle, pcsir._ptr(state), N, pcsir._ptr(img), W_IMG, H_IMG,
+                                            float(h), pcsir._q5(q), DRAWN_SEED, k, float(u0s[k]),
+                                            pcsir._stream_ptr(stream), None)
+        if r != 0:
+            ctx._raise(r)
+
+    def begin():
+        state.copy_(state0)
+        if deferred:
+            pcsir.pcsir_deferred_begin(ctx, state0, stream=stream)
+
+    begin()
+    for k in range(Wm):
+        step(k, images[k])
+    torch.cuda.synchronize()
+    ctx.timing_enable(K)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(Wm, Wm + K):
+        step(k, images[k])
+    if deferred:
+        pcsir.pcsir_deferred_state(ctx, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1)
+    r = ctx.last_result()
+    stages = np.array(ctx.timing_read(K)).mean(axis=0)
+    if pg:
+        elapsed = max_over_ranks(elapsed, pg, dev)
+    bytes_pb = DRAWN_DEFERRED_PROP_BIN_BYTES if deferred else DRAWN_PROP_BIN_BYTES
+    achieved = bytes_pb * N / (stages[0] * 1e-3) / 1e9
+
+    # end to end: image in, result out, every step (one stream; the image is 1 MB)
+    img_dev = torch.empty((H_IMG, W_IMG), dtype=torch.float32, device=dev)
+    K_e2e = max(3, K // 2)
+    begin()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K_e2e):
+        img_dev.copy_(img_host[k], non_blocking=True)
+        step(k, img_dev)
+        stream.synchronize()
+        pcsir.lib.pcsir_last_result(ctx.handle, pcsir.ctypes.byref(res1))
+    if deferred:
+        pcsir.pcsir_deferred_state(ctx, out, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    return {"value": N * K * 1e3 / elapsed, "unit": "particles/s", "ms_per_step": elapsed / K, "steps": K,
+            "api": ("pcsir_deferred_begin / pcsir_deferred_step_philox x K / pcsir_deferred_state (timed)"
+                    if deferred else "pcsir_step_philox"),
+            "noise": "Philox4x32-10 + Box-Muller in the propagation kernel, seed %#x, counter (i, frame)" % DRAWN_SEED,
+            "stages_ms": {"prop_bin": float(stages[0]), "dummies_lik": float(stages[1]), "weights": float(stages[2]),
+                          "scan_resample": float(stages[3])},
+            "roofline": {"kernel": "k_prop_bin (drawn noise%s)" % (", gathering" if deferred else ""), "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "peak_source": peak_kind, "algorithmic_bytes": bytes_pb * N},
+            "e2e": {"value": N * K_e2e / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": 4 * H_IMG * W_IMG,
+                    "d2h_bytes_per_step": pcsir.ctypes.sizeof(pcsir.pcsir_result), "steps": K_e2e, "copies": "serial"},
+            "device_error": int(r["device_error"])}
+
+
 def run_deferred(ctx, pcsir, state0, images, noise, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm, peak_kind):
     """The same steps as a deferred-resampling run (pcsir_deferred_*): each resampling recorded as
     ancestors, gathered by the next step's propagation.  Timed: K steps and, once at the end, the
@@ -984,6 +1073,11 @@ def main():
            "h2d_copy_gbs": h2d_gbs, "host_cpus": len(cpus) if cpus else None,
            "h2d_copy_gbs_overlapped": int(4 * H_IMG * W_IMG + 5 * 4 * N) * K_e2e / (copy_ms * 1e-3) / 1e9}
 
+    drawn = {"plain": run_drawn(ctx, pcsir, state0, images, img_host, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm,
+                                peak_kind, False),
+             "deferred": run_drawn(ctx, pcsir, state0, images, img_host, u0s, N, h, K, Wm, stream, seq, pg, dev,
+                                   hbm, peak_kind, True)}
+
     # plain SIR on the same workload (the comparison path; likelihood for every particle)
     sir = None
     if args.sir_steps > 0:
@@ -1069,7 +1163,7 @@ def main():
                           "scan_resample": st_mean[3], "share": [float(s) for s in share],
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
-            "deferred": deferred,
+            "deferred": deferred, "drawn_noise": drawn,
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
             "large_object": large, "tracking_3d": track3d, "ess_threshold": ess_cmp,
             "cpu_baseline": cpu,

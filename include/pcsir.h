@@ -193,6 +193,31 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
                         void* stream, pcsir_result* result_host);
 
 /*
+ * pcsir_step with the process noise drawn in the propagation kernel instead
+ * of read from a device array: the nearly-constant-velocity increments of
+ * Section 5.1, e_d = q_d z_d for the five components, with z standard
+ * normals from the counter-based generator Philox4x32-10 (Salmon, Moraes,
+ * Dror and Shaw, SC 2011) and the Box-Muller transform.
+ *   q      host double[5]: standard deviations of the increments of x, y,
+ *          vx, vy, I0 (finite, >= 0), rounded to float.
+ *   seed   64-bit key of the generator.
+ *   frame  0 .. 2^32 - 1: particle i of frame k draws from the counters
+ *          (i mod 2^32, i div 2^32, k, 0) and (..., 1); the same (seed, frame)
+ *          gives the same noise, whatever N or the launch shape.
+ * The transform uses only correctly rounded single-precision operations and
+ * series for its logarithm, sine and cosine, so that a CPU implementation of
+ * the same steps reproduces the noise bit for bit; the normals agree with the
+ * exact transform to a few units in the last place.  Per FP32 particle the
+ * propagation reads 24 bytes instead of 44 (no noise array): the end-to-end
+ * path then copies only the image per step.  FP32 state only
+ * (PCSIR_ENOTSUP otherwise); PCSIR_EINVAL for a NULL or invalid q or a frame
+ * of 2^32 or more.  Other arguments, outputs and errors as pcsir_step.
+ */
+pcsir_status pcsir_step_philox(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H,
+                               double h, const double* q, uint64_t seed, uint64_t frame, double u0, void* stream,
+                               pcsir_result* result_host);
+
+/*
  * Deferred resampling: a run of pcSIR steps (Algorithm 2, resampling every
  * step) whose particle set lives in the context between steps.  pcsir_step
  * gathers the resampled states x_k^i = x~_k^{a(i)} into the caller's buffer
@@ -222,6 +247,10 @@ pcsir_status pcsir_deferred_begin(pcsir_ctx* ctx, const void* state, int64_t N, 
 pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
                                  const void* noise, double u0, void* stream, pcsir_result* result_host);
 pcsir_status pcsir_deferred_state(pcsir_ctx* ctx, void* state, void* stream);
+/* A step of the run with the noise drawn in the kernel, as pcsir_step_philox. */
+pcsir_status pcsir_deferred_step_philox(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
+                                        const double* q, uint64_t seed, uint64_t frame, double u0, void* stream,
+                                        pcsir_result* result_host);
 
 /* One SIR step (Algorithm 1, bootstrap proposal, resampling every step): as
    pcsir_step without the bins; the likelihood is evaluated for every particle. */

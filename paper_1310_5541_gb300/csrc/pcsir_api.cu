@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "pcsir_internal.h"
+#include "pcsir_philox.cuh"
 
 using namespace pcsir;
 
@@ -228,11 +229,23 @@ pcsir_status pcsir_destroy(pcsir_ctx* ctx) {
   return PCSIR_OK;
 }
 
-pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H, double h,
-                        const void* noise, double u0, void* stream, pcsir_result* result_host) {
-  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
-  if (st != PCSIR_OK) return st;
-  end_deferred(ctx);
+namespace {
+
+// checks of the generator's arguments: FP32 state, finite non-negative deviations, a 32-bit frame
+pcsir_status make_noise_gen(pcsir_ctx* ctx, const double* q, uint64_t seed, uint64_t frame, NoiseGen* ng) {
+  if (ctx->cfg.state_dtype != PCSIR_F32) return fail(ctx, PCSIR_ENOTSUP, "drawn noise needs FP32 state");
+  if (!q) return fail(ctx, PCSIR_EINVAL, "q must point to five standard deviations");
+  if (frame > 0xFFFFFFFFull) return fail(ctx, PCSIR_EINVAL, "frame must be below 2^32");
+  for (int d = 0; d < 5; ++d)
+    if (!(q[d] >= 0.0) || !std::isfinite(q[d])) return fail(ctx, PCSIR_EINVAL, "q must be finite and >= 0");
+  ng->seed = seed;
+  ng->frame = (unsigned)frame;
+  for (int d = 0; d < 5; ++d) ng->q[d] = (float)q[d];
+  return PCSIR_OK;
+}
+
+pcsir_status step_impl(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H, double h,
+                       const void* noise, const NoiseGen* ng, double u0, void* stream, pcsir_result* result_host) {
   if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const StageEvents se = step_events(ctx);
@@ -255,7 +268,7 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reset of surrogate statistics");
   }
   e = launch_pcsir_front(ctx->b, ctx->m, ctx->cfg.state_dtype, state, noise, N, h, image, W, H, ctx->num_sms, s,
-                         se, ctx->sur_on ? &sp : nullptr);
+                         se, ctx->sur_on ? &sp : nullptr, nullptr, ng);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels");
   if (ctx->sur_on) ctx->sur_steps++;
   ctx->sur_ran = ctx->sur_on;
@@ -263,6 +276,28 @@ pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* ima
   if (e == cudaSuccess && se.ev) e = cudaEventRecord(se.ev[4], s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan/resample kernel");
   return finish_step(ctx, s, result_host, 1, N);
+}
+
+}  // namespace
+
+pcsir_status pcsir_step(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H, double h,
+                        const void* noise, double u0, void* stream, pcsir_result* result_host) {
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  end_deferred(ctx);
+  return step_impl(ctx, state, N, image, W, H, h, noise, nullptr, u0, stream, result_host);
+}
+
+pcsir_status pcsir_step_philox(pcsir_ctx* ctx, void* state, int64_t N, const float* image, int32_t W, int32_t H,
+                               double h, const double* q, uint64_t seed, uint64_t frame, double u0, void* stream,
+                               pcsir_result* result_host) {
+  // the noise argument of the common checks stands for the generator (non-NULL)
+  pcsir_status st = check_step_args(ctx, state, N, image, W, H, state, u0);
+  if (st != PCSIR_OK) return st;
+  NoiseGen ng{};
+  if ((st = make_noise_gen(ctx, q, seed, frame, &ng)) != PCSIR_OK) return st;
+  end_deferred(ctx);
+  return step_impl(ctx, state, N, image, W, H, h, nullptr, &ng, u0, stream, result_host);
 }
 
 pcsir_status pcsir_deferred_begin(pcsir_ctx* ctx, const void* state, int64_t N, void* stream) {
@@ -292,13 +327,12 @@ pcsir_status pcsir_deferred_begin(pcsir_ctx* ctx, const void* state, int64_t N, 
   return PCSIR_OK;
 }
 
-pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
-                                 const void* noise, double u0, void* stream, pcsir_result* result_host) {
-  if (!ctx) return PCSIR_EINVAL;
-  if (!ctx->def_active && !ctx->failed) return fail(ctx, PCSIR_ESTATE, "no deferred run: call pcsir_deferred_begin");
+namespace {
+
+pcsir_status deferred_step_impl(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h, const void* noise,
+                                const NoiseGen* ng, double u0, void* stream, pcsir_result* result_host) {
   const int64_t N = ctx->def_N;
-  pcsir_status st = check_step_args(ctx, ctx->b.prop, N, image, W, H, noise, u0);
-  if (st != PCSIR_OK) return st;
+  pcsir_status st;
   if (!(h > 0.0 && h <= MAX_H)) return fail(ctx, PCSIR_EINVAL, "h must lie in (0, 8]");
   if (ctx->sur_on) return fail(ctx, PCSIR_ENOTSUP, "deferred resampling does not use the likelihood surrogate");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -316,7 +350,7 @@ pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, 
   b.prop = dst;
   b.anc = ctx->def_anc;
   e = launch_pcsir_front(b, ctx->m, ctx->cfg.state_dtype, src, noise, N, h, image, W, H, ctx->num_sms, s, se,
-                         nullptr, ctx->def_has_anc ? ctx->def_anc : nullptr);
+                         nullptr, ctx->def_has_anc ? ctx->def_anc : nullptr, ng);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pcSIR front kernels (deferred)");
   e = launch_resample(b, ctx->cfg.state_dtype, nullptr, N, u0, WSRC_BINS, ctx->cfg.keep | PCSIR_KEEP_ANCESTORS,
                       ctx->num_sms, s);
@@ -329,6 +363,29 @@ pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, 
   st = finish_step(ctx, s, result_host, 1, N);
   ctx->last_deferred = true;
   return st;
+}
+
+}  // namespace
+
+pcsir_status pcsir_deferred_step(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
+                                 const void* noise, double u0, void* stream, pcsir_result* result_host) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (!ctx->def_active && !ctx->failed) return fail(ctx, PCSIR_ESTATE, "no deferred run: call pcsir_deferred_begin");
+  pcsir_status st = check_step_args(ctx, ctx->b.prop, ctx->def_N, image, W, H, noise, u0);
+  if (st != PCSIR_OK) return st;
+  return deferred_step_impl(ctx, image, W, H, h, noise, nullptr, u0, stream, result_host);
+}
+
+pcsir_status pcsir_deferred_step_philox(pcsir_ctx* ctx, const float* image, int32_t W, int32_t H, double h,
+                                        const double* q, uint64_t seed, uint64_t frame, double u0, void* stream,
+                                        pcsir_result* result_host) {
+  if (!ctx) return PCSIR_EINVAL;
+  if (!ctx->def_active && !ctx->failed) return fail(ctx, PCSIR_ESTATE, "no deferred run: call pcsir_deferred_begin");
+  pcsir_status st = check_step_args(ctx, ctx->b.prop, ctx->def_N, image, W, H, ctx->b.prop, u0);
+  if (st != PCSIR_OK) return st;
+  NoiseGen ng{};
+  if ((st = make_noise_gen(ctx, q, seed, frame, &ng)) != PCSIR_OK) return st;
+  return deferred_step_impl(ctx, image, W, H, h, nullptr, &ng, u0, stream, result_host);
 }
 
 pcsir_status pcsir_deferred_state(pcsir_ctx* ctx, void* state, void* stream) {

@@ -129,13 +129,15 @@ struct SurStep {
   SurStats* stats;
 };
 
+struct NoiseGen;  // counter-based process noise (pcsir_philox.cuh); ng != nullptr: noise ignored, FP32 only
+
 // Kernel launchers (pcsir_kernels.cu / pcsir_resample.cu).
 // sur == nullptr: exact likelihood of every dummy.  src_idx != nullptr: the input particle i is
 // state[., src_idx[i]] (a resampling recorded as ancestors only, gathered here).
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
                                int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur = nullptr,
-                               const int32_t* src_idx = nullptr);
+                               const int32_t* src_idx = nullptr, const NoiseGen* ng = nullptr);
 // out[c * N + i] = src[c * N + idx[i]] for the 5 state components (idx == nullptr: a copy)
 cudaError_t launch_gather_state(int dtype, const void* src, const int32_t* idx, void* out, int64_t N,
                                 cudaStream_t s);

@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "pcsir_device.cuh"
+#include "pcsir_philox.cuh"
 
 namespace pcsir {
 
@@ -44,6 +45,21 @@ __device__ __forceinline__ void propagate1(const T* __restrict__ st, const T* __
   v[2] = add_rn(vx, evx);
   v[3] = add_rn(vy, evy);
   v[4] = add_rn(a, ea);
+}
+
+// The same with the increments drawn from the counter-based generator (FP32 state).
+template <typename T>
+__device__ __forceinline__ void propagate1_gen(const T* __restrict__ st, const NoiseGen& ng, int64_t N, int64_t i,
+                                               T v[5], const int32_t* __restrict__ src_idx = nullptr) {
+  const int64_t j = src_idx ? (int64_t)src_idx[i] : i;
+  float e[5];
+  ng_noise5(ng, i, e);
+  const T x = st[j], y = st[N + j], vx = st[2 * N + j], vy = st[3 * N + j], a = st[4 * N + j];
+  v[0] = add_rn(add_rn(x, vx), (T)e[0]);
+  v[1] = add_rn(add_rn(y, vy), (T)e[1]);
+  v[2] = add_rn(vx, (T)e[2]);
+  v[3] = add_rn(vy, (T)e[3]);
+  v[4] = add_rn(a, (T)e[4]);
 }
 
 __device__ __forceinline__ float abs_t(float a) { return fabsf(a); }
@@ -197,10 +213,12 @@ __device__ __forceinline__ int64_t pb_index(int64_t base, int k) {
 
 // GATHER: the input particle set is st[., src_idx[i]] (deferred resampling: the
 // previous step recorded its ancestors and left the gather to this read).
-template <typename T, bool VEC, int LTB, bool GATHER = false>
+// GEN: the process noise is drawn here from the counter-based generator (ng)
+// instead of read from nz (FP32 state only).
+template <typename T, bool VEC, int LTB, bool GATHER = false, bool GEN = false>
 __global__ void __launch_bounds__(PbShape<LTB>::THREADS, LTB == 10 ? 2 : 1)
 k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, int64_t N, T h, long long hq,
-           const int32_t* __restrict__ src_idx = nullptr) {
+           const int32_t* __restrict__ src_idx = nullptr, NoiseGen ng = NoiseGen{}) {
   constexpr int THR = PbShape<LTB>::THREADS;
   constexpr int CHUNK = PbShape<LTB>::CHUNK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,26 +261,34 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
         const int4 a4 = *reinterpret_cast<const int4*>(src_idx + i0);
         const float* sf = reinterpret_cast<const float*>(st);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 5; ++c)
           sv[c] = make_float4(sf[c * N + a4.x], sf[c * N + a4.y], sf[c * N + a4.z], sf[c * N + a4.w]);
-          nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
-        }
       } else {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 5; ++c)
           sv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0);
+      }
+      if (!GEN) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
           nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
-        }
       }
       const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
       const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        v[k][0] = (T)add_rn(add_rn(sp[0][k], sp[2][k]), np[0][k]);
-        v[k][1] = (T)add_rn(add_rn(sp[1][k], sp[3][k]), np[1][k]);
-        v[k][2] = (T)add_rn(sp[2][k], np[2][k]);
-        v[k][3] = (T)add_rn(sp[3][k], np[3][k]);
-        v[k][4] = (T)add_rn(sp[4][k], np[4][k]);
+        float e[5];
+        if (GEN) {
+          ng_noise5(ng, i0 + k, e);  // drawn particle by particle: no array of all four's noise
+        } else {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) e[c] = np[c][k];
+        }
+        v[k][0] = (T)add_rn(add_rn(sp[0][k], sp[2][k]), e[0]);
+        v[k][1] = (T)add_rn(add_rn(sp[1][k], sp[3][k]), e[1]);
+        v[k][2] = (T)add_rn(sp[2][k], e[2]);
+        v[k][3] = (T)add_rn(sp[3][k], e[3]);
+        v[k][4] = (T)add_rn(sp[4][k], e[4]);
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -274,7 +300,10 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       for (int k = 0; k < PB_PER_THREAD; ++k) {
         const int64_t i = pb_index<false, THR>(base, k);
         if (i < N) {
-          propagate1(st, nz, N, i, v[k], GATHER ? src_idx : nullptr);
+          if (GEN)
+            propagate1_gen(st, ng, N, i, v[k], GATHER ? src_idx : nullptr);
+          else
+            propagate1(st, nz, N, i, v[k], GATHER ? src_idx : nullptr);
 #pragma unroll
           for (int c = 0; c < 5; ++c) prop[c * N + i] = v[k][c];
         }
@@ -782,21 +811,27 @@ int weight_scale_bits(int64_t N) {
 
 // One-time kernel attributes and occupancy, queried at context creation so
 // that step calls only enqueue work (and stay legal inside a stream capture).
+template <typename K>
+static cudaError_t prop_bin_attr(K kern, size_t smem, int threads, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int g = 1;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, kern, threads, smem);
+  if (g < *per_sm) *per_sm = g;
+  return e;
+}
+
 template <typename T, bool VEC, int LTB>
 static cudaError_t prop_bin_prepare1(int* per_sm) {
   const size_t smem = sizeof(LocalTable<LTB>);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_prop_bin<T, VEC, LTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_prop_bin<T, VEC, LTB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // the grid is sized from the plain variant; the gathering one must fit the same number of blocks
-  int g = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_prop_bin<T, VEC, LTB>, PbShape<LTB>::THREADS, smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_prop_bin<T, VEC, LTB, true>, PbShape<LTB>::THREADS,
-                                                      smem);
-  if (g < *per_sm) *per_sm = g;
+  constexpr int THR = PbShape<LTB>::THREADS;
+  // the grid is sized for the variant that fits the fewest blocks per SM
+  *per_sm = 1 << 20;
+  cudaError_t e = prop_bin_attr(k_prop_bin<T, VEC, LTB>, smem, THR, per_sm);
+  if (e == cudaSuccess) e = prop_bin_attr(k_prop_bin<T, VEC, LTB, true>, smem, THR, per_sm);
+  if (std::is_same<T, float>::value) {
+    if (e == cudaSuccess) e = prop_bin_attr(k_prop_bin<T, VEC, LTB, false, true>, smem, THR, per_sm);
+    if (e == cudaSuccess) e = prop_bin_attr(k_prop_bin<T, VEC, LTB, true, true>, smem, THR, per_sm);
+  }
   if (*per_sm < 1) *per_sm = 1;
   return e;
 }
@@ -824,7 +859,8 @@ cudaError_t prepare_kernels(int dtype, int* prop_bin_per_sm) {
 
 template <typename T, int LTB>
 static cudaError_t prop_bin_launch_t(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
-                                     int num_sms, int per_sm, cudaStream_t s, long long hq, const int32_t* src_idx) {
+                                     int num_sms, int per_sm, cudaStream_t s, long long hq, const int32_t* src_idx,
+                                     const NoiseGen* ng) {
   const size_t smem = sizeof(LocalTable<LTB>);
   constexpr int THR = PbShape<LTB>::THREADS;
   const int64_t nchunks = (N + PbShape<LTB>::CHUNK - 1) / PbShape<LTB>::CHUNK;
@@ -835,6 +871,23 @@ static cudaError_t prop_bin_launch_t(const StepBuffers& b, const void* state, co
                      reinterpret_cast<uintptr_t>(src_idx)) % 16 == 0);
   const T* st = static_cast<const T*>(state);
   const T* nz = static_cast<const T*>(noise);
+  if (ng != nullptr) {
+    if (!std::is_same<T, float>::value) return cudaErrorInvalidValue;  // FP32 state only
+    const bool vg = std::is_same<T, float>::value && (N % 4 == 0) &&
+                    ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(b.prop) |
+                      reinterpret_cast<uintptr_t>(b.pslot) | reinterpret_cast<uintptr_t>(src_idx)) % 16 == 0);
+    if (src_idx != nullptr) {
+      if (vg)
+        k_prop_bin<T, true, LTB, true, true><<<grid, THR, smem, s>>>(b, st, nullptr, N, (T)h, hq, src_idx, *ng);
+      else
+        k_prop_bin<T, false, LTB, true, true><<<grid, THR, smem, s>>>(b, st, nullptr, N, (T)h, hq, src_idx, *ng);
+    } else if (vg) {
+      k_prop_bin<T, true, LTB, false, true><<<grid, THR, smem, s>>>(b, st, nullptr, N, (T)h, hq, nullptr, *ng);
+    } else {
+      k_prop_bin<T, false, LTB, false, true><<<grid, THR, smem, s>>>(b, st, nullptr, N, (T)h, hq, nullptr, *ng);
+    }
+    return cudaGetLastError();
+  }
   if (src_idx != nullptr) {
     if (vec)
       k_prop_bin<T, true, LTB, true><<<grid, THR, smem, s>>>(b, st, nz, N, (T)h, hq, src_idx);
@@ -850,10 +903,11 @@ static cudaError_t prop_bin_launch_t(const StepBuffers& b, const void* state, co
 
 template <typename T>
 static cudaError_t prop_bin_launch(const StepBuffers& b, const void* state, const void* noise, int64_t N, double h,
-                                   int num_sms, cudaStream_t s, long long hq, const int32_t* src_idx) {
+                                   int num_sms, cudaStream_t s, long long hq, const int32_t* src_idx,
+                                   const NoiseGen* ng = nullptr) {
   if (b.big_table)
-    return prop_bin_launch_t<T, 12>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[1], s, hq, src_idx);
-  return prop_bin_launch_t<T, 10>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[0], s, hq, src_idx);
+    return prop_bin_launch_t<T, 12>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[1], s, hq, src_idx, ng);
+  return prop_bin_launch_t<T, 10>(b, state, noise, N, h, num_sms, b.prop_bin_per_sm[0], s, hq, src_idx, ng);
 }
 
 static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
@@ -863,10 +917,10 @@ static cudaError_t mark(StageEvents se, int j, cudaStream_t s) {
 cudaError_t launch_pcsir_front(const StepBuffers& b, const ModelParams& m, int dtype, const void* state,
                                const void* noise, int64_t N, double h, const float* img, int W, int H,
                                int num_sms, cudaStream_t s, StageEvents se, const SurStep* sur,
-                               const int32_t* src_idx) {
+                               const int32_t* src_idx, const NoiseGen* ng) {
   const long long hq = llrint(h * 2147483648.0);
-  cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq, src_idx)
-                                     : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq, src_idx);
+  cudaError_t e = dtype == PCSIR_F32 ? prop_bin_launch<float>(b, state, noise, N, h, num_sms, s, hq, src_idx, ng)
+                                     : prop_bin_launch<double>(b, state, noise, N, h, num_sms, s, hq, src_idx, ng);
   if (e != cudaSuccess || (e = mark(se, 1, s)) != cudaSuccess) return e;
   const LikParams lp = make_lik(m);
   if (sur == nullptr) {

@@ -119,6 +119,7 @@ def _load():
         raise ImportError("libpcsir.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
     P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    U64 = ctypes.c_uint64
     sig = {
         "pcsir_create": ([ctypes.POINTER(pcsir_config), ctypes.POINTER(ctypes.c_void_p)], I32),
         "pcsir_destroy": ([P], I32),
@@ -126,6 +127,8 @@ def _load():
         "pcsir_deferred_begin": ([P, P, I64, P], I32),
         "pcsir_deferred_step": ([P, P, I32, I32, D, P, D, P, P], I32),
         "pcsir_deferred_state": ([P, P, P], I32),
+        "pcsir_step_philox": ([P, P, I64, P, I32, I32, D, P, U64, U64, D, P, P], I32),
+        "pcsir_deferred_step_philox": ([P, P, I32, I32, D, P, U64, U64, D, P, P], I32),
         "sir_step": ([P, P, I64, P, I32, I32, P, D, P, P], I32),
         "pcsir_step_ess": ([P, P, P, I64, P, I32, I32, D, P, D, D, P, P], I32),
         "sir_step_ess": ([P, P, P, I64, P, I32, I32, P, D, D, P, P], I32),
@@ -358,6 +361,35 @@ def pcsir_deferred_step(ctx, image, h, noise, u0, stream=None):
     H, W = image.shape
     st = lib.pcsir_deferred_step(ctx.handle, _ptr(image), W, H, float(h), _ptr(noise), float(u0),
                                  _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def _q5(q):
+    q = [float(x) for x in q]
+    if len(q) != 5:
+        raise ValueError("q holds the five standard deviations of the increments")
+    return (ctypes.c_double * 5)(*q)  # ctypes passes the array as a pointer to its first element
+
+
+def pcsir_step_philox(ctx, state, image, h, q, seed, frame, u0, stream=None):
+    """One pcSIR step (Algorithm 2) on ``state`` [5, N] in place, the process noise drawn in the kernel."""
+    _check_cuda(state, "state", ctx.torch_dtype)
+    _check_cuda(image, "image", torch.float32)
+    N = state.shape[1]
+    H, W = image.shape
+    st = lib.pcsir_step_philox(ctx.handle, _ptr(state), N, _ptr(image), W, H, float(h), _q5(q), int(seed),
+                               int(frame), float(u0), _stream_ptr(stream), None)
+    if st != OK:
+        ctx._raise(st)
+
+
+def pcsir_deferred_step_philox(ctx, image, h, q, seed, frame, u0, stream=None):
+    """One step of the context's deferred run with the process noise drawn in the kernel."""
+    _check_cuda(image, "image", torch.float32)
+    H, W = image.shape
+    st = lib.pcsir_deferred_step_philox(ctx.handle, _ptr(image), W, H, float(h), _q5(q), int(seed), int(frame),
+                                        float(u0), _stream_ptr(stream), None)
     if st != OK:
         ctx._raise(st)
 
