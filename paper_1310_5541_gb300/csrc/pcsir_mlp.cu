@@ -16,6 +16,73 @@ namespace pcsir {
 constexpr int MM_M = 128;        // rows per CTA tile (TMEM lanes)
 constexpr int MM_THREADS = 128;  // four warps: one TMEM lane quarter each
 
+// Epilogue of a finished tile: thread tid owns TMEM lane (row) tid.
+template <int NT>
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int m0, int n0) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = m0 + tid;
+  const bool mrow = m < g.M;
+  for (int c = 0; c < NT; c += 8) {
+    float v[8];
+    tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+    if (g.epi == EPI_DACT) {
+      float cs[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = n0 + c + i;
+        float d = 0.0f;
+        if (mrow && n < g.N) d = v[i] * silu_grad_f(g.pre[(long long)m * g.ld_pre + n]);
+        v[i] = d;
+        cs[i] = d;
+      }
+      if (mrow) {
+        if (n0 + c + 8 <= g.N && (g.ld_act % 8) == 0) {
+          *reinterpret_cast<uint4*>(g.act + (long long)m * g.ld_act + n0 + c) = pack_bf16x8(v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (n0 + c + i < g.N) g.act[(long long)m * g.ld_act + n0 + c + i] = __float2bfloat16_rn(v[i]);
+        }
+      }
+      if (g.colsum) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float s = cs[i];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0 && n0 + c + i < g.N) atomicAdd(g.colsum + n0 + c + i, s);
+        }
+      }
+      continue;
+    }
+    if (!mrow) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = n0 + c + i;
+      if (n >= g.N) continue;
+      float* cp = g.C ? g.C + (long long)m * g.ldc + n : nullptr;
+      if (g.epi == EPI_STORE) {
+        *cp = g.accumulate ? *cp + v[i] : v[i];
+      } else if (g.epi == EPI_ATOMIC) {
+        atomicAdd(cp, v[i]);
+      } else {  // EPI_ACT
+        const float pre = v[i] + g.bias[n];
+        if (cp) *cp = pre;
+        v[i] = silu_f(pre);
+      }
+    }
+    if (g.epi == EPI_ACT && g.act) {
+      if (n0 + c + 8 <= g.N && (g.ld_act % 8) == 0) {
+        *reinterpret_cast<uint4*>(g.act + (long long)m * g.ld_act + n0 + c) = pack_bf16x8(v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (n0 + c + i < g.N) g.act[(long long)m * g.ld_act + n0 + c + i] = __float2bfloat16_rn(v[i]);
+      }
+    }
+  }
+}
+
 // One CTA: rows [m0, m0 + 128) x columns [n0, n0 + NT), K chunks of its slice.
 template <int NT>
 __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
@@ -25,7 +92,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   uint8_t* sB = mm_smem + MM_M * MM_K * 2;  // NT x 64 bf16
   uint64_t* bar = reinterpret_cast<uint64_t*>(mm_smem + MM_M * MM_K * 2 + NT * MM_K * 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int m0 = blockIdx.x * MM_M;
   const int n0 = blockIdx.y * NT;
   const int nk_total = (g.K + MM_K - 1) / MM_K;
@@ -67,72 +134,136 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   if (!ok) {
     if (tid == 0) atomicOr(g.err, (unsigned)PCSIR_DERR_TIMEOUT);
   } else {
-    // epilogue: thread tid owns TMEM lane (row) tid
-    const int m = m0 + tid;
-    const bool mrow = m < g.M;
-    for (int c = 0; c < NT; c += 8) {
-      float v[8];
-      tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      if (g.epi == EPI_DACT) {
-        float cs[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int n = n0 + c + i;
-          float d = 0.0f;
-          if (mrow && n < g.N) d = v[i] * silu_grad_f(g.pre[(long long)m * g.ld_pre + n]);
-          v[i] = d;
-          cs[i] = d;
-        }
-        if (mrow) {
-          if (n0 + c + 8 <= g.N && (g.ld_act % 8) == 0) {
-            *reinterpret_cast<uint4*>(g.act + (long long)m * g.ld_act + n0 + c) = pack_bf16x8(v);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (n0 + c + i < g.N) g.act[(long long)m * g.ld_act + n0 + c + i] = __float2bfloat16_rn(v[i]);
-          }
-        }
-        if (g.colsum) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float s = cs[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0 && n0 + c + i < g.N) atomicAdd(g.colsum + n0 + c + i, s);
-          }
-        }
-        continue;
-      }
-      if (!mrow) continue;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int n = n0 + c + i;
-        if (n >= g.N) continue;
-        float* cp = g.C ? g.C + (long long)m * g.ldc + n : nullptr;
-        if (g.epi == EPI_STORE) {
-          *cp = g.accumulate ? *cp + v[i] : v[i];
-        } else if (g.epi == EPI_ATOMIC) {
-          atomicAdd(cp, v[i]);
-        } else {  // EPI_ACT
-          const float pre = v[i] + g.bias[n];
-          if (cp) *cp = pre;
-          v[i] = silu_f(pre);
-        }
-      }
-      if (g.epi == EPI_ACT && g.act) {
-        if (n0 + c + 8 <= g.N && (g.ld_act % 8) == 0) {
-          *reinterpret_cast<uint4*>(g.act + (long long)m * g.ld_act + n0 + c) = pack_bf16x8(v);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (n0 + c + i < g.N) g.act[(long long)m * g.ld_act + n0 + c + i] = __float2bfloat16_rn(v[i]);
-        }
-      }
-    }
+    gemm_epilogue<NT>(g, tmem, m0, n0);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tc_dealloc(tmem, NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-stage variant for operands whose K elements are contiguous (sak = sbk = 1, rows on 16-byte
+// boundaries): each thread's 16-byte pieces of a K chunk go straight from global to their swizzled
+// place in shared memory by cp.async (zero-filled past K and past the last row), S chunks in flight,
+// so the tensor core does not wait for one chunk's loads after another.  Chunk kc + S - 1 is issued
+// into the buffer chunk kc - 1 used once that chunk's MMAs have completed (its mbarrier).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// copies of a NROWS x 64 chunk (rows r0.., K from k0) of a K-contiguous operand into dst
+template <int NROWS>
+__device__ __forceinline__ void mm_async_chunk(uint32_t dst, const __nv_bfloat16* src, long long srow, int r0,
+                                               int rows_valid, int k0, int K) {
+  constexpr int PER = NROWS * (MM_K / 8) / MM_THREADS;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int gi = threadIdx.x + j * MM_THREADS;
+    const int r = gi / (MM_K / 8), kg = (gi % (MM_K / 8)) * 8;
+    const int row = r0 + r, k = k0 + kg;
+    const int left = K - k;
+    const uint32_t bytes = (row < rows_valid && left > 0) ? (uint32_t)(left >= 8 ? 16 : 2 * left) : 0u;
+    // no byte is read when bytes == 0; the address stays a valid one all the same
+    const __nv_bfloat16* p = bytes ? src + (long long)row * srow + k : src;
+    cp_async16(dst + mm_off(r, kg), p, bytes);
+  }
+}
+
+template <int NT, int S>
+__global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16_async(GemmArgs g) {
+  static_assert(S >= 2 && S <= 4, "2 to 4 stages");
+  extern __shared__ __align__(1024) uint8_t mm_smem_raw[];
+  uint8_t* mm_smem = align1024(mm_smem_raw);
+  constexpr int SA = MM_M * MM_K * 2, ST = SA + NT * MM_K * 2;  // one stage: A 16 KB, then B
+  uint64_t* bar = reinterpret_cast<uint64_t*>(mm_smem + S * ST);  // one per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + S);
+  const uint32_t s0 = smem_u32(mm_smem);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * MM_M;
+  const int n0 = blockIdx.y * NT;
+  const int nk_total = (g.K + MM_K - 1) / MM_K;
+  int kc0 = 0, kc1 = nk_total;
+  if (g.kchunks_per_split > 0) {
+    kc0 = blockIdx.z * g.kchunks_per_split;
+    kc1 = min(nk_total, kc0 + g.kchunks_per_split);
+  }
+  if (kc0 >= kc1) return;  // empty K slice (uniform over the block)
+  constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;
+  if (warp == 0) tc_alloc(tslot, NCOLS);
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) mbar_init(&bar[j], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = mm_idesc(MM_M, NT);
+  auto issue = [&](int kc, int st) {
+    mm_async_chunk<MM_M>(s0 + st * ST, g.A, g.sam, m0, g.M, kc * MM_K, g.K);
+    mm_async_chunk<NT>(s0 + st * ST + SA, g.B, g.sbn, n0, g.N, kc * MM_K, g.K);
+  };
+#pragma unroll
+  for (int j = 0; j < S - 1; ++j) {
+    if (kc0 + j < kc1) issue(kc0 + j, j);
+    cp_async_commit();
+  }
+  uint32_t phase[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) phase[j] = 0u;
+  bool ok = true;
+  for (int kc = kc0; kc < kc1 && ok; ++kc) {
+    const int st = (kc - kc0) % S;
+    cp_async_wait<S - 2>();  // this thread's pieces of chunk kc have landed
+    proxy_fence();           // visible to the tensor core's reads
+    __syncthreads();         // and everyone else's
+    if (tid == 0) {
+      tc_fence_after();
+      tc_mma_chunk(tmem, s0 + st * ST, s0 + st * ST + SA, idesc, kc == kc0);
+      tc_commit(&bar[st]);
+    }
+    const int kn = kc + S - 1;
+    if (kn < kc1) {
+      const int sn = (kn - kc0) % S;  // the stage chunk kc - 1 used
+      if (kc > kc0) {
+        // thread 0 polls the mbarrier (polling by every warp would compete with the tensor core
+        // for shared memory); the block barrier releases the others
+        ok = __syncthreads_and(tid != 0 || mbar_wait(&bar[sn], phase[sn])) != 0;
+        phase[sn] ^= 1u;
+      }
+      if (ok) issue(kn, sn);
+    }
+    cp_async_commit();  // possibly empty: keeps the group count of the wait above uniform
+  }
+  // the commits not waited for yet: chunks max(kc0, kc1 - S) .. kc1 - 1, each on its own stage
+  for (int c = max(kc0, kc1 - S); c < kc1 && ok; ++c) {
+    const int st = (c - kc0) % S;
+    ok = __syncthreads_and(tid != 0 || mbar_wait(&bar[st], phase[st])) != 0;
+    phase[st] ^= 1u;
+  }
+  cp_async_wait<0>();
+  tc_fence_after();
+  if (!ok) {
+    if (tid == 0) atomicOr(g.err, (unsigned)PCSIR_DERR_TIMEOUT);
+  } else {
+    gemm_epilogue<NT>(g, tmem, m0, n0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, NCOLS);
+}
+
+constexpr int GEMM_ASYNC_STAGES = 4;
+template <int NT>
+constexpr int gemm_async_smem() {
+  return GEMM_ASYNC_STAGES * (MM_M * MM_K * 2 + NT * MM_K * 2) + 1024 + 64;
 }
 
 // 100 KB of dynamic shared memory (more than the 49 KB the 256-column tile
@@ -147,6 +278,12 @@ cudaError_t prepare_gemm() {
     status = cudaFuncSetAttribute(k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
     if (status == cudaSuccess)
       status = cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (status == cudaSuccess)
+      status = cudaFuncSetAttribute(k_gemm_bf16_async<256, GEMM_ASYNC_STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_async_smem<256>());
+    if (status == cudaSuccess)
+      status = cudaFuncSetAttribute(k_gemm_bf16_async<64, GEMM_ASYNC_STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_async_smem<64>());
   });
   return status;
 }
@@ -162,10 +299,19 @@ cudaError_t launch_gemm(GemmArgs g, cudaStream_t s, int nt, int splits) {
     splits = (nk + g.kchunks_per_split - 1) / g.kchunks_per_split;
   }
   dim3 grid((g.M + MM_M - 1) / MM_M, (g.N + nt - 1) / nt, splits);
-  if (nt == 256)
+  // K-contiguous operands on 16-byte boundaries take the multi-stage path
+  const bool async_ok = g.sak == 1 && g.sbk == 1 && (g.sam % 8) == 0 && (g.sbn % 8) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15u) == 0u;
+  if (async_ok) {
+    if (nt == 256)
+      k_gemm_bf16_async<256, GEMM_ASYNC_STAGES><<<grid, MM_THREADS, gemm_async_smem<256>(), s>>>(g);
+    else
+      k_gemm_bf16_async<64, GEMM_ASYNC_STAGES><<<grid, MM_THREADS, gemm_async_smem<64>(), s>>>(g);
+  } else if (nt == 256) {
     k_gemm_bf16<256><<<grid, MM_THREADS, GEMM_SMEM, s>>>(g);
-  else
+  } else {
     k_gemm_bf16<64><<<grid, MM_THREADS, GEMM_SMEM, s>>>(g);
+  }
   return cudaGetLastError();
 }
 

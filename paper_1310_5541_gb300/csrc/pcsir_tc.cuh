@@ -161,30 +161,55 @@ __device__ __forceinline__ uint4 mm_load8(const __nv_bfloat16* src, long long sr
   return v;
 }
 
+// A thread's share of one staged chunk: its 8-element groups, loaded into registers (mm_fetch) and
+// written to the swizzled layout later (mm_put), so that the loads of the next chunk can be in
+// flight while the tensor core works on the current one.
+template <int NTHREADS, int NROWS>
+struct MmFrag {
+  static constexpr int PER = NROWS * (MM_K / 8) / NTHREADS;  // 8-element groups per thread
+  static_assert(PER * NTHREADS == NROWS * (MM_K / 8), "tile not divisible among threads");
+  uint4 v[PER];
+};
+
+__device__ __forceinline__ void mm_group(int g, int nrows, bool mn_major, int* r, int* kg) {
+  if (mn_major) {
+    *r = g % nrows;
+    *kg = (g / nrows) * 8;
+  } else {
+    *r = g / (MM_K / 8);
+    *kg = (g % (MM_K / 8)) * 8;
+  }
+}
+
+template <int NTHREADS, int NROWS>
+__device__ __forceinline__ void mm_fetch(MmFrag<NTHREADS, NROWS>& f, const __nv_bfloat16* src, long long srow,
+                                         long long sk, int r0, int rows_valid, int k0, int K) {
+  const bool mn_major = (srow == 1 && sk != 1);
+#pragma unroll
+  for (int j = 0; j < MmFrag<NTHREADS, NROWS>::PER; ++j) {
+    int r, kg;
+    mm_group(threadIdx.x + j * NTHREADS, NROWS, mn_major, &r, &kg);
+    f.v[j] = mm_load8(src, srow, sk, r0 + r, rows_valid, k0 + kg, K);
+  }
+}
+
+template <int NTHREADS, int NROWS>
+__device__ __forceinline__ void mm_put(uint8_t* dst, const MmFrag<NTHREADS, NROWS>& f, long long srow, long long sk) {
+  const bool mn_major = (srow == 1 && sk != 1);
+#pragma unroll
+  for (int j = 0; j < MmFrag<NTHREADS, NROWS>::PER; ++j) {
+    int r, kg;
+    mm_group(threadIdx.x + j * NTHREADS, NROWS, mn_major, &r, &kg);
+    *reinterpret_cast<uint4*>(dst + mm_off(r, kg)) = f.v[j];
+  }
+}
+
 template <int NTHREADS, int NROWS>
 __device__ __forceinline__ void mm_stage(uint8_t* dst, const __nv_bfloat16* src, long long srow, long long sk,
                                          int r0, int rows_valid, int k0, int K) {
-  constexpr int PER = NROWS * (MM_K / 8) / NTHREADS;  // 8-element groups per thread
-  static_assert(PER * NTHREADS == NROWS * (MM_K / 8), "tile not divisible among threads");
-  const bool mn_major = (srow == 1 && sk != 1);
-  uint4 v[PER];
-  int off[PER];
-#pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    const int g = threadIdx.x + j * NTHREADS;
-    int r, kg;
-    if (mn_major) {
-      r = g % NROWS;
-      kg = (g / NROWS) * 8;
-    } else {
-      r = g / (MM_K / 8);
-      kg = (g % (MM_K / 8)) * 8;
-    }
-    off[j] = (int)mm_off(r, kg);
-    v[j] = mm_load8(src, srow, sk, r0 + r, rows_valid, k0 + kg, K);
-  }
-#pragma unroll
-  for (int j = 0; j < PER; ++j) *reinterpret_cast<uint4*>(dst + off[j]) = v[j];
+  MmFrag<NTHREADS, NROWS> f;
+  mm_fetch(f, src, srow, sk, r0, rows_valid, k0, K);
+  mm_put(dst, f, srow, sk);
 }
 
 // ---------------------------------------------------------------------------
