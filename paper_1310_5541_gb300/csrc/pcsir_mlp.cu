@@ -6,6 +6,8 @@
 // backward product through the SiLU derivative, and split-K weight
 // gradients).
 #include <algorithm>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <mutex>
 
 #include "pcsir_device.cuh"
@@ -260,16 +262,141 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16_async(GemmArgs g) {
   if (warp == 0) tc_dealloc(tmem, NCOLS);
 }
 
+// ---------------------------------------------------------------------------
+// TMA variant (same operand condition): the copy engine brings each K chunk of A and B into a stage
+// as two tensor tiles (cp.async.bulk.tensor with 128-byte swizzle, which is exactly the K-major
+// layout the MMAs read), completing on the stage's "full" mbarrier with its byte count; one thread
+// issues the copies, another the MMAs, which release the stage through its "empty" mbarrier.  No
+// block-wide barrier inside the K loop.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int NT, int S>
+__global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16_tma(GemmArgs g, const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ __align__(1024) uint8_t mm_smem_raw[];
+  uint8_t* mm_smem = align1024(mm_smem_raw);
+  constexpr int SA = MM_M * MM_K * 2, SB = NT * MM_K * 2, ST = SA + SB;
+  uint64_t* full = reinterpret_cast<uint64_t*>(mm_smem + S * ST);
+  uint64_t* empty = full + S;
+  uint64_t* done = empty + S;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_abort, s_issued, s_used;
+  const uint32_t s0 = smem_u32(mm_smem);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * MM_M;
+  const int n0 = blockIdx.y * NT;
+  const int nk_total = (g.K + MM_K - 1) / MM_K;
+  int kc0 = 0, kc1 = nk_total;
+  if (g.kchunks_per_split > 0) {
+    kc0 = blockIdx.z * g.kchunks_per_split;
+    kc1 = min(nk_total, kc0 + g.kchunks_per_split);
+  }
+  if (kc0 >= kc1) return;  // empty K slice (uniform over the block)
+  constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;
+  if (warp == 0) tc_alloc(tslot, NCOLS);
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], 1);
+    }
+    mbar_init(done, 1);
+    s_abort = 0;
+    s_issued = 0;
+    s_used = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int nk = kc1 - kc0;
+  if (tid == 0) {
+    // copies: stage i % S for chunk kc0 + i, after the MMAs of chunk kc0 + i - S released it
+    for (int i = 0; i < nk; ++i) {
+      const int st = i % S, use = i / S;
+      if (use > 0 && !mbar_wait(&empty[st], (uint32_t)((use - 1) & 1))) {
+        atomicExch(&s_abort, 1);
+        break;
+      }
+      if (*(volatile int*)&s_abort) break;
+      mbar_expect_tx(&full[st], (uint32_t)ST);
+      tma_load_2d(s0 + st * ST, &tmA, (kc0 + i) * MM_K, m0, &full[st]);
+      tma_load_2d(s0 + st * ST + SA, &tmB, (kc0 + i) * MM_K, n0, &full[st]);
+      s_issued = i + 1;
+    }
+  } else if (tid == 32) {
+    // MMAs of chunk kc0 + i once its two tiles have landed; each stage is released by a commit
+    const uint32_t idesc = mm_idesc(MM_M, NT);
+    for (int i = 0; i < nk; ++i) {
+      const int st = i % S, use = i / S;
+      if (!mbar_wait(&full[st], (uint32_t)(use & 1))) {
+        atomicExch(&s_abort, 1);
+        break;
+      }
+      s_used = i + 1;
+      tc_fence_after();
+      tc_mma_chunk(tmem, s0 + st * ST, s0 + st * ST + SA, idesc, i == 0);
+      tc_commit(&empty[st]);
+    }
+    tc_commit(done);  // arrives when every MMA issued above has completed
+  }
+  __syncthreads();
+  // the MMA thread always commits to done, so this wait also covers a stopped loop's MMAs
+  const bool drained = __syncthreads_and(tid != 0 || mbar_wait(done, 0u)) != 0;
+  const bool ok = s_abort == 0 && drained;
+  if (!ok && tid == 0) {
+    // copies issued but never waited for: let them land (bounded) before the block leaves
+    for (int i = s_used; i < s_issued; ++i) mbar_wait(&full[i % S], (uint32_t)((i / S) & 1));
+  }
+  tc_fence_after();
+  if (!ok) {
+    if (tid == 0) atomicOr(g.err, (unsigned)PCSIR_DERR_TIMEOUT);
+  } else {
+    gemm_epilogue<NT>(g, tmem, m0, n0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, NCOLS);
+}
+
 constexpr int GEMM_ASYNC_STAGES = 4;
 template <int NT>
 constexpr int gemm_async_smem() {
-  return GEMM_ASYNC_STAGES * (MM_M * MM_K * 2 + NT * MM_K * 2) + 1024 + 64;
+  // the stages, the 1024-byte alignment slack, and the barriers and TMEM slot (at most 2 S + 2 words)
+  return GEMM_ASYNC_STAGES * (MM_M * MM_K * 2 + NT * MM_K * 2) + 1024 + 128;
 }
 
 // 100 KB of dynamic shared memory (more than the 49 KB the 256-column tile
 // uses) caps residency at two CTAs per SM, so two tiles of 256 TMEM columns
 // always fit.
 constexpr int GEMM_SMEM = 100 * 1024;
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// a K-contiguous bf16 operand [rows][K] (row stride ld elements) as 64 x box_rows tiles
+bool make_operand_map(CUtensorMap* m, const __nv_bfloat16* base, int K, int rows, long long ld, int box_rows) {
+  if (!g_encode) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2u};
+  const cuuint32_t box[2] = {(cuuint32_t)MM_K, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
 
 cudaError_t prepare_gemm() {
   static std::once_flag once;
@@ -284,6 +411,20 @@ cudaError_t prepare_gemm() {
     if (status == cudaSuccess)
       status = cudaFuncSetAttribute(k_gemm_bf16_async<64, GEMM_ASYNC_STAGES>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_async_smem<64>());
+    if (status == cudaSuccess)
+      status = cudaFuncSetAttribute(k_gemm_bf16_tma<256, GEMM_ASYNC_STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_async_smem<256>());
+    if (status == cudaSuccess)
+      status = cudaFuncSetAttribute(k_gemm_bf16_tma<64, GEMM_ASYNC_STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_async_smem<64>());
+    // the tensor-map encoder, from the driver (none: the cp.async path is used)
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
   });
   return status;
 }
@@ -302,7 +443,13 @@ cudaError_t launch_gemm(GemmArgs g, cudaStream_t s, int nt, int splits) {
   // K-contiguous operands on 16-byte boundaries take the multi-stage path
   const bool async_ok = g.sak == 1 && g.sbk == 1 && (g.sam % 8) == 0 && (g.sbn % 8) == 0 &&
                         ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15u) == 0u;
-  if (async_ok) {
+  CUtensorMap ma, mb;
+  if (async_ok && make_operand_map(&ma, g.A, g.K, g.M, g.sam, MM_M) && make_operand_map(&mb, g.B, g.K, g.N, g.sbn, nt)) {
+    if (nt == 256)
+      k_gemm_bf16_tma<256, GEMM_ASYNC_STAGES><<<grid, MM_THREADS, gemm_async_smem<256>(), s>>>(g, ma, mb);
+    else
+      k_gemm_bf16_tma<64, GEMM_ASYNC_STAGES><<<grid, MM_THREADS, gemm_async_smem<64>(), s>>>(g, ma, mb);
+  } else if (async_ok) {
     if (nt == 256)
       k_gemm_bf16_async<256, GEMM_ASYNC_STAGES><<<grid, MM_THREADS, gemm_async_smem<256>(), s>>>(g);
     else
