@@ -741,6 +741,43 @@ def run_batched3(n_targets, n_per, steps, warmup, seed, world=1):
             "step_bytes_per_particle": bpp, "step_gbs": gbs, "step_frac_of_hbm": gbs / hbm, "peak_source": kind}
 
 
+def run_gemm(shapes, reps=10):
+    """The surrogate training's tcgen05 GEMM (pcsir_gemm_bf16: TMA tiles, FP32 accumulation in
+    tensor memory) on K-contiguous bf16 operands: CUDA-event time per product and TFLOP/s against the
+    measured bf16 peak."""
+    import torch
+
+    from paper_1310_5541_gb300 import pcsir
+
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = json.load(fh).get("bf16_tflops")
+    except (OSError, ValueError):
+        pass
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    rows = []
+    for (M, N, K) in shapes:
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        for _ in range(3):
+            pcsir.gemm_bf16(A, B, C)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            pcsir.gemm_bf16(A, B, C)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        rows.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf,
+                     "frac_of_measured_bf16": (tf / peak) if peak else None})
+    return {"kernel": "k_gemm_bf16_tma", "peak_tflops": peak, "rows": rows}
+
+
 def run_drawn(ctx, pcsir, state0, images, img_host, u0s, N, h, K, Wm, stream, seq, pg, dev, hbm, peak_kind,
               deferred):
     """The headline's steps with the process noise drawn in the kernel (pcsir_step_philox, or a
@@ -895,6 +932,7 @@ def main():
     ap.add_argument("--surrogate3-sequences", type=int, default=1200,
                     help="four-frame training sequences of the 3D surrogate")
     ap.add_argument("--surrogate3-steps", type=int, default=10_000, help="Adam steps of the 3D surrogate (0: none)")
+    ap.add_argument("--gemm", type=int, default=1, help="time the training GEMM at two shapes (0 skips it)")
     ap.add_argument("--ess-frames", type=int, default=20, help="frames of the ESS-threshold comparison (0 skips it)")
     ap.add_argument("--ess-frac", type=float, default=0.5, help="N_thr / N of the ESS-threshold comparison")
     args = ap.parse_args()
@@ -1100,6 +1138,8 @@ def main():
                                         sir_clocks),
                "clocks": sir_clocks}
 
+    gemm = run_gemm(((8192, 8192, 8192), (4096, 256, 448))) if args.gemm else None
+
     batched = None
     if args.batched_steps > 0:
         batched = run_batched(args.batched_targets, args.batched_steps, 3, SEED + 77 + 1000 * rank, world)
@@ -1163,7 +1203,7 @@ def main():
                           "scan_resample": st_mean[3], "share": [float(s) for s in share],
                           "dominant": ["prop_bin", "dummies_lik", "weights", "scan_resample"][dom],
                           "scan_resample_gbs": resample_gbs},
-            "deferred": deferred, "drawn_noise": drawn,
+            "deferred": deferred, "drawn_noise": drawn, "training_gemm": gemm,
             "e2e": e2e, "sir": sir, "batched": batched, "matched_rmse": matched, "pseudo_tracking": pseudo,
             "large_object": large, "tracking_3d": track3d, "ess_threshold": ess_cmp,
             "cpu_baseline": cpu,
