@@ -223,6 +223,19 @@ __device__ void tile_scan_tail(const StepBuffers& b, Control* ctl, int64_t N, do
     if (T == 0ull) atomicOr(&ctl->err, (unsigned)PCSIR_DERR_ZEROSUM);
   }
   __syncthreads();
+  // A tile with tile_sum N < (RS_CHUNK - 2) T owns fewer than RS_CHUNK outputs (U_i advances by
+  // T / N per output).  When every tile is such, the output ranges are left to the resampling
+  // blocks themselves (tile_ovx[nt] = -1: no further chunks); otherwise they are fixed here.
+  bool big = false;
+  for (int k = 0; k < per && t0 + k < nt; ++k) {
+    const unsigned long long v = (unsigned long long)*(volatile long long*)&b.tile_sum[t0 + k];
+    big |= (unsigned __int128)v * (unsigned long long)N >=
+           (unsigned __int128)(unsigned long long)(RS_CHUNK - 2) * (unsigned long long)total;
+  }
+  if (!__syncthreads_or(big)) {
+    if (tid == 0) b.tile_ovx[nt] = -1;
+    return;
+  }
   // first output of each tile (the last entry: N)
   const Map64 mp = s_mp;
   const float inv = s_inv;
@@ -386,7 +399,16 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       t = idle ? 0 : lo;
       chunk = idle ? 0 : (long long)(e - b.tile_ovx[lo]) + 1;
     }
-    const long long t_lo = b.tile_lo[t], t_hi = b.tile_lo[t + 1];
+    long long t_lo, t_hi;
+    if (b.tile_ovx[ntiles] < 0) {
+      // every tile owns fewer than RS_CHUNK outputs: its range from the first-output search
+      const Map64 m = load_map(ctl);
+      t_lo = first_out_f(m, b.tile_excl[t], N, ctl->inv_delta);
+      t_hi = t == ntiles - 1 ? N : first_out_f(m, b.tile_excl[t + 1], N, ctl->inv_delta);
+    } else {
+      t_lo = b.tile_lo[t];
+      t_hi = b.tile_lo[t + 1];
+    }
     const long long lo = t_lo + chunk * RS_CHUNK;
     s_tile = idle ? -1 : t;
     s_lo = lo;
