@@ -52,7 +52,7 @@ struct BatchCtl {  // zeroed every step
   unsigned int bar_count;
   unsigned int bar_gen;
   unsigned int abort;
-  unsigned int chunk_next;  // propagation phase: the next pair of chunks to hand out
+  unsigned int chunk_next;  // propagation phase: the next chunk to hand out
   unsigned long long phase_ns[8];  // global-timer reading of block 0 at the start and after each phase
 };
 
@@ -106,6 +106,7 @@ struct BatchBufs {
 constexpr int BT_THREADS = 512;
 constexpr int BT_PER_THREAD = 4;
 constexpr int BT_CHUNK = BT_THREADS * BT_PER_THREAD;
+constexpr long long BT_GRAB_MAX = 16;  // longest run of chunks a block takes at once (propagation phase)
 // the block-private cell table has 2^LTB slots (a kernel variant per LTB, chosen at run time by
 // the autotuner) and takes new cells until three quarters of them are used
 constexpr int BT_LTB_DEFAULT = 10;
@@ -226,6 +227,25 @@ __device__ unsigned bglobal_insert(const BatchBufs& b, unsigned long long key) {
   return 0;
 }
 
+// global slot of a cell the block's table has just taken: a chain of compare-and-swaps from slot h
+// (the key's home slot, or the one after a first probe that met another key; a slot that holds the
+// key or was empty and is now claimed ends it); created tells whether this call claimed the slot
+__device__ unsigned bglobal_claim(const BatchBufs& b, unsigned long long key, bool& created, unsigned h) {
+  const unsigned mask = (1u << b.hbits) - 1u;
+  created = false;
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const unsigned long long old = atomicCAS(&b.hkey[h], EMPTY_KEY, key);
+    if (old == EMPTY_KEY) {
+      created = true;
+      return h;
+    }
+    if (old == key) return h;
+    h = (h + 1u) & mask;
+  }
+  atomicOr(&b.ctl->err, (unsigned)PCSIR_DERR_RANGE);
+  return 0;
+}
+
 template <int LTB>
 __device__ int blocal_insert(BatchLocal<LTB>& t, unsigned long long key, bool& created) {
   constexpr int LT = BatchLocal<LTB>::LT;
@@ -247,6 +267,33 @@ __device__ int blocal_insert(BatchLocal<LTB>& t, unsigned long long key, bool& c
     h = (h + 1u) & (LT - 1u);
   }
   return -1;
+}
+
+// Global slots of the cells that entered the block's table since list entry n0 (all of them,
+// up to n1, after the chunk's insert pass): one claim chain per cell, all in parallel, and one
+// append to the occupied list per warp.  Found inline by the inserting thread, a chunk that meets
+// many new cells (many targets, small cells) waited on the thread with the most of them.
+template <int LTB>
+__device__ void blocal_resolve(BatchLocal<LTB>& t, const BatchBufs& b, unsigned n0, unsigned n1) {
+  const unsigned lane = threadIdx.x & 31u;
+  for (unsigned e0 = n0; e0 < n1; e0 += blockDim.x) {  // bound uniform over the block
+    const unsigned e = e0 + threadIdx.x;
+    bool created = false;
+    unsigned g = 0u;
+    if (e < n1) {
+      const unsigned j = t.list[e];
+      g = bglobal_claim(b, t.key[j], created, hash_bits(t.key[j], b.hbits));
+      t.gslot[j] = g;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, created);
+    if (m != 0u) {
+      const unsigned leader = (unsigned)__ffs((int)m) - 1u;
+      unsigned base = 0u;
+      if (lane == leader) base = atomicAdd(&b.ctl->nocc, (unsigned)__popc((int)m));
+      base = __shfl_sync(0xffffffffu, base, (int)leader);
+      if (created) b.occ[base + (unsigned)__popc((int)(m & ((1u << lane) - 1u)))] = g;
+    }
+  }
 }
 
 template <int LTB>
@@ -320,22 +367,31 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     tab.hot = 0u;
   }
   __syncthreads();
-  // each block takes pairs of consecutive chunks from a shared counter: two neighbouring chunks
-  // meet the cells of one or two targets (a grid-stride order would show every block every
-  // target's cells and overflow its table into per-particle global atomics), and a block slowed
-  // by many cells or global inserts takes fewer pairs instead of holding up the phase (a fixed
-  // contiguous range per block: 0.75 ms at 1000 targets, these pairs 0.66 ms)
-  constexpr long long GRAB = 2;
+  // each block takes runs of consecutive chunks from a shared counter, so that it meets the cells
+  // of one or two targets at a time (a grid-stride order would show every block every target's
+  // cells and overflow its table into per-particle global atomics), and a block slowed by many
+  // cells takes fewer runs instead of holding up the phase.  The runs are guided: a run is the
+  // remaining chunks over twice the grid, at most BT_GRAB_MAX, so that a block stays with a target
+  // while much work is left and the last runs are single chunks (at 1000 targets and 22M
+  // particles: a fixed range per block 0.75 ms, runs of two 0.66, guided runs 0.58, and with the
+  // proactive flush below 0.55 ms)
+  unsigned n_done = 0u, n_new = 0u;  // entries of tab.list whose global slot is known; cells new in the chunk
   const long long nchunks = (N + BT_CHUNK - 1) / BT_CHUNK;
-  __shared__ long long s_grab;
+  __shared__ long long s_grab, s_len;
   long long chunk = 0, c_end = 0;
   for (;;) {
     if (chunk >= c_end) {
       __syncthreads();  // every thread has read the previous s_grab
-      if (threadIdx.x == 0) s_grab = (long long)atomicAdd(&b.ctl->chunk_next, 1u) * GRAB;
+      if (threadIdx.x == 0) {
+        const long long seen = (long long)*(volatile unsigned*)&b.ctl->chunk_next;  // a lower bound
+        long long g = (nchunks - seen) / (2 * (long long)gridDim.x);
+        g = g < 1 ? 1 : (g > BT_GRAB_MAX ? BT_GRAB_MAX : g);
+        s_grab = (long long)atomicAdd(&b.ctl->chunk_next, (unsigned)g);
+        s_len = g;
+      }
       __syncthreads();
       chunk = s_grab;
-      c_end = chunk + GRAB < nchunks ? chunk + GRAB : nchunks;
+      c_end = chunk + s_len < nchunks ? chunk + s_len : nchunks;
       if (chunk >= nchunks) break;
     }
     const long long base = chunk * BT_CHUNK;
@@ -347,6 +403,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
     const long long i0 = base + (long long)BT_PER_THREAD * threadIdx.x;
     const int t0 = i0 < N ? target_of(offs, b.T, i0) : 0;
     int t = t0;
+    const float h0 = b.tg[t0].hf;  // the four particles' target is nearly always t0: its parameters once
     // the four consecutive particles of this thread with 16-byte loads and stores.  Row c of the
     // state and noise starts (c N) mod 4 floats off a 16-byte boundary: the thread reads the two
     // aligned quads around its four values (the second is the next thread's first, an L1 hit) and
@@ -399,7 +456,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
 #pragma unroll
         for (int c = 0; c < 5; ++c) b.prop[c * P + i] = v[k][c];
       }
-      const float h = b.tg[t].hf;
+      const float h = t == t0 ? h0 : b.tg[t].hf;
       float fx = floorf(__fdiv_rn(__fadd_rn(v[k][0], 0.5f), h));
       float fy = floorf(__fdiv_rn(__fadd_rn(v[k][1], 0.5f), h));
       bool ok = fabsf(fx) < 33554431.0f && fabsf(fy) < 33554431.0f;
@@ -413,11 +470,19 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       const unsigned long long key = bkey(t, (int)fx, (int)fy);
       bool created;
       ls[k] = blocal_insert(tab, key, created);
-      if (created) tab.gslot[ls[k]] = bglobal_insert(b, key);
       if (ls[k] == -1) ls[k] = -3 - (int)bglobal_insert(b, key);
     }
     __syncthreads();
-    unsigned gs[BT_PER_THREAD];
+    // global slots of the cells new in this chunk (list entries n_done .. n1): thread j claims entry
+    // n_done + j, whose first compare-and-swap is issued here and completes while the thread sums
+    // its particles below; the slots are read back after the chunk's closing barrier
+    const unsigned n1 = tab.nlist;  // stable until the next chunk's insert pass
+    const unsigned e_claim = n_done + threadIdx.x;
+    unsigned long long claim_old = 0ull;
+    if (e_claim < n1) {
+      const unsigned long long ck = tab.key[tab.list[e_claim]];
+      claim_old = atomicCAS(&b.hkey[hash_bits(ck, b.hbits)], EMPTY_KEY, ck);
+    }
     // a thread's four particles are consecutive, and after resampling neighbours are often
     // offspring of one ancestor in one cell: a run of equal local slots is summed in registers
     // (exact integer pieces) and reaches the shared counters with one set of atomics
@@ -425,20 +490,27 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
 #pragma unroll
     for (int a = 0; a < BT_NACC; ++a) run[a] = 0u;
     t = t0;
+    const long long hq0 = b.tg[t0].hq;
+    const long long an0 = b.st[t0].anchor[0], an1 = b.st[t0].anchor[1], an2 = b.st[t0].anchor[2];
 #pragma unroll
     for (int k = 0; k < BT_PER_THREAD; ++k) {
-      gs[k] = 0u;
       if (ls[k] == -2) continue;
       const long long i = i0 + k;
       while (t + 1 < b.T && offs[t + 1] <= i) ++t;
       const unsigned long long key = ls[k] >= 0 ? tab.key[ls[k]] : b.hkey[-3 - ls[k]];
-      const BatchTarget& T_ = b.tg[t];
-      const BatchStats& S_ = b.st[t];
+      long long hq = hq0, a0 = an0, a1 = an1, a2 = an2;
+      if (t != t0) {
+        hq = b.tg[t].hq;
+        a0 = b.st[t].anchor[0];
+        a1 = b.st[t].anchor[1];
+        a2 = b.st[t].anchor[2];
+      }
       long long bv[5];
-      bv[0] = to_fixed(v[k][0], 2147483648.0f) - (long long)bkey_bx(key) * T_.hq + BT_POS_BIAS;
-      bv[1] = to_fixed(v[k][1], 2147483648.0f) - (long long)bkey_by(key) * T_.hq + BT_POS_BIAS;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) bv[2 + c] = to_fixed(v[k][2 + c], 4194304.0f) - S_.anchor[c] + BT_VAL_BIAS;
+      bv[0] = to_fixed(v[k][0], 2147483648.0f) - (long long)bkey_bx(key) * hq + BT_POS_BIAS;
+      bv[1] = to_fixed(v[k][1], 2147483648.0f) - (long long)bkey_by(key) * hq + BT_POS_BIAS;
+      bv[2] = to_fixed(v[k][2], 4194304.0f) - a0 + BT_VAL_BIAS;
+      bv[3] = to_fixed(v[k][3], 4194304.0f) - a1 + BT_VAL_BIAS;
+      bv[4] = to_fixed(v[k][4], 4194304.0f) - a2 + BT_VAL_BIAS;
       bool bad = false;
 #pragma unroll
       for (int c = 0; c < 5; ++c) bad |= (bv[c] < 0 || bv[c] >= BT_BIASED_LIMIT);
@@ -447,10 +519,8 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
         bv[0] = bv[1] = BT_POS_BIAS;
         bv[2] = bv[3] = bv[4] = BT_VAL_BIAS;
       }
-      unsigned g;
       if (ls[k] >= 0) {
         const int s = ls[k];
-        g = tab.gslot[s];
         run[0] += 1u;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -468,7 +538,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
           }
         }
       } else {
-        g = (unsigned)(-3 - ls[k]);
+        const unsigned g = (unsigned)(-3 - ls[k]);
         atomicAdd(&b.hcnt[g], 1u);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -476,14 +546,57 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
           atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias));
         }
       }
-      gs[k] = g;
-      if (!vec) b.pslot[i] = g;
     }
-    if (vec) *reinterpret_cast<uint4*>(b.pslot + i0) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
+    {
+      // the claims issued above: a slot that was empty is now this cell's (appended to the occupied
+      // list, one append per warp), one that holds the key already was; on a collision the chain
+      // continues from the next slot
+      bool created = false;
+      if (e_claim < n1) {
+        const unsigned j = tab.list[e_claim];
+        const unsigned long long ck = tab.key[j];
+        const unsigned h0 = hash_bits(ck, b.hbits);
+        unsigned g = h0;
+        if (claim_old == EMPTY_KEY) created = true;
+        else if (claim_old != ck) g = bglobal_claim(b, ck, created, (h0 + 1u) & ((1u << b.hbits) - 1u));
+        tab.gslot[j] = g;
+      }
+      const unsigned lane = threadIdx.x & 31u;
+      const unsigned m = __ballot_sync(0xffffffffu, created);
+      if (m != 0u) {
+        const unsigned leader = (unsigned)__ffs((int)m) - 1u;
+        unsigned base = 0u;
+        if (lane == leader) base = atomicAdd(&b.ctl->nocc, (unsigned)__popc((int)m));
+        base = __shfl_sync(0xffffffffu, base, (int)leader);
+        if (created)
+          b.occ[base + (unsigned)__popc((int)(m & ((1u << lane) - 1u)))] = tab.gslot[tab.list[e_claim]];
+      }
+      if (n1 > n_done + blockDim.x) blocal_resolve(tab, b, n_done + blockDim.x, n1);  // more than one per thread
+      n_new = n1 - n_done;
+      n_done = n1;
+    }
     __syncthreads();
-    const bool full = tab.fill >= BatchLocal<LTB>::CAP;
+    // the slot of every particle: from the table for cells it holds (claimed above), from ls for the rest
+    {
+      unsigned gs[BT_PER_THREAD];
+#pragma unroll
+      for (int k = 0; k < BT_PER_THREAD; ++k)
+        gs[k] = ls[k] >= 0 ? tab.gslot[ls[k]] : (unsigned)(-3 - ls[k]);
+      if (vec) {
+        *reinterpret_cast<uint4*>(b.pslot + i0) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < BT_PER_THREAD; ++k)
+          if (ls[k] != -2) b.pslot[i0 + k] = gs[k];
+      }
+    }
+    // the table is emptied when it is full, or when a next chunk that met as many new cells as this
+    // one would fill it: such a chunk (a block moving on to another target) would otherwise send
+    // its particles past the full table to the global atomics one by one
+    const bool full = tab.fill + n_new >= BatchLocal<LTB>::CAP;
     if (full || tab.hot != 0u) {
       blocal_flush(tab, b, full);
+      if (full) n_done = 0u;
       // ordered before any count of the next chunk by that chunk's block barrier
       if (threadIdx.x == 0) tab.hot = 0u;
     }
