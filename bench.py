@@ -57,6 +57,10 @@ DEFERRED_RESAMPLE_BYTES = 12
 DRAWN_PROP_BIN_BYTES = 44
 DRAWN_DEFERRED_PROP_BIN_BYTES = 48
 DRAWN_SEED = 0x5EED_1310_5541
+# batched step (all targets, one launch): propagate/cells as above (64) + resampling (48); with
+# deferred resampling 68 + 12, as for one target
+BATCHED_BYTES = PROP_BIN_BYTES + RESAMPLE_BYTES
+BATCHED_DEFERRED_BYTES = DEFERRED_PROP_BIN_BYTES + DEFERRED_RESAMPLE_BYTES
 
 
 # SIR's likelihood (Eq. likelihood, Poisson): per pixel term the algorithmic work is
@@ -342,16 +346,56 @@ def run_batched(n_targets, steps, warmup, seed, world=1):
     res, derr = bt.results()
     est = np.array([r["estimate"][:2] for r in res])
     rmse = float(np.sqrt(np.mean(np.sum((est - batch.gt[frames, :, :2]) ** 2, axis=1))))
+    # the same steps with deferred resampling: each step records ancestors and the next step's
+    # propagation gathers through them; one graph per step, replayed once each in capture order
+    # (the two state buffers alternate at capture), and the resampled states written out once at
+    # the end of the timed region
+    state.copy_(torch.from_numpy(synth.batch_initial_state(batch, np.float32)).to(dev))
+    with torch.cuda.stream(s):
+        bt.deferred_begin(state, stream=s)
+    torch.cuda.synchronize()
+    dgraphs = []
+    for k in range(frames):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            bt.deferred_step(images[k], noise[k % NOISE_POOL], u0[k], stream=s)
+        dgraphs.append(g)
+    torch.cuda.synchronize()
+    for k in range(warmup):
+        dgraphs[k].replay()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        a.record(s)
+        for k in range(warmup, frames):
+            dgraphs[k].replay()
+        bt.deferred_state(state, stream=s)
+        b_.record(s)
+    torch.cuda.synchronize()
+    dms = a.elapsed_time(b_) / steps
+    dphases = bt.phase_times()
+    dres, dderr = bt.results()
+    dest = np.array([r["estimate"][:2] for r in dres])
+    drmse = float(np.sqrt(np.mean(np.sum((dest - batch.gt[frames, :, :2]) ** 2, axis=1))))
     bt.close()
+    hbm, kind = peaks()
+    dgbs = BATCHED_DEFERRED_BYTES * ntot / (dms * 1e-3) / 1e9
+    deferred = {"value": ntot * world / (dms / 1e3), "unit": UNIT, "ms_per_step": dms, "rmse_px": drmse,
+                "device_error": dderr, "step_bytes_per_particle": BATCHED_DEFERRED_BYTES, "step_gbs": dgbs,
+                "step_frac_of_hbm": dgbs / hbm,
+                "phase_ms_last_step": dict(zip(("setup", "prop_bin", "bins_lik", "weights", "tile_sums",
+                                                "target_scan", "resample"), dphases))}
     return {"workload": "batched pcSIR, %d targets, 1024x1024, %d particles FP32" % (T, ntot),
             "value": ntot * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "targets": T, "particles": ntot, "cells_last_step": int(sum(r["n_bins"] for r in res)),
             "launches_per_step": 1, "graph": True, "rmse_px": rmse,
-            "device_error": derr,
+            "device_error": derr, "step_bytes_per_particle": BATCHED_BYTES,
+            "step_gbs": BATCHED_BYTES * ntot / (ms * 1e-3) / 1e9,
+            "step_frac_of_hbm": BATCHED_BYTES * ntot / (ms * 1e-3) / 1e9 / hbm, "peak_source": kind,
             "autotune": {k: table.get(k) for k in ("c", "blocks_per_sm", "table_bits", "rmse", "rmse_limit",
                                                    "first_c_over_limit", "step_ms")},
             "phase_ms_last_step": dict(zip(("setup", "prop_bin", "bins_lik", "weights", "tile_sums", "target_scan",
-                                            "resample"), phases))}
+                                            "resample"), phases)),
+            "deferred": deferred}
 
 
 def run_matched(N, rows_target, train_steps, n_seq, n_frames, seed, sir_steps_cap=None):

@@ -439,6 +439,29 @@ pcsir_status pcsir_batch_set_table(pcsir_batch* batch, int32_t table_bits);
 pcsir_status pcsir_batched_step(pcsir_batch* batch, float* state, const float* image, int32_t W, int32_t H,
                                 const float* noise, const double* u0, void* stream);
 
+/* Deferred resampling of a batch (the paper has no counterpart; the same
+   filter as pcsir_batched_step, with the resampled states never written out
+   between steps).  pcsir_batch_deferred_begin copies `state` (device float32
+   [5][sum n_t], the states x_0 of every target, all weights equal) into the
+   batch on `stream` and starts a run; on its first call it allocates a second
+   propagated-state buffer and an ancestor array (24 B per particle), else
+   PCSIR_ENOMEM.  pcsir_batched_deferred_step is one step of every target,
+   image, noise and u0 as pcsir_batched_step: the resampling phase records
+   each output particle's ancestor instead of moving the states, and the next
+   step's propagation reads its input states through those ancestors (24 B
+   per particle instead of the resampling's 40 B of states).  Results,
+   outputs, bins and kept arrays are those of pcsir_batched_step.
+   pcsir_batch_deferred_state writes the run's current resampled states into
+   `state` ([5][sum n_t], caller-owned, device) on `stream`; the run
+   continues.  A pcsir_batched_step ends the run: the deferred calls then
+   return PCSIR_ESTATE until the next begin.  A captured graph of deferred
+   steps alternates the two state buffers step by step: replay it with an even
+   number of steps per graph.  Errors otherwise as pcsir_batched_step. */
+pcsir_status pcsir_batch_deferred_begin(pcsir_batch* batch, const float* state, void* stream);
+pcsir_status pcsir_batched_deferred_step(pcsir_batch* batch, const float* image, int32_t W, int32_t H,
+                                         const float* noise, const double* u0, void* stream);
+pcsir_status pcsir_batch_deferred_state(pcsir_batch* batch, float* state, void* stream);
+
 /* Results of the last step, one per target (out: host array of T), and the
    step's PCSIR_DERR_* flags (device_error may be NULL).  Synchronises the
    device first, so the results are those of the last step enqueued.  Returns PCSIR_ETIMEDOUT (with out and

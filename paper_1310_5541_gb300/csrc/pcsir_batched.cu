@@ -101,6 +101,12 @@ struct BatchBufs {
   unsigned int* dirty;
   int bar_spins;  // polls of each barrier wait before it gives up
   int bar_fail;   // index of a barrier made unreachable (its wait runs out), -1 = none
+  // deferred resampling (pcsir_batched_deferred_step), nullptr in a plain step: the step's input
+  // state of particle i is gsrc[c pstride + ganc[i]] (the previous step's propagated states
+  // through its ancestors, global indices), and the resampling phase writes each output's
+  // ancestor to ganc instead of moving the states
+  const float* gsrc;
+  int* ganc;
 };
 
 constexpr int BT_THREADS = 512;
@@ -350,7 +356,7 @@ __device__ __forceinline__ int target_of(const long long* offs, int T, long long
 // ---------------------------------------------------------------------------
 // Phase A: propagate, cell, centre-of-mass sums (cf. k_prop_bin)
 // ---------------------------------------------------------------------------
-template <int LTB>
+template <int LTB, bool DEF>
 __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st, const float* __restrict__ nz,
                                BatchLocal<LTB>& tab, const long long* offs) {
   const long long N = b.ntot;
@@ -412,18 +418,36 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
                      ((reinterpret_cast<uintptr_t>(st) | reinterpret_cast<uintptr_t>(nz)) & 15u) == 0u;
     if (vec) {
       float4 sv[5], nv[5];
+      if (DEF) {
+        // deferred resampling: the four inputs gathered through the previous step's ancestors
+        // (nondecreasing within a target, so a warp's reads stay within a few lines per row)
+        const int4 a4 = *reinterpret_cast<const int4*>(b.ganc + i0);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        const int m = (int)((c * N) & 3);
-        const long long a = c * N + i0 - m;
-        const float4 s0 = *reinterpret_cast<const float4*>(st + a);
-        const float4 n0 = *reinterpret_cast<const float4*>(nz + a);
-        if (m == 0) {
-          sv[c] = s0;
-          nv[c] = n0;
-        } else {
-          sv[c] = shift_quad(s0, *reinterpret_cast<const float4*>(st + a + 4), m);
-          nv[c] = shift_quad(n0, *reinterpret_cast<const float4*>(nz + a + 4), m);
+        for (int c = 0; c < 5; ++c) {
+          const float* row = b.gsrc + c * P;
+          sv[c] = make_float4(row[a4.x], row[a4.y], row[a4.z], row[a4.w]);
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const int m = (int)((c * N) & 3);
+          const long long a = c * N + i0 - m;
+          const float4 n0 = *reinterpret_cast<const float4*>(nz + a);
+          nv[c] = m == 0 ? n0 : shift_quad(n0, *reinterpret_cast<const float4*>(nz + a + 4), m);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const int m = (int)((c * N) & 3);
+          const long long a = c * N + i0 - m;
+          const float4 s0 = *reinterpret_cast<const float4*>(st + a);
+          const float4 n0 = *reinterpret_cast<const float4*>(nz + a);
+          if (m == 0) {
+            sv[c] = s0;
+            nv[c] = n0;
+          } else {
+            sv[c] = shift_quad(s0, *reinterpret_cast<const float4*>(st + a + 4), m);
+            nv[c] = shift_quad(n0, *reinterpret_cast<const float4*>(nz + a + 4), m);
+          }
         }
       }
       const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
@@ -447,7 +471,14 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       if (i >= N) continue;
       while (t + 1 < b.T && offs[t + 1] <= i) ++t;
       if (!vec) {
-        const float x = st[i], y = st[N + i], vx = st[2 * N + i], vy = st[3 * N + i], a = st[4 * N + i];
+        const float* sr = st;  // row c of the input state at sr + c rs
+        long long rs = N, j = i;
+        if (DEF) {
+          sr = b.gsrc;
+          rs = P;
+          j = b.ganc[i];
+        }
+        const float x = sr[j], y = sr[rs + j], vx = sr[2 * rs + j], vy = sr[3 * rs + j], a = sr[4 * rs + j];
         v[k][0] = __fadd_rn(__fadd_rn(x, vx), nz[i]);
         v[k][1] = __fadd_rn(__fadd_rn(y, vy), nz[N + i]);
         v[k][2] = __fadd_rn(vx, nz[2 * N + i]);
@@ -843,6 +874,7 @@ __device__ void phase_target_scan(const BatchBufs& b, const double* __restrict__
   }
 }
 
+template <bool DEF>
 __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, BatchResampleSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long Ntot = b.ntot;
@@ -909,20 +941,23 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
         // all weights zero: no distribution to sample, keep every particle
         src[j] = zero_sum ? T_.off + i : T_.off + lbase + a;
         if (b.anc != nullptr && i < hi) b.anc[T_.off + i] = (int)(src[j] - T_.off);
+        if (DEF && i < hi) b.ganc[T_.off + i] = (int)src[j];
       }
-      float v[4][5];
+      if (!DEF) {  // deferred: the next step gathers the states
+        float v[4][5];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool has = i0 + (long long)j * BT_THREADS < hi;
+        for (int j = 0; j < 4; ++j) {
+          const bool has = i0 + (long long)j * BT_THREADS < hi;
 #pragma unroll
-        for (int d = 0; d < 5; ++d) v[j][d] = has ? b.prop[d * b.pstride + src[j]] : 0.0f;
-      }
+          for (int d = 0; d < 5; ++d) v[j][d] = has ? b.prop[d * b.pstride + src[j]] : 0.0f;
+        }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const long long i = i0 + (long long)j * BT_THREADS;
-        if (i < hi) {
+        for (int j = 0; j < 4; ++j) {
+          const long long i = i0 + (long long)j * BT_THREADS;
+          if (i < hi) {
 #pragma unroll
-          for (int d = 0; d < 5; ++d) out[d * Ntot + T_.off + i] = v[j][d];
+            for (int d = 0; d < 5; ++d) out[d * Ntot + T_.off + i] = v[j][d];
+          }
         }
       }
     }
@@ -930,7 +965,7 @@ __device__ void phase_resample(const BatchBufs& b, float* __restrict__ out, Batc
   }
 }
 
-template <int LTB>
+template <int LTB, bool DEF>
 __global__ void __launch_bounds__(BT_THREADS, 2)
 k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restrict__ nz, float* __restrict__ out,
                const float* __restrict__ img, int W, int H, const double* __restrict__ u0s) {
@@ -954,12 +989,15 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.T; t += gridDim.x * blockDim.x) {
     const long long i = b.tg[t].off;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) b.st[t].anchor[c] = to_fixed(st[(2 + c) * b.ntot + i], 4194304.0f);
+    for (int c = 0; c < 3; ++c) {
+      const float x = DEF ? b.gsrc[(2 + c) * b.pstride + b.ganc[i]] : st[(2 + c) * b.ntot + i];
+      b.st[t].anchor[c] = to_fixed(x, 4194304.0f);
+    }
   }
   if (!grid_barrier(b, 0)) return;
   if (was_dirty && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(b.dirty, 0u);
   stamp(b.ctl, 1);
-  phase_prop_bin<LTB>(b, st, nz, *reinterpret_cast<BatchLocal<LTB>*>(bt_smem), offs);
+  phase_prop_bin<LTB, DEF>(b, st, nz, *reinterpret_cast<BatchLocal<LTB>*>(bt_smem), offs);
   if (!grid_barrier(b, 1)) return;
   stamp(b.ctl, 2);
   if (b.lik_group == 8)
@@ -992,24 +1030,34 @@ k_batched_step(BatchBufs b, const float* __restrict__ st, const float* __restric
   }
   if (!grid_barrier(b, 5)) return;
   stamp(b.ctl, 6);
-  phase_resample(b, out, *reinterpret_cast<BatchResampleSmem*>(bt_smem));
+  phase_resample<DEF>(b, out, *reinterpret_cast<BatchResampleSmem*>(bt_smem));
   if (!grid_barrier(b, 6)) return;
   stamp(b.ctl, 7);
 }
 
 // the kernel variant of a cell-table size and its dynamic shared memory
-const void* bt_kernel(int ltb) {
+const void* bt_kernel(int ltb, bool def = false) {
   switch (ltb) {
-    case 9: return reinterpret_cast<const void*>(k_batched_step<9>);
-    case 11: return reinterpret_cast<const void*>(k_batched_step<11>);
-    default: return reinterpret_cast<const void*>(k_batched_step<10>);
+    case 9: return def ? reinterpret_cast<const void*>(k_batched_step<9, true>)
+                       : reinterpret_cast<const void*>(k_batched_step<9, false>);
+    case 11: return def ? reinterpret_cast<const void*>(k_batched_step<11, true>)
+                        : reinterpret_cast<const void*>(k_batched_step<11, false>);
+    default: return def ? reinterpret_cast<const void*>(k_batched_step<10, true>)
+                        : reinterpret_cast<const void*>(k_batched_step<10, false>);
   }
 }
 size_t bt_smem_bytes(int ltb) {
   return ltb == 9 ? bt_smem<9>() : (ltb == 11 ? bt_smem<11>() : bt_smem<10>());
 }
+// blocks per SM that fit, for both variants of the kernel (plain and deferred resampling)
 cudaError_t bt_blocks_per_sm(int ltb, int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bt_kernel(ltb), BT_THREADS, bt_smem_bytes(ltb));
+  int a = 0, d = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bt_kernel(ltb, false), BT_THREADS,
+                                                                bt_smem_bytes(ltb));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, bt_kernel(ltb, true), BT_THREADS, bt_smem_bytes(ltb));
+  *per_sm = a < d ? a : d;
+  return e;
 }
 
 }  // namespace pcsir
@@ -1030,6 +1078,13 @@ struct pcsir_batch {
   pcsir_result* host_res = nullptr;
   std::string err = "no error";
   bool failed = false;
+  // deferred resampling: b.prop alternates between the two state buffers (the step gathers from
+  // the one the previous step wrote and writes the other); def_anc holds the last resampling's
+  // ancestors as global indices
+  float* prop_main = nullptr;
+  float* prop_alt = nullptr;
+  int* def_anc = nullptr;
+  bool def_active = false;
 };
 
 namespace {
@@ -1124,6 +1179,9 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   }
   b.tg = dtg;
   b.offs = doffs;
+  c->prop_main = b.prop;
+  b.gsrc = nullptr;
+  b.ganc = nullptr;
   b.tile_target = dtile_target;
   b.anc = nullptr;
   b.qout = nullptr;
@@ -1145,7 +1203,9 @@ pcsir_status pcsir_batch_create(const pcsir_target* targets, int32_t T, pcsir_ba
   if (e == cudaSuccess) e = cudaMemset(b.dirty, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_res, sizeof(pcsir_result) * T);
   for (int ltb = BT_LTB_MIN; ltb <= BT_LTB_MAX && e == cudaSuccess; ++ltb)
-    e = cudaFuncSetAttribute(bt_kernel(ltb), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem_bytes(ltb));
+    for (int def = 0; def < 2 && e == cudaSuccess; ++def)
+      e = cudaFuncSetAttribute(bt_kernel(ltb, def != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bt_smem_bytes(ltb));
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1196,6 +1256,26 @@ pcsir_status pcsir_batch_destroy(pcsir_batch* c) {
   return PCSIR_OK;
 }
 
+// the cooperative launch of one step and the copy of its results
+static pcsir_status bt_launch(pcsir_batch* c, BatchBufs b, const float* st_in, const float* nz, float* out,
+                              const float* img, int w, int h, const double* u0s, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(BatchCtl), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.st, 0, sizeof(BatchStats) * c->T, s);
+  if (e == cudaSuccess) {
+    void* args[] = {&b, &st_in, &nz, &out, &img, &w, &h, &u0s};
+    e = cudaLaunchCooperativeKernel(bt_kernel(c->ltb, b.gsrc != nullptr), dim3(c->grid), dim3(BT_THREADS), args, bt_smem_bytes(c->ltb),
+                                    s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->host_res, b.res, sizeof(pcsir_result) * c->T, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) {
+    c->err = std::string("batched step: ") + cudaGetErrorString(e);
+    c->failed = true;
+    return PCSIR_ECUDA;
+  }
+  return PCSIR_OK;
+}
+
 pcsir_status pcsir_batched_step(pcsir_batch* c, float* state, const float* image, int32_t W, int32_t H,
                                 const float* noise, const double* u0, void* stream) {
   if (!c) return PCSIR_EINVAL;
@@ -1204,25 +1284,94 @@ pcsir_status pcsir_batched_step(pcsir_batch* c, float* state, const float* image
     c->err = "NULL pointer or empty image";
     return PCSIR_EINVAL;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  BatchBufs b = c->b;
-  cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(BatchCtl), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b.st, 0, sizeof(BatchStats) * c->T, s);
-  if (e == cudaSuccess) {
-    const float* st_in = state;
-    const float* nz = noise;
-    float* out = state;
-    const float* img = image;
-    int w = W, h = H;
-    const double* u0s = u0;
-    void* args[] = {&b, &st_in, &nz, &out, &img, &w, &h, &u0s};
-    e = cudaLaunchCooperativeKernel(bt_kernel(c->ltb), dim3(c->grid), dim3(BT_THREADS), args, bt_smem_bytes(c->ltb),
-                                    s);
+  c->def_active = false;  // a plain step ends a deferred run
+  return bt_launch(c, c->b, state, noise, state, image, W, H, u0, static_cast<cudaStream_t>(stream));
+}
+
+__global__ void k_bt_iota(int* __restrict__ a, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = (int)i;
+}
+
+// out[c][i] = src[c][anc[i]]: the resampled states of a deferred run, rows of n (out) and P (src) floats
+__global__ void k_bt_gather(float* __restrict__ out, const float* __restrict__ src, long long P,
+                            const int* __restrict__ anc, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long a = anc[i];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) out[r * n + i] = src[r * P + a];
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->host_res, b.res, sizeof(pcsir_result) * c->T, cudaMemcpyDeviceToHost, s);
+}
+
+static int bt_elem_grid(const pcsir_batch* c) {
+  const long long g = (c->ntot + 255) / 256;
+  return (int)std::min<long long>(g, (long long)c->grid * 8);
+}
+
+pcsir_status pcsir_batch_deferred_begin(pcsir_batch* c, const float* state, void* stream) {
+  if (!c) return PCSIR_EINVAL;
+  if (c->failed) return PCSIR_ESTATE;
+  if (!state) {
+    c->err = "NULL state";
+    return PCSIR_EINVAL;
+  }
+  if ((!c->prop_alt && !balloc(c, &c->prop_alt, 5 * (size_t)c->b.pstride)) ||
+      (!c->def_anc && !balloc(c, &c->def_anc, (size_t)c->ntot))) {
+    c->err = "deferred run: out of device memory";
+    return PCSIR_ENOMEM;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t row = sizeof(float) * (size_t)c->ntot;
+  cudaError_t e = cudaMemcpy2DAsync(c->b.prop, sizeof(float) * (size_t)c->b.pstride, state, row, row, 5,
+                                    cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    k_bt_iota<<<bt_elem_grid(c), 256, 0, s>>>(c->def_anc, c->ntot);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
-    c->err = std::string("batched step: ") + cudaGetErrorString(e);
+    c->err = std::string("deferred begin: ") + cudaGetErrorString(e);
+    c->failed = true;
+    return PCSIR_ECUDA;
+  }
+  c->def_active = true;
+  return PCSIR_OK;
+}
+
+pcsir_status pcsir_batched_deferred_step(pcsir_batch* c, const float* image, int32_t W, int32_t H, const float* noise,
+                                         const double* u0, void* stream) {
+  if (!c) return PCSIR_EINVAL;
+  if (c->failed || !c->def_active) {
+    if (!c->def_active) c->err = "no deferred run: call pcsir_batch_deferred_begin first";
+    return PCSIR_ESTATE;
+  }
+  if (!image || !noise || !u0 || W < 1 || H < 1) {
+    c->err = "NULL pointer or empty image";
+    return PCSIR_EINVAL;
+  }
+  BatchBufs b = c->b;
+  b.gsrc = c->b.prop;
+  b.ganc = c->def_anc;
+  b.prop = c->b.prop == c->prop_main ? c->prop_alt : c->prop_main;
+  const pcsir_status st = bt_launch(c, b, nullptr, noise, nullptr, image, W, H, u0, static_cast<cudaStream_t>(stream));
+  if (st == PCSIR_OK) c->b.prop = b.prop;
+  return st;
+}
+
+pcsir_status pcsir_batch_deferred_state(pcsir_batch* c, float* state, void* stream) {
+  if (!c) return PCSIR_EINVAL;
+  if (c->failed || !c->def_active) {
+    if (!c->def_active) c->err = "no deferred run: call pcsir_batch_deferred_begin first";
+    return PCSIR_ESTATE;
+  }
+  if (!state) {
+    c->err = "NULL state";
+    return PCSIR_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_bt_gather<<<bt_elem_grid(c), 256, 0, s>>>(state, c->b.prop, c->b.pstride, c->def_anc, c->ntot);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->err = std::string("deferred state: ") + cudaGetErrorString(e);
     c->failed = true;
     return PCSIR_ECUDA;
   }

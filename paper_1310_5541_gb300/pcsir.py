@@ -146,6 +146,9 @@ def _load():
         "pcsir_batch_destroy": ([P], I32),
         "pcsir_batch_set_grid": ([P, I32], I32),
         "pcsir_batched_step": ([P, P, P, I32, I32, P, P, P], I32),
+        "pcsir_batch_deferred_begin": ([P, P, P], I32),
+        "pcsir_batched_deferred_step": ([P, P, I32, I32, P, P, P], I32),
+        "pcsir_batch_deferred_state": ([P, P, P], I32),
         "pcsir_batch_results": ([P, ctypes.POINTER(pcsir_result), I32, ctypes.POINTER(ctypes.c_int32)], I32),
         "pcsir_batch_outputs": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)], I32),
@@ -530,6 +533,31 @@ class Batch:
         H, W = image.shape
         st = lib.pcsir_batched_step(self.handle, _ptr(state), _ptr(image), W, H, _ptr(noise), _ptr(u0),
                                     _stream_ptr(stream))
+        if st != OK:
+            raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def deferred_begin(self, state, stream=None):
+        """Start a deferred-resampling run from state [5, sum N] float32 (copied)."""
+        _check_cuda(state, "state", torch.float32)
+        st = lib.pcsir_batch_deferred_begin(self.handle, _ptr(state), _stream_ptr(stream))
+        if st != OK:
+            raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def deferred_step(self, image, noise, u0, stream=None):
+        """One step of every target of the run (the resampling records ancestors; the next step gathers)."""
+        _check_cuda(noise, "noise", torch.float32)
+        _check_cuda(image, "image", torch.float32)
+        _check_cuda(u0, "u0", torch.float64)
+        H, W = image.shape
+        st = lib.pcsir_batched_deferred_step(self.handle, _ptr(image), W, H, _ptr(noise), _ptr(u0),
+                                             _stream_ptr(stream))
+        if st != OK:
+            raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
+
+    def deferred_state(self, out, stream=None):
+        """Write the run's current resampled states into out [5, sum N] float32."""
+        _check_cuda(out, "out", torch.float32)
+        st = lib.pcsir_batch_deferred_state(self.handle, _ptr(out), _stream_ptr(stream))
         if st != OK:
             raise PcsirError(st, lib.pcsir_batch_last_error(self.handle).decode())
 

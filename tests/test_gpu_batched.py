@@ -316,3 +316,73 @@ def test_batched_cell_table_size_does_not_change_the_step(pc):
         np.testing.assert_array_equal(outs[0][1], other[1])
         np.testing.assert_array_equal(outs[0][2], other[2])
         np.testing.assert_allclose(outs[0][3], other[3], rtol=1e-12)
+
+
+def test_batched_deferred_run_equals_plain_steps(pc):
+    """Deferred resampling of a batch (pcsir_batch_deferred_begin, pcsir_batched_deferred_step,
+    pcsir_batch_deferred_state) against plain batched steps on the same frames: at every frame the
+    resampled states, propagated states, kept ancestors and integer weights are identical and the
+    per-target results agree (cell counts exactly, means and ESS up to the order of FP64 atomics).
+    The total particle count leaves every state row off a 16-byte boundary, the run includes a
+    captured graph of two deferred steps replayed, and a plain step ends the run."""
+    Q = (0.5, 0.5, 0.1, 0.1, 1.0)
+    n = [4000, 3993, 10, 1500, 7]  # sum 9510: rows start 2, 0, 2, 0 floats (mod 4) past a 16-byte boundary
+    F = 7
+    batch = synth.make_batch(len(n), 192, 192, F, seed=SEED + 70, n_values=n, min_sep=30.0)
+    T = len(n)
+    st0 = torch.from_numpy(synth.batch_initial_state(batch, np.float32)).cuda()
+    plain = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    dfr = pc.Batch(batch.n, batch.h, batch.sigma, batch.bg, batch.patch)
+    for x in (plain, dfr):
+        x.keep(pc.KEEP_ANCESTORS | pc.KEEP_QWEIGHTS)
+    with pytest.raises(pc.PcsirError) as e:
+        dfr.deferred_step(torch.from_numpy(batch.images[0]).cuda(),
+                          torch.from_numpy(synth.batch_noise(batch, Q, SEED + 71, 0)).cuda(),
+                          torch.from_numpy(synth.batch_u0(T, SEED + 71, 0)).cuda())
+    assert e.value.status == pc.ESTATE
+    sa = st0.clone()
+    dfr.deferred_begin(st0)
+    out = torch.empty_like(st0)
+    frames = [(torch.from_numpy(batch.images[k]).cuda(), torch.from_numpy(synth.batch_noise(batch, Q, SEED + 71, k)).cuda(),
+               torch.from_numpy(synth.batch_u0(T, SEED + 71, k)).cuda()) for k in range(F)]
+    s = torch.cuda.Stream()
+    k = 0
+    while k < F:
+        if k == 3:
+            # frames 3 and 4 from one captured graph of two deferred steps (the state buffers alternate)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                dfr.deferred_step(*frames[3], stream=s)
+                dfr.deferred_step(*frames[4], stream=s)
+            graph.replay()
+            torch.cuda.synchronize()
+            plain.step(sa, *frames[3])
+            plain.step(sa, *frames[4])
+            k = 4
+        else:
+            plain.step(sa, *frames[k])
+            dfr.deferred_step(*frames[k])
+        dfr.deferred_state(out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, sa), k
+        pa, pd = plain.outputs(), dfr.outputs()
+        assert torch.equal(pa["prop_state"], pd["prop_state"]), k
+        ka, kd = plain.kept(), dfr.kept()
+        assert torch.equal(ka["ancestor"], kd["ancestor"]), k
+        assert torch.equal(ka["qweight"], kd["qweight"]), k
+        ra, ea = plain.results()
+        rd, ed = dfr.results()
+        assert ea == 0 and ed == 0
+        for t in range(T):
+            assert ra[t]["n_bins"] == rd[t]["n_bins"], (k, t)
+            np.testing.assert_allclose(rd[t]["estimate"], ra[t]["estimate"], rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(rd[t]["ess"], ra[t]["ess"], rtol=1e-12)
+        k += 1
+    # a plain step ends the run
+    dfr.step(out, *frames[0])
+    with pytest.raises(pc.PcsirError) as e:
+        dfr.deferred_state(out)
+    assert e.value.status == pc.ESTATE
+    plain.close()
+    dfr.close()
