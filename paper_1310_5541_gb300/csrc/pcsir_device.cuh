@@ -486,19 +486,18 @@ constexpr double POS_INV = 1.0 / 2147483648.0;
 constexpr double VAL_SCALE = 4194304.0;         // 2^22
 constexpr double VAL_INV = 1.0 / 4194304.0;
 
-// v * 2^shift rounded to the nearest integer (ties away from zero), by integer
-// instructions (|v| 2^shift < 2^62); exact whenever v * 2^shift is an integer.
+// v * 2^shift rounded to the nearest integer (ties to even); exact whenever v * 2^shift is an
+// integer.  v = t + f with t = trunc(v) and f = v - t, both exact: t 2^shift is an integer product
+// and f 2^shift (|f| < 1, an exact scaling) is rounded to an int32.  |v| is clamped to 2^30 first
+// (NaN to -2^30): every caller then finds the value outside its biased range and flags it, as it
+// does any state component of 10^9 or more.
 template <int SHIFT>
 __device__ __forceinline__ long long fix_round(float v) {
-  const unsigned b = __float_as_uint(v);
-  const int e = (int)((b >> 23) & 0xffu);
-  if (e == 0) return 0;
-  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
-  const int sh = e - 150 + SHIFT;  // v 2^SHIFT = m 2^sh
-  unsigned long long r;
-  if (sh >= 0) r = sh < 39 ? (m << sh) : (1ull << 62);
-  else r = sh > -25 ? ((m + (1ull << (-sh - 1))) >> (-sh)) : 0ull;
-  return (b >> 31) ? -(long long)r : (long long)r;
+  const float c = fminf(fmaxf(v, -1073741824.0f), 1073741824.0f);
+  const float t = truncf(c);
+  const int ti = __float2int_rz(t);
+  const int fi = __float2int_rn(__fmul_rn(__fsub_rn(c, t), (float)(1ll << SHIFT)));
+  return (long long)ti * (1ll << SHIFT) + (long long)fi;
 }
 __device__ __forceinline__ long long to_fixed(float v, float scale) {
   // the two scales used: 2^31 (positions) and 2^22 (other components)
