@@ -56,6 +56,20 @@ __device__ long long first_out_f(const Map64& mp, long long C, long long N, floa
   return i;
 }
 
+// i * Delta + U0 in full (integer part hi, fraction lo), and the sum of two such values
+struct U128 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ U128 u_full(const Map64& mp, unsigned long long i) {
+  const unsigned long long plo = i * mp.dlo;
+  const unsigned long long lo = plo + mp.ulo;
+  return U128{i * mp.dhi + mp.uhi + __umul64hi(i, mp.dlo) + (lo < plo ? 1ull : 0ull), lo};
+}
+__device__ __forceinline__ U128 u_add(U128 a, U128 b) {
+  const unsigned long long lo = a.lo + b.lo;
+  return U128{a.hi + b.hi + (lo < a.lo ? 1ull : 0ull), lo};
+}
+
 __device__ __forceinline__ Map64 load_map(const Control* ctl) {
   Map64 mp;
   mp.dhi = ctl->delta_hi;
@@ -506,7 +520,12 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const unsigned nb = (unsigned)N;
     const unsigned ub = (unsigned)base;
     constexpr int RO = 2;
-    for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS) {
+    // U of the thread's outputs r0 and r0 + SCAN_THREADS, advanced by RO SCAN_THREADS Delta per pass
+    // (exact 128-bit additions instead of a product per output)
+    const U128 d1 = u_full(Map64{mp.dhi, mp.dlo, 0ull, 0ull}, (unsigned long long)SCAN_THREADS);
+    const U128 d2 = u_add(d1, d1);
+    U128 u0r = u_full(mp, (unsigned long long)(lo + tid));
+    for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS, u0r = u_add(u0r, d2)) {
       unsigned ii[RO], aa[RO];
       bool has[RO];
 #pragma unroll
@@ -515,7 +534,7 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
         has[j] = i < hi;
         ii[j] = (unsigned)i;
         int a = 0;
-        if (has[j] && !zero_sum) a = tile_search(Cs, u_int(mp, i));
+        if (has[j] && !zero_sum) a = tile_search(Cs, (long long)(j == 0 ? u0r : u_add(u0r, d1)).hi);
         // all weights zero (Delta = 0): no distribution to sample, keep every particle
         aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
       }
