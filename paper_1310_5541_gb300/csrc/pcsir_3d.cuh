@@ -181,14 +181,18 @@ struct Local3 {
   unsigned int hot;  // some slot may reach 2^14 particles within the next chunk: flush
 };
 
-__device__ __forceinline__ int local_insert3(Local3& t, unsigned long long key, bool& created) {
+// filled: set when this call's claim brought the table to its capacity (the table is emptied
+// after the chunk)
+__device__ __forceinline__ int local_insert3(Local3& t, unsigned long long key, bool& created, bool& filled) {
   created = false;
   unsigned h = hash_bits(key, L3_BITS);
   for (int probe = 0; probe < L3; ++probe) {
     const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
     if (k == key) return (int)h;
     if (k == EMPTY_KEY) {
-      if (atomicAdd(&t.fill, 1u) >= L3_CAP) return -1;
+      const unsigned f = atomicAdd(&t.fill, 1u);
+      if (f + 1u >= L3_CAP) filled = true;
+      if (f >= L3_CAP) return -1;
       const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
       if (old == EMPTY_KEY) {
         created = true;
@@ -223,7 +227,10 @@ static __device__ void local_flush3(Local3& t, const StepBuffers& b, bool clear_
     if (clear_keys) t.key[j] = EMPTY_KEY;
   }
   __syncthreads();
-  if (clear_keys && threadIdx.x == 0) t.fill = 0u;
+  if (threadIdx.x == 0) {
+    if (clear_keys) t.fill = 0u;
+    t.hot = 0u;
+  }
   __syncthreads();
 }
 

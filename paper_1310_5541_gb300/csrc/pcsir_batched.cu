@@ -384,6 +384,7 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
   unsigned n_done = 0u, n_new = 0u;  // entries of tab.list whose global slot is known; cells new in the chunk
   const long long nchunks = (N + BT_CHUNK - 1) / BT_CHUNK;
   __shared__ long long s_grab, s_len;
+  __shared__ bool s_clear;
   long long chunk = 0, c_end = 0;
   for (;;) {
     if (chunk >= c_end) {
@@ -605,6 +606,13 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
       if (n1 > n_done + blockDim.x) blocal_resolve(tab, b, n_done + blockDim.x, n1);  // more than one per thread
       n_new = n1 - n_done;
       n_done = n1;
+      // the table is emptied after this chunk when it is full, or when a next chunk that met as many
+      // new cells as this one would fill it: such a chunk (a block moving on to another target)
+      // would otherwise send its particles past the full table to the global atomics one by one.
+      // The fill is read here, between the two barriers, where no thread inserts (after the second
+      // a thread may already insert the next chunk's cells), and the decision is read back after
+      // the second (no thread writes it again before the next chunk's first).
+      if (threadIdx.x == 0) s_clear = tab.fill + n_new >= BatchLocal<LTB>::CAP;
     }
     __syncthreads();
     // the slot of every particle: from the table for cells it holds (claimed above), from ls for the rest
@@ -621,10 +629,8 @@ __device__ void phase_prop_bin(const BatchBufs& b, const float* __restrict__ st,
           if (ls[k] != -2) b.pslot[i0 + k] = gs[k];
       }
     }
-    // the table is emptied when it is full, or when a next chunk that met as many new cells as this
-    // one would fill it: such a chunk (a block moving on to another target) would otherwise send
-    // its particles past the full table to the global atomics one by one
-    const bool full = tab.fill + n_new >= BatchLocal<LTB>::CAP;
+    // tab.hot is set only by the sums above and cleared below, both ordered by the barriers
+    const bool full = s_clear;
     if (full || tab.hot != 0u) {
       blocal_flush(tab, b, full);
       if (full) n_done = 0u;

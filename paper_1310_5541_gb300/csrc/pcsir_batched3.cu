@@ -129,17 +129,16 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
   for (long long chunk = c_begin; chunk < c_end; ++chunk) {
     const long long base = chunk * P3_CHUNK;
     float v[P3_PER_THREAD][NS3];
-    unsigned long long key[P3_PER_THREAD];
-    int ls[P3_PER_THREAD], tk[P3_PER_THREAD];
+    // each particle is summed into its cell as soon as the cell is found; ls: the cell's local
+    // slot, -3 - its global slot (table full), or -2 (no particle)
+    int ls[P3_PER_THREAD];
+    bool flag = false;  // this thread filled the table or brought a cell's count to the flush mark
     int t = b3_target_of(offs, B.T, base + threadIdx.x < N ? base + threadIdx.x : N - 1);
 #pragma unroll
     for (int k = 0; k < P3_PER_THREAD; ++k) {
       const long long i = base + (long long)k * P3_THREADS + threadIdx.x;
       ls[k] = -2;
-      tk[k] = 0;
       if (i >= N) continue;
-      while (t + 1 < B.T && offs[t + 1] <= i) ++t;
-      tk[k] = t;
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         v[k][p] = __fadd_rn(__fadd_rn(st[p * N + i], st[(3 + p) * N + i]), nz[p * N + i]);
@@ -148,6 +147,12 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
       v[k][6] = __fadd_rn(st[6 * N + i], nz[6 * N + i]);
 #pragma unroll
       for (int c = 0; c < NS3; ++c) prop[c * N + i] = v[k][c];
+    }
+#pragma unroll
+    for (int k = 0; k < P3_PER_THREAD; ++k) {
+      const long long i = base + (long long)k * P3_THREADS + threadIdx.x;
+      if (i >= N) continue;
+      while (t + 1 < B.T && offs[t + 1] <= i) ++t;
       const Target3& T_ = B.tg[t];
       bool ok = true;
       float f[3];
@@ -163,22 +168,15 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
         f[0] = f[1] = f[2] = 0.0f;
         v[k][0] = v[k][1] = v[k][2] = 0.0f;
       }
-      key[k] = b3_key(t, (int)f[0], (int)f[1], (int)f[2]);
+      const unsigned long long key = b3_key(t, (int)f[0], (int)f[1], (int)f[2]);
       bool created;
-      ls[k] = local_insert3(tab, key[k], created);
-      if (created) tab.gslot[ls[k]] = global_insert3(b, key[k]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < P3_PER_THREAD; ++k) {
-      if (ls[k] == -2) continue;
-      const long long i = base + (long long)k * P3_THREADS + threadIdx.x;
-      const Target3& T_ = B.tg[tk[k]];
-      const TStats3& S_ = B.ts[tk[k]];
+      int s = local_insert3(tab, key, created, flag);
+      if (created) tab.gslot[s] = global_insert3(b, key);
+      const TStats3& S_ = B.ts[t];
       long long bv[NS3];
 #pragma unroll
       for (int p = 0; p < 3; ++p)
-        bv[p] = to_fixed(v[k][p], 2147483648.0f) - (long long)b3_axis(key[k], p) * T_.hq[p] + P3_POS_BIAS;
+        bv[p] = to_fixed(v[k][p], 2147483648.0f) - (long long)(int)f[p] * T_.hq[p] + P3_POS_BIAS;
 #pragma unroll
       for (int c = 0; c < 4; ++c) bv[3 + c] = to_fixed(v[k][3 + c], 4194304.0f) - S_.anchor[c] + P3_VAL_BIAS;
       bool bad = false;
@@ -189,32 +187,34 @@ k_b3_prop_bin(B3Bufs B, const float* __restrict__ st, const float* __restrict__ 
 #pragma unroll
         for (int c = 0; c < NS3; ++c) bv[c] = bias3(c);
       }
-      unsigned g;
-      if (ls[k] >= 0) {
-        const int s = ls[k];
-        g = tab.gslot[s];
-        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == P3_HOT_AT) tab.hot = 1u;
+      if (s >= 0) {
+        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == P3_HOT_AT) flag = true;
 #pragma unroll
         for (int c = 0; c < NS3; ++c) {
           atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & P3_PIECE_MASK));
           atomicAdd(&tab.acc[2 + 2 * c][s], (unsigned)(bv[c] >> P3_PIECE_BITS));
         }
       } else {
-        g = global_insert3(b, key[k]);
+        const unsigned g = global_insert3(b, key);
         atomicAdd(&b.hcnt[g], 1u);
 #pragma unroll
         for (int c = 0; c < NS3; ++c)
           atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias3(c)));
+        s = -3 - (int)g;
       }
-      b.pslot[i] = g;
+      ls[k] = s;
     }
-    __syncthreads();
-    const bool full = tab.fill >= L3_CAP;
-    if (full || tab.hot != 0u) {
-      local_flush3(tab, b, full);
-      // ordered before any count of the next chunk by that chunk's block barrier
-      if (threadIdx.x == 0) tab.hot = 0u;
+    // flushed after this chunk when some thread filled the table or raised a cell to the flush
+    // mark: every thread learns it from the barrier itself, never from the table's counters,
+    // which the next chunk's inserts may already change
+    const bool flush = __syncthreads_or(flag) != 0;
+#pragma unroll
+    for (int k = 0; k < P3_PER_THREAD; ++k) {
+      if (ls[k] == -2) continue;
+      const long long i = base + (long long)k * P3_THREADS + threadIdx.x;
+      b.pslot[i] = ls[k] >= 0 ? tab.gslot[ls[k]] : (unsigned)(-3 - ls[k]);
     }
+    if (flush) local_flush3(tab, b, tab.fill >= L3_CAP);  // read before the flush's first barrier
   }
   local_flush3(tab, b, false);
 }

@@ -146,8 +146,11 @@ struct LocalTable {
   unsigned int hot;  // some slot may reach SLOT_PARTICLES within the next chunk: flush
 };
 
+// filled: set when this call's claim brought the table to its capacity (the table is emptied
+// after the chunk)
 template <int LTB>
-__device__ __forceinline__ int local_find_or_insert(LocalTable<LTB>& t, unsigned long long key, bool& created) {
+__device__ __forceinline__ int local_find_or_insert(LocalTable<LTB>& t, unsigned long long key, bool& created,
+                                                    bool& filled) {
   constexpr int LT = LocalTable<LTB>::LT;
   created = false;
   unsigned h = hash_bits(key, LTB);
@@ -155,7 +158,9 @@ __device__ __forceinline__ int local_find_or_insert(LocalTable<LTB>& t, unsigned
     const unsigned long long k = ((volatile unsigned long long*)t.key)[h];
     if (k == key) return (int)h;
     if (k == EMPTY_KEY) {
-      if (atomicAdd(&t.fill, 1u) >= LocalTable<LTB>::CAP) return -1;
+      const unsigned f = atomicAdd(&t.fill, 1u);
+      if (f + 1u >= LocalTable<LTB>::CAP) filled = true;
+      if (f >= LocalTable<LTB>::CAP) return -1;
       const unsigned long long old = atomicCAS(&t.key[h], EMPTY_KEY, key);
       if (old == EMPTY_KEY) {
         created = true;
@@ -192,7 +197,10 @@ __device__ __forceinline__ void local_flush(LocalTable<LTB>& t, const StepBuffer
     if (clear_keys) t.key[j] = EMPTY_KEY;
   }
   __syncthreads();
-  if (clear_keys && threadIdx.x == 0) t.fill = 0u;
+  if (threadIdx.x == 0) {
+    if (clear_keys) t.fill = 0u;
+    t.hot = 0u;
+  }
   __syncthreads();
 }
 
@@ -203,6 +211,14 @@ struct PbShape {
   static constexpr int THREADS = LTB == 10 ? PB_THREADS : 2 * PB_THREADS;
   static constexpr int CHUNK = THREADS * PB_PER_THREAD;
 };
+
+// A streamed load of state or noise.  With the large table (224 KB of shared memory) almost none of
+// the SM's unified L1 is left, and loads cached there throttled the kernel (lg_throttle stalls):
+// they bypass L1 (cached in L2 only) in that variant.
+template <int LTB>
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  return LTB == 12 ? __ldcg(p) : *p;
+}
 
 // i-th particle (0..3) of this thread in the chunk: four consecutive indices
 // when the rows allow 16-byte vector access, otherwise strided by the block.
@@ -266,12 +282,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       } else {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          sv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0);
+          sv[c] = ld_stream<LTB>(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(st) + c * N + i0));
       }
       if (!GEN) {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          nv[c] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0);
+          nv[c] = ld_stream<LTB>(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(nz) + c * N + i0));
       }
       const float* sp[5] = {&sv[0].x, &sv[1].x, &sv[2].x, &sv[3].x, &sv[4].x};
       const float* np[5] = {&nv[0].x, &nv[1].x, &nv[2].x, &nv[3].x, &nv[4].x};
@@ -310,8 +326,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
       }
     }
     const bool vec_chunk = VEC && base + CHUNK <= N;
-    unsigned long long key[PB_PER_THREAD];
+    // each particle is summed into its cell as soon as the cell is found: the cell's counters are
+    // usable at once, and only its global slot (written by the thread that took the cell into the
+    // table) waits for the barrier below, before the slots are stored.  ls: the cell's local slot,
+    // -3 - its global slot (table full), or -2 (no particle)
     int ls[PB_PER_THREAD];
+    bool flag = false;  // this thread filled the table or brought a cell's count to the flush mark
 #pragma unroll
     for (int k = 0; k < PB_PER_THREAD; ++k) {
       const int64_t i = vec_chunk ? pb_index<true, THR>(base, k) : pb_index<false, THR>(base, k);
@@ -326,19 +346,12 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
         v[k][0] = T(0);
         v[k][1] = T(0);
       }
-      key[k] = pack_key((int)fx, (int)fy);
+      const int bx = (int)fx, by = (int)fy;
+      const unsigned long long key = pack_key(bx, by);
       bool created;
-      ls[k] = local_find_or_insert(tab, key[k], created);
-      if (created) tab.gslot[ls[k]] = global_find_or_insert(b, key[k]);
-    }
-    __syncthreads();
-    unsigned gs[PB_PER_THREAD];
-#pragma unroll
-    for (int k = 0; k < PB_PER_THREAD; ++k) {
-      gs[k] = 0u;
-      if (ls[k] == -2) continue;
+      int s = local_find_or_insert(tab, key, created, flag);
+      if (created) tab.gslot[s] = global_find_or_insert(b, key);
       long long bv[5];
-      const int bx = key_bx(key[k]), by = key_by(key[k]);
       bv[0] = to_fixed(v[k][0], Scales<T>::POS) - (long long)bx * hq + POS_BIAS;
       bv[1] = to_fixed(v[k][1], Scales<T>::POS) - (long long)by * hq + POS_BIAS;
 #pragma unroll
@@ -351,40 +364,49 @@ k_prop_bin(StepBuffers b, const T* __restrict__ st, const T* __restrict__ nz, in
         bv[0] = bv[1] = POS_BIAS;
         bv[2] = bv[3] = bv[4] = VAL_BIAS;
       }
-      if (ls[k] >= 0) {
-        const int s = ls[k];
-        gs[k] = tab.gslot[s];
-        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == HOT_AT) tab.hot = 1u;
+      if (s >= 0) {
+        if (atomicAdd(&tab.acc[0][s], 1u) + 1u == HOT_AT) {
+          tab.hot = 1u;
+          flag = true;
+        }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           atomicAdd(&tab.acc[1 + 2 * c][s], (unsigned)(bv[c] & PIECE_MASK));
           atomicAdd(&tab.acc[2 + 2 * c][s], (unsigned)(bv[c] >> PIECE_BITS));
         }
       } else {
-        const unsigned g = global_find_or_insert(b, key[k]);
-        gs[k] = g;
+        const unsigned g = global_find_or_insert(b, key);
         atomicAdd(&b.hcnt[g], 1u);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const long long bias = c < 2 ? POS_BIAS : VAL_BIAS;
           atomicAdd((unsigned long long*)&b.hsum[c * hcap + g], (unsigned long long)(bv[c] - bias));
         }
+        s = -3 - (int)g;
       }
+      ls[k] = s;
     }
-    if (vec_chunk) {
-      *reinterpret_cast<uint4*>(b.pslot + base + 4 * threadIdx.x) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
-    } else {
+    // the table is flushed after this chunk when some thread filled it or raised a cell to the
+    // flush mark: every thread learns it from this barrier itself, so none reads the table's
+    // counters while another may already be inserting the next chunk's cells
+    const bool flush = __syncthreads_or(flag) != 0;
+    {
+      // the particles' global slots: a cell taken into the table during this chunk has its slot
+      // written before the barrier; the table's next changes (a flush, new cells in empty slots)
+      // touch no slot read here
+      unsigned gs[PB_PER_THREAD];
 #pragma unroll
       for (int k = 0; k < PB_PER_THREAD; ++k)
-        if (ls[k] != -2) b.pslot[pb_index<false, THR>(base, k)] = gs[k];
+        gs[k] = ls[k] >= 0 ? tab.gslot[ls[k]] : (ls[k] == -2 ? 0u : (unsigned)(-3 - ls[k]));
+      if (vec_chunk) {
+        *reinterpret_cast<uint4*>(b.pslot + base + 4 * threadIdx.x) = make_uint4(gs[0], gs[1], gs[2], gs[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < PB_PER_THREAD; ++k)
+          if (ls[k] != -2) b.pslot[pb_index<false, THR>(base, k)] = gs[k];
+      }
     }
-    __syncthreads();
-    const bool full = tab.fill >= LocalTable<LTB>::CAP;
-    if (full || tab.hot != 0u) {
-      local_flush(tab, b, full);
-      // ordered before any count of the next chunk by that chunk's block barrier
-      if (threadIdx.x == 0) tab.hot = 0u;
-    }
+    if (flush) local_flush(tab, b, tab.fill >= LocalTable<LTB>::CAP);  // read before the flush's first barrier
   }
   local_flush(tab, b, false);
 }
