@@ -70,6 +70,14 @@ __device__ __forceinline__ U128 u_add(U128 a, U128 b) {
   return U128{a.hi + b.hi + (lo < a.lo ? 1ull : 0ull), lo};
 }
 
+// two consecutive values at an 8-byte (float) or 16-byte (double) aligned address
+__device__ __forceinline__ void store_pair(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void store_pair(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
 __device__ __forceinline__ Map64 load_map(const Control* ctl) {
   Map64 mp;
   mp.dhi = ctl->delta_hi;
@@ -507,11 +515,12 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
       }
     }
     __syncthreads();
-    // 5. the tile's outputs, two per thread and pass (both gathers issued before the stores).
-    //    Output i's ancestor is the particle j with C_{j-1} <= U_i < C_j, i.e. the number of
-    //    C_j <= floor(U_i) (the C_j are integers): a 12-step search over the tile's cumulative
-    //    weights in shared memory, independent for every output, so a particle with many
-    //    offspring does not serialise one thread.  Row offsets fit 32 bits (N <= 2^26).
+    // 5. the tile's outputs, two per thread and pass.  Output i's ancestor is the particle j with
+    //    C_{j-1} <= U_i < C_j, i.e. the number of C_j <= floor(U_i) (the C_j are integers): a
+    //    12-step search over the tile's cumulative weights in shared memory, or for the second
+    //    output of a pair at most WALK comparisons before it; every output costs a bounded number
+    //    of steps, so a particle with many offspring does not serialise one thread.  Row offsets
+    //    fit 32 bits (N <= 2^26).
     // the tile's outputs are [tile_lo[t], tile_lo[t + 1]) (U >= C_{-1} = excl and U < C_{cnt-1}, the
     // next tile's excl); this block writes its chunk [s_lo, s_hi) of them
     const T* __restrict__ prop = static_cast<const T*>(b.prop);
@@ -519,48 +528,102 @@ k_resample(StepBuffers b, const double* __restrict__ lsrc, T* __restrict__ out, 
     const bool zero_sum = (mp.dhi == 0ull && mp.dlo == 0ull);
     const unsigned nb = (unsigned)N;
     const unsigned ub = (unsigned)base;
-    constexpr int RO = 2;
-    // U of the thread's outputs r0 and r0 + SCAN_THREADS, advanced by RO SCAN_THREADS Delta per pass
-    // (exact 128-bit additions instead of a product per output)
-    const U128 d1 = u_full(Map64{mp.dhi, mp.dlo, 0ull, 0ull}, (unsigned long long)SCAN_THREADS);
-    const U128 d2 = u_add(d1, d1);
-    U128 u0r = u_full(mp, (unsigned long long)(lo + tid));
-    for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS, u0r = u_add(u0r, d2)) {
-      unsigned ii[RO], aa[RO];
-      bool has[RO];
+    if (out == nullptr) {
+      // ancestors only (deferred resampling, the stand-alone calls): two outputs SCAN_THREADS
+      // apart per thread and pass, each by the fixed-step search (measured faster here than the
+      // pairs below, whose walk pays only where the states are gathered too)
+      constexpr int RO = 2;
+      // U of the thread's outputs r0 and r0 + SCAN_THREADS, advanced by RO SCAN_THREADS Delta per pass
+      // (exact 128-bit additions instead of a product per output)
+      const U128 d1 = u_full(Map64{mp.dhi, mp.dlo, 0ull, 0ull}, (unsigned long long)SCAN_THREADS);
+      const U128 d2 = u_add(d1, d1);
+      U128 u0r = u_full(mp, (unsigned long long)(lo + tid));
+      for (long long r0 = lo + tid; r0 < hi; r0 += RO * SCAN_THREADS, u0r = u_add(u0r, d2)) {
+        unsigned ii[RO], aa[RO];
+        bool has[RO];
 #pragma unroll
-      for (int j = 0; j < RO; ++j) {
-        const long long i = r0 + (long long)j * SCAN_THREADS;
-        has[j] = i < hi;
-        ii[j] = (unsigned)i;
-        int a = 0;
-        if (has[j] && !zero_sum) a = tile_search(Cs, (long long)(j == 0 ? u0r : u_add(u0r, d1)).hi);
-        // all weights zero (Delta = 0): no distribution to sample, keep every particle
-        aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
+        for (int j = 0; j < RO; ++j) {
+          const long long i = r0 + (long long)j * SCAN_THREADS;
+          has[j] = i < hi;
+          ii[j] = (unsigned)i;
+          int a = 0;
+          if (has[j] && !zero_sum) a = tile_search(Cs, (long long)(j == 0 ? u0r : u_add(u0r, d1)).hi);
+          // all weights zero (Delta = 0): no distribution to sample, keep every particle
+          aa[j] = has[j] ? (zero_sum ? ii[j] : ub + (unsigned)clamp_item(a, cnt)) : 0u;
+        }
+        if (keep & PCSIR_KEEP_ANCESTORS) {
+#pragma unroll
+          for (int j = 0; j < RO; ++j)
+            if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
+        }
+        // resampled particles restart from uniform weights
+        if (b.lw_out != nullptr) {
+#pragma unroll
+          for (int j = 0; j < RO; ++j)
+            if (has[j]) b.lw_out[ii[j]] = 0;
+        }
       }
-      if (out != nullptr) {
-        T v[RO][NS];
-#pragma unroll
-        for (int j = 0; j < RO; ++j)
-#pragma unroll
-          for (int d = 0; d < NS; ++d) v[j][d] = has[j] ? prop[d * nb + aa[j]] : T(0);
-#pragma unroll
-        for (int j = 0; j < RO; ++j)
-          if (has[j]) {
-#pragma unroll
-            for (int d = 0; d < NS; ++d) out[d * nb + ii[j]] = v[j][d];
+    } else {
+      // each thread takes two consecutive outputs r0, r0 + 1 per pass (r0 even): the first ancestor
+      // by the search, the second by walking on from it over the few cumulative weights up to
+      // U_{r0+1} = U_{r0} + Delta (a search again after WALK steps), so that most outputs cost a
+      // comparison or two instead of twelve.  The two outputs' states leave with one 8-byte store per
+      // component where the rows allow it.
+      constexpr int WALK = 4;
+      const long long lo2 = lo & ~1ll;
+      const bool pair_st = (N & 1) == 0 && (reinterpret_cast<uintptr_t>(out) & (2 * sizeof(T) - 1)) == 0;
+      // a caller's ancestor array may start off an 8-byte boundary
+      const bool pair_anc = (reinterpret_cast<uintptr_t>(b.anc) & 7) == 0;
+      const U128 dd = u_full(Map64{mp.dhi, mp.dlo, 0ull, 0ull}, 1ull);
+      const U128 dstep = u_full(Map64{mp.dhi, mp.dlo, 0ull, 0ull}, 2ull * SCAN_THREADS);
+      U128 ur = u_full(mp, (unsigned long long)(lo2 + 2 * tid));
+      for (long long r0 = lo2 + 2 * tid; r0 < hi; r0 += 2 * SCAN_THREADS, ur = u_add(ur, dstep)) {
+        const bool h0 = r0 >= lo, h1 = r0 + 1 < hi;
+        int a0 = 0, a1 = 0;
+        if (!zero_sum) {
+          a0 = tile_search(Cs, (long long)ur.hi);
+          const long long u1 = (long long)u_add(ur, dd).hi;
+          a1 = a0;
+          int k = 0;
+          while (k < WALK && Cs[pad_idx(a1)] <= u1) {  // entries past the tile's end are LLONG_MAX
+            ++a1;
+            ++k;
           }
-      }
-      if (keep & PCSIR_KEEP_ANCESTORS) {
+          if (k == WALK && Cs[pad_idx(a1)] <= u1) a1 = tile_search(Cs, u1);
+        }
+        const unsigned i0 = (unsigned)r0;
+        // all weights zero (Delta = 0): no distribution to sample, keep every particle
+        const unsigned s0 = zero_sum ? i0 : ub + (unsigned)clamp_item(a0, cnt);
+        const unsigned s1 = zero_sum ? i0 + 1u : ub + (unsigned)clamp_item(a1, cnt);
+        T v0[NS], v1[NS];
 #pragma unroll
-        for (int j = 0; j < RO; ++j)
-          if (has[j]) b.anc[ii[j]] = (int32_t)aa[j];
-      }
-      // resampled particles restart from uniform weights
-      if (b.lw_out != nullptr) {
+        for (int d = 0; d < NS; ++d) {
+          v0[d] = h0 ? prop[d * nb + s0] : T(0);
+          v1[d] = h1 ? prop[d * nb + s1] : T(0);
+        }
+        if (pair_st && h0 && h1) {
 #pragma unroll
-        for (int j = 0; j < RO; ++j)
-          if (has[j]) b.lw_out[ii[j]] = 0;
+          for (int d = 0; d < NS; ++d) store_pair(out + d * nb + i0, v0[d], v1[d]);
+        } else {
+#pragma unroll
+          for (int d = 0; d < NS; ++d) {
+            if (h0) out[d * nb + i0] = v0[d];
+            if (h1) out[d * nb + i0 + 1u] = v1[d];
+          }
+        }
+        if (keep & PCSIR_KEEP_ANCESTORS) {
+          if (h0 && h1 && pair_anc) {
+            *reinterpret_cast<int2*>(b.anc + i0) = make_int2((int)s0, (int)s1);  // i0 even
+          } else {
+            if (h0) b.anc[i0] = (int32_t)s0;
+            if (h1) b.anc[i0 + 1u] = (int32_t)s1;
+          }
+        }
+        // resampled particles restart from uniform weights
+        if (b.lw_out != nullptr) {
+          if (h0) b.lw_out[i0] = 0;
+          if (h1) b.lw_out[i0 + 1u] = 0;
+        }
       }
     }
   }

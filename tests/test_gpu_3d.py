@@ -171,3 +171,26 @@ def test_cell_index_range_is_flagged(pc, case):
     torch.cuda.synchronize()
     assert ctx.last_result()["device_error"] == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("comp,value", [(6, np.nan), (5, np.inf), (3, -2.0e9), (4, -5000.0)])
+def test_out_of_range_component_is_flagged(pc, case, comp, value):
+    """A 3D state component that is not finite, of magnitude 10^9 or more, or (velocities and
+    intensity) 2^12 or more below particle 0's value raises the range flag; the context stays
+    usable."""
+    seq, m, N, st = case
+    n = 3000
+    st = np.ascontiguousarray(st[:, :n]).copy()
+    st[comp, 2000] = np.float32(value)
+    nz = torch.from_numpy(np.zeros((7, n), np.float32)).cuda()
+    ctx = pc.Context3(n)
+    d = torch.from_numpy(st).cuda()
+    ctx.step(d, torch.from_numpy(seq.images[2]).cuda(), (0.5, 0.5, 1.0), nz, 0.4)
+    torch.cuda.synchronize()
+    assert ctx.last_result()["device_error"] & pc.DERR_RANGE, (comp, value)
+    st[comp, 2000] = st[comp, 1999]
+    d = torch.from_numpy(st).cuda()
+    ctx.step(d, torch.from_numpy(seq.images[2]).cuda(), (0.5, 0.5, 1.0), nz, 0.4)
+    torch.cuda.synchronize()
+    assert ctx.last_result()["device_error"] == 0
+    ctx.close()

@@ -420,6 +420,26 @@ def test_resample_entry_point_exact_when_weights_are_exact(pc):
     ctx.close()
 
 
+def test_resample_entry_point_into_an_unaligned_ancestor_array(pc):
+    """The caller's ancestor array may start on any 4-byte boundary (here a slice one element into
+    a buffer): the same ancestors as into an aligned array, for the context and the no-allocation
+    entry points."""
+    rng = np.random.default_rng(14)
+    ctx = _ctx(pc, 300_000, torch.float32, MODEL_SMALL)
+    for N in (2, 4097, 250_001):
+        lw = torch.from_numpy(rng.normal(size=N)).cuda()
+        u0 = float(rng.random())
+        ref = pc.pcsir_resample(ctx, lw, u0).clone()
+        buf = torch.full((N + 1,), -7, dtype=torch.int32, device="cuda")
+        pc.pcsir_resample(ctx, lw, u0, out=buf[1:])
+        assert torch.equal(buf[1:], ref) and int(buf[0]) == -7
+        buf2 = torch.full((N + 1,), -7, dtype=torch.int32, device="cuda")
+        pc.pcsir_resample_noalloc(lw, u0, out=buf2[1:])
+        torch.cuda.synchronize()
+        assert torch.equal(buf2[1:], ref) and int(buf2[0]) == -7
+    ctx.close()
+
+
 def test_resample_entry_point_random_weights(pc):
     rng = np.random.default_rng(13)
     N = 1_000_003
@@ -514,6 +534,28 @@ def test_nonfinite_state_is_flagged(pc):
     assert ctx.last_result()["device_error"] & pc.DERR_RANGE
     # the context stays usable
     st[0, 5] = st[0, 4]
+    compare_pcsir(pc, ctx, st, seq.images[0], nz, 0.5, 0.5, MODEL_SMALL)
+    ctx.close()
+
+
+@pytest.mark.parametrize("comp,value", [(2, np.inf), (3, -np.inf), (4, np.nan), (2, 2.0e9), (3, 20000.0),
+                                        (4, -5000.0), (0, 3.0e9)])
+def test_out_of_range_component_is_flagged(pc, comp, value):
+    """A state component that is not finite, of magnitude 10^9 or more, or (velocities and
+    intensity) 2^12 or more away from particle 0's value, outside what the fixed-point sums
+    represent (biased by 2^12 below it and 3 2^12 above), raises the range flag; the context
+    stays usable."""
+    seq = synth.make_sequence(32, 32, 1, MODEL_SMALL, seed=SEED + 13)
+    N = 4096 + 8
+    st = synth.initial_state(seq.gt[0], N, np.float32)
+    nz = np.zeros((5, N), np.float32)
+    bad = st.copy()
+    bad[comp, 4100] = np.float32(value)
+    ctx = _ctx(pc, N, torch.float32, MODEL_SMALL)
+    t = torch.from_numpy(np.ascontiguousarray(bad)).cuda()
+    pc.pcsir_step(ctx, t, torch.from_numpy(seq.images[0]).cuda(), 0.5, torch.from_numpy(nz).cuda(), 0.5)
+    torch.cuda.synchronize()
+    assert ctx.last_result()["device_error"] & pc.DERR_RANGE, (comp, value)
     compare_pcsir(pc, ctx, st, seq.images[0], nz, 0.5, 0.5, MODEL_SMALL)
     ctx.close()
 
