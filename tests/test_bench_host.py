@@ -32,3 +32,35 @@ def test_sir_roofline_arithmetic():
 def test_all_core_oracle_baseline_runs_in_spawned_processes():
     rate, steps, busiest = bench.cpu_oracle_rate_all_cores(2048, 0.3, 5, 0.5, 2)
     assert rate > 0 and steps >= 4 and busiest > 0
+
+
+def test_algorithmic_bytes_follow_the_fp32_state_layout():
+    """Per-particle bytes behind the reported HBM fractions: five FP32 state components (20 B), a
+    4-byte cell slot, a 4-byte ancestor.  Propagate/bin reads state and noise and writes the
+    propagated state and the slot; resampling reads the slot twice (tile sums, scan) and gathers and
+    writes one state; the deferred form gathers through the ancestor and writes only the ancestor."""
+    import bench
+
+    state, slot, anc = 5 * 4, 4, 4
+    assert bench.PROP_BIN_BYTES == 2 * state + state + slot
+    assert bench.RESAMPLE_BYTES == 2 * slot + 2 * state
+    assert bench.DEFERRED_PROP_BIN_BYTES == anc + 2 * state + state + slot
+    assert bench.DEFERRED_RESAMPLE_BYTES == 2 * slot + anc
+    assert bench.DRAWN_PROP_BIN_BYTES == bench.PROP_BIN_BYTES - state
+    assert bench.DRAWN_DEFERRED_PROP_BIN_BYTES == bench.DEFERRED_PROP_BIN_BYTES - state
+    assert bench.BATCHED_BYTES == 112 and bench.BATCHED_DEFERRED_BYTES == 80
+
+
+def test_profiled_traffic_scales_the_committed_capture():
+    """The ncu traffic of the committed propagate/bin summary is taken only for the kernel source it
+    was captured on, per particle, scaled to the launch size; it stays within the algorithmic bytes
+    (no re-reads) and above three quarters of them."""
+    import bench
+
+    n = 1 << 24
+    t = bench.profiled_traffic(n)
+    tg = bench.profiled_traffic(n, "gathering dram bytes per particle")
+    assert t is not None and tg is not None
+    assert 0.75 * bench.PROP_BIN_BYTES * n <= t <= bench.PROP_BIN_BYTES * n
+    assert 0.75 * bench.DEFERRED_PROP_BIN_BYTES * n <= tg <= bench.DEFERRED_PROP_BIN_BYTES * n
+    assert bench.profiled_traffic(2 * n) == 2 * t
